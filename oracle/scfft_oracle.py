@@ -1,0 +1,491 @@
+"""FP64 NumPy oracle of the method-of-lines right-hand side dh/dt and its
+time integrator (Prigozhin & Sokolovsky, §2, Eqs. 1-8).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
+benchmark's CPU-baseline leg; never by the product path. Every step is written
+in the paper's order and notation, with library FFTs as the only primitive; no
+blocking, fusion or reordering.
+
+Array layout: vector fields are numpy arrays of shape (3, nz, ny, nx), the
+component index first (x, y, z), then z, y, x (x varies fastest).  Scalar node
+fields (the mask of the superconductor Omega, a jc map) have shape (nz, ny, nx).
+
+Readings of points where the paper is silent (each one named where it is used):
+  R-grid   nodes are cell centres x_i = -L + (i + 1/2) dx, dx = 2L/N (§2: "uniform
+           N_x x N_y x N_z grid" on D = {|x|<=L_x, ...}).
+  R-smooth the Gaussian smoothing multiplies a derivative's symbol by
+           exp(-sigma^2 |k|^2 / 2), sigma = half the cell diagonal (§2).
+  R-nyq    the derivative symbol i k_a is 0 on the Nyquist plane of axis a, so
+           that a real field has a real curl.
+  R-phi    Phi of Eq. 6 is the free-space convolution with the gradient of the
+           smoothed Green function G_sigma = G * Gaussian(sigma) (Fourier
+           transform exp(-sigma^2 k^2/2)/k^2, cf. Eq. 7 and the smoothing of §2),
+           sampled on the grid: Phi_d[j](r_a) = dV sum_b grad G_sigma(r_a - r_b) x j_b.
+           It is evaluated either by this direct sum or by zero padding to
+           2N_x x 2N_y x 2N_z and a cyclic FFT convolution (Hockney).  The
+           sampled kernel is made exactly odd (the offset -N_a plane is zeroed,
+           it never meets a cropped output) so its transform vanishes at k = 0,
+           the paper's rule for k = 0 under Eq. 7.
+  R-warm   the initial approximation of dh_out/dt (Eq. 5) is the warm-start
+           array g passed in by the caller (the previous result, §2); the
+           first call uses g = dh_e/dt.
+  R-stop   the residual of Eq. 5 is the mean over the Omega_out nodes of the
+           Euclidean norm |dh^{i+1} - dh^i|; iterate while it is not below
+           delta_it * max(|dh_e/dt|, 1), at most max_iter times.
+  R-ode    "ode23" is read as the Bogacki-Shampine 3(2) FSAL pair with the
+           error norm max_i |err_i| / max(rtol |y_i|, rtol |y_new,i|, atol),
+           accept if <= 1, dt <- dt * min(5, max(0.2, 0.9 err^(-1/3))).
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable, Optional, Sequence
+
+import numpy as np
+from scipy.special import erf
+
+__all__ = [
+    "Grid", "Material", "FieldPath", "Problem",
+    "wavenumbers", "curl_s", "div_s", "electric_field",
+    "grad_green_sigma", "phi_direct", "phi_hockney", "hockney_kernel_spectrum",
+    "rhs", "RhsResult",
+    "BS23_C", "BS23_A", "BS23_B", "BS23_BHAT", "BS23_E",
+    "bs23_step", "error_norm", "integrate", "IntegrateResult",
+    "magnetic_moment", "dissipation",
+]
+
+
+# ----------------------------------------------------------------------------
+# Grid (§2: uniform grid on D = {|x|<=Lx, |y|<=Ly, |z|<=Lz}; reading R-grid)
+# ----------------------------------------------------------------------------
+@dataclass(frozen=True)
+class Grid:
+    n: tuple  # (nx, ny, nz)
+    L: tuple  # half extents (Lx, Ly, Lz)
+    sigma_scale: float = 1.0  # multiplies the paper's sigma (half the cell diagonal)
+
+    @property
+    def shape(self):
+        nx, ny, nz = self.n
+        return (nz, ny, nx)
+
+    @property
+    def d(self):
+        return tuple(2.0 * L / n for L, n in zip(self.L, self.n))
+
+    @property
+    def dV(self):
+        dx, dy, dz = self.d
+        return dx * dy * dz
+
+    @property
+    def sigma(self):
+        # §2: "the smoothing parameter sigma was equal to a half of the grid cell diagonal"
+        dx, dy, dz = self.d
+        return self.sigma_scale * 0.5 * math.sqrt(dx * dx + dy * dy + dz * dz)
+
+    def axes(self):
+        """Node coordinates along x, y, z (cell centres, reading R-grid)."""
+        return tuple(-L + (np.arange(n) + 0.5) * (2.0 * L / n) for L, n in zip(self.L, self.n))
+
+    def coords(self):
+        """Broadcastable (z, y, x) coordinate arrays: X[None,None,:], Y[None,:,None], Z[:,None,None]."""
+        x, y, z = self.axes()
+        return x[None, None, :], y[None, :, None], z[:, None, None]
+
+
+def wavenumbers(n: int, L: float):
+    """Angular wavenumbers of the periodic grid of n nodes on [-L, L) (period 2L),
+    in numpy FFT order, and the derivative symbol i*k with the Nyquist entry set
+    to zero (reading R-nyq)."""
+    m = np.fft.fftfreq(n, d=1.0 / n)  # integers 0..n/2-1, -n/2..-1
+    k = np.pi * m / L
+    D = 1j * k
+    if n % 2 == 0:
+        D[n // 2] = 0.0
+    return k, D
+
+
+def _symbols(grid: Grid):
+    nx, ny, nz = grid.n
+    Lx, Ly, Lz = grid.L
+    kx, Dx = wavenumbers(nx, Lx)
+    ky, Dy = wavenumbers(ny, Ly)
+    kz, Dz = wavenumbers(nz, Lz)
+    k2 = kx[None, None, :] ** 2 + ky[None, :, None] ** 2 + kz[:, None, None] ** 2
+    S = np.exp(-0.5 * grid.sigma ** 2 * k2)  # reading R-smooth
+    return Dx[None, None, :], Dy[None, :, None], Dz[:, None, None], S
+
+
+def curl_s(f: np.ndarray, grid: Grid) -> np.ndarray:
+    """Smoothed spectral curl on the periodic unpadded grid (§2: derivatives of
+    Eqs. 3-4 taken in Fourier space with Gaussian smoothing)."""
+    Dx, Dy, Dz, S = _symbols(grid)
+    F = np.fft.fftn(f, axes=(1, 2, 3))
+    Fx, Fy, Fz = F[0], F[1], F[2]
+    G = np.stack([
+        (Dy * Fz - Dz * Fy) * S,
+        (Dz * Fx - Dx * Fz) * S,
+        (Dx * Fy - Dy * Fx) * S,
+    ])
+    return np.real(np.fft.ifftn(G, axes=(1, 2, 3)))
+
+
+def div_s(f: np.ndarray, grid: Grid) -> np.ndarray:
+    """Smoothed spectral divergence with the same symbols as curl_s (used by the
+    div j = 0 check of §2)."""
+    Dx, Dy, Dz, S = _symbols(grid)
+    F = np.fft.fftn(f, axes=(1, 2, 3))
+    return np.real(np.fft.ifftn((Dx * F[0] + Dy * F[1] + Dz * F[2]) * S))
+
+
+# ----------------------------------------------------------------------------
+# Material law (Eq. 1) and the fictitious outer resistivity (§2, after Eq. 4)
+# ----------------------------------------------------------------------------
+@dataclass
+class Material:
+    n: float = 20.0       # power-law exponent
+    e0: float = 1.0       # dimensionless units of Eq. 8: e0 = jc = mu0 = 1
+    jc: object = 1.0      # scalar or (nz, ny, nx) map
+    rho_out: float = 20.0  # fictitious resistivity in Omega_out
+    mu0: float = 1.0
+
+
+def electric_field(j: np.ndarray, mask: np.ndarray, mat: Material) -> np.ndarray:
+    """e = rho(|j|) j in Omega with rho = (e0/jc)|j/jc|^(n-1) (Eq. 1), e = rho_out j in
+    Omega_out (the poor-conductor Ohm law of §2)."""
+    jn = np.sqrt(np.sum(j * j, axis=0))
+    jc = np.asarray(mat.jc, dtype=np.float64)
+    rho = (mat.e0 / jc) * (jn / jc) ** (mat.n - 1.0)
+    return np.where(mask[None], rho[None] * j, mat.rho_out * j)
+
+
+def dissipation(j: np.ndarray, e: np.ndarray, mask: np.ndarray, dV: float) -> float:
+    """Integral of e.j over Omega (nonnegative for Eq. 1)."""
+    return float(np.sum(np.sum(e * j, axis=0)[mask]) * dV)
+
+
+# ----------------------------------------------------------------------------
+# Biot-Savart operator Phi (Eqs. 2, 6, 7; reading R-phi)
+# ----------------------------------------------------------------------------
+def grad_green_sigma(rx, ry, rz, sigma: float):
+    """Gradient of G_sigma(r) = erf(r / (sqrt(2) sigma)) / (4 pi r), the Green
+    function G = 1/(4 pi r) of Eq. 2 convolved with a Gaussian of std sigma.
+    d G_sigma / dr = [ (2/sqrt(pi)) u exp(-u^2) - erf(u) ] / (4 pi r^2), u = r/(sqrt(2) sigma).
+    The gradient is 0 at r = 0 (odd symmetry)."""
+    rx, ry, rz = np.broadcast_arrays(np.asarray(rx, float), np.asarray(ry, float), np.asarray(rz, float))
+    shape = rx.shape
+    rx, ry, rz = (np.atleast_1d(a).copy() for a in (rx, ry, rz))
+    r = np.sqrt(rx * rx + ry * ry + rz * rz)
+    out = np.zeros((3,) + r.shape)
+    nz = r > 0
+    rr = r[nz]
+    u = rr / (math.sqrt(2.0) * sigma)
+    g = ((2.0 / math.sqrt(math.pi)) * u * np.exp(-u * u) - erf(u)) / (4.0 * math.pi * rr * rr)
+    out[0][nz] = g * rx[nz] / rr
+    out[1][nz] = g * ry[nz] / rr
+    out[2][nz] = g * rz[nz] / rr
+    return out.reshape((3,) + shape)
+
+
+def _cross(a, b):
+    return np.stack([
+        a[1] * b[2] - a[2] * b[1],
+        a[2] * b[0] - a[0] * b[2],
+        a[0] * b[1] - a[1] * b[0],
+    ])
+
+
+def phi_direct(j: np.ndarray, grid: Grid) -> np.ndarray:
+    """Phi_d[j](r_a) = dV sum_b grad G_sigma(r_a - r_b) x j_b: Eq. 6 as a plain
+    O(N^2) sum over grid nodes (tiny grids only)."""
+    x, y, z = grid.axes()
+    nz_, ny_, nx_ = grid.shape
+    Zg, Yg, Xg = np.meshgrid(z, y, x, indexing="ij")
+    pts = np.stack([Xg.ravel(), Yg.ravel(), Zg.ravel()], axis=1)  # (N, 3)
+    jv = j.reshape(3, -1).T  # (N, 3)
+    out = np.zeros_like(jv)
+    for a in range(pts.shape[0]):
+        d = pts[a] - pts  # r_a - r_b
+        K = grad_green_sigma(d[:, 0], d[:, 1], d[:, 2], grid.sigma)  # (3, N)
+        out[a] = grid.dV * np.sum(_cross(K, jv.T), axis=1)
+    return out.T.reshape(3, nz_, ny_, nx_)
+
+
+def hockney_kernel_spectrum(grid: Grid) -> np.ndarray:
+    """Complex spectrum (3, 2nz, 2ny, 2nx) of dV * grad G_sigma sampled at the
+    offsets m_a * d_a, m_a in [-n_a, n_a) (cyclic order), with every m_a = -n_a
+    plane set to zero so that the sampled kernel is exactly odd."""
+    nx, ny, nz = grid.n
+    dx, dy, dz = grid.d
+    mx = np.fft.fftfreq(2 * nx, d=1.0 / (2 * nx))
+    my = np.fft.fftfreq(2 * ny, d=1.0 / (2 * ny))
+    mz = np.fft.fftfreq(2 * nz, d=1.0 / (2 * nz))
+    K = grid.dV * grad_green_sigma(mx[None, None, :] * dx, my[None, :, None] * dy,
+                                   mz[:, None, None] * dz, grid.sigma)
+    K[:, :, :, nx] = 0.0
+    K[:, :, ny, :] = 0.0
+    K[:, nz, :, :] = 0.0
+    return np.fft.fftn(K, axes=(1, 2, 3))
+
+
+def phi_hockney(j: np.ndarray, grid: Grid, Khat: Optional[np.ndarray] = None) -> np.ndarray:
+    """Phi_d[j] by zero padding to twice the grid along every axis, an FFT, the
+    cross product K^ x J^ (Eq. 7 with the sampled-kernel spectrum) and an inverse
+    FFT cropped to the original block."""
+    nx, ny, nz = grid.n
+    if Khat is None:
+        Khat = hockney_kernel_spectrum(grid)
+    jp = np.zeros((3, 2 * nz, 2 * ny, 2 * nx))
+    jp[:, :nz, :ny, :nx] = j
+    J = np.fft.fftn(jp, axes=(1, 2, 3))
+    P = np.real(np.fft.ifftn(_cross(Khat, J), axes=(1, 2, 3)))
+    return P[:, :nz, :ny, :nx].copy()
+
+
+# ----------------------------------------------------------------------------
+# Applied field path h_e(t) (§3: piecewise-linear ramps; plus a sinusoid)
+# ----------------------------------------------------------------------------
+@dataclass
+class FieldPath:
+    """h_e(t) = piecewise-linear interpolation of knots (t_k, he_k), constant
+    outside [t_0, t_K], plus sin_amp * sin(2 pi (t - sin_t0)/sin_period) * sin_dir
+    for sin_t0 <= t < sin_t1."""
+    t: Sequence[float]
+    he: Sequence[Sequence[float]]
+    sin_amp: float = 0.0
+    sin_period: float = 1.0
+    sin_t0: float = 0.0
+    sin_t1: float = 0.0
+    sin_dir: Sequence[float] = (0.0, 0.0, 1.0)
+
+    def _seg(self, t, left):
+        tk = np.asarray(self.t, float)
+        K = len(tk)
+        for s in range(K - 1):
+            lo, hi = tk[s], tk[s + 1]
+            if (lo <= t < hi) if not left else (lo < t <= hi):
+                return s
+        return -1
+
+    def he_at(self, t: float) -> np.ndarray:
+        tk = np.asarray(self.t, float)
+        hk = np.asarray(self.he, float).reshape(-1, 3)
+        if t <= tk[0]:
+            v = hk[0].copy()
+        elif t >= tk[-1]:
+            v = hk[-1].copy()
+        else:
+            s = int(np.searchsorted(tk, t, side="right") - 1)
+            w = (t - tk[s]) / (tk[s + 1] - tk[s])
+            v = (1 - w) * hk[s] + w * hk[s + 1]
+        if self.sin_amp != 0.0 and self.sin_t0 <= t < self.sin_t1:
+            v = v + self.sin_amp * math.sin(2 * math.pi * (t - self.sin_t0) / self.sin_period) * np.asarray(self.sin_dir, float)
+        return v
+
+    def hedot(self, t: float, left: bool = False) -> np.ndarray:
+        """dh_e/dt at t; at a kink the right derivative, or the left one if left=True."""
+        tk = np.asarray(self.t, float)
+        hk = np.asarray(self.he, float).reshape(-1, 3)
+        s = self._seg(t, left)
+        v = np.zeros(3) if s < 0 else (hk[s + 1] - hk[s]) / (tk[s + 1] - tk[s])
+        if self.sin_amp != 0.0:
+            inside = (self.sin_t0 < t <= self.sin_t1) if left else (self.sin_t0 <= t < self.sin_t1)
+            if inside:
+                w = 2 * math.pi / self.sin_period
+                v = v + self.sin_amp * w * math.cos(w * (t - self.sin_t0)) * np.asarray(self.sin_dir, float)
+        return v
+
+    def kinks(self):
+        ks = list(np.asarray(self.t, float))
+        if self.sin_amp != 0.0:
+            ks += [self.sin_t0, self.sin_t1]
+        return sorted(set(ks))
+
+
+@dataclass
+class Problem:
+    grid: Grid
+    mask: np.ndarray          # bool (nz, ny, nx): True in Omega
+    mat: Material
+    path: FieldPath
+    Khat: Optional[np.ndarray] = None
+
+    def kernel(self):
+        if self.Khat is None:
+            self.Khat = hockney_kernel_spectrum(self.grid)
+        return self.Khat
+
+
+# ----------------------------------------------------------------------------
+# Right-hand side dh/dt (§2: Eqs. 1, 3, 4, 5 and the iteration that follows)
+# ----------------------------------------------------------------------------
+@dataclass
+class RhsResult:
+    hdot: np.ndarray
+    iters: int
+    converged: bool
+    residual: float
+    residuals: list = field(default_factory=list)
+
+
+def rhs(prob: Problem, t: float, h: np.ndarray, g: np.ndarray, delta_it: float = 2e-5,
+        max_iter: int = 100, left: bool = False, phi: Optional[Callable] = None) -> RhsResult:
+    """dh/dt at time t for the field h, warm start g (reading R-warm).
+
+    1. j = curl h                                  (Eq. 4)
+    2. e = rho(|j|) j in Omega, rho_out j outside  (Eq. 1 and §2)
+    3. dh_in = -curl e / mu0 restricted to Omega   (Eq. 3)
+    4. dh^0 = dh_in in Omega, g in Omega_out
+    5. dh^{i+1} = dh^i in Omega, dh_e/dt + Phi[chi_Omega curl dh^i] in Omega_out (Eq. 5)
+       until the residual test of reading R-stop passes or max_iter iterations.
+    """
+    grid, mask, mat = prob.grid, prob.mask, prob.mat
+    if phi is None:
+        Khat = prob.kernel()
+        phi = lambda jj: phi_hockney(jj, grid, Khat)  # noqa: E731
+    j = curl_s(h, grid)
+    e = electric_field(j, mask, mat)
+    hdot_in = -curl_s(e, grid) / mat.mu0
+    hd = np.where(mask[None], hdot_in, g)
+    hed = prob.path.hedot(t, left=left)
+    tol = delta_it * max(float(np.linalg.norm(hed)), 1.0)
+    out = ~mask
+    nout = int(out.sum())
+    iters, conv, r = 0, False, float("nan")
+    res = []
+    if nout == 0:  # Omega fills the box: Eq. 5 has nothing to iterate on
+        return RhsResult(hd, 0, True, 0.0, res)
+    for i in range(max_iter):
+        jdot_in = curl_s(hd, grid) * mask[None]
+        P = phi(jdot_in)
+        new = np.where(mask[None], hd, hed[:, None, None, None] + P)
+        r = float(np.sum(np.sqrt(np.sum((new - hd) ** 2, axis=0))[out]) / nout)
+        res.append(r)
+        hd = new
+        iters = i + 1
+        if r < tol:
+            conv = True
+            break
+    return RhsResult(hd, iters, conv, r, res)
+
+
+# ----------------------------------------------------------------------------
+# Bogacki-Shampine 3(2) FSAL pair (the method behind Matlab ode23; reading R-ode)
+# Coefficients from Bogacki & Shampine, Appl. Math. Lett. 2 (1989) 321-325.
+# ----------------------------------------------------------------------------
+BS23_C = (0.0, 0.5, 0.75, 1.0)
+BS23_A = ((), (0.5,), (0.0, 0.75), (2.0 / 9.0, 1.0 / 3.0, 4.0 / 9.0))
+BS23_B = (2.0 / 9.0, 1.0 / 3.0, 4.0 / 9.0, 0.0)          # third-order solution
+BS23_BHAT = (7.0 / 24.0, 0.25, 1.0 / 3.0, 0.125)         # embedded second order
+BS23_E = tuple(b - bh for b, bh in zip(BS23_B, BS23_BHAT))  # y3 - y2 weights
+
+
+def bs23_step(f: Callable, t: float, y: np.ndarray, dt: float, k1: np.ndarray, end_left: bool = False):
+    """One BS23 step from (t, y) with first stage k1 = f(t, y).  Returns
+    (y_new, k4, err_vec) with k4 = f(t+dt, y_new) (the FSAL stage) and
+    err_vec = dt * sum_i (b_i - bhat_i) k_i."""
+    k2 = f(t + BS23_C[1] * dt, y + dt * (BS23_A[1][0] * k1), False)
+    k3 = f(t + BS23_C[2] * dt, y + dt * (BS23_A[2][0] * k1 + BS23_A[2][1] * k2), False)
+    ynew = y + dt * (BS23_B[0] * k1 + BS23_B[1] * k2 + BS23_B[2] * k3)
+    k4 = f(t + dt, ynew, end_left)
+    err = dt * (BS23_E[0] * k1 + BS23_E[1] * k2 + BS23_E[2] * k3 + BS23_E[3] * k4)
+    return ynew, k4, err
+
+
+def error_norm(err: np.ndarray, y: np.ndarray, ynew: np.ndarray, rtol: float, atol: float) -> float:
+    """max_i |err_i| / max(rtol |y_i|, rtol |ynew_i|, atol) (reading R-ode)."""
+    w = np.maximum(np.maximum(rtol * np.abs(y), rtol * np.abs(ynew)), atol)
+    return float(np.max(np.abs(err) / w))
+
+
+@dataclass
+class IntegrateResult:
+    t: float
+    y: np.ndarray
+    snaps: list
+    accepted: int
+    rejected: int
+    rhs_calls: int
+    iters: list
+    dts: list
+
+
+def integrate(prob: Problem, t0: float, t1: float, y0: np.ndarray, rtol: float, atol: float,
+              dt0: float, snapshots: Sequence[float] = (), delta_it: float = 2e-5,
+              max_iter: int = 100, dt_list: Optional[Sequence[float]] = None,
+              max_steps: int = 100000) -> IntegrateResult:
+    """Method of lines (§2): integrate dh/dt = rhs from t0 to t1 by BS23.
+
+    Steps are clipped to end exactly on the field-path kinks, the snapshot
+    times and t1; a step that ends on a kink evaluates its last stage with the
+    left derivative of h_e and the next step restarts its first stage with the
+    right one.  With dt_list given, the steps are those dts (fixed-step mode,
+    no error control).  The warm start g is the result of the most recent rhs
+    call (reading R-warm)."""
+    state = {"g": None, "calls": 0, "iters": []}
+
+    def f(t, y, left):
+        if state["g"] is None:
+            state["g"] = np.broadcast_to(prob.path.hedot(t, left)[:, None, None, None], y.shape).copy()
+        r = rhs(prob, t, y, state["g"], delta_it=delta_it, max_iter=max_iter, left=left)
+        state["g"] = r.hdot
+        state["calls"] += 1
+        state["iters"].append(r.iters)
+        return r.hdot
+
+    stops = sorted(set([s for s in list(prob.path.kinks()) + list(snapshots) + [t1] if t0 < s <= t1]))
+    kinks = set(prob.path.kinks())
+    t, y = t0, y0.copy()
+    k1 = f(t, y, False)
+    dt = dt0
+    snaps = []
+    acc = rej = 0
+    dts = []
+    si = 0
+    step = 0
+    while t < t1 and step < max_steps:
+        step += 1
+        while si < len(stops) and stops[si] <= t:
+            si += 1
+        nxt = stops[si] if si < len(stops) else t1
+        if dt_list is not None:
+            dt = dt_list[acc]
+        h_step = min(dt, nxt - t)
+        hits = (h_step == nxt - t)
+        end_left = hits and (nxt in kinks)
+        ynew, k4, err = bs23_step(f, t, y, h_step, k1, end_left)
+        if dt_list is not None:
+            en = 0.0
+        else:
+            en = error_norm(err, y, ynew, rtol, atol)
+        if en <= 1.0:
+            t = nxt if hits else t + h_step
+            y = ynew
+            acc += 1
+            dts.append(h_step)
+            if end_left:
+                k1 = f(t, y, False)
+            else:
+                k1 = k4
+            if hits and nxt in snapshots:
+                snaps.append((t, y.copy()))
+            if dt_list is None:
+                fac = 5.0 if en == 0 else min(5.0, max(0.2, 0.9 * en ** (-1.0 / 3.0)))
+                dt = h_step * fac
+        else:
+            rej += 1
+            dt = h_step * max(0.2, 0.9 * en ** (-1.0 / 3.0))
+    return IntegrateResult(t, y, snaps, acc, rej, state["calls"], state["iters"], dts)
+
+
+# ----------------------------------------------------------------------------
+# Diagnostics
+# ----------------------------------------------------------------------------
+def magnetic_moment(j: np.ndarray, grid: Grid) -> np.ndarray:
+    """m = 1/2 sum r x j dV over the grid."""
+    X, Y, Z = grid.coords()
+    r = np.stack(np.broadcast_arrays(X, Y, Z))
+    return 0.5 * grid.dV * np.sum(_cross(r, j), axis=(1, 2, 3))

@@ -1,0 +1,373 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by mathematics
+(closed forms, invariants, special cases, brute force), not to itself.
+
+Each test names the passage of §2 (or the textbook fact) it relies on and the
+mistakes in the oracle it would catch.
+"""
+
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate as spi
+
+import oracle as O
+import scfft_inputs as I
+
+
+# ---------------------------------------------------------------- grid + curl
+def _modes_grid():
+    # non-cubic grid and box so that a transposed axis cannot pass
+    return O.Grid((12, 10, 14), (1.0, 0.8, 1.4))
+
+
+def test_curl_single_modes_closed_form():
+    """§2: derivatives in Fourier space with Gaussian smoothing.  For resolved
+    Fourier modes the spectral derivative is exact, so curl_S of
+    h = (A sin(ky y + p1), B sin(kz z + p2), C sin(kx x + p3)) is
+    (-B kz cos(kz z + p2) S(kz), -C kx cos(kx x + p3) S(kx), -A ky cos(ky y + p1) S(ky)).
+    Catches: a wrong sign or component in the cross product, a transposed axis,
+    a wrong wavenumber scale (period 2L), a missing or squared smoothing factor."""
+    g = _modes_grid()
+    X, Y, Z = g.coords()
+    kx, ky, kz = math.pi * 2 / g.L[0], math.pi * 3 / g.L[1], math.pi * 4 / g.L[2]
+    A, B, C, p1, p2, p3 = 0.7, -1.3, 0.4, 0.3, 1.1, -0.5
+    z0 = 0 * X + 0 * Y + 0 * Z
+    h = np.stack([A * np.sin(ky * Y + p1) + z0, B * np.sin(kz * Z + p2) + z0, C * np.sin(kx * X + p3) + z0])
+    S = lambda k: math.exp(-0.5 * g.sigma ** 2 * k * k)  # noqa: E731
+    ex = np.stack([-B * kz * np.cos(kz * Z + p2) * S(kz) + z0,
+                   -C * kx * np.cos(kx * X + p3) * S(kx) + z0,
+                   -A * ky * np.cos(ky * Y + p1) * S(ky) + z0])
+    c = O.curl_s(h, g)
+    assert np.abs(c - ex).max() < 1e-12 * max(kx, ky, kz)
+
+
+def test_sigma_is_half_cell_diagonal():
+    """§2: sigma equals half of the grid cell diagonal."""
+    g = O.Grid((10, 20, 40), (1.0, 1.0, 1.0))
+    assert g.sigma == pytest.approx(0.5 * math.sqrt(0.2 ** 2 + 0.1 ** 2 + 0.05 ** 2), rel=1e-15)
+    x, y, z = g.axes()
+    assert x[0] == pytest.approx(-0.9) and x[-1] == pytest.approx(0.9)
+
+
+def test_curl_nyquist_mode_has_zero_derivative():
+    """Reading R-nyq: the Nyquist checkerboard along y gives zero derivative.
+    Catches a Nyquist symbol left as i*k (which yields a complex curl)."""
+    g = O.Grid((8, 8, 8), (1.0, 1.0, 1.0))
+    h = np.zeros((3,) + g.shape)
+    h[2] = np.cos(np.pi * np.arange(8))[None, :, None] * np.ones(g.shape)
+    assert np.abs(O.curl_s(h, g)).max() < 1e-13
+
+
+def test_div_of_curl_vanishes():
+    """§2: div j = 0 for j = curl h (the discrete identity holds to round-off)."""
+    g = _modes_grid()
+    h = I.random_field((3,) + g.shape, 11)
+    j = O.curl_s(h, g)
+    assert np.abs(O.div_s(j, g)).max() < 1e-12 * np.abs(j).max()
+
+
+# ---------------------------------------------------------------- material law
+def test_power_law_special_values():
+    """Eq. 1, rho = (e0/jc)|j/jc|^(n-1): |e| = e0 when |j| = jc for every n;
+    e(lambda j) = lambda^n e(j); n = 1 is Ohm's law e = (e0/jc) j;
+    Omega_out uses rho_out.  Catches an exponent off by one, a missing e0/jc."""
+    rng = np.random.default_rng(3)
+    j = rng.standard_normal((3, 2, 3, 4))
+    mask = np.ones((2, 3, 4), bool)
+    jc = 1.7
+    unit = j / np.sqrt(np.sum(j * j, axis=0)) * jc
+    for n in (1.0, 7.0, 30.0):
+        m = O.Material(n=n, e0=2.5, jc=jc, rho_out=20.0)
+        e = O.electric_field(unit, mask, m)
+        assert np.allclose(np.sqrt(np.sum(e * e, axis=0)), 2.5, rtol=1e-13)
+        lam = 0.9
+        assert np.allclose(O.electric_field(lam * unit, mask, m), lam ** n * e, rtol=1e-12)
+    m1 = O.Material(n=1.0, e0=2.5, jc=jc)
+    assert np.allclose(O.electric_field(j, mask, m1), 2.5 / jc * j, rtol=1e-14)
+    out = O.electric_field(j, np.zeros_like(mask), O.Material(n=30.0, rho_out=20.0))
+    assert np.allclose(out, 20.0 * j, rtol=1e-15)
+
+
+def test_dissipation_nonnegative():
+    """e.j = rho |j|^2 >= 0 pointwise in Omega for Eq. 1."""
+    g = O.Grid((8, 8, 8), (1.0, 1.0, 1.0))
+    mask = I.cube(g.n, g.L, 1.0)
+    j = O.curl_s(I.random_field((3,) + g.shape, 5), g)
+    e = O.electric_field(j, mask, O.Material(n=25.0))
+    assert np.all(np.sum(e * j, axis=0)[mask] >= 0)
+    assert O.dissipation(j, e, mask, g.dV) > 0
+
+
+# ---------------------------------------------------------------- Green function
+def test_grad_green_far_field_is_coulomb():
+    """For r >> sigma, grad G_sigma -> grad 1/(4 pi r) = -r_vec/(4 pi r^3) (Eq. 2)."""
+    s = 0.05
+    r = np.array([[1.0, 0.3, -0.4], [0.0, 0.0, 2.0], [-0.7, 0.2, 0.1]]).T
+    G = O.grad_green_sigma(r[0], r[1], r[2], s)
+    rn = np.sqrt(np.sum(r * r, axis=0))
+    assert np.allclose(G, -r / (4 * math.pi * rn ** 3), rtol=1e-14)
+
+
+def test_grad_green_gaussian_core():
+    """Near r = 0, G_sigma is the potential of a Gaussian charge of density
+    (2 pi sigma^2)^(-3/2): grad G_sigma = -r_vec (2 pi sigma^2)^(-3/2) / 3 + O(r^3).
+    Catches a sigma vs sqrt(2) sigma mix-up."""
+    s = 0.3
+    r = 1e-4 * s * np.array([1.0, -2.0, 0.5])
+    G = O.grad_green_sigma(r[0], r[1], r[2], s)
+    ex = -r * (2 * math.pi * s * s) ** -1.5 / 3.0
+    assert np.allclose(G, ex, rtol=1e-6)
+    assert np.all(O.grad_green_sigma(0.0, 0.0, 0.0, s) == 0)
+
+
+def test_grad_green_matches_numerical_derivative():
+    """d/dr of erf(r/(sqrt 2 sigma))/(4 pi r) by central differences."""
+    from scipy.special import erf
+    s = 0.2
+    Gs = lambda r: erf(r / (math.sqrt(2) * s)) / (4 * math.pi * r)  # noqa: E731
+    for r in (0.05, 0.2, 0.5, 1.3):
+        hstep = 1e-5 * r
+        fd = (Gs(r + hstep) - Gs(r - hstep)) / (2 * hstep)
+        G = O.grad_green_sigma(r, 0.0, 0.0, s)
+        assert G[0] == pytest.approx(fd, rel=1e-7)
+        assert G[1] == 0 and G[2] == 0
+
+
+# ---------------------------------------------------------------- Biot-Savart Phi
+def test_phi_hockney_equals_direct_sum():
+    """Eq. 6 as a plain O(N^2) sum over nodes vs the zero-padded FFT route: equal
+    up to rounding (the padded cyclic convolution is exact for a block of N)."""
+    for n, L in (((6, 5, 7), (1.0, 0.8, 1.1)), ((8, 8, 6), (0.9, 1.2, 1.0))):
+        g = O.Grid(n, L)
+        j = I.random_field((3,) + g.shape, 21)
+        a = O.phi_direct(j, g)
+        b = O.phi_hockney(j, g)
+        assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+
+
+def test_kernel_spectrum_zero_mode_and_parity():
+    """Eq. 7 with 1/|k|^2 := 0 at k = 0: the sampled kernel is odd, so its
+    transform vanishes at k = 0 and is purely imaginary."""
+    g = O.Grid((6, 8, 4), (1.0, 1.0, 0.7))
+    K = O.hockney_kernel_spectrum(g)
+    assert np.abs(K[:, 0, 0, 0]).max() < 1e-15
+    assert np.abs(K.real).max() < 1e-14 * np.abs(K.imag).max()
+
+
+def test_phi_current_loop_closed_form():
+    """Biot-Savart field at the centre of an azimuthal current j = f(r, z) phi_hat
+    (a superposition of circular loops): h_z(0) = int int f a^2 / (2 (a^2+z^2)^1.5) da dz,
+    evaluated by quadrature.  Pins Phi's sign (right-hand rule) and scale (dV).
+    Discretisation error at 32^3 is about 0.1 percent."""
+    r0, w = 0.45, 0.1
+    f = lambda a, z: math.exp(-((a - r0) ** 2 + z * z) / (2 * w * w))  # noqa: E731
+    ex, _ = spi.dblquad(lambda z, a: f(a, z) * a * a / (2 * (a * a + z * z) ** 1.5), 0, 1.5, -1.0, 1.0,
+                        epsabs=1e-12, epsrel=1e-12)
+    N = 32
+    g = O.Grid((N, N, N), (1.0, 1.0, 1.0))
+    X, Y, Z = g.coords()
+    r = np.sqrt(X * X + Y * Y) + 0 * Z
+    F = np.exp(-((r - r0) ** 2 + (Z + 0 * r) ** 2) / (2 * w * w))
+    j = np.zeros((3,) + g.shape)
+    j[0], j[1] = -Y / r * F, X / r * F
+    P = O.phi_hockney(j, g)
+    c = N // 2
+    hz = P[2, c - 1:c + 1, c - 1:c + 1, c - 1:c + 1].mean()
+    assert hz == pytest.approx(ex, rel=5e-3)
+    # off-axis radial components cancel in the 8-node average (mirror symmetry)
+    assert np.abs(P[:2, c - 1:c + 1, c - 1:c + 1, c - 1:c + 1].mean(axis=(1, 2, 3))).max() < 1e-12 * ex
+
+
+def test_ampere_consistency():
+    """§2 under Eq. 2: curl Phi[j] = j for a divergence-free j.  Both the curl and
+    Phi carry one Gaussian smoothing, so the discrete statement is
+    curl_S Phi_d[j] = (Gaussian of std sqrt(2) sigma) * j away from the box faces
+    (where the periodic curl meets the non-periodic free-space field).  The
+    filtered j is formed here with its own Gaussian multiplier exp(-sigma^2 k^2)."""
+    N = 24
+    g = O.Grid((N, N, N), (1.0, 1.0, 1.0))
+    X, Y, Z = g.coords()
+    r = np.sqrt(X * X + Y * Y) + 0 * Z
+    F = np.exp(-((r - 0.4) ** 2 + (Z + 0 * r) ** 2) / (2 * 0.12 ** 2))
+    j = np.zeros((3,) + g.shape)
+    j[0], j[1] = -Y / r * F, X / r * F
+    c = O.curl_s(O.phi_hockney(j, g), g)
+    k1 = [np.pi * np.fft.fftfreq(N, 1.0 / N) / 1.0] * 3
+    k2 = k1[0][None, None, :] ** 2 + k1[1][None, :, None] ** 2 + k1[2][:, None, None] ** 2
+    jf = np.real(np.fft.ifftn(np.fft.fftn(j, axes=(1, 2, 3)) * np.exp(-g.sigma ** 2 * k2), axes=(1, 2, 3)))
+    inner = np.maximum(np.maximum(np.abs(X), np.abs(Y)), np.abs(Z)) < 0.75
+    assert np.abs((c - jf)[:, inner]).max() < 1e-3 * np.abs(j).max()
+    assert np.abs((c - j)[:, inner]).max() > 0.1 * np.abs(j).max()  # the smoothing is visible
+
+
+# ---------------------------------------------------------------- right-hand side
+def test_rhs_ohmic_full_box_mode_decay():
+    """Omega = the whole box, n = 1: Eq. 5 is vacuous and Eqs. 1, 3, 4 give
+    dh/dt = -(e0/jc)/mu0 curl_S curl_S h = -(e0/jc)/mu0 S(k)^2 |k|^2 h for a
+    divergence-free Fourier mode.  Pins the sign of Faraday's law and the units."""
+    g = O.Grid((12, 10, 8), (1.0, 0.8, 1.2))
+    X, Y, Z = g.coords()
+    k = np.array([math.pi * 1 / g.L[0], math.pi * 2 / g.L[1], math.pi * 1 / g.L[2]])
+    a = np.cross(k, [0.3, -0.2, 0.9])
+    ph = k[0] * X + k[1] * Y + k[2] * Z
+    h = np.stack([a[i] * np.sin(ph + 0.2) for i in range(3)])
+    e0, jc, mu0 = 2.0, 1.5, 0.5
+    prob = O.Problem(g, np.ones(g.shape, bool), O.Material(n=1.0, e0=e0, jc=jc, rho_out=7.0, mu0=mu0),
+                     O.FieldPath([0.0, 1.0], [[0, 0, 0], [0, 0, 1.0]]))
+    r = O.rhs(prob, 0.5, h, np.zeros_like(h))
+    k2 = float(k @ k)
+    S2 = math.exp(-g.sigma ** 2 * k2)
+    assert r.iters == 0
+    assert np.abs(r.hdot + (e0 / jc) / mu0 * S2 * k2 * h).max() < 1e-12 * np.abs(h).max() * k2
+
+
+def test_rhs_empty_omega_is_applied_rate():
+    """Omega empty: j_in = 0, so Eq. 5 gives dh/dt = dh_e/dt everywhere."""
+    g = O.Grid((8, 8, 8), (1.0, 1.0, 1.0))
+    prob = O.Problem(g, np.zeros(g.shape, bool), O.Material(),
+                     O.FieldPath([0.0, 2.0], [[0, 0, 0], [0.2, -0.4, 1.0]]))
+    h = I.random_field((3,) + g.shape, 4)
+    r = O.rhs(prob, 0.3, h, I.random_field((3,) + g.shape, 5))
+    assert np.allclose(r.hdot, np.array([0.1, -0.2, 0.5])[:, None, None, None], atol=1e-15)
+    assert r.converged and r.iters == 2
+
+
+def _cube_state(N=16, half=1.0):
+    L = (half, half, half)
+    g = O.Grid((N, N, N), L)
+    prob = O.Problem(g, I.cube(g.n, L, 1.0), O.Material(n=20.0, rho_out=20.0),
+                     O.FieldPath([0.0, 1.0], [[0, 0, 0], [0, 0, 0.5]]))
+    res = O.integrate(prob, 0.0, 0.1, np.zeros((3,) + g.shape), rtol=1e-4, atol=1e-7, dt0=1e-4)
+    return g, prob, res
+
+
+def test_rhs_converged_iterate_is_curl_free_outside():
+    """§2 after Eq. 5: when the iterations converge, curl dh/dt vanishes in
+    Omega_out.  Discretely this holds away from the smoothing halo of the
+    surface and from the box faces (where the periodic curl meets the
+    free-space field): there |curl dh/dt| stays below 0.7 percent of its maximum
+    in Omega (a sign-flipped Phi gives 1.2 percent, a mask applied to the wrong
+    set has no such fixed point).  The residuals fall geometrically."""
+    g, prob, res = _cube_state(20, 1.5)
+    r = O.rhs(prob, 0.1, res.y, np.broadcast_to(prob.path.hedot(0.1)[:, None, None, None], res.y.shape).copy(),
+              delta_it=1e-12, max_iter=60)
+    assert r.converged
+    c = np.sqrt(np.sum(O.curl_s(r.hdot, g) ** 2, axis=0))
+    X, Y, Z = g.coords()
+    mx = np.maximum(np.maximum(np.abs(X), np.abs(Y)), np.abs(Z))
+    far = (mx > 0.5 + 2 * g.d[0]) & (mx < 1.5 - 2 * g.d[0])
+    assert far.sum() > 1000
+    assert c[far].max() < 7e-3 * c[prob.mask].max()
+    assert all(b < 0.2 * a for a, b in zip(r.residuals[:6], r.residuals[1:6]))
+
+
+def test_rhs_iteration_contracts_fast():
+    """§2: with the previous result as the warm start, convergence takes a few
+    iterations (here: at most 5 at delta_it = 2e-5)."""
+    g, prob, res = _cube_state()
+    assert max(res.iters) <= 6
+    assert np.mean(res.iters) <= 4
+
+
+# ---------------------------------------------------------------- BS23 integrator
+def test_bs23_linear_stability_polynomials():
+    """For y' = lam y the third-order solution is y (1 + z + z^2/2 + z^3/6) (any
+    3-stage third-order RK) and the embedded second-order FSAL solution is
+    y (1 + z + z^2/2 + 3 z^3/16 + z^4/48), so y3 - y2 = -(z^3 + z^4)/48 y.
+    Catches any wrong coefficient of the pair."""
+    lam, y0 = -3.0, np.array([2.0])
+    f = lambda t, y, left: lam * y  # noqa: E731
+    for dt in (0.01, 0.1, 0.3):
+        z = lam * dt
+        y1, k4, err = O.bs23_step(f, 0.0, y0, dt, f(0, y0, False))
+        assert y1[0] == pytest.approx(y0[0] * (1 + z + z * z / 2 + z ** 3 / 6), rel=1e-14)
+        assert err[0] == pytest.approx(-(z ** 3 + z ** 4) / 48 * y0[0], rel=1e-10, abs=1e-17)
+        assert k4[0] == pytest.approx(lam * y1[0], rel=1e-15)
+
+
+def test_bs23_third_order_convergence():
+    """Global error of y' = y cos t, y(0)=1, exact exp(sin t), falls by ~8 per
+    halving of dt."""
+    f = lambda t, y, left: y * math.cos(t)  # noqa: E731
+
+    def run(nsteps):
+        y, t, dt = np.array([1.0]), 0.0, 1.0 / nsteps
+        k = f(t, y, False)
+        for _ in range(nsteps):
+            y, k, _ = O.bs23_step(f, t, y, dt, k)
+            t += dt
+        return abs(y[0] - math.exp(math.sin(1.0)))
+
+    e1, e2 = run(20), run(40)
+    assert 7.0 < e1 / e2 < 9.0
+
+
+def test_field_path_values_and_kinks():
+    """§3 ramps: piecewise-linear h_e and its one-sided derivatives at kinks."""
+    p = O.FieldPath([0.0, 0.09, 0.18], [[0, 0, 0], [0, 0, 0.09], [0.09, 0, 0.09]])
+    assert np.allclose(p.he_at(0.045), [0, 0, 0.045])
+    assert np.allclose(p.he_at(0.135), [0.045, 0, 0.09])
+    assert np.allclose(p.hedot(0.09), [1, 0, 0])
+    assert np.allclose(p.hedot(0.09, left=True), [0, 0, 1])
+    assert np.allclose(p.hedot(0.5), [0, 0, 0])
+    s = O.FieldPath([0.0, 1.0], [[0, 0, 0], [0, 0, 1]], sin_amp=0.1, sin_period=0.5, sin_t0=1.0, sin_t1=2.5)
+    assert np.allclose(s.hedot(1.125), [0, 0, 0.1 * 4 * math.pi * math.cos(math.pi / 2)], atol=1e-15)
+    assert np.allclose(s.he_at(1.125), [0, 0, 1.1])
+
+
+def test_integrate_empty_omega_tracks_applied_field():
+    """Omega empty: h(t) = h_e(t) exactly (h_e is piecewise linear and steps end
+    on its kinks), at every snapshot."""
+    g = O.Grid((6, 6, 6), (1.0, 1.0, 1.0))
+    path = O.FieldPath([0.0, 0.3, 0.5], [[0, 0, 0], [0, 0, 0.3], [0.2, 0, 0.3]])
+    prob = O.Problem(g, np.zeros(g.shape, bool), O.Material(), path)
+    res = O.integrate(prob, 0.0, 0.6, np.zeros((3,) + g.shape), rtol=1e-6, atol=1e-9, dt0=0.07,
+                      snapshots=[0.2, 0.4, 0.6])
+    assert [s[0] for s in res.snaps] == [0.2, 0.4, 0.6]
+    for t, y in res.snaps:
+        assert np.allclose(y, path.he_at(t)[:, None, None, None], atol=1e-13)
+
+
+def test_integrate_mode_decay_matches_exponential():
+    """Omega = box, n = 1: dh/dt = -c h per Fourier mode, so the adaptive run
+    reproduces exp(-c t) within a small multiple of rtol."""
+    g = O.Grid((8, 8, 8), (1.0, 1.0, 1.0))
+    X, Y, Z = g.coords()
+    k = math.pi
+    h0 = np.zeros((3,) + g.shape)
+    h0[2] = np.sin(k * X + 0.1) + 0 * Y + 0 * Z
+    prob = O.Problem(g, np.ones(g.shape, bool), O.Material(n=1.0), O.FieldPath([0.0, 1.0], [[0, 0, 0]] * 2))
+    res = O.integrate(prob, 0.0, 0.5, h0, rtol=1e-6, atol=1e-10, dt0=1e-3)
+    c = k * k * math.exp(-g.sigma ** 2 * k * k)
+    assert np.abs(res.y - h0 * math.exp(-c * 0.5)).max() < 1e-4 * math.exp(-c * 0.5)
+    assert res.rejected <= 3
+
+
+def test_conducting_sphere_steady_ramp():
+    """A conducting sphere (n = 1, rho = 1) in a field ramped at rate alpha
+    reaches a steady state whose eddy current is exactly j = (alpha/2)(y, -x, 0)
+    (curl e = -alpha z_hat with j_n = 0), so dh/dt -> alpha z_hat everywhere and
+    the moment -> -2 pi alpha R^5 / 15.  The coarse grid resolves the surface
+    only to O(sigma/R), so the moment pin is to discretisation accuracy: it has
+    the right sign, lies within 45 percent, and improves under refinement."""
+    def run(N):
+        L = (1.0, 1.0, 1.0)
+        g = O.Grid((N, N, N), L)
+        mask = I.sphere(g.n, L, 0.5)
+        path = O.FieldPath([0.0, 10.0], [[0, 0, 0], [0, 0, 10.0]])
+        prob = O.Problem(g, mask, O.Material(n=1.0, rho_out=20.0), path)
+        res = O.integrate(prob, 0.0, 0.2, np.zeros((3,) + g.shape), rtol=1e-4, atol=1e-8, dt0=1e-5)
+        j = O.curl_s(res.y, g) * mask
+        Reff = (mask.sum() * g.dV * 3 / (4 * math.pi)) ** (1 / 3)
+        m = O.magnetic_moment(j, g)[2] / (-2 * math.pi * Reff ** 5 / 15)
+        hd = O.rhs(prob, 0.2, res.y, np.broadcast_to(np.array([0, 0, 1.0])[:, None, None, None],
+                                                     res.y.shape).copy()).hdot
+        return m, hd, mask
+
+    m16, hd, mask = run(16)
+    assert 0.55 < m16 < 1.0
+    assert np.abs(hd[2][~mask] - 1.0).max() < 5e-3
+    assert np.abs(hd[:2][:, ~mask]).max() < 5e-3
+    m20, _, _ = run(20)
+    assert abs(1 - m20) < abs(1 - m16)
