@@ -1,0 +1,170 @@
+/*
+ * scfft.h - C ABI of the GB300 (sm_103a) implementation of the method-of-lines
+ * right-hand side of the FFT-based 3D bulk-magnetization method of
+ * Prigozhin & Sokolovsky ("3D simulation of superconducting magnetic shields
+ * and lenses using the fast Fourier transform", §2, Eqs. 1-8), and of its
+ * time integrator.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid (§2, "uniform Nx x Ny x Nz grid" on D = {|x|<=Lx, |y|<=Ly, |z|<=Lz}):
+ *   nodes are cell centres x_i = -Lx + (i + 1/2) dx, dx = 2 Lx / Nx; every
+ *   N_a is even and 16 <= N_a <= 128 with N_a = 2^p 3^q (16, 32, 48, 64, 96, 128).
+ * Vector fields: double arrays of 3*N entries, N = Nx*Ny*Nz, laid out
+ *   [component x,y,z][z][y][x] (x fastest).  Scalar node fields: N entries
+ *   [z][y][x].
+ * Units: the dimensionless variables of Eq. 8 (e0 = jc = mu0 = 1 by default).
+ * Memory: pointers documented "device" are CUDA device pointers owned by the
+ *   caller (the library never frees them); "host" pointers are read during the
+ *   call only.  Every device-side call is asynchronous on the context's CUDA
+ *   stream unless stated otherwise.
+ * Errors: invalid arguments are rejected on the host before any work is
+ *   queued (SCFFT_EINVAL, nothing changed).  CUDA failures return SCFFT_ECUDA.
+ *   No entry point aborts or throws.
+ */
+#ifndef SCFFT_H
+#define SCFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct scfft_ctx scfft_ctx; /* opaque; owns every internal workspace */
+
+typedef enum {
+  SCFFT_OK = 0,
+  SCFFT_EINVAL = 1,    /* bad argument or unsupported size */
+  SCFFT_ENOMEM = 2,    /* device or host allocation failed */
+  SCFFT_ECUDA = 3,     /* a CUDA runtime call failed */
+  SCFFT_ENOCONV = 4,   /* Eq. 5 iteration stopped at max_iter (result still written) */
+  SCFFT_ESTEP = 5,     /* integrator step size fell below its floor */
+  SCFFT_ENONFINITE = 6,/* NaN/Inf met in a residual or error norm */
+  SCFFT_ETIMEOUT = 7,  /* reserved: a bounded device wait gave up */
+  SCFFT_ESTATE = 8     /* call out of order (e.g. rhs before precompute_kernel) */
+} scfft_status;
+
+/* Arithmetic of the FFTs and pointwise steps.  The integrator state, its stage
+ * sums, error norm and step control are FP64 in both modes. */
+#define SCFFT_PREC_F64 0
+#define SCFFT_PREC_F32 1
+
+typedef struct {
+  int nx, ny, nz;      /* nodes per axis */
+  double Lx, Ly, Lz;   /* half extents of the box D */
+} scfft_grid;
+
+/* Eq. 1: rho(|j|) = (e0/jc) |j/jc|^(n-1) in Omega; rho_out in Omega_out (§2). */
+typedef struct {
+  double n, e0, jc, rho_out, mu0;
+} scfft_material;
+
+typedef struct {
+  int precision;       /* SCFFT_PREC_F64 or SCFFT_PREC_F32 */
+  double delta_it;     /* Eq. 5 stop tolerance (§2 uses 2e-5); 0 = never stop early */
+  int max_iter;        /* iteration cap of Eq. 5 (>= 0) */
+  double sigma_scale;  /* multiplies sigma = half the cell diagonal (§2); 1 = paper */
+  double rtol, atol;   /* integrator tolerances (§2 uses rtol 2e-4) */
+} scfft_options;
+
+/* Applied field h_e(t) (§3): piecewise-linear through (t[k], he[3k..3k+2]),
+ * constant outside [t[0], t[nknots-1]], plus
+ * sin_amp * sin(2 pi (t - sin_t0) / sin_period) * sin_dir for sin_t0 <= t < sin_t1. */
+typedef struct {
+  int nknots;          /* 1..64 */
+  const double* t;     /* host, nknots, strictly increasing */
+  const double* he;    /* host, 3*nknots */
+  double sin_amp, sin_period, sin_t0, sin_t1;
+  double sin_dir[3];
+} scfft_field_path;
+
+typedef struct {
+  long long rhs_calls;     /* right-hand-side evaluations */
+  long long iterations;    /* Eq. 5 iterations summed over those calls */
+  long long accepted, rejected;
+  int last_iters;          /* iterations of the most recent rhs */
+  double last_residual;    /* its final Eq. 5 residual */
+  double t, dt;            /* integrator time and proposed step */
+} scfft_stats;
+
+/* Create a context for one grid.  stream: a cudaStream_t (NULL = legacy
+ * default stream).  Allocates every device workspace (sizes grow as
+ * (3*N complex) * 8 words in FP64).  Errors: EINVAL for an unsupported grid,
+ * nonpositive extents, n < 1, negative rho_out, max_iter < 0; ENOMEM. */
+scfft_status scfft_create(const scfft_grid* grid, const scfft_material* mat, const scfft_options* opt,
+                          void* stream, scfft_ctx** out);
+
+/* Omega (§2): mask[N] (host, [z][y][x]), nonzero = node in the superconductor.
+ * Copied to the device.  EINVAL if Omega is empty or touches the two outermost
+ * node layers of any box face (the free-space Phi needs the margin). */
+scfft_status scfft_set_geometry(scfft_ctx* ctx, const uint8_t* mask);
+
+/* Per-node critical current density jc(x) (device, N doubles, > 0), or NULL
+ * for the uniform material jc.  Copied (converted to the FFT precision). */
+scfft_status scfft_set_jc_map(scfft_ctx* ctx, const double* jc_dev);
+
+/* Applied-field path h_e(t); copied.  EINVAL on bad knots. */
+scfft_status scfft_set_field_path(scfft_ctx* ctx, const scfft_field_path* path);
+
+/* Sample grad G_sigma (G_sigma = G of Eq. 2 smoothed by a Gaussian of std sigma)
+ * on the offsets of the zero-padded 2Nx x 2Ny x 2Nz grid, with the offset -N_a
+ * planes zeroed so the kernel is odd (transform 0 at k = 0, the rule under
+ * Eq. 7), and keep its purely imaginary transform on one octant.  Queued on
+ * the stream; must precede rhs. */
+scfft_status scfft_precompute_kernel(scfft_ctx* ctx);
+
+/* One right-hand side dh/dt at time t (§2, Eqs. 1, 3, 4, 5):
+ *   j = curl_S h; e = rho(|j|) j in Omega, rho_out j outside;
+ *   dh_in = -curl_S e / mu0 on Omega; dh^0 = dh_in on Omega, warm on Omega_out;
+ *   dh^{i+1} = dh^i on Omega, dh_e/dt + Phi[chi_Omega curl_S dh^i] on Omega_out,
+ *   until mean_{Omega_out} |dh^{i+1} - dh^i| < delta_it max(|dh_e/dt|, 1) or max_iter.
+ * left != 0 evaluates dh_e/dt as the left derivative at a kink of the path.
+ * h, warm, hdot: device, 3*N doubles; warm is read (its Omega_out part is the
+ * initial approximation of Eq. 5) and then overwritten with hdot.  hdot must
+ * not alias h.  iters_out: host int* or NULL; if non-NULL the call waits for
+ * the stream and stores the iteration count (and returns ENOCONV if the cap
+ * stopped it); if NULL the call returns after queueing the work (the early
+ * stop of Eq. 5 is decided on the device). */
+scfft_status scfft_rhs(scfft_ctx* ctx, double t, int left, const double* h, double* warm, double* hdot,
+                       int* iters_out);
+
+/* Smoothed spectral curl alone (§2, derivatives of Eqs. 3-4): out = curl_S f.
+ * f, out: device, 3*N doubles (may not alias).  Asynchronous. */
+scfft_status scfft_curl(scfft_ctx* ctx, const double* f, double* out);
+
+/* Biot-Savart operator alone (Eqs. 6-7 by zero padding): out = Phi_d[j] on the
+ * grid, j taken as given (no mask).  j, out: device, 3*N doubles.  Asynchronous. */
+scfft_status scfft_phi(scfft_ctx* ctx, const double* j, double* out);
+
+/* Integrate dh/dt = rhs from t0 to t1 by the Bogacki-Shampine 3(2) FSAL pair
+ * (the method of Matlab ode23 used in §2) with error norm
+ * max_i |err_i| / max(rtol |y_i|, rtol |y_new,i|, atol), accept if <= 1,
+ * dt <- dt min(5, max(0.2, 0.9 err^(-1/3))).  Steps end exactly on the
+ * path's kinks, on each snapshot time and on t1.  dt0 > 0 is the first trial
+ * step.  h: device, 3*N doubles, in: h(t0), out: h(t1).  tsnap: host, nsnap
+ * increasing times in (t0, t1]; snaps: device, nsnap*3*N doubles (may be NULL
+ * when nsnap = 0).  warm: device 3*N doubles, in/out warm start of Eq. 5
+ * (NULL: dh_e/dt(t0) everywhere).  dt_fixed: host array of nfixed steps for
+ * fixed-step mode (no error control), or NULL.  Synchronous: returns when
+ * done.  stats: host or NULL. */
+scfft_status scfft_integrate(scfft_ctx* ctx, double t0, double t1, double dt0, int nsnap, const double* tsnap,
+                             double* h, double* snaps, double* warm, const double* dt_fixed, int nfixed,
+                             scfft_stats* stats);
+
+/* Wait for the stream; returns the first latched device-side status. */
+scfft_status scfft_sync(scfft_ctx* ctx);
+
+/* Counters since create (host copy). */
+scfft_status scfft_get_stats(scfft_ctx* ctx, scfft_stats* out);
+
+const char* scfft_status_string(scfft_status s);
+
+/* Free every workspace.  NULL is a no-op. */
+void scfft_destroy(scfft_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCFFT_H */

@@ -383,14 +383,16 @@ BS23_BHAT = (7.0 / 24.0, 0.25, 1.0 / 3.0, 0.125)         # embedded second order
 BS23_E = tuple(b - bh for b, bh in zip(BS23_B, BS23_BHAT))  # y3 - y2 weights
 
 
-def bs23_step(f: Callable, t: float, y: np.ndarray, dt: float, k1: np.ndarray, end_left: bool = False):
+def bs23_step(f: Callable, t: float, y: np.ndarray, dt: float, k1: np.ndarray, end_left: bool = False,
+              t_end: Optional[float] = None):
     """One BS23 step from (t, y) with first stage k1 = f(t, y).  Returns
-    (y_new, k4, err_vec) with k4 = f(t+dt, y_new) (the FSAL stage) and
+    (y_new, k4, err_vec) with k4 = f(t_end, y_new) (the FSAL stage; t_end
+    defaults to t+dt, a step clipped to a stop passes the stop itself) and
     err_vec = dt * sum_i (b_i - bhat_i) k_i."""
     k2 = f(t + BS23_C[1] * dt, y + dt * (BS23_A[1][0] * k1), False)
     k3 = f(t + BS23_C[2] * dt, y + dt * (BS23_A[2][0] * k1 + BS23_A[2][1] * k2), False)
     ynew = y + dt * (BS23_B[0] * k1 + BS23_B[1] * k2 + BS23_B[2] * k3)
-    k4 = f(t + dt, ynew, end_left)
+    k4 = f(t + dt if t_end is None else t_end, ynew, end_left)
     err = dt * (BS23_E[0] * k1 + BS23_E[1] * k2 + BS23_E[2] * k3 + BS23_E[3] * k4)
     return ynew, k4, err
 
@@ -456,7 +458,7 @@ def integrate(prob: Problem, t0: float, t1: float, y0: np.ndarray, rtol: float, 
         h_step = min(dt, nxt - t)
         hits = (h_step == nxt - t)
         end_left = hits and (nxt in kinks)
-        ynew, k4, err = bs23_step(f, t, y, h_step, k1, end_left)
+        ynew, k4, err = bs23_step(f, t, y, h_step, k1, end_left, t_end=nxt if hits else None)
         if dt_list is not None:
             en = 0.0
         else:

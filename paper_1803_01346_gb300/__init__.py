@@ -1,0 +1,214 @@
+"""GB300 (sm_103a) implementation of the method-of-lines right-hand side of the
+FFT-based 3D bulk-magnetization method (Prigozhin & Sokolovsky, §2) and of its
+Bogacki-Shampine time integrator.
+
+All arithmetic runs in the CUDA library libscfft.so behind the C ABI of
+include/scfft.h.  This module only marshals arguments (ctypes): device arrays
+are torch CUDA tensors (float64, contiguous) passed by pointer, host arrays are
+numpy arrays.  There is no CPU fallback: importing works without a GPU, but
+every call that reaches the library fails loudly if the library is missing or
+no GPU is present.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+__all__ = ["ScfftError", "Context", "load_library", "library_path", "PREC_F64", "PREC_F32", "EXPORTS"]
+
+PREC_F64 = 0
+PREC_F32 = 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBNAME = "libscfft.so"
+
+# every entry point declared in include/scfft.h
+EXPORTS = ("scfft_create", "scfft_set_geometry", "scfft_set_jc_map", "scfft_set_field_path",
+           "scfft_precompute_kernel", "scfft_rhs", "scfft_curl", "scfft_phi", "scfft_integrate",
+           "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy")
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, _LIBNAME)
+
+
+class ScfftError(RuntimeError):
+    def __init__(self, code: int, what: str, msg: str):
+        super().__init__(f"{what}: {msg} (status {code})")
+        self.code = code
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("Lz", ctypes.c_double)]
+
+
+class _Material(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_double), ("e0", ctypes.c_double), ("jc", ctypes.c_double),
+                ("rho_out", ctypes.c_double), ("mu0", ctypes.c_double)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("delta_it", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("sigma_scale", ctypes.c_double), ("rtol", ctypes.c_double), ("atol", ctypes.c_double)]
+
+
+class _FieldPath(ctypes.Structure):
+    _fields_ = [("nknots", ctypes.c_int), ("t", ctypes.POINTER(ctypes.c_double)),
+                ("he", ctypes.POINTER(ctypes.c_double)), ("sin_amp", ctypes.c_double),
+                ("sin_period", ctypes.c_double), ("sin_t0", ctypes.c_double), ("sin_t1", ctypes.c_double),
+                ("sin_dir", ctypes.c_double * 3)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("rhs_calls", ctypes.c_longlong), ("iterations", ctypes.c_longlong),
+                ("accepted", ctypes.c_longlong), ("rejected", ctypes.c_longlong),
+                ("last_iters", ctypes.c_int), ("last_residual", ctypes.c_double),
+                ("t", ctypes.c_double), ("dt", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None):
+    """Load libscfft.so (build it first with paper_1803_01346_gb300.build)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or library_path()
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: run `python -m paper_1803_01346_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(p)
+    P, D, I, V = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, None
+    sig = {
+        "scfft_create": (I, [ctypes.POINTER(_Grid), ctypes.POINTER(_Material), ctypes.POINTER(_Options), P,
+                             ctypes.POINTER(P)]),
+        "scfft_set_geometry": (I, [P, P]),
+        "scfft_set_jc_map": (I, [P, P]),
+        "scfft_set_field_path": (I, [P, ctypes.POINTER(_FieldPath)]),
+        "scfft_precompute_kernel": (I, [P]),
+        "scfft_rhs": (I, [P, D, I, P, P, P, ctypes.POINTER(I)]),
+        "scfft_curl": (I, [P, P, P]),
+        "scfft_phi": (I, [P, P, P]),
+        "scfft_integrate": (I, [P, D, D, D, I, P, P, P, P, P, I, ctypes.POINTER(_Stats)]),
+        "scfft_sync": (I, [P]),
+        "scfft_get_stats": (I, [P, ctypes.POINTER(_Stats)]),
+        "scfft_status_string": (ctypes.c_char_p, [I]),
+        "scfft_destroy": (V, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _ptr(x) -> int:
+    """Device pointer of a contiguous float64 CUDA tensor (or None -> 0)."""
+    if x is None:
+        return None
+    import torch
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return x.data_ptr()
+
+
+class Context:
+    """One grid, material, option set and CUDA stream (§2 of the paper).
+
+    grid: (nx, ny, nz), L: half extents (Lx, Ly, Lz)."""
+
+    def __init__(self, n: Sequence[int], L: Sequence[float], n_power: float = 20.0, rho_out: float = 20.0,
+                 e0: float = 1.0, jc: float = 1.0, mu0: float = 1.0, precision: int = PREC_F64,
+                 delta_it: float = 2e-5, max_iter: int = 100, sigma_scale: float = 1.0,
+                 rtol: float = 2e-4, atol: float = 1e-6, stream=None):
+        self._lib = load_library()
+        self.n = tuple(int(v) for v in n)
+        self.N = self.n[0] * self.n[1] * self.n[2]
+        g = _Grid(self.n[0], self.n[1], self.n[2], float(L[0]), float(L[1]), float(L[2]))
+        m = _Material(float(n_power), float(e0), float(jc), float(rho_out), float(mu0))
+        o = _Options(int(precision), float(delta_it), int(max_iter), float(sigma_scale), float(rtol), float(atol))
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        self._h = ctypes.c_void_p()
+        self._check(self._lib.scfft_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(o),
+                                           ctypes.c_void_p(int(stream) if stream else 0), ctypes.byref(self._h)),
+                    "scfft_create")
+
+    def _check(self, code: int, what: str, ok=(0,)):
+        if code not in ok:
+            raise ScfftError(code, what, self._lib.scfft_status_string(code).decode())
+        return code
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.scfft_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_geometry(self, mask: np.ndarray):
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        if m.size != self.N:
+            raise ValueError("mask must have nx*ny*nz entries")
+        self._check(self._lib.scfft_set_geometry(self._h, m.ctypes.data), "scfft_set_geometry")
+
+    def set_jc_map(self, jc=None):
+        self._check(self._lib.scfft_set_jc_map(self._h, _ptr(jc)), "scfft_set_jc_map")
+
+    def set_field_path(self, t, he, sin_amp=0.0, sin_period=1.0, sin_t0=0.0, sin_t1=0.0, sin_dir=(0.0, 0.0, 1.0)):
+        tt = np.ascontiguousarray(t, dtype=np.float64)
+        hh = np.ascontiguousarray(he, dtype=np.float64).reshape(-1)
+        self._keep = (tt, hh)
+        fp = _FieldPath(len(tt), tt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        hh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(sin_amp), float(sin_period),
+                        float(sin_t0), float(sin_t1), (ctypes.c_double * 3)(*[float(v) for v in sin_dir]))
+        self._check(self._lib.scfft_set_field_path(self._h, ctypes.byref(fp)), "scfft_set_field_path")
+
+    def precompute_kernel(self):
+        self._check(self._lib.scfft_precompute_kernel(self._h), "scfft_precompute_kernel")
+
+    def rhs(self, t: float, h, warm, hdot, left: bool = False, sync: bool = True):
+        """dh/dt into hdot; warm is the Eq. 5 warm start (overwritten with hdot).
+        Returns the iteration count when sync is True."""
+        it = ctypes.c_int(0)
+        code = self._lib.scfft_rhs(self._h, float(t), 1 if left else 0, _ptr(h), _ptr(warm), _ptr(hdot),
+                                   ctypes.byref(it) if sync else None)
+        self._check(code, "scfft_rhs", ok=(0, 4))
+        return it.value if sync else None
+
+    def curl(self, f, out):
+        self._check(self._lib.scfft_curl(self._h, _ptr(f), _ptr(out)), "scfft_curl")
+
+    def phi(self, j, out):
+        self._check(self._lib.scfft_phi(self._h, _ptr(j), _ptr(out)), "scfft_phi")
+
+    def integrate(self, t0, t1, dt0, h, tsnap=(), snaps=None, warm=None, dt_fixed=None):
+        ts = np.ascontiguousarray(tsnap, dtype=np.float64)
+        df = None if dt_fixed is None else np.ascontiguousarray(dt_fixed, dtype=np.float64)
+        st = _Stats()
+        self._check(self._lib.scfft_integrate(self._h, float(t0), float(t1), float(dt0), len(ts),
+                                              ts.ctypes.data if len(ts) else None, _ptr(h), _ptr(snaps),
+                                              _ptr(warm), df.ctypes.data if df is not None else None,
+                                              0 if df is None else len(df), ctypes.byref(st)),
+                    "scfft_integrate")
+        return {k: getattr(st, k) for k, _ in _Stats._fields_}
+
+    def sync(self):
+        self._check(self._lib.scfft_sync(self._h), "scfft_sync")
+
+    def stats(self):
+        st = _Stats()
+        self._check(self._lib.scfft_get_stats(self._h, ctypes.byref(st)), "scfft_get_stats")
+        return {k: getattr(st, k) for k, _ in _Stats._fields_}

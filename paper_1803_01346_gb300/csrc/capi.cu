@@ -1,0 +1,580 @@
+// capi.cu - the C ABI of include/scfft.h: context, geometry, kernel-spectrum
+// precompute, the right-hand side driver (§2, Eqs. 1-5) and the BS23 time
+// integrator (the method of lines with "ode23", §2).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "scfft.h"
+#include "scfft_internal.cuh"
+
+using namespace scfft;
+
+struct scfft_ctx {
+  Geo g{};
+  double L[3]{};
+  scfft_material mat{};
+  scfft_options opt{};
+  cudaStream_t st = nullptr;
+  Work<float> wf;
+  Work<double> wd;
+  Ctrl* ctrl = nullptr;        // device
+  double* partials = nullptr;  // device
+  uint8_t* mask = nullptr;     // device
+  long long nout = 0;
+  bool have_geom = false, have_kernel = false, have_path = false;
+  // field path
+  std::vector<double> kt, khe;
+  double sin_amp = 0, sin_period = 1, sin_t0 = 0, sin_t1 = 0, sin_dir[3] = {0, 0, 1};
+  // host mirror of Ctrl and synchronisation
+  Ctrl* hctrl = nullptr;  // pinned
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  // integrator (FP64)
+  double* ib = nullptr;   // 7 * 3N doubles: ynew, k1..k4, ytmp, g
+  unsigned long long* errbits = nullptr;  // device
+  unsigned long long* herr = nullptr;     // pinned
+  scfft_stats stats{};
+};
+
+namespace {
+
+#define CK(x)                                  \
+  do {                                         \
+    cudaError_t e_ = (x);                      \
+    if (e_ != cudaSuccess) return SCFFT_ECUDA; \
+  } while (0)
+
+int round_up(int a, int m) { return (a + m - 1) / m * m; }
+
+bool grid_ok(int n) {
+  return n == 16 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128;
+}
+
+template <typename T> Work<T>& work(scfft_ctx* c);
+template <> Work<float>& work<float>(scfft_ctx* c) { return c->wf; }
+template <> Work<double>& work<double>(scfft_ctx* c) { return c->wd; }
+
+template <typename T> Launch<T> launch_of(scfft_ctx* c) {
+  Launch<T> L;
+  L.g = c->g;
+  L.w = &work<T>(c);
+  L.ctrl = c->ctrl;
+  L.mask = c->mask;
+  L.partials = c->partials;
+  L.st = c->st;
+  return L;
+}
+
+// dh_e/dt at t (right derivative, or left at a kink when left != 0)
+void hedot_at(const scfft_ctx* c, double t, int left, double out[3]) {
+  out[0] = out[1] = out[2] = 0;
+  const int K = (int)c->kt.size();
+  for (int s = 0; s + 1 < K; ++s) {
+    const double lo = c->kt[s], hi = c->kt[s + 1];
+    const bool in = left ? (lo < t && t <= hi) : (lo <= t && t < hi);
+    if (in) {
+      for (int a = 0; a < 3; ++a) out[a] = (c->khe[3 * (s + 1) + a] - c->khe[3 * s + a]) / (hi - lo);
+      break;
+    }
+  }
+  if (c->sin_amp != 0) {
+    const bool in = left ? (c->sin_t0 < t && t <= c->sin_t1) : (c->sin_t0 <= t && t < c->sin_t1);
+    if (in) {
+      const double w = 2 * M_PI / c->sin_period;
+      const double v = c->sin_amp * w * cos(w * (t - c->sin_t0));
+      for (int a = 0; a < 3; ++a) out[a] += v * c->sin_dir[a];
+    }
+  }
+}
+
+template <typename T> scfft_status alloc_work(scfft_ctx* c) {
+  typedef typename cplx_of<T>::type V;
+  Work<T>& w = work<T>(c);
+  const Geo& g = c->g;
+  const long long N = g.N;
+  CK(cudaMalloc(&w.U, sizeof(V) * 3 * (size_t)g.nz * g.ny * g.sxu));
+  CK(cudaMalloc(&w.Pd, sizeof(V) * 3 * (size_t)g.nz * 2 * g.ny * g.sxp));
+  CK(cudaMalloc(&w.Hd[0], sizeof(T) * 3 * N));
+  CK(cudaMalloc(&w.Hd[1], sizeof(T) * 3 * N));
+  CK(cudaMalloc(&w.kap, sizeof(T) * 3 * (size_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1)));
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const double sig = c->opt.sigma_scale * 0.5 *
+                     sqrt(pow(2 * c->L[0] / g.nx, 2) + pow(2 * c->L[1] / g.ny, 2) + pow(2 * c->L[2] / g.nz, 2));
+  for (int a = 0; a < 3; ++a) {
+    // derivative wavenumbers k = pi m / L_a (period 2 L_a), 0 on the Nyquist entry; smoothing exp(-sigma^2 k^2/2)
+    const int len = a == 0 ? n[0] / 2 + 1 : n[a];
+    std::vector<T> kt(len), st(len);
+    for (int i = 0; i < len; ++i) {
+      const int m = (a == 0) ? i : (i < n[a] / 2 ? i : i - n[a]);
+      const double k = M_PI * m / c->L[a];
+      kt[i] = (i == n[a] / 2) ? (T)0 : (T)k;
+      st[i] = (T)exp(-0.5 * sig * sig * k * k);
+    }
+    CK(cudaMalloc(&w.kt[a], sizeof(T) * len));
+    CK(cudaMalloc(&w.st[a], sizeof(T) * len));
+    CK(cudaMemcpy(w.kt[a], kt.data(), sizeof(T) * len, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(w.st[a], st.data(), sizeof(T) * len, cudaMemcpyHostToDevice));
+    for (int pad = 0; pad < 2; ++pad) {
+      const int Lt = pad ? 2 * n[a] : n[a];
+      std::vector<V> tw(Lt);
+      for (int m = 0; m < Lt; ++m) {
+        const long double ang = 2.0L * 3.14159265358979323846264338327950288L * m / Lt;
+        V v;
+        v.x = (T)cosl(ang);
+        v.y = (T)(-sinl(ang));
+        tw[m] = v;
+      }
+      V** dst = pad ? &w.twp[a] : &w.twu[a];
+      CK(cudaMalloc(dst, sizeof(V) * Lt));
+      CK(cudaMemcpy(*dst, tw.data(), sizeof(V) * Lt, cudaMemcpyHostToDevice));
+    }
+  }
+  return SCFFT_OK;
+}
+
+template <typename T> void free_work(Work<T>& w) {
+  cudaFree(w.U); cudaFree(w.Pd); cudaFree(w.Hd[0]); cudaFree(w.Hd[1]); cudaFree(w.jc); cudaFree(w.kap);
+  for (int a = 0; a < 3; ++a) { cudaFree(w.kt[a]); cudaFree(w.st[a]); cudaFree(w.twu[a]); cudaFree(w.twp[a]); }
+  w = Work<T>();
+}
+
+PointParams base_params(const scfft_ctx* c) {
+  PointParams pp{};
+  pp.n = c->mat.n;
+  pp.e0 = c->mat.e0;
+  pp.jc = c->mat.jc;
+  pp.rho_out = c->mat.rho_out;
+  pp.inv_mu0 = 1.0 / c->mat.mu0;
+  pp.inv_nout = c->nout > 0 ? 1.0 / (double)c->nout : 0.0;
+  pp.max_iter = c->opt.max_iter;
+  return pp;
+}
+
+// Spectral curl of the half spectrum held in U: y fwd, z (fwd, curl, inv), y inv.
+template <typename T> cudaError_t curl_in_U(const Launch<T>& L, bool check_done) {
+  cudaError_t e;
+  if ((e = launch_y<T>(L, false, false, check_done)) != cudaSuccess) return e;
+  if ((e = launch_z_curl<T>(L, check_done, 1.0 / (double)L.g.N)) != cudaSuccess) return e;
+  return launch_y<T>(L, false, true, check_done);
+}
+
+// One iteration of Eq. 5 (i-th): U holds R2C_x of dh^i on entry and of dh^{i+1} on exit.
+template <typename T> cudaError_t iteration(const Launch<T>& L, PointParams pp, int i, bool check_done) {
+  cudaError_t e;
+  if ((e = curl_in_U<T>(L, check_done)) != cudaSuccess) return e;
+  if ((e = launch_x<T>(L, X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, check_done)) != cudaSuccess) return e;
+  if ((e = launch_y<T>(L, true, false, check_done)) != cudaSuccess) return e;
+  if ((e = launch_z_kernel<T>(L, check_done)) != cudaSuccess) return e;
+  if ((e = launch_y<T>(L, true, true, check_done)) != cudaSuccess) return e;
+  pp.iter = i;
+  return launch_x<T>(L, X_UPDATE, pp, nullptr, nullptr, nullptr, i & 1, (i + 1) & 1, check_done);
+}
+
+template <typename T>
+scfft_status rhs_impl(scfft_ctx* c, double t, int left, const double* h, double* warm, double* hdot, int* iters_out) {
+  Launch<T> L = launch_of<T>(c);
+  PointParams pp = base_params(c);
+  hedot_at(c, t, left, pp.hedot);
+  const double hn = sqrt(pp.hedot[0] * pp.hedot[0] + pp.hedot[1] * pp.hedot[1] + pp.hedot[2] * pp.hedot[2]);
+  pp.tol = c->opt.delta_it * (hn > 1.0 ? hn : 1.0);
+  // pre-stage: j = curl h; e = rho(j) j; dh^0 = -curl e / mu0 on Omega, warm on Omega_out
+  CK(launch_x<T>(L, X_FWD_F64, pp, h, nullptr, nullptr, 0, 0, false));
+  CK(curl_in_U<T>(L, false));
+  CK(launch_x<T>(L, X_POWERLAW, pp, nullptr, nullptr, nullptr, 0, 0, false));
+  CK(curl_in_U<T>(L, false));
+  CK(launch_x<T>(L, X_ASSEMBLE, pp, nullptr, nullptr, warm, 0, 0, false));
+  const int maxit = c->opt.max_iter;
+  const bool early = c->opt.delta_it > 0 && c->nout > 0;
+  int launched = 0;
+  if (c->nout > 0) {
+    // With an early stop the host keeps one iteration queued ahead: before
+    // queueing iteration i it waits for the flag copied after iteration i-2.
+    // An iteration queued after convergence returns at entry (device flag), so
+    // at most one iteration of launches is wasted.
+    for (int i = 0; i < maxit; ++i) {
+      if (early && i >= 2) {
+        CK(cudaEventSynchronize(c->ev[i & 1]));
+        if (c->hctrl[i & 1].done) break;
+      }
+      CK(iteration<T>(L, pp, i, early));
+      ++launched;
+      if (early) {
+        CK(cudaMemcpyAsync(&c->hctrl[i & 1], c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaEventRecord(c->ev[i & 1], c->st));
+      }
+    }
+  }
+  CK(launch_finalize<T>(L, hdot, warm));
+  c->stats.rhs_calls += 1;
+  if (iters_out || early) {
+    Ctrl hc;
+    CK(cudaMemcpyAsync(c->hctrl + 2, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    hc = c->hctrl[2];
+    c->stats.iterations += hc.iters;
+    c->stats.last_iters = hc.iters;
+    c->stats.last_residual = hc.residual;
+    if (iters_out) *iters_out = hc.iters;
+    if (hc.status != 0) return (scfft_status)hc.status;
+    if (iters_out && c->nout > 0 && maxit > 0 && !(hc.residual < pp.tol) && c->opt.delta_it > 0)
+      return SCFFT_ENOCONV;
+  } else {
+    c->stats.iterations += launched;
+    c->stats.last_iters = launched;
+  }
+  return SCFFT_OK;
+}
+
+template <typename T> scfft_status curl_impl(scfft_ctx* c, const double* f, double* out) {
+  Launch<T> L = launch_of<T>(c);
+  PointParams pp = base_params(c);
+  CK(launch_x<T>(L, X_FWD_F64, pp, f, nullptr, nullptr, 0, 0, false));
+  CK(curl_in_U<T>(L, false));
+  CK(launch_x<T>(L, X_TO_F64, pp, nullptr, out, nullptr, 0, 0, false));
+  return SCFFT_OK;
+}
+
+template <typename T> scfft_status phi_impl(scfft_ctx* c, const double* j, double* out) {
+  Launch<T> L = launch_of<T>(c);
+  PointParams pp = base_params(c);
+  CK(launch_x<T>(L, X_PAD_F64, pp, j, nullptr, nullptr, 0, 0, false));
+  CK(launch_y<T>(L, true, false, false));
+  CK(launch_z_kernel<T>(L, false));
+  CK(launch_y<T>(L, true, true, false));
+  CK(launch_x<T>(L, X_CROP_F64, pp, nullptr, out, nullptr, 0, 0, false));
+  return SCFFT_OK;
+}
+
+// ---------------------------------------------------------------- BS23 kernels (FP64 state)
+__global__ void combine_kernel(double* __restrict__ out, const double* __restrict__ y, double h, double c1,
+                               const double* __restrict__ k1, double c2, const double* __restrict__ k2, double c3,
+                               const double* __restrict__ k3, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double s = c1 * k1[i];
+    if (k2) s += c2 * k2[i];
+    if (k3) s += c3 * k3[i];
+    out[i] = y[i] + h * s;
+  }
+}
+
+// err_i = h (e1 k1 + e2 k2 + e3 k3 + e4 k4); norm = max_i |err_i| / max(rtol|y|, rtol|ynew|, atol)
+__global__ void errnorm_kernel(const double* __restrict__ y, const double* __restrict__ yn, double h, double e1,
+                               const double* __restrict__ k1, double e2, const double* __restrict__ k2, double e3,
+                               const double* __restrict__ k3, double e4, const double* __restrict__ k4, double rtol,
+                               double atol, long long n, unsigned long long* out) {
+  double m = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double e = h * (e1 * k1[i] + e2 * k2[i] + e3 * k3[i] + e4 * k4[i]);
+    const double w = fmax(fmax(rtol * fabs(y[i]), rtol * fabs(yn[i])), atol);
+    const double r = fabs(e) / w;
+    m = (r > m || r != r) ? r : m;  // NaN propagates
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double q = __shfl_xor_sync(0xffffffffu, m, o);
+    m = (q > m || q != q) ? q : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void fill3_kernel(double* __restrict__ g, double a, double b, double c, long long N) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    g[i] = a; g[N + i] = b; g[2 * N + i] = c;
+  }
+}
+
+int blocks_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)std::min<long long>(std::max<long long>(b, 1), 152 * 8);
+}
+
+scfft_status rhs_any(scfft_ctx* c, double t, int left, const double* h, double* warm, double* hdot, int* it) {
+  return c->opt.precision == SCFFT_PREC_F32 ? rhs_impl<float>(c, t, left, h, warm, hdot, it)
+                                            : rhs_impl<double>(c, t, left, h, warm, hdot, it);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* scfft_status_string(scfft_status s) {
+  switch (s) {
+    case SCFFT_OK: return "ok";
+    case SCFFT_EINVAL: return "invalid argument";
+    case SCFFT_ENOMEM: return "out of memory";
+    case SCFFT_ECUDA: return "CUDA runtime error";
+    case SCFFT_ENOCONV: return "Eq. 5 iteration hit max_iter";
+    case SCFFT_ESTEP: return "step size underflow";
+    case SCFFT_ENONFINITE: return "non-finite value in a residual or error norm";
+    case SCFFT_ETIMEOUT: return "bounded device wait timed out";
+    case SCFFT_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+scfft_status scfft_create(const scfft_grid* grid, const scfft_material* mat, const scfft_options* opt, void* stream,
+                          scfft_ctx** out) {
+  if (!grid || !mat || !opt || !out) return SCFFT_EINVAL;
+  *out = nullptr;
+  if (!grid_ok(grid->nx) || !grid_ok(grid->ny) || !grid_ok(grid->nz)) return SCFFT_EINVAL;
+  if (!(grid->Lx > 0) || !(grid->Ly > 0) || !(grid->Lz > 0)) return SCFFT_EINVAL;
+  if (!(mat->n >= 1) || !(mat->e0 > 0) || !(mat->jc > 0) || !(mat->rho_out >= 0) || !(mat->mu0 > 0))
+    return SCFFT_EINVAL;
+  if (opt->max_iter < 0 || !(opt->delta_it >= 0) || !(opt->sigma_scale >= 0)) return SCFFT_EINVAL;
+  if (opt->precision != SCFFT_PREC_F64 && opt->precision != SCFFT_PREC_F32) return SCFFT_EINVAL;
+  scfft_ctx* c = new (std::nothrow) scfft_ctx();
+  if (!c) return SCFFT_ENOMEM;
+  c->g.nx = grid->nx; c->g.ny = grid->ny; c->g.nz = grid->nz;
+  c->g.sxu = round_up(grid->nx / 2 + 1, 8);
+  c->g.sxp = round_up(grid->nx + 1, 8);
+  c->g.N = (long long)grid->nx * grid->ny * grid->nz;
+  c->L[0] = grid->Lx; c->L[1] = grid->Ly; c->L[2] = grid->Lz;
+  c->mat = *mat;
+  c->opt = *opt;
+  c->st = (cudaStream_t)stream;
+  scfft_status s = SCFFT_OK;
+  if (cudaMalloc(&c->ctrl, sizeof(Ctrl)) != cudaSuccess ||
+      cudaMalloc(&c->partials, sizeof(double) * (c->g.ny * c->g.nz / 2 + 8)) != cudaSuccess ||
+      cudaMalloc(&c->mask, c->g.N) != cudaSuccess || cudaHostAlloc(&c->hctrl, 3 * sizeof(Ctrl), 0) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev[1], cudaEventDisableTiming) != cudaSuccess ||
+      cudaMalloc(&c->errbits, sizeof(unsigned long long)) != cudaSuccess ||
+      cudaHostAlloc(&c->herr, sizeof(unsigned long long), 0) != cudaSuccess) {
+    s = SCFFT_ENOMEM;
+  }
+  if (s == SCFFT_OK) s = (opt->precision == SCFFT_PREC_F32) ? alloc_work<float>(c) : alloc_work<double>(c);
+  if (s == SCFFT_OK && cudaMemset(c->ctrl, 0, sizeof(Ctrl)) != cudaSuccess) s = SCFFT_ECUDA;
+  if (s != SCFFT_OK) {
+    scfft_destroy(c);
+    return s == SCFFT_ECUDA ? SCFFT_ENOMEM : s;
+  }
+  memset(c->hctrl, 0, 3 * sizeof(Ctrl));
+  *out = c;
+  return SCFFT_OK;
+}
+
+void scfft_destroy(scfft_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  else cudaDeviceSynchronize();
+  free_work(c->wf);
+  free_work(c->wd);
+  cudaFree(c->ctrl); cudaFree(c->partials); cudaFree(c->mask); cudaFree(c->ib); cudaFree(c->errbits);
+  if (c->hctrl) cudaFreeHost(c->hctrl);
+  if (c->herr) cudaFreeHost(c->herr);
+  for (int i = 0; i < 2; ++i) if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  delete c;
+}
+
+scfft_status scfft_set_geometry(scfft_ctx* c, const uint8_t* mask) {
+  if (!c || !mask) return SCFFT_EINVAL;
+  const Geo& g = c->g;
+  long long nin = 0;
+  for (int z = 0; z < g.nz; ++z)
+    for (int y = 0; y < g.ny; ++y)
+      for (int x = 0; x < g.nx; ++x) {
+        if (!mask[((long long)z * g.ny + y) * g.nx + x]) continue;
+        ++nin;
+        if (x < 2 || y < 2 || z < 2 || x >= g.nx - 2 || y >= g.ny - 2 || z >= g.nz - 2) return SCFFT_EINVAL;
+      }
+  if (nin == 0) return SCFFT_EINVAL;
+  std::vector<uint8_t> m(mask, mask + g.N);
+  for (auto& v : m) v = v ? 1 : 0;
+  CK(cudaMemcpy(c->mask, m.data(), g.N, cudaMemcpyHostToDevice));
+  c->nout = g.N - nin;
+  c->have_geom = true;
+  return SCFFT_OK;
+}
+
+scfft_status scfft_set_jc_map(scfft_ctx* c, const double* jc) {
+  if (!c) return SCFFT_EINVAL;
+  const long long N = c->g.N;
+  if (c->opt.precision == SCFFT_PREC_F32) {
+    cudaFree(c->wf.jc);
+    c->wf.jc = nullptr;
+    if (jc) {
+      CK(cudaMalloc(&c->wf.jc, sizeof(float) * N));
+      CK(launch_convert<float>(jc, c->wf.jc, N, c->st));
+    }
+  } else {
+    cudaFree(c->wd.jc);
+    c->wd.jc = nullptr;
+    if (jc) {
+      CK(cudaMalloc(&c->wd.jc, sizeof(double) * N));
+      CK(launch_convert<double>(jc, c->wd.jc, N, c->st));
+    }
+  }
+  return SCFFT_OK;
+}
+
+scfft_status scfft_set_field_path(scfft_ctx* c, const scfft_field_path* p) {
+  if (!c || !p || p->nknots < 1 || p->nknots > 64 || !p->t || !p->he) return SCFFT_EINVAL;
+  for (int k = 0; k + 1 < p->nknots; ++k)
+    if (!(p->t[k + 1] > p->t[k])) return SCFFT_EINVAL;
+  if (p->sin_amp != 0 && (!(p->sin_period > 0) || !(p->sin_t1 >= p->sin_t0))) return SCFFT_EINVAL;
+  c->kt.assign(p->t, p->t + p->nknots);
+  c->khe.assign(p->he, p->he + 3 * p->nknots);
+  c->sin_amp = p->sin_amp;
+  c->sin_period = p->sin_period;
+  c->sin_t0 = p->sin_t0;
+  c->sin_t1 = p->sin_t1;
+  for (int a = 0; a < 3; ++a) c->sin_dir[a] = p->sin_dir[a];
+  c->have_path = true;
+  return SCFFT_OK;
+}
+
+scfft_status scfft_precompute_kernel(scfft_ctx* c) {
+  if (!c) return SCFFT_EINVAL;
+  const Geo& g = c->g;
+  const long long oct = (long long)(g.nx + 1) * (g.ny + 1) * (g.nz + 1);
+  double* scratch = nullptr;
+  if (cudaMalloc(&scratch, sizeof(double) * 6 * oct) != cudaSuccess) return SCFFT_ENOMEM;
+  const double dx = 2 * c->L[0] / g.nx, dy = 2 * c->L[1] / g.ny, dz = 2 * c->L[2] / g.nz;
+  const double sig = c->opt.sigma_scale * 0.5 * sqrt(dx * dx + dy * dy + dz * dz);
+  cudaError_t e = (c->opt.precision == SCFFT_PREC_F32)
+                      ? launch_kernel_spectrum<float>(launch_of<float>(c), c->L[0], c->L[1], c->L[2], sig, scratch)
+                      : launch_kernel_spectrum<double>(launch_of<double>(c), c->L[0], c->L[1], c->L[2], sig, scratch);
+  cudaError_t e2 = cudaStreamSynchronize(c->st);
+  cudaFree(scratch);
+  if (e != cudaSuccess || e2 != cudaSuccess) return SCFFT_ECUDA;
+  c->have_kernel = true;
+  return SCFFT_OK;
+}
+
+scfft_status scfft_rhs(scfft_ctx* c, double t, int left, const double* h, double* warm, double* hdot, int* iters_out) {
+  if (!c || !h || !warm || !hdot || hdot == h) return SCFFT_EINVAL;
+  if (!c->have_geom || !c->have_kernel || !c->have_path) return SCFFT_ESTATE;
+  return rhs_any(c, t, left, h, warm, hdot, iters_out);
+}
+
+scfft_status scfft_curl(scfft_ctx* c, const double* f, double* out) {
+  if (!c || !f || !out || f == out) return SCFFT_EINVAL;
+  return c->opt.precision == SCFFT_PREC_F32 ? curl_impl<float>(c, f, out) : curl_impl<double>(c, f, out);
+}
+
+scfft_status scfft_phi(scfft_ctx* c, const double* j, double* out) {
+  if (!c || !j || !out || j == out) return SCFFT_EINVAL;
+  if (!c->have_kernel) return SCFFT_ESTATE;
+  return c->opt.precision == SCFFT_PREC_F32 ? phi_impl<float>(c, j, out) : phi_impl<double>(c, j, out);
+}
+
+scfft_status scfft_integrate(scfft_ctx* c, double t0, double t1, double dt0, int nsnap, const double* tsnap, double* h,
+                             double* snaps, double* warm, const double* dt_fixed, int nfixed, scfft_stats* stats) {
+  if (!c || !h || !(t1 > t0) || !(dt0 > 0) || nsnap < 0 || (nsnap > 0 && (!tsnap || !snaps))) return SCFFT_EINVAL;
+  if (dt_fixed && nfixed <= 0) return SCFFT_EINVAL;
+  for (int i = 0; i < nsnap; ++i)
+    if (!(tsnap[i] > t0 && tsnap[i] <= t1) || (i > 0 && !(tsnap[i] > tsnap[i - 1]))) return SCFFT_EINVAL;
+  if (!c->have_geom || !c->have_kernel || !c->have_path) return SCFFT_ESTATE;
+  const long long n3 = 3 * c->g.N;
+  if (!c->ib) CK(cudaMalloc(&c->ib, sizeof(double) * 7 * n3));
+  double* ynew = c->ib;
+  double* k[4] = {c->ib + n3, c->ib + 2 * n3, c->ib + 3 * n3, c->ib + 4 * n3};
+  double* ytmp = c->ib + 5 * n3;
+  double* g = warm ? warm : c->ib + 6 * n3;
+  if (!warm) {
+    double hd[3];
+    hedot_at(c, t0, 0, hd);
+    fill3_kernel<<<blocks_for(c->g.N), 256, 0, c->st>>>(g, hd[0], hd[1], hd[2], c->g.N);
+    CK(cudaGetLastError());
+  }
+  // stops: kinks of the path, snapshot times and t1, inside (t0, t1]
+  std::vector<double> kinks(c->kt.begin(), c->kt.end());
+  if (c->sin_amp != 0) { kinks.push_back(c->sin_t0); kinks.push_back(c->sin_t1); }
+  std::vector<double> stops;
+  for (double v : kinks) if (v > t0 && v <= t1) stops.push_back(v);
+  for (int i = 0; i < nsnap; ++i) stops.push_back(tsnap[i]);
+  stops.push_back(t1);
+  std::sort(stops.begin(), stops.end());
+  stops.erase(std::unique(stops.begin(), stops.end()), stops.end());
+  auto is_kink = [&](double v) { return std::find(kinks.begin(), kinks.end(), v) != kinks.end(); };
+  // Bogacki-Shampine 3(2): c = (0, 1/2, 3/4, 1); a21 = 1/2; a32 = 3/4; b = (2/9, 1/3, 4/9);
+  // e = b - bhat = (-5/72, 1/12, 1/9, -1/8)
+  const double a21 = 0.5, a32 = 0.75, b1 = 2.0 / 9.0, b2 = 1.0 / 3.0, b3 = 4.0 / 9.0;
+  const double e1 = 2.0 / 9.0 - 7.0 / 24.0, e2 = 1.0 / 3.0 - 0.25, e3 = 4.0 / 9.0 - 1.0 / 3.0, e4 = -0.125;
+  const double rtol = c->opt.rtol, atol = c->opt.atol;
+  scfft_status s;
+  double t = t0, dt = dt0;
+  if ((s = rhs_any(c, t, 0, h, g, k[0], nullptr)) != SCFFT_OK) return s;
+  size_t si = 0;
+  int snap_i = 0;
+  long long acc = 0, rej = 0;
+  const int blocks = blocks_for(n3);
+  while (t < t1) {
+    while (si < stops.size() && stops[si] <= t) ++si;
+    const double nxt = si < stops.size() ? stops[si] : t1;
+    if (dt_fixed) {
+      if (acc >= nfixed) break;
+      dt = dt_fixed[acc];
+    }
+    double hs = std::min(dt, nxt - t);
+    const bool hits = (hs == nxt - t);
+    const bool end_left = hits && is_kink(nxt);
+    if (!(hs > 1e-14 * std::max(1.0, fabs(t)))) return SCFFT_ESTEP;
+    combine_kernel<<<blocks, 256, 0, c->st>>>(ytmp, h, hs, a21, k[0], 0, nullptr, 0, nullptr, n3);
+    if ((s = rhs_any(c, t + 0.5 * hs, 0, ytmp, g, k[1], nullptr)) != SCFFT_OK) return s;
+    combine_kernel<<<blocks, 256, 0, c->st>>>(ytmp, h, hs, 0.0, k[0], a32, k[1], 0, nullptr, n3);
+    if ((s = rhs_any(c, t + 0.75 * hs, 0, ytmp, g, k[2], nullptr)) != SCFFT_OK) return s;
+    combine_kernel<<<blocks, 256, 0, c->st>>>(ynew, h, hs, b1, k[0], b2, k[1], b3, k[2], n3);
+    if ((s = rhs_any(c, hits ? nxt : t + hs, end_left ? 1 : 0, ynew, g, k[3], nullptr)) != SCFFT_OK) return s;
+    double en = 0.0;
+    if (!dt_fixed) {
+      CK(cudaMemsetAsync(c->errbits, 0, sizeof(unsigned long long), c->st));
+      errnorm_kernel<<<blocks, 256, 0, c->st>>>(h, ynew, hs, e1, k[0], e2, k[1], e3, k[2], e4, k[3], rtol, atol, n3,
+                                               c->errbits);
+      CK(cudaMemcpyAsync(c->herr, c->errbits, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      unsigned long long bits = *c->herr;
+      memcpy(&en, &bits, sizeof(double));
+      if (!(en == en)) return SCFFT_ENONFINITE;
+    }
+    if (en <= 1.0) {
+      t = hits ? nxt : t + hs;
+      CK(cudaMemcpyAsync(h, ynew, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->st));
+      ++acc;
+      if (end_left) {
+        if ((s = rhs_any(c, t, 0, h, g, k[0], nullptr)) != SCFFT_OK) return s;
+      } else {
+        std::swap(k[0], k[3]);
+      }
+      if (hits && snap_i < nsnap && tsnap[snap_i] == nxt) {
+        CK(cudaMemcpyAsync(snaps + (size_t)snap_i * n3, h, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->st));
+        ++snap_i;
+      }
+      if (!dt_fixed) {
+        const double fac = en == 0.0 ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * pow(en, -1.0 / 3.0)));
+        dt = hs * fac;
+      }
+    } else {
+      ++rej;
+      dt = hs * std::max(0.2, 0.9 * pow(en, -1.0 / 3.0));
+    }
+  }
+  CK(cudaStreamSynchronize(c->st));
+  c->stats.accepted += acc;
+  c->stats.rejected += rej;
+  c->stats.t = t;
+  c->stats.dt = dt;
+  if (stats) {
+    *stats = c->stats;
+    stats->accepted = acc;
+    stats->rejected = rej;
+  }
+  return SCFFT_OK;
+}
+
+scfft_status scfft_sync(scfft_ctx* c) {
+  if (!c) return SCFFT_EINVAL;
+  CK(cudaStreamSynchronize(c->st));
+  CK(cudaMemcpy(c->hctrl + 2, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+  return (scfft_status)c->hctrl[2].status;
+}
+
+scfft_status scfft_get_stats(scfft_ctx* c, scfft_stats* out) {
+  if (!c || !out) return SCFFT_EINVAL;
+  *out = c->stats;
+  return SCFFT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// scfft_internal.cuh - device workspaces, control block and pass launchers
+// shared by the translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_core.cuh"
+
+namespace scfft {
+
+constexpr int kThreads = 256;  // every FFT pass kernel runs 256-thread CTAs
+
+// Device-side control block of one context (one rhs at a time per context).
+struct Ctrl {
+  int done;           // Eq. 5 stop reached: loop kernels of later iterations return at entry
+  int iters;          // iterations executed in the current rhs
+  int cur;            // which iterate buffer (0/1) holds the latest dh/dt
+  int status;         // latched device status (scfft_status value)
+  unsigned counter;   // arrival counter of the last-CTA reduction
+  unsigned pad_;
+  double residual;    // last Eq. 5 residual
+  double err;         // last integrator error norm
+  unsigned counter2;  // arrival counter of the error-norm reduction
+  unsigned pad2_;
+};
+
+// Grid geometry and strides.
+struct Geo {
+  int nx, ny, nz;
+  int sxu;        // row stride (complex) of the unpadded half spectrum, >= nx/2+1
+  int sxp;        // row stride of the padded half spectrum, >= nx+1
+  long long N;    // nx*ny*nz
+};
+
+// Device workspaces of one FFT precision T.
+template <typename T>
+struct Work {
+  typedef typename cplx_of<T>::type V;
+  V* U = nullptr;        // [3][nz][ny][sxu]  unpadded half spectrum
+  V* Pd = nullptr;       // [3][nz][2ny][sxp] padded half spectrum, z pruned to nz planes
+  T* Hd[2] = {nullptr, nullptr};  // [3][N] iterates dh^i of Eq. 5
+  T* jc = nullptr;       // [N] jc map or nullptr (uniform)
+  T* kap = nullptr;      // [3][nz+1][ny+1][nx+1] imaginary part of the kernel spectrum / (8N)
+  T* kt[3] = {nullptr, nullptr, nullptr};  // derivative wavenumbers (0 on Nyquist): nx/2+1, ny, nz
+  T* st[3] = {nullptr, nullptr, nullptr};  // Gaussian smoothing factor per axis: nx/2+1, ny, nz
+  V* twu[3] = {nullptr, nullptr, nullptr}; // twiddles W_L^m, L = nx, ny, nz
+  V* twp[3] = {nullptr, nullptr, nullptr}; // twiddles, L = 2nx, 2ny, 2nz
+};
+
+enum XMode : int {
+  X_FWD_F64 = 0,  // real f64 rows -> R2C(nx) -> U
+  X_POWERLAW = 1, // U -> C2R(nx) -> e(j) (Eq. 1 / rho_out) -> R2C(nx) -> U
+  X_ASSEMBLE = 2, // U -> C2R(nx) -> dh^0 = -c/mu0 on Omega, warm on Omega_out -> Hd[0]; R2C(nx) -> U
+  X_MASKPAD = 3,  // U -> C2R(nx) -> chi_Omega * (.) , zero pad -> R2C(2nx) -> Pd
+  X_UPDATE = 4,   // Pd -> C2R(2nx), crop -> Eq. 5 update + residual -> Hd[next]; R2C(nx) -> U
+  X_TO_F64 = 5,   // U -> C2R(nx) -> real f64 rows
+  X_PAD_F64 = 6,  // real f64 rows -> zero pad -> R2C(2nx) -> Pd
+  X_CROP_F64 = 7  // Pd -> C2R(2nx), crop -> real f64 rows
+};
+
+// Scalars of the material law and the Eq. 5 update.
+struct PointParams {
+  double n;           // power-law exponent
+  double e0;          // e0
+  double jc;          // uniform jc (used when the map is absent)
+  double rho_out;     // Omega_out resistivity
+  double inv_mu0;     // 1/mu0
+  double hedot[3];    // dh_e/dt at the rhs time
+  double tol;         // Eq. 5 stop threshold delta_it * max(|dh_e/dt|, 1)
+  double inv_nout;    // 1 / |Omega_out|
+  int iter;           // iteration index i (X_UPDATE)
+  int max_iter;
+};
+
+template <typename T>
+struct Launch {
+  Geo g;
+  Work<T>* w;          // host copy of the workspace pointers
+  Ctrl* ctrl;          // device
+  const uint8_t* mask; // device [N]
+  double* partials;    // device, one double per CTA of the x passes
+  cudaStream_t st;
+};
+
+// Pass launchers (defined in passes.cu, instantiated for float and double).
+template <typename T> cudaError_t launch_x(const Launch<T>& L, XMode mode, const PointParams& pp,
+                                           const double* src_f64, double* dst_f64, const double* warm,
+                                           int in_buf, int out_buf, bool check_done);
+template <typename T> cudaError_t launch_y(const Launch<T>& L, bool padded, bool inverse, bool check_done);
+template <typename T> cudaError_t launch_z_curl(const Launch<T>& L, bool check_done, double scale);
+template <typename T> cudaError_t launch_z_kernel(const Launch<T>& L, bool check_done);
+template <typename T> cudaError_t launch_finalize(const Launch<T>& L, double* hdot, double* warm);
+template <typename T> cudaError_t launch_kernel_spectrum(const Launch<T>& L, double Lx, double Ly, double Lz,
+                                                         double sigma, double* scratch);
+template <typename T> cudaError_t launch_convert(const double* src, T* dst, long long n, cudaStream_t st);
+
+FftPlan make_plan(int L);
+bool length_supported(int L);
+
+}  // namespace scfft

@@ -1,0 +1,145 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs, element by element.
+
+Tolerances (relative to the largest oracle magnitude of each field):
+  FP64 path      <= 1e-10 (every stage is a sum of at most ~1e3 rounded terms)
+  FP32 path      stated per field in the tests below (FP32 FFT round-off
+                 ~1e-6 amplified by the power law's exponent n).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import scfft_inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1803_01346_gb300 as S  # noqa: E402
+from paper_1803_01346_gb300 import build as B  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def make(n, L, mask, n_power=20.0, rho_out=20.0, prec=S.PREC_F64, delta_it=0.0, max_iter=3, path=None,
+         jc_map=None, sigma_scale=1.0, rtol=2e-4, atol=1e-6):
+    ctx = S.Context(n, L, n_power=n_power, rho_out=rho_out, precision=prec, delta_it=delta_it,
+                    max_iter=max_iter, sigma_scale=sigma_scale, rtol=rtol, atol=atol)
+    ctx.set_geometry(mask)
+    t, he = path if path is not None else ([0.0, 1.0], [[0, 0, 0], [0.3, -0.2, 0.9]])
+    ctx.set_field_path(t, he)
+    if jc_map is not None:
+        ctx.set_jc_map(dev(jc_map))
+    ctx.precompute_kernel()
+    g = O.Grid(tuple(n), tuple(L), sigma_scale=sigma_scale)
+    prob = O.Problem(g, mask.astype(bool), O.Material(n=n_power, rho_out=rho_out,
+                                                      jc=1.0 if jc_map is None else jc_map),
+                     O.FieldPath(t, he))
+    return ctx, prob
+
+
+GRIDS = [((16, 16, 16), (1.0, 1.0, 1.0)),
+         ((48, 32, 16), (1.2, 0.9, 0.8)),     # ragged column tiles (25 and 17 spectral columns)
+         ((32, 16, 96), (0.8, 0.5, 2.0))]
+
+
+@pytest.mark.parametrize("n,L", GRIDS)
+def test_curl_fp64_matches_oracle(n, L):
+    g = O.Grid(n, L)
+    f = I.random_field((3,) + g.shape, 7)
+    ctx = S.Context(n, L)
+    out = torch.empty(3 * g.shape[0] * g.shape[1] * g.shape[2], dtype=torch.float64, device="cuda")
+    ctx.curl(dev(f).reshape(-1), out)
+    assert rel(host(out).reshape(f.shape), O.curl_s(f, g)) < 1e-12
+
+
+@pytest.mark.parametrize("n,L", GRIDS)
+def test_phi_fp64_matches_oracle(n, L):
+    g = O.Grid(n, L)
+    j = I.random_field((3,) + g.shape, 8)
+    ctx = S.Context(n, L)
+    ctx.precompute_kernel()
+    out = torch.empty(j.size, dtype=torch.float64, device="cuda")
+    ctx.phi(dev(j).reshape(-1), out)
+    assert rel(host(out).reshape(j.shape), O.phi_hockney(j, g)) < 1e-12
+
+
+def test_phi_fp64_matches_direct_sum():
+    n, L = (16, 16, 16), (1.0, 1.1, 0.9)
+    g = O.Grid(n, L)
+    j = I.random_field((3,) + g.shape, 9)
+    ctx = S.Context(n, L)
+    ctx.precompute_kernel()
+    out = torch.empty(j.size, dtype=torch.float64, device="cuda")
+    ctx.phi(dev(j).reshape(-1), out)
+    assert rel(host(out).reshape(j.shape), O.phi_direct(j, g)) < 1e-12
+
+
+def _state(prob, seed):
+    """A smooth, nonzero field: h_e plus the field of a random current in Omega."""
+    g = prob.grid
+    j = O.curl_s(I.random_field((3,) + g.shape, seed, 0.3), g) * prob.mask[None]
+    return O.phi_hockney(j, g) + np.array([0.05, -0.02, 0.1])[:, None, None, None]
+
+
+@pytest.mark.parametrize("n,L", GRIDS)
+def test_rhs_fp64_fixed_iterations_matches_oracle(n, L):
+    mask = I.cube(n, L, 0.6 * min(L) * 2)
+    ctx, prob = make(n, L, mask, max_iter=3)
+    h = _state(prob, 3)
+    g0 = I.random_field(h.shape, 4, 0.1)
+    ref = O.rhs(prob, 0.4, h, g0, delta_it=0.0, max_iter=3)
+    hd = torch.empty(h.size, dtype=torch.float64, device="cuda")
+    warm = dev(g0).reshape(-1)
+    it = ctx.rhs(0.4, dev(h).reshape(-1), warm, hd)
+    assert it == 3
+    assert rel(host(hd).reshape(h.shape), ref.hdot) < 1e-10
+    assert rel(host(warm).reshape(h.shape), ref.hdot) < 1e-10
+
+
+def test_rhs_fp64_early_stop_and_jc_map():
+    n, L = (32, 32, 32), (1.0, 1.0, 1.0)
+    mask = I.lens(n, L, 0.6, 0.5, 0.1, 0.1)
+    jc = I.jc_noise((32, 32, 32), 5)
+    ctx, prob = make(n, L, mask, n_power=30.0, rho_out=100.0, delta_it=2e-5, max_iter=50, jc_map=jc)
+    h = _state(prob, 6)
+    g0 = np.broadcast_to(prob.path.hedot(0.2)[:, None, None, None], h.shape).copy()
+    ref = O.rhs(prob, 0.2, h, g0, delta_it=2e-5, max_iter=50)
+    hd = torch.empty(h.size, dtype=torch.float64, device="cuda")
+    it = ctx.rhs(0.2, dev(h).reshape(-1), dev(g0).reshape(-1), hd)
+    assert it == ref.iters
+    assert rel(host(hd).reshape(h.shape), ref.hdot) < 1e-10
+
+
+def test_rhs_fp32_error_is_stated():
+    n, L = (32, 32, 32), (1.0, 1.0, 1.0)
+    mask = I.sphere(n, L, 0.6)
+    ctx, prob = make(n, L, mask, n_power=25.0, prec=S.PREC_F32, max_iter=3)
+    h = _state(prob, 11)
+    g0 = I.random_field(h.shape, 12, 0.1)
+    ref = O.rhs(prob, 0.4, h, g0, delta_it=0.0, max_iter=3)
+    hd = torch.empty(h.size, dtype=torch.float64, device="cuda")
+    ctx.rhs(0.4, dev(h).reshape(-1), dev(g0).reshape(-1), hd)
+    err = rel(host(hd).reshape(h.shape), ref.hdot)
+    assert err < 2e-4, err
