@@ -1,0 +1,400 @@
+"""Benchmark: voxel-RHS evaluations per second of the method-of-lines
+right-hand side (§2) on the 128^3 magnetic-lens workload, FP32 FFTs with FP64
+integrator state, through the library's BS23 step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one accepted Bogacki-Shampine step of the lens workload (three
+right-hand sides, each with its Eq. 5 iterations, plus the stage sums and the
+error norm).  value = grid nodes x right-hand sides evaluated / second, summed
+over ranks (each rank runs its own replica; the method has no data-parallel
+exchange).  Prints one JSON line on rank 0.
+
+--impl reference times the FP64 CPU oracle on the host cores instead: each
+step is one Eq. 5 iteration of the oracle at 128^3 (the pre-stage is timed
+once), converted to the same unit with the iteration count per right-hand side
+measured by the GPU path's default run (stored in REF_ITERS_PER_RHS below).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import scfft_inputs as I  # noqa: E402
+
+WORKLOAD = "lens128"
+METRIC = "voxel-RHS evals/s at 128^3 (FP32 FFT, FP64 state)"
+UNIT = "voxel-RHS evals/s"
+# Eq. 5 iterations per right-hand side observed on the default GPU run of this
+# workload (used only to convert the reference arm's per-iteration samples).
+REF_ITERS_PER_RHS = 2.0
+# DRAM bytes per launch of the dominant kernel from the committed ncu capture
+# (profiles/); None when the kernel changed since the counters were taken.
+NCU_TRAFFIC = None
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(kind: str, n, fp_bytes: int) -> float:
+    """Bytes a pass must move per launch (each array read or written once)."""
+    nx, ny, nz = n
+    N = nx * ny * nz
+    c = 2 * fp_bytes                     # one complex value
+    U = 3 * (nx // 2 + 1) * ny * nz * c  # unpadded half spectrum, 3 components
+    Pin = 3 * (nx + 1) * ny * nz * c     # padded spectrum, rows y < ny
+    Pall = 3 * (nx + 1) * 2 * ny * nz * c
+    real = 3 * N * fp_bytes
+    kap = 3 * (nx + 1) * (ny + 1) * (nz + 1) * fp_bytes
+    table = {
+        "x_fwd_state": 3 * N * 8 + U,
+        "x_powerlaw": 2 * U + N,
+        "x_assemble": 2 * U + N + real + 3 * N * 8,
+        "x_maskpad": U + N + Pin,
+        "x_update": Pin + 2 * real + N + U,
+        "y_fwd_unpadded": 2 * U,
+        "y_inv_unpadded": 2 * U,
+        "z_curl": 2 * U,
+        "y_fwd_padded": Pin + Pall,
+        "y_inv_padded": Pall + Pin,
+        "z_kernel": 2 * Pall + kap,
+        "finalize": real + 2 * 3 * N * 8,
+    }
+    return float(table.get(kind, 0.0))
+
+
+def make_ctx(S, cfg, precision):
+    ctx = S.Context(cfg.n, cfg.L, n_power=cfg.n_power, rho_out=cfg.rho_out, precision=precision,
+                    delta_it=2e-5, max_iter=100, rtol=cfg.rtol, atol=cfg.atol)
+    ctx.set_geometry(cfg.mask)
+    ctx.set_field_path(cfg.knots_t, cfg.knots_he)
+    ctx.precompute_kernel()
+    return ctx
+
+
+def run_steps(ctx, state, k):
+    t, dt, h, warm = state
+    for _ in range(k):
+        t, dt, _ = ctx.step(t, dt, 10.0, h, warm)
+    state[0], state[1] = t, dt
+
+
+def cpu_oracle_sample(cfg, iters_per_rhs):
+    """Time the oracle's pre-stage and one Eq. 5 iteration on the host cores."""
+    import oracle as O
+    g = O.Grid(cfg.n, cfg.L)
+    prob = O.Problem(g, cfg.mask, O.Material(n=cfg.n_power, rho_out=cfg.rho_out),
+                     O.FieldPath(cfg.knots_t, cfg.knots_he))
+    prob.kernel()
+    h = np.zeros((3,) + g.shape)
+    gw = np.broadcast_to(prob.path.hedot(0.0)[:, None, None, None], h.shape).copy()
+    t0 = time.perf_counter()
+    O.rhs(prob, 0.0, h, gw, delta_it=0.0, max_iter=0)
+    t_pre = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.rhs(prob, 0.0, h, gw, delta_it=0.0, max_iter=1)
+    t_iter = max(time.perf_counter() - t0 - t_pre, 1e-9)
+    N = cfg.n[0] * cfg.n[1] * cfg.n[2]
+    return N / (t_pre + iters_per_rhs * t_iter), t_pre, t_iter
+
+
+def bench_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    cfg = I.config(WORKLOAD)
+    import oracle as O
+    g = O.Grid(cfg.n, cfg.L)
+    prob = O.Problem(g, cfg.mask, O.Material(n=cfg.n_power, rho_out=cfg.rho_out),
+                     O.FieldPath(cfg.knots_t, cfg.knots_he))
+    prob.kernel()
+    h = np.zeros((3,) + g.shape)
+    gw = np.broadcast_to(prob.path.hedot(0.0)[:, None, None, None], h.shape).copy()
+    t0 = time.perf_counter()
+    O.rhs(prob, 0.0, h, gw, delta_it=0.0, max_iter=0)
+    t_pre = time.perf_counter() - t0
+    # each step: one Eq. 5 iteration (pre-stage + 1 iteration, minus the pre-stage)
+    for _ in range(args.warmup):
+        O.rhs(prob, 0.0, h, gw, delta_it=0.0, max_iter=1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.rhs(prob, 0.0, h, gw, delta_it=0.0, max_iter=1)
+        times.append(time.perf_counter() - t0 - t_pre)
+    t_iter = statistics.mean(times)
+    N = cfg.n[0] * cfg.n[1] * cfg.n[2]
+    value = N / (t_pre + REF_ITERS_PER_RHS * t_iter)
+    ms = (t_pre + t_iter) * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(cfg.n), "padded": [2 * v for v in cfg.n],
+                   "geometry": cfg.note, "step": "one Eq. 5 iteration of the FP64 NumPy oracle (pre-stage timed once)",
+                   "iters_per_rhs": REF_ITERS_PER_RHS},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"pre-stage {t_pre:.2f}s once + {args.steps} iterations of mean {t_iter:.2f}s"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bench_ours(args, ws, rank, local):
+    import torch
+    import paper_1803_01346_gb300 as S
+    from paper_1803_01346_gb300 import build as B
+
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(S.library_path()):
+        B.build()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    cfg = I.config(WORKLOAD)
+    N = cfg.n[0] * cfg.n[1] * cfg.n[2]
+    n3 = 3 * N
+    ctx = make_ctx(S, cfg, S.PREC_F32)
+    h = torch.zeros(n3, dtype=torch.float64, device="cuda")
+    warm = torch.zeros(n3, dtype=torch.float64, device="cuda")
+    warm.view(3, N)[2] = cfg.knots_he[1][2] / cfg.knots_t[1]  # dh_e/dt at t = 0
+    state = [0.0, 1e-6, h, warm]
+    run_steps(ctx, state, args.warmup)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- timed region (device time, CUDA events on the library's stream)
+    clocks = ClockSampler(local)
+    clocks.start()
+    s0 = ctx.stats()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run_steps(ctx, state, args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    s1 = ctx.stats()
+    clk = clocks.stop()
+    rhs_calls = s1["rhs_calls"] - s0["rhs_calls"]
+    iters = s1["iterations"] - s0["iterations"]
+    launches = s1["launches"] - s0["launches"]
+    units = float(N * rhs_calls)
+    t_max = ms
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms, units], dtype=torch.float64, device="cuda")
+        tm = tt.clone()
+        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tm[1:2], op=dist.ReduceOp.SUM)
+        t_max, units = float(tm[0]), float(tm[1])
+    value = units / (t_max * 1e-3)
+
+    # ---- per-pass profile over the same number of steps (separate pass, events around each launch)
+    ctx.profile(True)
+    run_steps(ctx, state, args.steps)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    kinds = {k: v for k, v in prof.items() if v[0] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][1])
+    cnt, tot = kinds[dom]
+    avg_ms = tot / cnt
+    peak, peak_src = _peaks()
+    achieved = algorithmic_bytes(dom, cfg.n, 4) / (avg_ms * 1e-3) / 1e9
+    total_prof_ms = sum(v[1] for v in kinds.values())
+    shares = {k: round(v[1] / total_prof_ms, 4) for k, v in sorted(kinds.items(), key=lambda kv: -kv[1][1])}
+
+    # ---- end to end through the public API with host buffers (pinned), copies inside the timed region
+    h_host = h.cpu().pin_memory()
+    w_host = warm.cpu().pin_memory()
+    hd = torch.empty_like(h)
+    wd = torch.empty_like(warm)
+    ke = max(1, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize()
+    c0 = ctx.stats()["rhs_calls"]
+    st = [state[0], state[1], hd, wd]
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(ke):
+        hd.copy_(h_host, non_blocking=True)
+        wd.copy_(w_host, non_blocking=True)
+        st[0], st[1], _ = ctx.step(st[0], st[1], 10.0, hd, wd)
+        h_host.copy_(hd, non_blocking=True)
+        w_host.copy_(wd, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e2.elapsed_time(e3)
+    e2e_units = N * (ctx.stats()["rhs_calls"] - c0)
+    e2e_value = e2e_units / (e2e_ms * 1e-3) * ws
+
+    # ---- FP64 path on the same state (one step) and the FP32 error against it
+    ctx64 = make_ctx(S, cfg, S.PREC_F64)
+    hA = h.clone()
+    w32 = warm.clone()
+    w64 = warm.clone()
+    o32 = torch.empty_like(h)
+    o64 = torch.empty_like(h)
+    ctx64.rhs(state[0], hA, w64, o64)
+    ctx.rhs(state[0], hA, w32, o32)
+    fp32_err = {}
+    for ci, nm in enumerate(("x", "y", "z")):
+        a, b = o32.view(3, N)[ci], o64.view(3, N)[ci]
+        fp32_err["dhdt_" + nm] = float((a - b).abs().max() / b.abs().max().clamp_min(1e-300))
+    st64 = [state[0], state[1], h.clone(), warm.clone()]
+    torch.cuda.synchronize()
+    c0 = ctx64.stats()["rhs_calls"]
+    k64 = max(1, min(args.steps, 3))
+    e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e4.record(stream)
+    run_steps(ctx64, st64, k64)
+    e5.record(stream)
+    torch.cuda.synchronize()
+    fp64_value = N * (ctx64.stats()["rhs_calls"] - c0) / (e4.elapsed_time(e5) * 1e-3)
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        v, tp, ti = cpu_oracle_sample(cfg, iters / max(rhs_calls, 1))
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 NumPy oracle on the 128^3 lens: pre-stage {tp:.2f}s + one Eq. 5 iteration "
+                         f"{ti:.2f}s, scaled to {iters / max(rhs_calls, 1):.2f} iterations per RHS"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(cfg.n), "padded": [2 * v for v in cfg.n],
+                   "geometry": cfg.note, "state_dtype": "f64", "n": cfg.n_power, "rho_out": cfg.rho_out,
+                   "rtol": cfg.rtol, "delta_it": 2e-5, "t_start": None, "rhs_per_step": rhs_calls / args.steps,
+                   "iters_per_rhs": iters / max(rhs_calls, 1), "l2": "inputs larger than L2 (FP64 state and "
+                   "stage buffers 7 x 50 MB, padded spectrum 101 MB per pass)",
+                   "parallelism": f"replicas x{ws}"},
+        "fp64_path": {"value": fp64_value, "unit": UNIT, "steps": k64},
+        "fp32_error_vs_fp64": fp32_err,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * n3 * 8, "d2h_bytes_per_step": 2 * n3 * 8,
+                "steps": ke},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_src, "traffic": NCU_TRAFFIC,
+                     "bytes_per_launch": algorithmic_bytes(dom, cfg.n, 4), "avg_launch_ms": avg_ms,
+                     "launches": cnt},
+        "pass_shares": shares,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    line["config"]["t_start"] = None
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        return bench_reference(args, ws, rank)
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    try:
+        return bench_ours(args, ws, rank, local)
+    finally:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -81,6 +81,7 @@ typedef struct {
 } scfft_field_path;
 
 typedef struct {
+  long long launches;      /* CUDA kernels launched by the library */
   long long rhs_calls;     /* right-hand-side evaluations */
   long long iterations;    /* Eq. 5 iterations summed over those calls */
   long long accepted, rejected;
@@ -152,6 +153,43 @@ scfft_status scfft_phi(scfft_ctx* ctx, const double* j, double* out);
 scfft_status scfft_integrate(scfft_ctx* ctx, double t0, double t1, double dt0, int nsnap, const double* tsnap,
                              double* h, double* snaps, double* warm, const double* dt_fixed, int nfixed,
                              scfft_stats* stats);
+
+/* One accepted BS23 step (the pair and error control of scfft_integrate) from
+ * *t with trial step *dt; rejected trials are retried with smaller steps.  The
+ * step never passes tstop or a kink of the path and ends exactly on them when
+ * clipped.  On return *t is the new time and *dt the proposed next step.
+ * h, warm: device, 3*N doubles, in/out (state and Eq. 5 warm start).  The
+ * first stage is reused from the previous accepted step when it was taken on
+ * the same h and warm buffers and ended at *t (FSAL).  rejected: host int* or
+ * NULL (rejected trials).  Synchronous (reads the error norm). */
+scfft_status scfft_step(scfft_ctx* ctx, double* t, double* dt, double tstop, double* h, double* warm,
+                        int* rejected);
+
+/* Per-pass profiling: when enabled, every kernel the library launches is
+ * bracketed by CUDA events on the context's stream and its elapsed time is
+ * added to the counter of its pass kind.  Enabling resets the counters.
+ * profile_read waits for the stream and fills counts[SCFFT_NKINDS] and
+ * ms[SCFFT_NKINDS] (host arrays). */
+enum {
+  SCFFT_K_X_FWD = 0,       /* x pass: state rows -> R2C                          */
+  SCFFT_K_X_POWERLAW = 1,  /* x pass: C2R, Eq. 1 / rho_out, R2C                   */
+  SCFFT_K_X_ASSEMBLE = 2,  /* x pass: C2R, dh^0 assembly, R2C                     */
+  SCFFT_K_X_MASKPAD = 3,   /* x pass: C2R, mask, zero pad, padded R2C             */
+  SCFFT_K_X_UPDATE = 4,    /* x pass: padded C2R, Eq. 5 update + residual, R2C    */
+  SCFFT_K_Y_FWD_U = 5,     /* y pass, unpadded, forward                           */
+  SCFFT_K_Y_INV_U = 6,     /* y pass, unpadded, inverse                           */
+  SCFFT_K_Z_CURL = 7,      /* z pass: forward, curl multiply, inverse             */
+  SCFFT_K_Y_FWD_P = 8,     /* y pass, padded, forward (pruned input)              */
+  SCFFT_K_Y_INV_P = 9,     /* y pass, padded, inverse (pruned output)             */
+  SCFFT_K_Z_KERNEL = 10,   /* z pass, padded: forward, K^ x F (Eq. 7), inverse    */
+  SCFFT_K_FINALIZE = 11,   /* dh/dt and warm start written out                    */
+  SCFFT_K_RK = 12,         /* integrator stage sums and error norm                */
+  SCFFT_K_OTHER = 13,      /* passes of scfft_curl / scfft_phi                    */
+  SCFFT_NKINDS = 14
+};
+scfft_status scfft_profile(scfft_ctx* ctx, int enable);
+scfft_status scfft_profile_read(scfft_ctx* ctx, long long* counts, double* ms);
+const char* scfft_kind_name(int kind);
 
 /* Wait for the stream; returns the first latched device-side status. */
 scfft_status scfft_sync(scfft_ctx* ctx);

@@ -29,7 +29,10 @@ _LIBNAME = "libscfft.so"
 # every entry point declared in include/scfft.h
 EXPORTS = ("scfft_create", "scfft_set_geometry", "scfft_set_jc_map", "scfft_set_field_path",
            "scfft_precompute_kernel", "scfft_rhs", "scfft_curl", "scfft_phi", "scfft_integrate",
+           "scfft_step", "scfft_profile", "scfft_profile_read", "scfft_kind_name",
            "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy")
+
+NKINDS = 14
 
 
 def library_path() -> str:
@@ -65,7 +68,8 @@ class _FieldPath(ctypes.Structure):
 
 
 class _Stats(ctypes.Structure):
-    _fields_ = [("rhs_calls", ctypes.c_longlong), ("iterations", ctypes.c_longlong),
+    _fields_ = [("launches", ctypes.c_longlong), ("rhs_calls", ctypes.c_longlong),
+                ("iterations", ctypes.c_longlong),
                 ("accepted", ctypes.c_longlong), ("rejected", ctypes.c_longlong),
                 ("last_iters", ctypes.c_int), ("last_residual", ctypes.c_double),
                 ("t", ctypes.c_double), ("dt", ctypes.c_double)]
@@ -95,6 +99,10 @@ def load_library(path: Optional[str] = None):
         "scfft_curl": (I, [P, P, P]),
         "scfft_phi": (I, [P, P, P]),
         "scfft_integrate": (I, [P, D, D, D, I, P, P, P, P, P, I, ctypes.POINTER(_Stats)]),
+        "scfft_step": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), D, P, P, ctypes.POINTER(I)]),
+        "scfft_profile": (I, [P, I]),
+        "scfft_profile_read": (I, [P, P, P]),
+        "scfft_kind_name": (ctypes.c_char_p, [I]),
         "scfft_sync": (I, [P]),
         "scfft_get_stats": (I, [P, ctypes.POINTER(_Stats)]),
         "scfft_status_string": (ctypes.c_char_p, [I]),
@@ -204,6 +212,23 @@ class Context:
                                               0 if df is None else len(df), ctypes.byref(st)),
                     "scfft_integrate")
         return {k: getattr(st, k) for k, _ in _Stats._fields_}
+
+    def step(self, t: float, dt: float, tstop: float, h, warm):
+        """One accepted BS23 step; returns (t_new, dt_next, rejected_trials)."""
+        tt, dd, rj = ctypes.c_double(t), ctypes.c_double(dt), ctypes.c_int(0)
+        self._check(self._lib.scfft_step(self._h, ctypes.byref(tt), ctypes.byref(dd), float(tstop), _ptr(h),
+                                         _ptr(warm), ctypes.byref(rj)), "scfft_step")
+        return tt.value, dd.value, rj.value
+
+    def profile(self, enable: bool = True):
+        self._check(self._lib.scfft_profile(self._h, 1 if enable else 0), "scfft_profile")
+
+    def profile_read(self):
+        """{pass name: (launches, total ms)} since profiling was enabled."""
+        cnt = (ctypes.c_longlong * NKINDS)()
+        ms = (ctypes.c_double * NKINDS)()
+        self._check(self._lib.scfft_profile_read(self._h, cnt, ms), "scfft_profile_read")
+        return {self._lib.scfft_kind_name(k).decode(): (cnt[k], ms[k]) for k in range(NKINDS)}
 
     def sync(self):
         self._check(self._lib.scfft_sync(self._h), "scfft_sync")

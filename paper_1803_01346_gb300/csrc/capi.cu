@@ -1,17 +1,22 @@
 // capi.cu - the C ABI of include/scfft.h: context, geometry, kernel-spectrum
-// precompute, the right-hand side driver (§2, Eqs. 1-5) and the BS23 time
-// integrator (the method of lines with "ode23", §2).
+// precompute, the right-hand side driver (§2, Eqs. 1-5), the BS23 time
+// integrator (the method of lines with "ode23", §2) and per-pass profiling.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <new>
 #include <vector>
 
 #include "scfft.h"
 #include "scfft_internal.cuh"
 
 using namespace scfft;
+
+namespace {
+constexpr int kProfPool = 1 << 14;  // event pairs buffered before a flush
+}
 
 struct scfft_ctx {
   Geo g{};
@@ -30,13 +35,25 @@ struct scfft_ctx {
   std::vector<double> kt, khe;
   double sin_amp = 0, sin_period = 1, sin_t0 = 0, sin_t1 = 0, sin_dir[3] = {0, 0, 1};
   // host mirror of Ctrl and synchronisation
-  Ctrl* hctrl = nullptr;  // pinned
+  Ctrl* hctrl = nullptr;  // pinned, 3 slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
-  // integrator (FP64)
-  double* ib = nullptr;   // 7 * 3N doubles: ynew, k1..k4, ytmp, g
+  // integrator (FP64): ynew, k1..k4, ytmp, internal warm start
+  double* ib = nullptr;
+  double* k[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool fsal_valid = false;
+  double fsal_t = 0;
+  const double* fsal_h = nullptr;
+  const double* fsal_g = nullptr;
   unsigned long long* errbits = nullptr;  // device
   unsigned long long* herr = nullptr;     // pinned
   scfft_stats stats{};
+  // profiling
+  bool prof_on = false;
+  std::vector<cudaEvent_t> pev;
+  std::vector<int> pkind;
+  int pused = 0;
+  double pms[SCFFT_NKINDS]{};
+  long long pcnt[SCFFT_NKINDS]{};
 };
 
 namespace {
@@ -47,11 +64,15 @@ namespace {
     if (e_ != cudaSuccess) return SCFFT_ECUDA; \
   } while (0)
 
+#define CS_(x)                            \
+  do {                                    \
+    scfft_status s_ = (x);                \
+    if (s_ != SCFFT_OK) return s_;        \
+  } while (0)
+
 int round_up(int a, int m) { return (a + m - 1) / m * m; }
 
-bool grid_ok(int n) {
-  return n == 16 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128;
-}
+bool grid_ok(int n) { return n == 16 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128; }
 
 template <typename T> Work<T>& work(scfft_ctx* c);
 template <> Work<float>& work<float>(scfft_ctx* c) { return c->wf; }
@@ -68,6 +89,41 @@ template <typename T> Launch<T> launch_of(scfft_ctx* c) {
   return L;
 }
 
+// ---------------------------------------------------------------- profiling
+cudaError_t prof_flush(scfft_ctx* c) {
+  if (c->pused == 0) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < c->pused; ++i) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, c->pev[2 * i], c->pev[2 * i + 1]) == cudaSuccess) {
+      c->pms[c->pkind[i]] += ms;
+      c->pcnt[c->pkind[i]] += 1;
+    }
+  }
+  c->pused = 0;
+  return cudaSuccess;
+}
+
+// Run one kernel launcher, counting it and (when profiling) bracketing it with events.
+template <typename F> cudaError_t run(scfft_ctx* c, int kind, F&& f) {
+  int slot = -1;
+  if (c->prof_on) {
+    if (c->pused == kProfPool) {
+      cudaError_t e = prof_flush(c);
+      if (e != cudaSuccess) return e;
+    }
+    slot = c->pused++;
+    c->pkind[slot] = kind;
+    cudaEventRecord(c->pev[2 * slot], c->st);
+  }
+  cudaError_t e = f();
+  if (slot >= 0) cudaEventRecord(c->pev[2 * slot + 1], c->st);
+  c->stats.launches += 1;
+  return e;
+}
+
+// ---------------------------------------------------------------- field path
 // dh_e/dt at t (right derivative, or left at a kink when left != 0)
 void hedot_at(const scfft_ctx* c, double t, int left, double out[3]) {
   out[0] = out[1] = out[2] = 0;
@@ -90,6 +146,17 @@ void hedot_at(const scfft_ctx* c, double t, int left, double out[3]) {
   }
 }
 
+std::vector<double> kinks_of(const scfft_ctx* c) {
+  std::vector<double> k(c->kt.begin(), c->kt.end());
+  if (c->sin_amp != 0) {
+    k.push_back(c->sin_t0);
+    k.push_back(c->sin_t1);
+  }
+  std::sort(k.begin(), k.end());
+  return k;
+}
+
+// ---------------------------------------------------------------- workspaces
 template <typename T> scfft_status alloc_work(scfft_ctx* c) {
   typedef typename cplx_of<T>::type V;
   Work<T>& w = work<T>(c);
@@ -153,24 +220,30 @@ PointParams base_params(const scfft_ctx* c) {
   return pp;
 }
 
+// ---------------------------------------------------------------- rhs
 // Spectral curl of the half spectrum held in U: y fwd, z (fwd, curl, inv), y inv.
-template <typename T> cudaError_t curl_in_U(const Launch<T>& L, bool check_done) {
+template <typename T> cudaError_t curl_in_U(scfft_ctx* c, const Launch<T>& L, bool check_done) {
   cudaError_t e;
-  if ((e = launch_y<T>(L, false, false, check_done)) != cudaSuccess) return e;
-  if ((e = launch_z_curl<T>(L, check_done, 1.0 / (double)L.g.N)) != cudaSuccess) return e;
-  return launch_y<T>(L, false, true, check_done);
+  if ((e = run(c, SCFFT_K_Y_FWD_U, [&] { return launch_y<T>(L, false, false, check_done); })) != cudaSuccess) return e;
+  if ((e = run(c, SCFFT_K_Z_CURL, [&] { return launch_z_curl<T>(L, check_done, 1.0 / (double)L.g.N); })) !=
+      cudaSuccess)
+    return e;
+  return run(c, SCFFT_K_Y_INV_U, [&] { return launch_y<T>(L, false, true, check_done); });
 }
 
-// One iteration of Eq. 5 (i-th): U holds R2C_x of dh^i on entry and of dh^{i+1} on exit.
-template <typename T> cudaError_t iteration(const Launch<T>& L, PointParams pp, int i, bool check_done) {
+// One iteration of Eq. 5 (the i-th): U holds R2C_x of dh^i on entry and of dh^{i+1} on exit.
+template <typename T> cudaError_t iteration(scfft_ctx* c, const Launch<T>& L, PointParams pp, int i, bool chk) {
   cudaError_t e;
-  if ((e = curl_in_U<T>(L, check_done)) != cudaSuccess) return e;
-  if ((e = launch_x<T>(L, X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, check_done)) != cudaSuccess) return e;
-  if ((e = launch_y<T>(L, true, false, check_done)) != cudaSuccess) return e;
-  if ((e = launch_z_kernel<T>(L, check_done)) != cudaSuccess) return e;
-  if ((e = launch_y<T>(L, true, true, check_done)) != cudaSuccess) return e;
+  if ((e = curl_in_U<T>(c, L, chk)) != cudaSuccess) return e;
+  if ((e = run(c, SCFFT_K_X_MASKPAD,
+               [&] { return launch_x<T>(L, X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, chk); })) != cudaSuccess)
+    return e;
+  if ((e = run(c, SCFFT_K_Y_FWD_P, [&] { return launch_y<T>(L, true, false, chk); })) != cudaSuccess) return e;
+  if ((e = run(c, SCFFT_K_Z_KERNEL, [&] { return launch_z_kernel<T>(L, chk); })) != cudaSuccess) return e;
+  if ((e = run(c, SCFFT_K_Y_INV_P, [&] { return launch_y<T>(L, true, true, chk); })) != cudaSuccess) return e;
   pp.iter = i;
-  return launch_x<T>(L, X_UPDATE, pp, nullptr, nullptr, nullptr, i & 1, (i + 1) & 1, check_done);
+  return run(c, SCFFT_K_X_UPDATE,
+             [&] { return launch_x<T>(L, X_UPDATE, pp, nullptr, nullptr, nullptr, i & 1, (i + 1) & 1, chk); });
 }
 
 template <typename T>
@@ -181,11 +254,12 @@ scfft_status rhs_impl(scfft_ctx* c, double t, int left, const double* h, double*
   const double hn = sqrt(pp.hedot[0] * pp.hedot[0] + pp.hedot[1] * pp.hedot[1] + pp.hedot[2] * pp.hedot[2]);
   pp.tol = c->opt.delta_it * (hn > 1.0 ? hn : 1.0);
   // pre-stage: j = curl h; e = rho(j) j; dh^0 = -curl e / mu0 on Omega, warm on Omega_out
-  CK(launch_x<T>(L, X_FWD_F64, pp, h, nullptr, nullptr, 0, 0, false));
-  CK(curl_in_U<T>(L, false));
-  CK(launch_x<T>(L, X_POWERLAW, pp, nullptr, nullptr, nullptr, 0, 0, false));
-  CK(curl_in_U<T>(L, false));
-  CK(launch_x<T>(L, X_ASSEMBLE, pp, nullptr, nullptr, warm, 0, 0, false));
+  CK(run(c, SCFFT_K_X_FWD, [&] { return launch_x<T>(L, X_FWD_F64, pp, h, nullptr, nullptr, 0, 0, false); }));
+  CK(curl_in_U<T>(c, L, false));
+  CK(run(c, SCFFT_K_X_POWERLAW,
+         [&] { return launch_x<T>(L, X_POWERLAW, pp, nullptr, nullptr, nullptr, 0, 0, false); }));
+  CK(curl_in_U<T>(c, L, false));
+  CK(run(c, SCFFT_K_X_ASSEMBLE, [&] { return launch_x<T>(L, X_ASSEMBLE, pp, nullptr, nullptr, warm, 0, 0, false); }));
   const int maxit = c->opt.max_iter;
   const bool early = c->opt.delta_it > 0 && c->nout > 0;
   int launched = 0;
@@ -199,7 +273,7 @@ scfft_status rhs_impl(scfft_ctx* c, double t, int left, const double* h, double*
         CK(cudaEventSynchronize(c->ev[i & 1]));
         if (c->hctrl[i & 1].done) break;
       }
-      CK(iteration<T>(L, pp, i, early));
+      CK(iteration<T>(c, L, pp, i, early));
       ++launched;
       if (early) {
         CK(cudaMemcpyAsync(&c->hctrl[i & 1], c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->st));
@@ -207,13 +281,12 @@ scfft_status rhs_impl(scfft_ctx* c, double t, int left, const double* h, double*
       }
     }
   }
-  CK(launch_finalize<T>(L, hdot, warm));
+  CK(run(c, SCFFT_K_FINALIZE, [&] { return launch_finalize<T>(L, hdot, warm); }));
   c->stats.rhs_calls += 1;
   if (iters_out || early) {
-    Ctrl hc;
     CK(cudaMemcpyAsync(c->hctrl + 2, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
-    hc = c->hctrl[2];
+    const Ctrl hc = c->hctrl[2];
     c->stats.iterations += hc.iters;
     c->stats.last_iters = hc.iters;
     c->stats.last_residual = hc.residual;
@@ -228,27 +301,32 @@ scfft_status rhs_impl(scfft_ctx* c, double t, int left, const double* h, double*
   return SCFFT_OK;
 }
 
+scfft_status rhs_any(scfft_ctx* c, double t, int left, const double* h, double* warm, double* hdot, int* it) {
+  return c->opt.precision == SCFFT_PREC_F32 ? rhs_impl<float>(c, t, left, h, warm, hdot, it)
+                                            : rhs_impl<double>(c, t, left, h, warm, hdot, it);
+}
+
 template <typename T> scfft_status curl_impl(scfft_ctx* c, const double* f, double* out) {
   Launch<T> L = launch_of<T>(c);
   PointParams pp = base_params(c);
-  CK(launch_x<T>(L, X_FWD_F64, pp, f, nullptr, nullptr, 0, 0, false));
-  CK(curl_in_U<T>(L, false));
-  CK(launch_x<T>(L, X_TO_F64, pp, nullptr, out, nullptr, 0, 0, false));
+  CK(run(c, SCFFT_K_OTHER, [&] { return launch_x<T>(L, X_FWD_F64, pp, f, nullptr, nullptr, 0, 0, false); }));
+  CK(curl_in_U<T>(c, L, false));
+  CK(run(c, SCFFT_K_OTHER, [&] { return launch_x<T>(L, X_TO_F64, pp, nullptr, out, nullptr, 0, 0, false); }));
   return SCFFT_OK;
 }
 
 template <typename T> scfft_status phi_impl(scfft_ctx* c, const double* j, double* out) {
   Launch<T> L = launch_of<T>(c);
   PointParams pp = base_params(c);
-  CK(launch_x<T>(L, X_PAD_F64, pp, j, nullptr, nullptr, 0, 0, false));
-  CK(launch_y<T>(L, true, false, false));
-  CK(launch_z_kernel<T>(L, false));
-  CK(launch_y<T>(L, true, true, false));
-  CK(launch_x<T>(L, X_CROP_F64, pp, nullptr, out, nullptr, 0, 0, false));
+  CK(run(c, SCFFT_K_OTHER, [&] { return launch_x<T>(L, X_PAD_F64, pp, j, nullptr, nullptr, 0, 0, false); }));
+  CK(run(c, SCFFT_K_Y_FWD_P, [&] { return launch_y<T>(L, true, false, false); }));
+  CK(run(c, SCFFT_K_Z_KERNEL, [&] { return launch_z_kernel<T>(L, false); }));
+  CK(run(c, SCFFT_K_Y_INV_P, [&] { return launch_y<T>(L, true, true, false); }));
+  CK(run(c, SCFFT_K_OTHER, [&] { return launch_x<T>(L, X_CROP_F64, pp, nullptr, out, nullptr, 0, 0, false); }));
   return SCFFT_OK;
 }
 
-// ---------------------------------------------------------------- BS23 kernels (FP64 state)
+// ---------------------------------------------------------------- BS23 (FP64 state)
 __global__ void combine_kernel(double* __restrict__ out, const double* __restrict__ y, double h, double c1,
                                const double* __restrict__ k1, double c2, const double* __restrict__ k2, double c3,
                                const double* __restrict__ k3, long long n) {
@@ -261,6 +339,7 @@ __global__ void combine_kernel(double* __restrict__ out, const double* __restric
 }
 
 // err_i = h (e1 k1 + e2 k2 + e3 k3 + e4 k4); norm = max_i |err_i| / max(rtol|y|, rtol|ynew|, atol)
+// (a max is order independent, so the atomic combine is deterministic)
 __global__ void errnorm_kernel(const double* __restrict__ y, const double* __restrict__ yn, double h, double e1,
                                const double* __restrict__ k1, double e2, const double* __restrict__ k2, double e3,
                                const double* __restrict__ k3, double e4, const double* __restrict__ k4, double rtol,
@@ -290,9 +369,110 @@ int blocks_for(long long n) {
   return (int)std::min<long long>(std::max<long long>(b, 1), 152 * 8);
 }
 
-scfft_status rhs_any(scfft_ctx* c, double t, int left, const double* h, double* warm, double* hdot, int* it) {
-  return c->opt.precision == SCFFT_PREC_F32 ? rhs_impl<float>(c, t, left, h, warm, hdot, it)
-                                            : rhs_impl<double>(c, t, left, h, warm, hdot, it);
+scfft_status ensure_rk(scfft_ctx* c) {
+  if (c->ib) return SCFFT_OK;
+  const long long n3 = 3 * c->g.N;
+  if (cudaMalloc(&c->ib, sizeof(double) * 7 * n3) != cudaSuccess) return SCFFT_ENOMEM;
+  for (int i = 0; i < 4; ++i) c->k[i] = c->ib + (1 + i) * n3;
+  return SCFFT_OK;
+}
+
+// One accepted BS23 step from *t (rejected trials are retried with a smaller
+// step).  The step never passes tstop nor a kink of the path and ends exactly
+// on them when clipped.  dt_fixed > 0: take exactly that step (clipped the
+// same way) with no error control.  FSAL: the first stage is reused from the
+// previous accepted step of the same (h, g) unless that step ended on a kink.
+scfft_status bs23_step(scfft_ctx* c, double* t_io, double* dt_io, double tstop, double* h, double* g,
+                       double dt_fixed, int* rej_out) {
+  CS_(ensure_rk(c));
+  const long long n3 = 3 * c->g.N;
+  double* ynew = c->ib;
+  double* ytmp = c->ib + 5 * n3;
+  double** k = c->k;
+  const double t = *t_io;
+  double dt = dt_fixed > 0 ? dt_fixed : *dt_io;
+  const std::vector<double> kinks = kinks_of(c);
+  double nxt = tstop;
+  for (double v : kinks)
+    if (v > t && v < nxt) nxt = v;
+  if (!(c->fsal_valid && c->fsal_t == t && c->fsal_h == h && c->fsal_g == g)) {
+    CS_(rhs_any(c, t, 0, h, g, k[0], nullptr));
+  }
+  // Bogacki-Shampine 3(2): c = (0, 1/2, 3/4, 1); a21 = 1/2; a31 = 0, a32 = 3/4;
+  // b = (2/9, 1/3, 4/9, 0); bhat = (7/24, 1/4, 1/3, 1/8); e = b - bhat
+  const double a21 = 0.5, a32 = 0.75, b1 = 2.0 / 9.0, b2 = 1.0 / 3.0, b3 = 4.0 / 9.0;
+  const double e1 = 2.0 / 9.0 - 7.0 / 24.0, e2 = 1.0 / 3.0 - 0.25, e3 = 4.0 / 9.0 - 1.0 / 3.0, e4 = -0.125;
+  const int blocks = blocks_for(n3);
+  int rej = 0;
+  for (;;) {
+    const double hs = std::min(dt, nxt - t);
+    const bool hits = (hs == nxt - t);
+    const bool end_left = hits && std::binary_search(kinks.begin(), kinks.end(), nxt);
+    if (!(hs > 1e-14 * std::max(1.0, fabs(t)))) {
+      c->fsal_valid = false;
+      return SCFFT_ESTEP;
+    }
+    CK(run(c, SCFFT_K_RK, [&] {
+      combine_kernel<<<blocks, 256, 0, c->st>>>(ytmp, h, hs, a21, k[0], 0, nullptr, 0, nullptr, n3);
+      return cudaGetLastError();
+    }));
+    CS_(rhs_any(c, t + 0.5 * hs, 0, ytmp, g, k[1], nullptr));
+    CK(run(c, SCFFT_K_RK, [&] {
+      combine_kernel<<<blocks, 256, 0, c->st>>>(ytmp, h, hs, 0.0, k[0], a32, k[1], 0, nullptr, n3);
+      return cudaGetLastError();
+    }));
+    CS_(rhs_any(c, t + 0.75 * hs, 0, ytmp, g, k[2], nullptr));
+    CK(run(c, SCFFT_K_RK, [&] {
+      combine_kernel<<<blocks, 256, 0, c->st>>>(ynew, h, hs, b1, k[0], b2, k[1], b3, k[2], n3);
+      return cudaGetLastError();
+    }));
+    CS_(rhs_any(c, hits ? nxt : t + hs, end_left ? 1 : 0, ynew, g, k[3], nullptr));
+    double en = 0.0;
+    if (!(dt_fixed > 0)) {
+      CK(cudaMemsetAsync(c->errbits, 0, sizeof(unsigned long long), c->st));
+      CK(run(c, SCFFT_K_RK, [&] {
+        errnorm_kernel<<<blocks, 256, 0, c->st>>>(h, ynew, hs, e1, k[0], e2, k[1], e3, k[2], e4, k[3], c->opt.rtol,
+                                                 c->opt.atol, n3, c->errbits);
+        return cudaGetLastError();
+      }));
+      CK(cudaMemcpyAsync(c->herr, c->errbits, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      const unsigned long long bits = *c->herr;
+      memcpy(&en, &bits, sizeof(double));
+      if (!(en == en)) {
+        c->fsal_valid = false;
+        return SCFFT_ENONFINITE;
+      }
+    }
+    if (en <= 1.0) {
+      const double tn = hits ? nxt : t + hs;
+      CK(cudaMemcpyAsync(h, ynew, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->st));
+      c->stats.accepted += 1;
+      if (end_left) {
+        c->fsal_valid = false;  // the next first stage takes the right derivative at the kink
+      } else {
+        std::swap(k[0], k[3]);
+        c->fsal_valid = true;
+        c->fsal_t = tn;
+        c->fsal_h = h;
+        c->fsal_g = g;
+      }
+      *t_io = tn;
+      if (dt_fixed > 0) {
+        *dt_io = dt_fixed;
+      } else {
+        const double fac = en == 0.0 ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * pow(en, -1.0 / 3.0)));
+        *dt_io = hs * fac;
+      }
+      if (rej_out) *rej_out = rej;
+      c->stats.t = tn;
+      c->stats.dt = *dt_io;
+      return SCFFT_OK;
+    }
+    ++rej;
+    c->stats.rejected += 1;
+    dt = hs * std::max(0.2, 0.9 * pow(en, -1.0 / 3.0));
+  }
 }
 
 }  // namespace
@@ -314,6 +494,13 @@ const char* scfft_status_string(scfft_status s) {
   return "unknown status";
 }
 
+const char* scfft_kind_name(int kind) {
+  static const char* names[SCFFT_NKINDS] = {
+      "x_fwd_state", "x_powerlaw", "x_assemble", "x_maskpad", "x_update", "y_fwd_unpadded", "y_inv_unpadded",
+      "z_curl",      "y_fwd_padded", "y_inv_padded", "z_kernel", "finalize", "rk_stage", "io_pass"};
+  return (kind >= 0 && kind < SCFFT_NKINDS) ? names[kind] : "unknown";
+}
+
 scfft_status scfft_create(const scfft_grid* grid, const scfft_material* mat, const scfft_options* opt, void* stream,
                           scfft_ctx** out) {
   if (!grid || !mat || !opt || !out) return SCFFT_EINVAL;
@@ -323,6 +510,7 @@ scfft_status scfft_create(const scfft_grid* grid, const scfft_material* mat, con
   if (!(mat->n >= 1) || !(mat->e0 > 0) || !(mat->jc > 0) || !(mat->rho_out >= 0) || !(mat->mu0 > 0))
     return SCFFT_EINVAL;
   if (opt->max_iter < 0 || !(opt->delta_it >= 0) || !(opt->sigma_scale >= 0)) return SCFFT_EINVAL;
+  if (!(opt->rtol > 0) || !(opt->atol > 0)) return SCFFT_EINVAL;
   if (opt->precision != SCFFT_PREC_F64 && opt->precision != SCFFT_PREC_F32) return SCFFT_EINVAL;
   scfft_ctx* c = new (std::nothrow) scfft_ctx();
   if (!c) return SCFFT_ENOMEM;
@@ -365,6 +553,7 @@ void scfft_destroy(scfft_ctx* c) {
   if (c->hctrl) cudaFreeHost(c->hctrl);
   if (c->herr) cudaFreeHost(c->herr);
   for (int i = 0; i < 2; ++i) if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  for (cudaEvent_t e : c->pev) cudaEventDestroy(e);
   delete c;
 }
 
@@ -385,12 +574,14 @@ scfft_status scfft_set_geometry(scfft_ctx* c, const uint8_t* mask) {
   CK(cudaMemcpy(c->mask, m.data(), g.N, cudaMemcpyHostToDevice));
   c->nout = g.N - nin;
   c->have_geom = true;
+  c->fsal_valid = false;
   return SCFFT_OK;
 }
 
 scfft_status scfft_set_jc_map(scfft_ctx* c, const double* jc) {
   if (!c) return SCFFT_EINVAL;
   const long long N = c->g.N;
+  c->fsal_valid = false;
   if (c->opt.precision == SCFFT_PREC_F32) {
     cudaFree(c->wf.jc);
     c->wf.jc = nullptr;
@@ -422,6 +613,7 @@ scfft_status scfft_set_field_path(scfft_ctx* c, const scfft_field_path* p) {
   c->sin_t1 = p->sin_t1;
   for (int a = 0; a < 3; ++a) c->sin_dir[a] = p->sin_dir[a];
   c->have_path = true;
+  c->fsal_valid = false;
   return SCFFT_OK;
 }
 
@@ -440,12 +632,14 @@ scfft_status scfft_precompute_kernel(scfft_ctx* c) {
   cudaFree(scratch);
   if (e != cudaSuccess || e2 != cudaSuccess) return SCFFT_ECUDA;
   c->have_kernel = true;
+  c->fsal_valid = false;
   return SCFFT_OK;
 }
 
 scfft_status scfft_rhs(scfft_ctx* c, double t, int left, const double* h, double* warm, double* hdot, int* iters_out) {
   if (!c || !h || !warm || !hdot || hdot == h) return SCFFT_EINVAL;
   if (!c->have_geom || !c->have_kernel || !c->have_path) return SCFFT_ESTATE;
+  c->fsal_valid = false;
   return rhs_any(c, t, left, h, warm, hdot, iters_out);
 }
 
@@ -460,6 +654,12 @@ scfft_status scfft_phi(scfft_ctx* c, const double* j, double* out) {
   return c->opt.precision == SCFFT_PREC_F32 ? phi_impl<float>(c, j, out) : phi_impl<double>(c, j, out);
 }
 
+scfft_status scfft_step(scfft_ctx* c, double* t, double* dt, double tstop, double* h, double* warm, int* rejected) {
+  if (!c || !t || !dt || !h || !warm || !(*dt > 0) || !(tstop > *t)) return SCFFT_EINVAL;
+  if (!c->have_geom || !c->have_kernel || !c->have_path) return SCFFT_ESTATE;
+  return bs23_step(c, t, dt, tstop, h, warm, 0.0, rejected);
+}
+
 scfft_status scfft_integrate(scfft_ctx* c, double t0, double t1, double dt0, int nsnap, const double* tsnap, double* h,
                              double* snaps, double* warm, const double* dt_fixed, int nfixed, scfft_stats* stats) {
   if (!c || !h || !(t1 > t0) || !(dt0 > 0) || nsnap < 0 || (nsnap > 0 && (!tsnap || !snaps))) return SCFFT_EINVAL;
@@ -467,99 +667,39 @@ scfft_status scfft_integrate(scfft_ctx* c, double t0, double t1, double dt0, int
   for (int i = 0; i < nsnap; ++i)
     if (!(tsnap[i] > t0 && tsnap[i] <= t1) || (i > 0 && !(tsnap[i] > tsnap[i - 1]))) return SCFFT_EINVAL;
   if (!c->have_geom || !c->have_kernel || !c->have_path) return SCFFT_ESTATE;
+  CS_(ensure_rk(c));
   const long long n3 = 3 * c->g.N;
-  if (!c->ib) CK(cudaMalloc(&c->ib, sizeof(double) * 7 * n3));
-  double* ynew = c->ib;
-  double* k[4] = {c->ib + n3, c->ib + 2 * n3, c->ib + 3 * n3, c->ib + 4 * n3};
-  double* ytmp = c->ib + 5 * n3;
   double* g = warm ? warm : c->ib + 6 * n3;
   if (!warm) {
     double hd[3];
     hedot_at(c, t0, 0, hd);
-    fill3_kernel<<<blocks_for(c->g.N), 256, 0, c->st>>>(g, hd[0], hd[1], hd[2], c->g.N);
-    CK(cudaGetLastError());
+    CK(run(c, SCFFT_K_RK, [&] {
+      fill3_kernel<<<blocks_for(c->g.N), 256, 0, c->st>>>(g, hd[0], hd[1], hd[2], c->g.N);
+      return cudaGetLastError();
+    }));
   }
-  // stops: kinks of the path, snapshot times and t1, inside (t0, t1]
-  std::vector<double> kinks(c->kt.begin(), c->kt.end());
-  if (c->sin_amp != 0) { kinks.push_back(c->sin_t0); kinks.push_back(c->sin_t1); }
-  std::vector<double> stops;
-  for (double v : kinks) if (v > t0 && v <= t1) stops.push_back(v);
-  for (int i = 0; i < nsnap; ++i) stops.push_back(tsnap[i]);
-  stops.push_back(t1);
-  std::sort(stops.begin(), stops.end());
-  stops.erase(std::unique(stops.begin(), stops.end()), stops.end());
-  auto is_kink = [&](double v) { return std::find(kinks.begin(), kinks.end(), v) != kinks.end(); };
-  // Bogacki-Shampine 3(2): c = (0, 1/2, 3/4, 1); a21 = 1/2; a32 = 3/4; b = (2/9, 1/3, 4/9);
-  // e = b - bhat = (-5/72, 1/12, 1/9, -1/8)
-  const double a21 = 0.5, a32 = 0.75, b1 = 2.0 / 9.0, b2 = 1.0 / 3.0, b3 = 4.0 / 9.0;
-  const double e1 = 2.0 / 9.0 - 7.0 / 24.0, e2 = 1.0 / 3.0 - 0.25, e3 = 4.0 / 9.0 - 1.0 / 3.0, e4 = -0.125;
-  const double rtol = c->opt.rtol, atol = c->opt.atol;
-  scfft_status s;
+  const scfft_stats before = c->stats;
+  c->fsal_valid = false;
   double t = t0, dt = dt0;
-  if ((s = rhs_any(c, t, 0, h, g, k[0], nullptr)) != SCFFT_OK) return s;
-  size_t si = 0;
-  int snap_i = 0;
-  long long acc = 0, rej = 0;
-  const int blocks = blocks_for(n3);
+  int snap_i = 0, nsteps = 0;
   while (t < t1) {
-    while (si < stops.size() && stops[si] <= t) ++si;
-    const double nxt = si < stops.size() ? stops[si] : t1;
-    if (dt_fixed) {
-      if (acc >= nfixed) break;
-      dt = dt_fixed[acc];
-    }
-    double hs = std::min(dt, nxt - t);
-    const bool hits = (hs == nxt - t);
-    const bool end_left = hits && is_kink(nxt);
-    if (!(hs > 1e-14 * std::max(1.0, fabs(t)))) return SCFFT_ESTEP;
-    combine_kernel<<<blocks, 256, 0, c->st>>>(ytmp, h, hs, a21, k[0], 0, nullptr, 0, nullptr, n3);
-    if ((s = rhs_any(c, t + 0.5 * hs, 0, ytmp, g, k[1], nullptr)) != SCFFT_OK) return s;
-    combine_kernel<<<blocks, 256, 0, c->st>>>(ytmp, h, hs, 0.0, k[0], a32, k[1], 0, nullptr, n3);
-    if ((s = rhs_any(c, t + 0.75 * hs, 0, ytmp, g, k[2], nullptr)) != SCFFT_OK) return s;
-    combine_kernel<<<blocks, 256, 0, c->st>>>(ynew, h, hs, b1, k[0], b2, k[1], b3, k[2], n3);
-    if ((s = rhs_any(c, hits ? nxt : t + hs, end_left ? 1 : 0, ynew, g, k[3], nullptr)) != SCFFT_OK) return s;
-    double en = 0.0;
-    if (!dt_fixed) {
-      CK(cudaMemsetAsync(c->errbits, 0, sizeof(unsigned long long), c->st));
-      errnorm_kernel<<<blocks, 256, 0, c->st>>>(h, ynew, hs, e1, k[0], e2, k[1], e3, k[2], e4, k[3], rtol, atol, n3,
-                                               c->errbits);
-      CK(cudaMemcpyAsync(c->herr, c->errbits, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->st));
-      CK(cudaStreamSynchronize(c->st));
-      unsigned long long bits = *c->herr;
-      memcpy(&en, &bits, sizeof(double));
-      if (!(en == en)) return SCFFT_ENONFINITE;
-    }
-    if (en <= 1.0) {
-      t = hits ? nxt : t + hs;
-      CK(cudaMemcpyAsync(h, ynew, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->st));
-      ++acc;
-      if (end_left) {
-        if ((s = rhs_any(c, t, 0, h, g, k[0], nullptr)) != SCFFT_OK) return s;
-      } else {
-        std::swap(k[0], k[3]);
-      }
-      if (hits && snap_i < nsnap && tsnap[snap_i] == nxt) {
-        CK(cudaMemcpyAsync(snaps + (size_t)snap_i * n3, h, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->st));
-        ++snap_i;
-      }
-      if (!dt_fixed) {
-        const double fac = en == 0.0 ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * pow(en, -1.0 / 3.0)));
-        dt = hs * fac;
-      }
-    } else {
-      ++rej;
-      dt = hs * std::max(0.2, 0.9 * pow(en, -1.0 / 3.0));
+    const double tstop = snap_i < nsnap ? tsnap[snap_i] : t1;
+    if (dt_fixed && nsteps >= nfixed) break;
+    CS_(bs23_step(c, &t, &dt, tstop, h, g, dt_fixed ? dt_fixed[nsteps] : 0.0, nullptr));
+    ++nsteps;
+    if (snap_i < nsnap && t == tsnap[snap_i]) {
+      CK(cudaMemcpyAsync(snaps + (size_t)snap_i * n3, h, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->st));
+      ++snap_i;
     }
   }
   CK(cudaStreamSynchronize(c->st));
-  c->stats.accepted += acc;
-  c->stats.rejected += rej;
-  c->stats.t = t;
-  c->stats.dt = dt;
   if (stats) {
     *stats = c->stats;
-    stats->accepted = acc;
-    stats->rejected = rej;
+    stats->accepted = c->stats.accepted - before.accepted;
+    stats->rejected = c->stats.rejected - before.rejected;
+    stats->rhs_calls = c->stats.rhs_calls - before.rhs_calls;
+    stats->iterations = c->stats.iterations - before.iterations;
+    stats->launches = c->stats.launches - before.launches;
   }
   return SCFFT_OK;
 }
@@ -574,6 +714,28 @@ scfft_status scfft_sync(scfft_ctx* c) {
 scfft_status scfft_get_stats(scfft_ctx* c, scfft_stats* out) {
   if (!c || !out) return SCFFT_EINVAL;
   *out = c->stats;
+  return SCFFT_OK;
+}
+
+scfft_status scfft_profile(scfft_ctx* c, int enable) {
+  if (!c) return SCFFT_EINVAL;
+  if (enable && c->pev.empty()) {
+    c->pev.resize(2 * kProfPool);
+    c->pkind.resize(kProfPool);
+    for (auto& e : c->pev) CK(cudaEventCreate(&e));
+  }
+  if (enable) {
+    CK(prof_flush(c));
+    for (int k = 0; k < SCFFT_NKINDS; ++k) { c->pms[k] = 0; c->pcnt[k] = 0; }
+  }
+  c->prof_on = enable != 0;
+  return SCFFT_OK;
+}
+
+scfft_status scfft_profile_read(scfft_ctx* c, long long* counts, double* ms) {
+  if (!c || !counts || !ms) return SCFFT_EINVAL;
+  CK(prof_flush(c));
+  for (int k = 0; k < SCFFT_NKINDS; ++k) { counts[k] = c->pcnt[k]; ms[k] = c->pms[k]; }
   return SCFFT_OK;
 }
 

@@ -143,3 +143,72 @@ def test_rhs_fp32_error_is_stated():
     ctx.rhs(0.4, dev(h).reshape(-1), dev(g0).reshape(-1), hd)
     err = rel(host(hd).reshape(h.shape), ref.hdot)
     assert err < 2e-4, err
+
+
+def _cube_cfg():
+    cfg = I.config("cube16")
+    prob = O.Problem(O.Grid(cfg.n, cfg.L), cfg.mask, O.Material(n=cfg.n_power, rho_out=cfg.rho_out),
+                     O.FieldPath(cfg.knots_t, cfg.knots_he))
+    return cfg, prob
+
+
+def test_integrate_fixed_steps_fp64_matches_oracle():
+    """Parity tier T2: fixed dt list, Eq. 5 iterated to its fixed point."""
+    cfg, prob = _cube_cfg()
+    dts = [0.002, 0.003, 0.004, 0.004, 0.005, 0.005]
+    ctx = S.Context(cfg.n, cfg.L, n_power=cfg.n_power, rho_out=cfg.rho_out, delta_it=1e-13, max_iter=80)
+    ctx.set_geometry(cfg.mask)
+    ctx.set_field_path(cfg.knots_t, cfg.knots_he)
+    ctx.precompute_kernel()
+    N = int(np.prod(cfg.n))
+    h = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    t1 = float(np.sum(dts))
+    st = ctx.integrate(0.0, t1, dts[0], h, dt_fixed=dts)
+    ref = O.integrate(prob, 0.0, t1, np.zeros((3,) + prob.grid.shape), rtol=1e-6, atol=1e-9, dt0=dts[0],
+                      delta_it=1e-13, max_iter=80, dt_list=dts)
+    assert st["accepted"] == len(dts) == ref.accepted
+    assert rel(host(h).reshape(ref.y.shape), ref.y) < 1e-10
+
+
+def test_integrate_adaptive_fp64_tracks_oracle():
+    """Parity tier T3: adaptive BS23 with the paper's iteration tolerance; the
+    step sequences may differ, the states agree to a small multiple of rtol."""
+    cfg, prob = _cube_cfg()
+    rtol, atol = 1e-5, 1e-8
+    ctx = S.Context(cfg.n, cfg.L, n_power=cfg.n_power, rho_out=cfg.rho_out, delta_it=2e-5, max_iter=100,
+                    rtol=rtol, atol=atol)
+    ctx.set_geometry(cfg.mask)
+    ctx.set_field_path(cfg.knots_t, cfg.knots_he)
+    ctx.precompute_kernel()
+    N = int(np.prod(cfg.n))
+    h = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    snaps = torch.zeros(2 * 3 * N, dtype=torch.float64, device="cuda")
+    st = ctx.integrate(0.0, 0.2, 1e-4, h, tsnap=[0.1, 0.2], snaps=snaps)
+    ref = O.integrate(prob, 0.0, 0.2, np.zeros((3,) + prob.grid.shape), rtol=rtol, atol=atol, dt0=1e-4,
+                      snapshots=[0.1, 0.2])
+    s = host(snaps).reshape((2,) + ref.y.shape)
+    for i, (t, y) in enumerate(ref.snaps):
+        assert rel(s[i], y) < 20 * rtol, (t, rel(s[i], y))
+    assert abs(st["accepted"] - ref.accepted) <= max(3, 0.2 * ref.accepted)
+
+
+def test_step_matches_integrate_and_counts_launches():
+    cfg, prob = _cube_cfg()
+    ctx = S.Context(cfg.n, cfg.L, n_power=cfg.n_power, rho_out=cfg.rho_out, delta_it=2e-5, max_iter=100,
+                    rtol=1e-5, atol=1e-8)
+    ctx.set_geometry(cfg.mask)
+    ctx.set_field_path(cfg.knots_t, cfg.knots_he)
+    ctx.precompute_kernel()
+    N = int(np.prod(cfg.n))
+    h = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    warm = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    warm.view(3, N)[2] = 0.5
+    t, dt = 0.0, 1e-4
+    s0 = ctx.stats()
+    while t < 0.05:
+        t, dt, _ = ctx.step(t, dt, 0.05, h, warm)
+    assert t == 0.05
+    s1 = ctx.stats()
+    assert s1["launches"] > s0["launches"] and s1["rhs_calls"] > s0["rhs_calls"]
+    ref = O.integrate(prob, 0.0, 0.05, np.zeros((3,) + prob.grid.shape), rtol=1e-5, atol=1e-8, dt0=1e-4)
+    assert rel(host(h).reshape(ref.y.shape), ref.y) < 2e-4
