@@ -43,7 +43,8 @@ typedef enum {
   SCFFT_ESTEP = 5,     /* integrator step size fell below its floor */
   SCFFT_ENONFINITE = 6,/* NaN/Inf met in a residual or error norm */
   SCFFT_ETIMEOUT = 7,  /* reserved: a bounded device wait gave up */
-  SCFFT_ESTATE = 8     /* call out of order (e.g. rhs before precompute_kernel) */
+  SCFFT_ESTATE = 8,    /* call out of order (e.g. rhs before precompute_kernel) */
+  SCFFT_ESIZE = 9      /* problem larger than a fixed, preallocated maximum */
 } scfft_status;
 
 /* Arithmetic of the FFTs and pointwise steps.  The integrator state, its stage
@@ -190,6 +191,24 @@ enum {
 scfft_status scfft_profile(scfft_ctx* ctx, int enable);
 scfft_status scfft_profile_read(scfft_ctx* ctx, long long* counts, double* ms);
 const char* scfft_kind_name(int kind);
+
+/* Allocation-free spectral curl: out = curl_S f, the same result as
+ * scfft_curl (FP64) on the same grid and sigma_scale, for callers that cannot
+ * allocate device memory when they need it (inside a region where cudaMalloc
+ * is forbidden or unsafe, under a fixed memory budget, or under a host
+ * framework that owns every allocation).  This entry point has no counterpart
+ * in the paper; it only repackages the curl.
+ * It needs no context: grid (host) gives the sizes and half extents;
+ * stream is a cudaStream_t (NULL = legacy default stream); f, out: device,
+ * 3*N doubles, not aliased.  Its scratch is one static 8 MiB device array per
+ * GPU (grids up to 64^3 nodes fit); larger grids return SCFFT_ESIZE and
+ * nothing is queued.  It calls no allocator.  The first call on a device looks
+ * up that array's device address; make that first call before any stream
+ * capture.  Calls share the array: calls that overlap on the GPU (other
+ * streams or host threads on the same device) race and must be serialized.
+ * Asynchronous on stream. */
+scfft_status scfft_curl_noalloc(const scfft_grid* grid, double sigma_scale, const double* f, double* out,
+                                void* stream);
 
 /* Wait for the stream; returns the first latched device-side status. */
 scfft_status scfft_sync(scfft_ctx* ctx);

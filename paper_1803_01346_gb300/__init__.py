@@ -30,7 +30,7 @@ _LIBNAME = "libscfft.so"
 EXPORTS = ("scfft_create", "scfft_set_geometry", "scfft_set_jc_map", "scfft_set_field_path",
            "scfft_precompute_kernel", "scfft_rhs", "scfft_curl", "scfft_phi", "scfft_integrate",
            "scfft_step", "scfft_profile", "scfft_profile_read", "scfft_kind_name",
-           "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy")
+           "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy", "scfft_curl_noalloc")
 
 NKINDS = 14
 
@@ -107,6 +107,7 @@ def load_library(path: Optional[str] = None):
         "scfft_get_stats": (I, [P, ctypes.POINTER(_Stats)]),
         "scfft_status_string": (ctypes.c_char_p, [I]),
         "scfft_destroy": (V, [P]),
+        "scfft_curl_noalloc": (I, [ctypes.POINTER(_Grid), D, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -125,6 +126,23 @@ def _ptr(x) -> int:
     if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
         raise TypeError("expected a contiguous float64 CUDA tensor")
     return x.data_ptr()
+
+
+def curl_noalloc(n: Sequence[int], L: Sequence[float], f, out, sigma_scale: float = 1.0, stream=None):
+    """curl_S f into out without any allocation (FP64, grids up to 64^3 nodes).
+
+    For callers that cannot allocate device memory when they need the curl;
+    it uses one static device array per GPU, so calls that overlap on the GPU
+    race.  Raises ScfftError (status 9) for grids beyond the fixed maximum."""
+    lib = load_library()
+    g = _Grid(int(n[0]), int(n[1]), int(n[2]), float(L[0]), float(L[1]), float(L[2]))
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    code = lib.scfft_curl_noalloc(ctypes.byref(g), float(sigma_scale), _ptr(f), _ptr(out),
+                                  ctypes.c_void_p(int(stream) if stream else 0))
+    if code != 0:
+        raise ScfftError(code, "scfft_curl_noalloc", lib.scfft_status_string(code).decode())
 
 
 class Context:

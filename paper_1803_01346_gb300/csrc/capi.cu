@@ -490,6 +490,7 @@ const char* scfft_status_string(scfft_status s) {
     case SCFFT_ENONFINITE: return "non-finite value in a residual or error norm";
     case SCFFT_ETIMEOUT: return "bounded device wait timed out";
     case SCFFT_ESTATE: return "call out of order";
+    case SCFFT_ESIZE: return "problem larger than the fixed preallocated maximum";
   }
   return "unknown status";
 }
