@@ -564,6 +564,7 @@ template <typename T> static int col_tile() { return sizeof(T) == 4 ? 16 : 8; }
 template <typename T>
 cudaError_t launch_y(const Launch<T>& L, bool padded, bool inverse, bool check_done) {
   typedef typename cplx_of<T>::type V;
+  if constexpr (sizeof(T) == 4) return launch_y_reg(L, padded, inverse, check_done);
   const Geo& g = L.g;
   YArgs<T> a{};
   a.base = padded ? L.w->Pd : L.w->U;
@@ -594,6 +595,7 @@ cudaError_t launch_y(const Launch<T>& L, bool padded, bool inverse, bool check_d
 template <typename T>
 static cudaError_t launch_z(const Launch<T>& L, bool padded, bool check_done, double scale) {
   typedef typename cplx_of<T>::type V;
+  if constexpr (sizeof(T) == 4) return launch_z_reg(L, padded, check_done, scale);
   const Geo& g = L.g;
   ZArgs<T> a{};
   a.base = padded ? L.w->Pd : L.w->U;

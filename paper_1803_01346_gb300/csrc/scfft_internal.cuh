@@ -94,6 +94,10 @@ template <typename T> cudaError_t launch_kernel_spectrum(const Launch<T>& L, dou
                                                          double sigma, double* scratch);
 template <typename T> cudaError_t launch_convert(const double* src, T* dst, long long n, cudaStream_t st);
 
+// Register-resident FP32 y and z passes (passes_reg.cu); the FP32 path uses these.
+cudaError_t launch_y_reg(const Launch<float>& L, bool padded, bool inverse, bool check_done);
+cudaError_t launch_z_reg(const Launch<float>& L, bool padded, bool check_done, double scale);
+
 FftPlan make_plan(int L);
 bool length_supported(int L);
 

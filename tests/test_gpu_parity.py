@@ -85,6 +85,35 @@ def test_phi_fp64_matches_oracle(n, L):
     assert rel(host(out).reshape(j.shape), O.phi_hockney(j, g)) < 1e-12
 
 
+# every FFT length on both grids: 16 32 48 64 96 128 (unpadded), 32 ... 256 (padded)
+GRIDS32 = [((16, 32, 48), (0.8, 1.0, 1.2)),
+           ((48, 64, 96), (1.0, 1.1, 1.5)),
+           ((32, 96, 128), (0.7, 1.2, 1.6)),
+           ((64, 128, 16), (1.0, 1.6, 0.5))]
+
+
+@pytest.mark.parametrize("n,L", GRIDS32)
+def test_curl_fp32_matches_oracle(n, L):
+    """FP32 register passes vs the FP64 oracle: FP32 FFT round-off only."""
+    g = O.Grid(n, L)
+    f = I.random_field((3,) + g.shape, 17)
+    ctx = S.Context(n, L, precision=S.PREC_F32)
+    out = torch.empty(f.size, dtype=torch.float64, device="cuda")
+    ctx.curl(dev(f).reshape(-1), out)
+    assert rel(host(out).reshape(f.shape), O.curl_s(f, g)) < 2e-5
+
+
+@pytest.mark.parametrize("n,L", GRIDS32)
+def test_phi_fp32_matches_oracle(n, L):
+    g = O.Grid(n, L)
+    j = I.random_field((3,) + g.shape, 18)
+    ctx = S.Context(n, L, precision=S.PREC_F32)
+    ctx.precompute_kernel()
+    out = torch.empty(j.size, dtype=torch.float64, device="cuda")
+    ctx.phi(dev(j).reshape(-1), out)
+    assert rel(host(out).reshape(j.shape), O.phi_hockney(j, g)) < 2e-5
+
+
 def test_phi_fp64_matches_direct_sum():
     n, L = (16, 16, 16), (1.0, 1.1, 0.9)
     g = O.Grid(n, L)
