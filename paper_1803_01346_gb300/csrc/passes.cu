@@ -508,6 +508,8 @@ template <typename T>
 cudaError_t launch_x(const Launch<T>& L, XMode mode, const PointParams& pp, const double* src_f64, double* dst_f64,
                      const double* warm, int in_buf, int out_buf, bool check_done) {
   typedef typename cplx_of<T>::type V;
+  if constexpr (sizeof(T) == 4)
+    return launch_x_reg(L, mode, pp, src_f64, dst_f64, warm, in_buf, out_buf, check_done);
   XArgs<T> a{};
   const Geo& g = L.g;
   a.g = g;

@@ -307,3 +307,404 @@ cudaError_t launch_z_reg(const Launch<float>& L, bool padded, bool check_done, d
 }
 
 }  // namespace scfft
+
+// ============================================================================
+// x passes (FP32): C2R of a half-spectrum row pair, the node-wise step, R2C.
+//
+// Two real rows a, b of one component travel as z = a + i b.  The C2R of
+// length Li = R1i R2i leaves thread (p, k2) with z at x = k2 + R2i k1; with
+// the R2C split R1o = R2i those are exactly the inputs n1' + R1o n2' (n1' = k2,
+// n2' = k1) of the forward transform of length Lo = R1o R2o, so the node-wise
+// step and the R2C start from the C2R's registers.  A last pass through
+// shared memory pairs Z[k] with Z[Lo-k] to separate the two rows' spectra.
+// ============================================================================
+namespace scfft {
+
+struct XRArgs {
+  Geo g;
+  const float2* spec_in;
+  int in_rows, in_sx;
+  float2* spec_out;
+  int out_rows, out_sx;
+  const float2* tw_in;
+  const float2* tw_out;
+  const double* src_f64;
+  double* dst_f64;
+  const double* warm;
+  const uint8_t* mask;
+  const float* jc;
+  const float* hold;
+  float* hnew;
+  PointParams pp;
+  Ctrl* ctrl;
+  double* partials;
+  int check_done;
+  int out_buf;
+};
+
+namespace {
+
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+template <int MODE, int R1i, int R2i, int R2o> struct XS {
+  static constexpr bool C2R = !(MODE == X_FWD_F64 || MODE == X_PAD_F64);
+  static constexpr bool R2C = !(MODE == X_TO_F64 || MODE == X_CROP_F64);
+  static constexpr bool PADIN = (MODE == X_UPDATE || MODE == X_CROP_F64);   // C2R length 2nx, keep x < nx
+  static constexpr bool PADOUT = (MODE == X_MASKPAD || MODE == X_PAD_F64);  // R2C length 2nx, input x < nx
+  static constexpr int R1o = R2i;
+  static constexpr int Li = R1i * R2i;
+  static constexpr int Lo = R1o * R2o;
+  static constexpr int TP = cmax(cmax(R1i, R2i), R2o);
+  static constexpr int KX = PADIN ? R1i / 2 : R1i;  // k1 slots that hold x < nx after the C2R
+  static constexpr int TB = cmax(cmax(3 * R2i * (R1i + 1), 3 * R2o * (R1o + 1)), 3 * Lo);  // smem per pair
+};
+
+__device__ __forceinline__ float rho_of(float jx, float jy, float jz, bool in, float jcv, const PointParams& pp) {
+  if (!in) return (float)pp.rho_out;
+  const float jn = sqrtf(jx * jx + jy * jy + jz * jz);
+  const float n = (float)pp.n, e0 = (float)pp.e0;
+  if (jn == 0.f) return n == 1.f ? e0 / jcv : 0.f;
+  return (e0 / jcv) * exp2f((n - 1.f) * log2f(jn / jcv));
+}
+
+}  // namespace
+
+template <int MODE, int R1i, int R2i, int R2o, int P>
+__global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP)
+    xpass_reg_kernel(const XRArgs a) {
+  typedef XS<MODE, R1i, R2i, R2o> S;
+  constexpr int TP = S::TP, R1o = S::R1o, Li = S::Li, Lo = S::Lo;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (a.check_done && a.ctrl->done) return;
+  float2* twi = reinterpret_cast<float2*>(smem_raw);
+  float2* two = twi + (Li > 0 ? Li : 1);
+  float2* sm = two + (Lo > 0 ? Lo : 1);
+  const int tid = threadIdx.x, nth = P * TP;
+  const int p = tid / TP, r = tid % TP;
+  if (S::C2R)
+    for (int i = tid; i < Li; i += nth) twi[i] = a.tw_in[i];
+  if (S::R2C)
+    for (int i = tid; i < Lo; i += nth) two[i] = a.tw_out[i];
+  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+  const long long N = a.g.N;
+  const int npairs = ny * nz / 2;
+  const int gp = blockIdx.x * P + p;  // global row pair
+  const bool pok = gp < npairs;
+  const int qa = 2 * (pok ? gp : 0);  // row a (flattened z*ny + y); row b = qa + 1
+  const int z = qa / ny, ya = qa - z * ny;
+  float2* smp = sm + p * S::TB;  // this pair's shared slice
+
+  // registers carried from the C2R to the R2C: z at x = r + R2i k1
+  float2 w[3][S::C2R ? cmax(R1i, R2o) : R2o];
+
+  if constexpr (S::C2R) {
+    // ---- stage A: thread (p, n1 < R1i) builds z-spectrum entries k = n1 + R1i n2
+    float2 v[3][R2i];
+    const int n1 = r;
+    if (n1 < R1i) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float2* ra = a.spec_in + ((size_t)(q * nz + z) * a.in_rows + ya) * a.in_sx;
+        const float2* rb = ra + a.in_sx;
+#pragma unroll
+        for (int n2 = 0; n2 < R2i; ++n2) {
+          const int k = n1 + R1i * n2;
+          const bool lo = k <= Li / 2;
+          const int kk = lo ? k : Li - k;
+          float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+          if (pok) { A = ra[kk]; B = rb[kk]; }
+          if (kk == 0 || kk == Li / 2) { A.y = 0.f; B.y = 0.f; }
+          v[q][n2] = lo ? make_float2(A.x - B.y, A.y + B.x) : make_float2(A.x + B.y, B.x - A.y);
+        }
+      }
+    }
+    __syncthreads();  // twiddles staged
+    if (n1 < R1i) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        DFT<R2i, true, float2>::run(v[q]);
+#pragma unroll
+        for (int k2 = 0; k2 < R2i; ++k2) {
+          const float2 t = k2 == 0 ? v[q][k2] : cmulc(v[q][k2], twi[n1 * k2]);
+          smp[(q * R2i + k2) * (R1i + 1) + n1] = t;
+        }
+      }
+    }
+    __syncthreads();
+    // ---- stage B: thread (p, k2 < R2i): z at x = k2 + R2i k1
+    const int k2 = r;
+    if (k2 < R2i) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+#pragma unroll
+        for (int m = 0; m < R1i; ++m) w[q][m] = smp[(q * R2i + k2) * (R1i + 1) + m];
+        DFT<R1i, true, float2>::run(w[q]);
+      }
+    }
+    __syncthreads();  // transpose buffer free
+  } else {
+    // ---- real f64 rows straight into the R2C's stage-A layout
+    const int n1 = r;
+    if (n1 < R1o) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int n2 = 0; n2 < R2o; ++n2) {
+          const int x = n1 + R1o * n2;
+          float2 zv = make_float2(0.f, 0.f);
+          if (pok && (!S::PADOUT || n2 < R2o / 2)) {
+            const size_t na = (size_t)qa * nx + x;
+            zv = make_float2((float)a.src_f64[q * N + na], (float)a.src_f64[q * N + na + nx]);
+          }
+          w[q][n2] = zv;
+        }
+    }
+    __syncthreads();  // twiddles staged
+  }
+
+  // ---- node-wise step on x = r + R2i k1 (C2R modes)
+  double part = 0.0;
+  if constexpr (S::C2R) {
+    const int k2 = r;
+    if (k2 < R2i && pok) {
+      const PointParams& pp = a.pp;
+#pragma unroll
+      for (int k1 = 0; k1 < S::KX; ++k1) {
+        const int x = k2 + R2i * k1;
+        const size_t na = (size_t)qa * nx + x, nb = na + nx;
+        if (MODE == X_POWERLAW) {
+          const bool ia = a.mask[na], ib = a.mask[nb];
+          const float ca = a.jc ? a.jc[na] : (float)pp.jc, cb = a.jc ? a.jc[nb] : (float)pp.jc;
+          const float ra = rho_of(w[0][k1].x, w[1][k1].x, w[2][k1].x, ia, ca, pp);
+          const float rb = rho_of(w[0][k1].y, w[1][k1].y, w[2][k1].y, ib, cb, pp);
+#pragma unroll
+          for (int q = 0; q < 3; ++q) w[q][k1] = make_float2(w[q][k1].x * ra, w[q][k1].y * rb);
+        } else if (MODE == X_ASSEMBLE) {
+          const bool ia = a.mask[na], ib = a.mask[nb];
+          const float s = -(float)pp.inv_mu0;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const float va = ia ? s * w[q][k1].x : (float)a.warm[q * N + na];
+            const float vb = ib ? s * w[q][k1].y : (float)a.warm[q * N + nb];
+            a.hnew[q * N + na] = va;
+            a.hnew[q * N + nb] = vb;
+            w[q][k1] = make_float2(va, vb);
+          }
+        } else if (MODE == X_MASKPAD) {
+          const bool ia = a.mask[na], ib = a.mask[nb];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) w[q][k1] = make_float2(ia ? w[q][k1].x : 0.f, ib ? w[q][k1].y : 0.f);
+        } else if (MODE == X_UPDATE) {
+          const bool ia = a.mask[na], ib = a.mask[nb];
+          double da = 0.0, db = 0.0;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const float oa = a.hold[q * N + na], ob = a.hold[q * N + nb];
+            const float he = (float)pp.hedot[q];
+            const float va = ia ? oa : he + w[q][k1].x;
+            const float vb = ib ? ob : he + w[q][k1].y;
+            a.hnew[q * N + na] = va;
+            a.hnew[q * N + nb] = vb;
+            const double dda = (double)va - (double)oa, ddb = (double)vb - (double)ob;
+            da += dda * dda;
+            db += ddb * ddb;
+            w[q][k1] = make_float2(va, vb);
+          }
+          if (!ia) part += sqrt(da);
+          if (!ib) part += sqrt(db);
+        } else {  // X_TO_F64, X_CROP_F64
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            a.dst_f64[q * N + na] = (double)w[q][k1].x;
+            a.dst_f64[q * N + nb] = (double)w[q][k1].y;
+          }
+        }
+      }
+    }
+  }
+
+  if constexpr (S::R2C) {
+    // ---- R2C stage A': thread (p, n1' = r < R1o) holds z[n1' + R1o n2'], n2' < R2o
+    const int n1 = r;
+    if (n1 < R1o) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        float2 u[R2o];
+#pragma unroll
+        for (int n2 = 0; n2 < R2o; ++n2) {
+          if (S::C2R) u[n2] = (n2 < S::KX && !(S::PADOUT && n2 >= R2o / 2)) ? w[q][n2] : make_float2(0.f, 0.f);
+          else u[n2] = w[q][n2];
+        }
+        DFT<R2o, false, float2>::run(u);
+#pragma unroll
+        for (int k2 = 0; k2 < R2o; ++k2) {
+          const float2 t = k2 == 0 ? u[k2] : cmul(u[k2], two[n1 * k2]);
+          smp[(q * R2o + k2) * (R1o + 1) + n1] = t;
+        }
+      }
+    }
+    __syncthreads();
+    // ---- stage B': thread (p, k2' < R2o): Z[k2' + R2o k1']
+    float2 Zr[3][R1o];
+    const int k2 = r;
+    if (k2 < R2o) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+#pragma unroll
+        for (int m = 0; m < R1o; ++m) Zr[q][m] = smp[(q * R2o + k2) * (R1o + 1) + m];
+        DFT<R1o, false, float2>::run(Zr[q]);
+      }
+    }
+    __syncthreads();  // transpose buffer free
+    if (k2 < R2o) {
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int k1 = 0; k1 < R1o; ++k1) smp[q * Lo + k2 + R2o * k1] = Zr[q][k1];
+    }
+    __syncthreads();
+    // ---- separate the two rows: A = (Z[k] + conj Z[Lo-k])/2, B = (Z[k] - conj Z[Lo-k])/(2i)
+    constexpr int H = Lo / 2 + 1;
+    for (int idx = tid; idx < P * 3 * 2 * H; idx += nth) {
+      const int k = idx % H, rr = (idx / H) % 2, q = (idx / (2 * H)) % 3, pp2 = idx / (6 * H);
+      const int g2 = blockIdx.x * P + pp2;
+      if (g2 >= npairs) continue;
+      const float2* zs = sm + pp2 * S::TB + q * Lo;
+      const float2 Zk = zs[k], Zm = zs[(Lo - k) % Lo];
+      const float2 o = rr == 0 ? make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y))
+                               : make_float2(0.5f * (Zk.y + Zm.y), 0.5f * (Zm.x - Zk.x));
+      const int qrow = 2 * g2 + rr;
+      const int zz = qrow / ny, yy = qrow - zz * ny;
+      a.spec_out[((size_t)(q * nz + zz) * a.out_rows + yy) * a.out_sx + k] = o;
+    }
+  }
+
+  if (MODE == X_UPDATE) {
+    __shared__ double red[32];
+    __shared__ int am_last;
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int i = 0; i < (nth + 31) / 32; ++i) s += red[i];
+      a.partials[blockIdx.x] = s;
+      __threadfence();
+      const unsigned prev = atomicAdd(&a.ctrl->counter, 1u);
+      am_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (am_last) {
+      __threadfence();
+      double s = 0.0;
+      for (int i = tid; i < (int)gridDim.x; i += nth) s += __ldcg(&a.partials[i]);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      __syncthreads();
+      if ((tid & 31) == 0) red[tid >> 5] = s;
+      __syncthreads();
+      if (tid == 0) {
+        double tot = 0.0;
+        for (int i = 0; i < (nth + 31) / 32; ++i) tot += red[i];
+        const double rres = tot * a.pp.inv_nout;
+        Ctrl* c = a.ctrl;
+        c->residual = rres;
+        c->iters = a.pp.iter + 1;
+        c->cur = a.out_buf;
+        const bool finite = isfinite(rres);
+        if (!finite) c->status = 6;  // SCFFT_ENONFINITE
+        c->done = (!finite || rres < a.pp.tol) ? 1 : 0;
+        c->counter = 0;
+      }
+    }
+  }
+  if (MODE == X_ASSEMBLE && blockIdx.x == 0 && tid == 0) {
+    a.ctrl->done = 0;
+    a.ctrl->iters = 0;
+    a.ctrl->cur = 0;
+    a.ctrl->counter = 0;
+    a.ctrl->residual = 0.0;
+  }
+}
+
+namespace {
+
+constexpr int kPairs = 8;  // row pairs per CTA (x 3 components)
+
+template <int MODE, int R1i, int R2i, int R2o>
+cudaError_t go_x(const XRArgs& a, cudaStream_t st) {
+  typedef XS<MODE, R1i, R2i, R2o> S;
+  const size_t smem = sizeof(float2) * ((S::Li > 0 ? S::Li : 1) + (S::Lo > 0 ? S::Lo : 1) + kPairs * S::TB);
+  auto k = xpass_reg_kernel<MODE, R1i, R2i, R2o, kPairs>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int npairs = a.g.ny * a.g.nz / 2;
+  k<<<(npairs + kPairs - 1) / kPairs, kPairs * S::TP, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Splits per unpadded length n: C2R(n) = (a, b), C2R(2n) = (c, d); the R2C
+// splits follow from R1o = R2i (see the section comment).
+template <int MODE> cudaError_t go_x_n(int n, const XRArgs& a, cudaStream_t st) {
+#define XN(NN, A_, B_, C_, D_)                                                                   \
+  case NN:                                                                                       \
+    if constexpr (MODE == X_FWD_F64) return go_x<MODE, 1, B_, A_>(a, st);                        \
+    else if constexpr (MODE == X_PAD_F64) return go_x<MODE, 1, B_, 2 * A_>(a, st);               \
+    else if constexpr (MODE == X_POWERLAW || MODE == X_ASSEMBLE) return go_x<MODE, A_, B_, A_>(a, st); \
+    else if constexpr (MODE == X_MASKPAD) return go_x<MODE, A_, B_, 2 * A_>(a, st);              \
+    else if constexpr (MODE == X_TO_F64) return go_x<MODE, A_, B_, 1>(a, st);                    \
+    else if constexpr (MODE == X_UPDATE) return go_x<MODE, C_, D_, C_ / 2>(a, st);               \
+    else return go_x<MODE, C_, D_, 1>(a, st);
+  switch (n) {
+    XN(16, 4, 4, 8, 4)
+    XN(32, 4, 8, 8, 8)
+    XN(48, 4, 12, 8, 12)
+    XN(64, 4, 16, 8, 16)
+    XN(96, 8, 12, 16, 12)
+    XN(128, 8, 16, 16, 16)
+  }
+#undef XN
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_x_reg(const Launch<float>& L, XMode mode, const PointParams& pp, const double* src_f64,
+                         double* dst_f64, const double* warm, int in_buf, int out_buf, bool check_done) {
+  const Geo& g = L.g;
+  XRArgs a{};
+  a.g = g;
+  const bool pin = (mode == X_UPDATE || mode == X_CROP_F64);
+  const bool pout = (mode == X_MASKPAD || mode == X_PAD_F64);
+  a.spec_in = pin ? L.w->Pd : L.w->U;
+  a.in_rows = pin ? 2 * g.ny : g.ny;
+  a.in_sx = pin ? g.sxp : g.sxu;
+  a.spec_out = pout ? L.w->Pd : L.w->U;
+  a.out_rows = pout ? 2 * g.ny : g.ny;
+  a.out_sx = pout ? g.sxp : g.sxu;
+  a.tw_in = pin ? L.w->twp[0] : L.w->twu[0];
+  a.tw_out = pout ? L.w->twp[0] : L.w->twu[0];
+  a.src_f64 = src_f64;
+  a.dst_f64 = dst_f64;
+  a.warm = warm;
+  a.mask = L.mask;
+  a.jc = L.w->jc;
+  a.hold = L.w->Hd[in_buf];
+  a.hnew = L.w->Hd[out_buf];
+  a.pp = pp;
+  a.ctrl = L.ctrl;
+  a.partials = L.partials;
+  a.check_done = check_done ? 1 : 0;
+  a.out_buf = out_buf;
+  switch (mode) {
+    case X_FWD_F64: return go_x_n<X_FWD_F64>(g.nx, a, L.st);
+    case X_POWERLAW: return go_x_n<X_POWERLAW>(g.nx, a, L.st);
+    case X_ASSEMBLE: return go_x_n<X_ASSEMBLE>(g.nx, a, L.st);
+    case X_MASKPAD: return go_x_n<X_MASKPAD>(g.nx, a, L.st);
+    case X_UPDATE: return go_x_n<X_UPDATE>(g.nx, a, L.st);
+    case X_TO_F64: return go_x_n<X_TO_F64>(g.nx, a, L.st);
+    case X_PAD_F64: return go_x_n<X_PAD_F64>(g.nx, a, L.st);
+    case X_CROP_F64: return go_x_n<X_CROP_F64>(g.nx, a, L.st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace scfft

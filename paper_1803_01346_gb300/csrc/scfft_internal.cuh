@@ -97,6 +97,8 @@ template <typename T> cudaError_t launch_convert(const double* src, T* dst, long
 // Register-resident FP32 y and z passes (passes_reg.cu); the FP32 path uses these.
 cudaError_t launch_y_reg(const Launch<float>& L, bool padded, bool inverse, bool check_done);
 cudaError_t launch_z_reg(const Launch<float>& L, bool padded, bool check_done, double scale);
+cudaError_t launch_x_reg(const Launch<float>& L, XMode mode, const PointParams& pp, const double* src_f64,
+                         double* dst_f64, const double* warm, int in_buf, int out_buf, bool check_done);
 
 FftPlan make_plan(int L);
 bool length_supported(int L);

@@ -161,6 +161,24 @@ def test_rhs_fp64_early_stop_and_jc_map():
     assert rel(host(hd).reshape(h.shape), ref.hdot) < 1e-10
 
 
+@pytest.mark.parametrize("n,L", [((16, 32, 48), (0.8, 1.0, 1.2)), ((48, 64, 96), (1.0, 1.1, 1.5)),
+                                 ((96, 32, 16), (1.5, 0.6, 0.4)), ((128, 16, 32), (1.6, 0.3, 0.6)),
+                                 ((64, 48, 32), (1.0, 0.8, 0.6))])
+def test_rhs_fp32_fixed_iterations_all_x_lengths(n, L):
+    """FP32 x passes of every length (power law, assembly, mask + pad, Eq. 5
+    update) against the oracle, fixed iteration count; FP32 round-off only."""
+    mask = I.cube(n, L, 0.6 * min(L) * 2)
+    ctx, prob = make(n, L, mask, n_power=15.0, prec=S.PREC_F32, max_iter=3)
+    h = _state(prob, 23)
+    g0 = I.random_field(h.shape, 24, 0.1)
+    ref = O.rhs(prob, 0.4, h, g0, delta_it=0.0, max_iter=3)
+    hd = torch.empty(h.size, dtype=torch.float64, device="cuda")
+    it = ctx.rhs(0.4, dev(h).reshape(-1), dev(g0).reshape(-1), hd)
+    assert it == 3
+    err = rel(host(hd).reshape(h.shape), ref.hdot)
+    assert err < 2e-4, err
+
+
 def test_rhs_fp32_error_is_stated():
     n, L = (32, 32, 32), (1.0, 1.0, 1.0)
     mask = I.sphere(n, L, 0.6)
