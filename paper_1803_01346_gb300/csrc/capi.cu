@@ -46,6 +46,16 @@ struct scfft_ctx {
   const double* fsal_g = nullptr;
   unsigned long long* errbits = nullptr;  // device
   unsigned long long* herr = nullptr;     // pinned
+  // FP32-path integrator: stage derivatives, stage state, increment (FP32),
+  // candidate state and Kahan compensation of the accepted sums (FP64)
+  float* ib32 = nullptr;
+  float* k32[4] = {nullptr, nullptr, nullptr, nullptr};
+  float* ytmp32 = nullptr;
+  float* g32 = nullptr;
+  float* d32 = nullptr;
+  double* ynew64 = nullptr;
+  double* comp64 = nullptr;
+  const float* last32 = nullptr;  // output of the most recent rhs (the next warm start)
   scfft_stats stats{};
   // profiling
   bool prof_on = false;
@@ -246,20 +256,47 @@ template <typename T> cudaError_t iteration(scfft_ctx* c, const Launch<T>& L, Po
              [&] { return launch_x<T>(L, X_UPDATE, pp, nullptr, nullptr, nullptr, i & 1, (i + 1) & 1, chk); });
 }
 
+// Inputs and outputs of one rhs: FP64 arrays (public entry points, the FP64
+// integrator) or FP32 arrays (stages of the FP32 integrator).
+struct RhsIO {
+  const double* h64 = nullptr;
+  const float* h32 = nullptr;
+  const double* warm64 = nullptr;
+  const float* warm32 = nullptr;
+  double* out64 = nullptr;       // dh/dt
+  double* warm_out64 = nullptr;  // dh/dt again, as the next warm start
+  float* out32 = nullptr;
+};
+
+__global__ void finalize_f32_kernel(const float* __restrict__ h0, const float* __restrict__ h1, const Ctrl* ctrl,
+                                    float* __restrict__ out, long long n3) {
+  const float* src = ctrl->cur ? h1 : h0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n3; i += (long long)gridDim.x * blockDim.x)
+    out[i] = src[i];
+}
+
 template <typename T>
-scfft_status rhs_impl(scfft_ctx* c, double t, int left, const double* h, double* warm, double* hdot, int* iters_out) {
+cudaError_t x_io(const Launch<T>& L, XMode mode, const PointParams& pp, const RhsIO& io) {
+  if constexpr (sizeof(T) == 4)
+    return launch_x_reg_io(L, mode, pp, io.h64, io.h32, nullptr, io.warm64, io.warm32, 0, 0, false);
+  else
+    return launch_x<T>(L, mode, pp, io.h64, nullptr, io.warm64, 0, 0, false);
+}
+
+template <typename T>
+scfft_status rhs_impl(scfft_ctx* c, double t, int left, const RhsIO& io, int* iters_out) {
   Launch<T> L = launch_of<T>(c);
   PointParams pp = base_params(c);
   hedot_at(c, t, left, pp.hedot);
   const double hn = sqrt(pp.hedot[0] * pp.hedot[0] + pp.hedot[1] * pp.hedot[1] + pp.hedot[2] * pp.hedot[2]);
   pp.tol = c->opt.delta_it * (hn > 1.0 ? hn : 1.0);
   // pre-stage: j = curl h; e = rho(j) j; dh^0 = -curl e / mu0 on Omega, warm on Omega_out
-  CK(run(c, SCFFT_K_X_FWD, [&] { return launch_x<T>(L, X_FWD_F64, pp, h, nullptr, nullptr, 0, 0, false); }));
+  CK(run(c, SCFFT_K_X_FWD, [&] { return x_io<T>(L, X_FWD_F64, pp, io); }));
   CK(curl_in_U<T>(c, L, false));
   CK(run(c, SCFFT_K_X_POWERLAW,
          [&] { return launch_x<T>(L, X_POWERLAW, pp, nullptr, nullptr, nullptr, 0, 0, false); }));
   CK(curl_in_U<T>(c, L, false));
-  CK(run(c, SCFFT_K_X_ASSEMBLE, [&] { return launch_x<T>(L, X_ASSEMBLE, pp, nullptr, nullptr, warm, 0, 0, false); }));
+  CK(run(c, SCFFT_K_X_ASSEMBLE, [&] { return x_io<T>(L, X_ASSEMBLE, pp, io); }));
   const int maxit = c->opt.max_iter;
   const bool early = c->opt.delta_it > 0 && c->nout > 0;
   int launched = 0;
@@ -267,11 +304,14 @@ scfft_status rhs_impl(scfft_ctx* c, double t, int left, const double* h, double*
     // With an early stop the host keeps one iteration queued ahead: before
     // queueing iteration i it waits for the flag copied after iteration i-2.
     // An iteration queued after convergence returns at entry (device flag), so
-    // at most one iteration of launches is wasted.
+    // at most one iteration of launches is wasted.  (While profiling, the host
+    // waits for iteration i-1 instead, so that every profiled launch does real
+    // work.)
+    const int ahead = c->prof_on ? 1 : 2;
     for (int i = 0; i < maxit; ++i) {
-      if (early && i >= 2) {
-        CK(cudaEventSynchronize(c->ev[i & 1]));
-        if (c->hctrl[i & 1].done) break;
+      if (early && i >= ahead) {
+        CK(cudaEventSynchronize(c->ev[(i - ahead) & 1]));
+        if (c->hctrl[(i - ahead) & 1].done) break;
       }
       CK(iteration<T>(c, L, pp, i, early));
       ++launched;
@@ -281,7 +321,21 @@ scfft_status rhs_impl(scfft_ctx* c, double t, int left, const double* h, double*
       }
     }
   }
-  CK(run(c, SCFFT_K_FINALIZE, [&] { return launch_finalize<T>(L, hdot, warm); }));
+  if (io.out32) {
+    if constexpr (sizeof(T) == 4) {
+      const long long n3 = 3 * c->g.N;
+      const Work<float>& w = c->wf;
+      CK(run(c, SCFFT_K_FINALIZE, [&] {
+        finalize_f32_kernel<<<(int)std::min<long long>((n3 + 255) / 256, 152 * 8), 256, 0, c->st>>>(
+            w.Hd[0], w.Hd[1], c->ctrl, io.out32, n3);
+        return cudaGetLastError();
+      }));
+    } else {
+      return SCFFT_EINVAL;
+    }
+  } else {
+    CK(run(c, SCFFT_K_FINALIZE, [&] { return launch_finalize<T>(L, io.out64, io.warm_out64); }));
+  }
   c->stats.rhs_calls += 1;
   if (iters_out || early) {
     CK(cudaMemcpyAsync(c->hctrl + 2, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->st));
@@ -302,8 +356,12 @@ scfft_status rhs_impl(scfft_ctx* c, double t, int left, const double* h, double*
 }
 
 scfft_status rhs_any(scfft_ctx* c, double t, int left, const double* h, double* warm, double* hdot, int* it) {
-  return c->opt.precision == SCFFT_PREC_F32 ? rhs_impl<float>(c, t, left, h, warm, hdot, it)
-                                            : rhs_impl<double>(c, t, left, h, warm, hdot, it);
+  RhsIO io;
+  io.h64 = h;
+  io.warm64 = warm;
+  io.out64 = hdot;
+  io.warm_out64 = warm;
+  return c->opt.precision == SCFFT_PREC_F32 ? rhs_impl<float>(c, t, left, io, it) : rhs_impl<double>(c, t, left, io, it);
 }
 
 template <typename T> scfft_status curl_impl(scfft_ctx* c, const double* f, double* out) {
@@ -475,6 +533,214 @@ scfft_status bs23_step(scfft_ctx* c, double* t_io, double* dt_io, double tstop, 
   }
 }
 
+// ---------------------------------------------------------------- BS23, FP32 FFT path
+// Stage derivatives and stage states are FP32 (the precision the FP32 rhs
+// produces and consumes); the accepted state stays FP64 and its sums are
+// compensated (Kahan), so no per-element FP64 arithmetic beyond one add and the
+// compensation update runs per step.
+__global__ void combine32_kernel(float* __restrict__ out, const double* __restrict__ y, float h, float c1,
+                                 const float* __restrict__ k1, float c2, const float* __restrict__ k2, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float s = c1 * k1[i];
+    if (k2) s += c2 * k2[i];
+    out[i] = (float)y[i] + h * s;
+  }
+}
+
+// ynew = y + d with d = h (b1 k1 + b2 k2 + b3 k3) (d kept for the compensated accept)
+__global__ void candidate32_kernel(double* __restrict__ ynew, float* __restrict__ d, const double* __restrict__ y,
+                                   float h, float b1, const float* __restrict__ k1, float b2,
+                                   const float* __restrict__ k2, float b3, const float* __restrict__ k3, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float di = h * (b1 * k1[i] + b2 * k2[i] + b3 * k3[i]);
+    d[i] = di;
+    ynew[i] = y[i] + (double)di;
+  }
+}
+
+// max_i |h sum_j e_j k_j| / max(rtol |y|, rtol |ynew|, atol), FP32; nonnegative
+// float bit patterns order like the floats, so an integer max combines them
+__global__ void errnorm32_kernel(const double* __restrict__ y, const double* __restrict__ yn, float h, float e1,
+                                 const float* __restrict__ k1, float e2, const float* __restrict__ k2, float e3,
+                                 const float* __restrict__ k3, float e4, const float* __restrict__ k4, float rtol,
+                                 float atol, long long n, unsigned* out) {
+  float m = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float e = h * (e1 * k1[i] + e2 * k2[i] + e3 * k3[i] + e4 * k4[i]);
+    const float w = fmaxf(fmaxf(rtol * fabsf((float)y[i]), rtol * fabsf((float)yn[i])), atol);
+    const float r = fabsf(e) / w;
+    m = (r > m || r != r) ? r : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float q = __shfl_xor_sync(0xffffffffu, m, o);
+    m = (q > m || q != q) ? q : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+// accept: y <- y + d with Kahan compensation c
+__global__ void accept32_kernel(double* __restrict__ y, double* __restrict__ c, const float* __restrict__ d,
+                                long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double yi = y[i];
+    const double u = (double)d[i] - c[i];
+    const double t = yi + u;
+    c[i] = (t - yi) - u;
+    y[i] = t;
+  }
+}
+
+__global__ void f64_to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+__global__ void f32_to_f64_kernel(const float* __restrict__ a, double* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+
+scfft_status ensure_rk32(scfft_ctx* c) {
+  if (c->ib32) return SCFFT_OK;
+  const long long n3 = 3 * c->g.N;
+  if (cudaMalloc(&c->ib32, sizeof(float) * 7 * n3) != cudaSuccess) return SCFFT_ENOMEM;
+  if (cudaMalloc(&c->ynew64, sizeof(double) * 2 * n3) != cudaSuccess) return SCFFT_ENOMEM;
+  for (int i = 0; i < 4; ++i) c->k32[i] = c->ib32 + i * n3;
+  c->ytmp32 = c->ib32 + 4 * n3;
+  c->g32 = c->ib32 + 5 * n3;
+  c->d32 = c->ib32 + 6 * n3;
+  c->comp64 = c->ynew64 + n3;
+  return SCFFT_OK;
+}
+
+scfft_status rhs32(scfft_ctx* c, double t, int left, const double* h64, const float* h32, const float* warm32,
+                   float* out) {
+  RhsIO io;
+  io.h64 = h64;
+  io.h32 = h32;
+  io.warm32 = warm32;
+  io.out32 = out;
+  scfft_status s = rhs_impl<float>(c, t, left, io, nullptr);
+  c->last32 = out;
+  return s;
+}
+
+// One accepted BS23 step of the FP32 path (same control as bs23_step).
+scfft_status bs23_step_f32(scfft_ctx* c, double* t_io, double* dt_io, double tstop, double* h, double* warm,
+                           double dt_fixed, int* rej_out) {
+  CS_(ensure_rk32(c));
+  const long long n3 = 3 * c->g.N;
+  float** k = c->k32;
+  const double t = *t_io;
+  double dt = dt_fixed > 0 ? dt_fixed : *dt_io;
+  const std::vector<double> kinks = kinks_of(c);
+  double nxt = tstop;
+  for (double v : kinks)
+    if (v > t && v < nxt) nxt = v;
+  const int blocks = blocks_for(n3);
+  if (!(c->fsal_valid && c->fsal_t == t && c->fsal_h == h && c->fsal_g == warm)) {
+    // new trajectory (or the caller changed h / warm): warm start from the caller,
+    // fresh first stage, compensation reset
+    CK(run(c, SCFFT_K_RK, [&] {
+      f64_to_f32_kernel<<<blocks, 256, 0, c->st>>>(warm, c->g32, n3);
+      return cudaGetLastError();
+    }));
+    CK(cudaMemsetAsync(c->comp64, 0, sizeof(double) * n3, c->st));
+    CS_(rhs32(c, t, 0, h, nullptr, c->g32, k[0]));
+  }
+  const float a21 = 0.5f, a32 = 0.75f, b1 = 2.0f / 9.0f, b2 = 1.0f / 3.0f, b3 = 4.0f / 9.0f;
+  const float e1 = (float)(2.0 / 9.0 - 7.0 / 24.0), e2 = (float)(1.0 / 3.0 - 0.25),
+              e3 = (float)(4.0 / 9.0 - 1.0 / 3.0), e4 = -0.125f;
+  int rej = 0;
+  for (;;) {
+    const double hs = std::min(dt, nxt - t);
+    const bool hits = (hs == nxt - t);
+    const bool end_left = hits && std::binary_search(kinks.begin(), kinks.end(), nxt);
+    if (!(hs > 1e-14 * std::max(1.0, fabs(t)))) {
+      c->fsal_valid = false;
+      return SCFFT_ESTEP;
+    }
+    const float hf = (float)hs;
+    CK(run(c, SCFFT_K_RK, [&] {
+      combine32_kernel<<<blocks, 256, 0, c->st>>>(c->ytmp32, h, hf, a21, k[0], 0.f, nullptr, n3);
+      return cudaGetLastError();
+    }));
+    CS_(rhs32(c, t + 0.5 * hs, 0, nullptr, c->ytmp32, c->last32, k[1]));
+    CK(run(c, SCFFT_K_RK, [&] {
+      combine32_kernel<<<blocks, 256, 0, c->st>>>(c->ytmp32, h, hf, 0.f, k[0], a32, k[1], n3);
+      return cudaGetLastError();
+    }));
+    CS_(rhs32(c, t + 0.75 * hs, 0, nullptr, c->ytmp32, c->last32, k[2]));
+    CK(run(c, SCFFT_K_RK, [&] {
+      candidate32_kernel<<<blocks, 256, 0, c->st>>>(c->ynew64, c->d32, h, hf, b1, k[0], b2, k[1], b3, k[2], n3);
+      return cudaGetLastError();
+    }));
+    CS_(rhs32(c, hits ? nxt : t + hs, end_left ? 1 : 0, c->ynew64, nullptr, c->last32, k[3]));
+    double en = 0.0;
+    if (!(dt_fixed > 0)) {
+      CK(cudaMemsetAsync(c->errbits, 0, sizeof(unsigned long long), c->st));
+      CK(run(c, SCFFT_K_RK, [&] {
+        errnorm32_kernel<<<blocks, 256, 0, c->st>>>(h, c->ynew64, hf, e1, k[0], e2, k[1], e3, k[2], e4, k[3],
+                                                   (float)c->opt.rtol, (float)c->opt.atol, n3,
+                                                   reinterpret_cast<unsigned*>(c->errbits));
+        return cudaGetLastError();
+      }));
+      CK(cudaMemcpyAsync(c->herr, c->errbits, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      unsigned bits;
+      memcpy(&bits, c->herr, sizeof(unsigned));
+      float ef;
+      memcpy(&ef, &bits, sizeof(float));
+      en = (double)ef;
+      if (!(en == en)) {
+        c->fsal_valid = false;
+        return SCFFT_ENONFINITE;
+      }
+    }
+    if (en <= 1.0) {
+      const double tn = hits ? nxt : t + hs;
+      CK(run(c, SCFFT_K_RK, [&] {
+        accept32_kernel<<<blocks, 256, 0, c->st>>>(h, c->comp64, c->d32, n3);
+        return cudaGetLastError();
+      }));
+      // the caller's warm start (FP64) follows the most recent rhs result
+      CK(run(c, SCFFT_K_RK, [&] {
+        f32_to_f64_kernel<<<blocks, 256, 0, c->st>>>(c->last32, warm, n3);
+        return cudaGetLastError();
+      }));
+      c->stats.accepted += 1;
+      if (end_left) {
+        c->fsal_valid = false;
+      } else {
+        std::swap(k[0], k[3]);
+        c->fsal_valid = true;
+        c->fsal_t = tn;
+        c->fsal_h = h;
+        c->fsal_g = warm;
+      }
+      *t_io = tn;
+      if (dt_fixed > 0) {
+        *dt_io = dt_fixed;
+      } else {
+        const double fac = en == 0.0 ? 5.0 : std::min(5.0, std::max(0.2, 0.9 * pow(en, -1.0 / 3.0)));
+        *dt_io = hs * fac;
+      }
+      if (rej_out) *rej_out = rej;
+      c->stats.t = tn;
+      c->stats.dt = *dt_io;
+      return SCFFT_OK;
+    }
+    ++rej;
+    c->stats.rejected += 1;
+    dt = hs * std::max(0.2, 0.9 * pow(en, -1.0 / 3.0));
+  }
+}
+
+scfft_status step_any(scfft_ctx* c, double* t, double* dt, double tstop, double* h, double* warm, double dt_fixed,
+                      int* rej) {
+  return c->opt.precision == SCFFT_PREC_F32 ? bs23_step_f32(c, t, dt, tstop, h, warm, dt_fixed, rej)
+                                            : bs23_step(c, t, dt, tstop, h, warm, dt_fixed, rej);
+}
+
 }  // namespace
 
 extern "C" {
@@ -551,6 +817,7 @@ void scfft_destroy(scfft_ctx* c) {
   free_work(c->wf);
   free_work(c->wd);
   cudaFree(c->ctrl); cudaFree(c->partials); cudaFree(c->mask); cudaFree(c->ib); cudaFree(c->errbits);
+  cudaFree(c->ib32); cudaFree(c->ynew64);
   if (c->hctrl) cudaFreeHost(c->hctrl);
   if (c->herr) cudaFreeHost(c->herr);
   for (int i = 0; i < 2; ++i) if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -658,7 +925,7 @@ scfft_status scfft_phi(scfft_ctx* c, const double* j, double* out) {
 scfft_status scfft_step(scfft_ctx* c, double* t, double* dt, double tstop, double* h, double* warm, int* rejected) {
   if (!c || !t || !dt || !h || !warm || !(*dt > 0) || !(tstop > *t)) return SCFFT_EINVAL;
   if (!c->have_geom || !c->have_kernel || !c->have_path) return SCFFT_ESTATE;
-  return bs23_step(c, t, dt, tstop, h, warm, 0.0, rejected);
+  return step_any(c, t, dt, tstop, h, warm, 0.0, rejected);
 }
 
 scfft_status scfft_integrate(scfft_ctx* c, double t0, double t1, double dt0, int nsnap, const double* tsnap, double* h,
@@ -686,7 +953,7 @@ scfft_status scfft_integrate(scfft_ctx* c, double t0, double t1, double dt0, int
   while (t < t1) {
     const double tstop = snap_i < nsnap ? tsnap[snap_i] : t1;
     if (dt_fixed && nsteps >= nfixed) break;
-    CS_(bs23_step(c, &t, &dt, tstop, h, g, dt_fixed ? dt_fixed[nsteps] : 0.0, nullptr));
+    CS_(step_any(c, &t, &dt, tstop, h, g, dt_fixed ? dt_fixed[nsteps] : 0.0, nullptr));
     ++nsteps;
     if (snap_i < nsnap && t == tsnap[snap_i]) {
       CK(cudaMemcpyAsync(snaps + (size_t)snap_i * n3, h, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->st));

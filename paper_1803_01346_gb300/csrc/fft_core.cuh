@@ -60,11 +60,23 @@ __host__ __device__ constexpr double sin24(int m) { return cos24(m - 12); }
 // a * W_R^m with W_R = exp(-2 pi i / R) (forward) or its conjugate (inverse); R divides 48.
 template <typename V, int R, bool INV>
 __device__ __forceinline__ V twiddle_const(V a, int m) {
-  // angle 2 pi m / R = (2 m * 24 / R) * pi / 24
-  const int q = 2 * m * 24 / R;
+  // angle 2 pi m / R = (2 m * 24 / R) * pi / 24; m is a compile-time constant at every
+  // call site, so the branches below fold and multiples of pi/2 cost no multiply
+  // (IEEE forbids the compiler from dropping x*0 or x*1 on its own)
+  const int q = ((2 * m * 24 / R) % 48 + 48) % 48;
   typedef decltype(a.x) T;
+  if (q == 0) return a;
+  if (q == 24) return mk(-a.x, -a.y);
+  if (q == 12) return INV ? mk(-a.y, a.x) : mk(a.y, -a.x);  // * (+i) / (-i)
+  if (q == 36) return INV ? mk(a.y, -a.x) : mk(-a.y, a.x);
   const T c = (T)cos24(q), s = (T)sin24(q);
-  // forward: a * (c - i s); inverse: a * (c + i s)
+  if (q % 12 == 6) {  // odd multiples of pi/4: |c| = |s|
+    const T h = (T)0.7071067811865475244008444;
+    const T sc = c > 0 ? (T)1 : (T)-1, ss = s > 0 ? (T)1 : (T)-1;
+    // forward: a * (c - i s); inverse: a * (c + i s)
+    return INV ? mk(h * (sc * a.x - ss * a.y), h * (ss * a.x + sc * a.y))
+               : mk(h * (sc * a.x + ss * a.y), h * (sc * a.y - ss * a.x));
+  }
   return INV ? mk(a.x * c - a.y * s, a.x * s + a.y * c) : mk(a.x * c + a.y * s, a.y * c - a.x * s);
 }
 

@@ -23,7 +23,8 @@ namespace scfft {
 
 namespace {
 
-constexpr int kPad8 = 8;  // row padding (complex elements) that spreads half-warps over all banks
+constexpr int kPad8 = 8;
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }  // row padding (complex elements) that spreads half-warps over all banks
 
 template <int R1, int R2> struct RegGeom {
   static constexpr int L = R1 * R2;
@@ -211,6 +212,14 @@ __global__ void __launch_bounds__(TC * R1) zpass_reg_kernel(typename cplx_of<T>:
   }
 }
 
+template <int R1, int R2, int TC, int KIND>
+__global__ void zpass_reg2_kernel(float2* __restrict__ base, int rows, int sx, int HX, int nzs,
+                                  const float2* __restrict__ twg, const float* __restrict__ kt0,
+                                  const float* __restrict__ kt1, const float* __restrict__ kt2,
+                                  const float* __restrict__ st0, const float* __restrict__ st1,
+                                  const float* __restrict__ st2, float scale, const float* __restrict__ kap, int nx,
+                                  int ny, int nz, const Ctrl* ctrl, int check_done);
+
 // ---------------------------------------------------------------- launchers
 namespace {
 
@@ -229,10 +238,9 @@ template <int R1, int R2, int TC, int KIND>
 cudaError_t go_z(const Launch<float>& L, float2* base, int rows, int sx, int HX, const float2* tw, double scale,
                  bool chk) {
   constexpr int Lt = R1 * R2;
-  constexpr int CSF = R2 * (R1 * TC + kPad8), CSI = R1 * (R2 * TC + kPad8);
-  constexpr int CS = CSF > CSI ? CSF : CSI;
+  constexpr int CS = cmax(cmax(R2 * (R1 * TC + kPad8), R1 * (R2 * TC + kPad8)), Lt * TC);
   const size_t smem = sizeof(float2) * (Lt + 3 * CS);
-  auto k = zpass_reg_kernel<float, R1, R2, TC, KIND>;
+  auto k = zpass_reg2_kernel<R1, R2, TC, KIND>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((HX + TC - 1) / TC, rows, 1);
   const Work<float>& w = *L.w;
@@ -329,8 +337,10 @@ struct XRArgs {
   const float2* tw_in;
   const float2* tw_out;
   const double* src_f64;
+  const float* src_f32;   // FP32 source rows instead of src_f64 (integrator stages)
   double* dst_f64;
   const double* warm;
+  const float* warm_f32;  // FP32 warm start instead of warm
   const uint8_t* mask;
   const float* jc;
   const float* hold;
@@ -344,7 +354,6 @@ struct XRArgs {
 
 namespace {
 
-__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
 template <int MODE, int R1i, int R2i, int R2o> struct XS {
   static constexpr bool C2R = !(MODE == X_FWD_F64 || MODE == X_PAD_F64);
@@ -626,6 +635,9 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP)
   }
 }
 
+template <int MODE, int R1i, int R2i, int R2o, int P>
+__global__ void xpass_reg2_kernel(const XRArgs a);
+
 namespace {
 
 constexpr int kPairs = 8;  // row pairs per CTA (x 3 components)
@@ -633,8 +645,11 @@ constexpr int kPairs = 8;  // row pairs per CTA (x 3 components)
 template <int MODE, int R1i, int R2i, int R2o>
 cudaError_t go_x(const XRArgs& a, cudaStream_t st) {
   typedef XS<MODE, R1i, R2i, R2o> S;
-  const size_t smem = sizeof(float2) * ((S::Li > 0 ? S::Li : 1) + (S::Lo > 0 ? S::Lo : 1) + kPairs * S::TB);
-  auto k = xpass_reg_kernel<MODE, R1i, R2i, R2o, kPairs>;
+  constexpr int XL = S::C2R ? (S::PADIN ? S::Li / 2 : S::Li) : (S::PADOUT ? S::Lo / 2 : S::Lo);
+  constexpr int TT = cmax(cmax(S::C2R ? R2i * (R1i + 1) : 1, S::R2C ? R2o * (S::R1o + 1) : 1), S::R2C ? S::Lo : 1);
+  const size_t smem =
+      sizeof(float2) * ((S::Li > 0 ? S::Li : 1) + (S::Lo > 0 ? S::Lo : 1) + 3 * kPairs * XL + kPairs * TT);
+  auto k = xpass_reg2_kernel<MODE, R1i, R2i, R2o, kPairs>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int npairs = a.g.ny * a.g.nz / 2;
   k<<<(npairs + kPairs - 1) / kPairs, kPairs * S::TP, smem, st>>>(a);
@@ -669,6 +684,12 @@ template <int MODE> cudaError_t go_x_n(int n, const XRArgs& a, cudaStream_t st) 
 
 cudaError_t launch_x_reg(const Launch<float>& L, XMode mode, const PointParams& pp, const double* src_f64,
                          double* dst_f64, const double* warm, int in_buf, int out_buf, bool check_done) {
+  return launch_x_reg_io(L, mode, pp, src_f64, nullptr, dst_f64, warm, nullptr, in_buf, out_buf, check_done);
+}
+
+cudaError_t launch_x_reg_io(const Launch<float>& L, XMode mode, const PointParams& pp, const double* src_f64,
+                            const float* src_f32, double* dst_f64, const double* warm, const float* warm_f32,
+                            int in_buf, int out_buf, bool check_done) {
   const Geo& g = L.g;
   XRArgs a{};
   a.g = g;
@@ -683,8 +704,10 @@ cudaError_t launch_x_reg(const Launch<float>& L, XMode mode, const PointParams& 
   a.tw_in = pin ? L.w->twp[0] : L.w->twu[0];
   a.tw_out = pout ? L.w->twp[0] : L.w->twu[0];
   a.src_f64 = src_f64;
+  a.src_f32 = src_f32;
   a.dst_f64 = dst_f64;
   a.warm = warm;
+  a.warm_f32 = warm_f32;
   a.mask = L.mask;
   a.jc = L.w->jc;
   a.hold = L.w->Hd[in_buf];
@@ -705,6 +728,381 @@ cudaError_t launch_x_reg(const Launch<float>& L, XMode mode, const PointParams& 
     case X_CROP_F64: return go_x_n<X_CROP_F64>(g.nx, a, L.st);
   }
   return cudaErrorInvalidValue;
+}
+
+}  // namespace scfft
+
+// ============================================================================
+// Lower-register variants: the three components go through the FFT stages one
+// after another (16 complex values per thread at a time), and the
+// cross-component steps (curl / kernel-spectrum product in z, the node-wise
+// step in x) read all three from shared memory.  This doubles the resident
+// warps per SM of the 3-component register versions above.
+// ============================================================================
+namespace scfft {
+
+template <int R1, int R2, int TC, int KIND>
+__global__ void __launch_bounds__(TC * R1) zpass_reg2_kernel(float2* __restrict__ base, int rows, int sx, int HX,
+                                                             int nzs, const float2* __restrict__ twg,
+                                                             const float* __restrict__ kt0,
+                                                             const float* __restrict__ kt1,
+                                                             const float* __restrict__ kt2,
+                                                             const float* __restrict__ st0,
+                                                             const float* __restrict__ st1,
+                                                             const float* __restrict__ st2, float scale,
+                                                             const float* __restrict__ kap, int nx, int ny, int nz,
+                                                             const Ctrl* ctrl, int check_done) {
+  constexpr int L = R1 * R2;
+  constexpr bool PR = (KIND == 1);
+  constexpr int S2 = R1 * TC + kPad8;  // forward transpose [k2][n1][c]
+  constexpr int S1 = R2 * TC + kPad8;  // inverse transpose [m1][k2][c]
+  constexpr int CS = cmax(cmax(R2 * S2, R1 * S1), L * TC);
+  constexpr int NT = TC * R1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (check_done && ctrl->done) return;
+  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  float2* F = tw + L;
+  const int t = threadIdx.x;
+  for (int i = t; i < L; i += NT) tw[i] = twg[i];
+  const int c = t % TC, n1 = t / TC;
+  const int y = blockIdx.y, kx = blockIdx.x * TC + c;
+  const bool colok = kx < HX;
+  const size_t zstride = (size_t)rows * sx;
+  const size_t cstride = (size_t)nzs * zstride;
+  float2* col = base + (size_t)y * sx + kx;
+  __syncthreads();  // twiddles staged
+
+  // all three components' inputs are loaded up front (one memory latency, not three)
+  constexpr int NL = PR ? R2 / 2 : R2;
+  float2 pre[3][NL];
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int n2 = 0; n2 < NL; ++n2)
+      pre[q][n2] = colok ? col[q * cstride + (size_t)(n1 + R1 * n2) * zstride] : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    float2* Fq = F + q * CS;
+    float2 v[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) v[n2] = n2 < NL ? pre[q][n2] : make_float2(0.f, 0.f);
+    DFT<R2, false, float2>::run(v);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) Fq[k2 * S2 + n1 * TC + c] = k2 == 0 ? v[0] : cmul(v[k2], tw[n1 * k2]);
+    __syncthreads();
+    float2 w[R1];
+    if (n1 < R2) {
+#pragma unroll
+      for (int m = 0; m < R1; ++m) w[m] = Fq[n1 * S2 + m * TC + c];
+      DFT<R1, false, float2>::run(w);
+    }
+    __syncthreads();
+    if (n1 < R2) {
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) Fq[(n1 + R2 * k1) * TC + c] = w[k1];
+    }
+  }
+  __syncthreads();
+  // ---- product on the natural-order spectra [kz][c]
+  const int kxc0 = blockIdx.x * TC;
+  for (int idx = t; idx < L * TC; idx += NT) {
+    const int cc = idx % TC, kz = idx / TC;
+    const int kxx = kxc0 + cc < HX ? kxc0 + cc : 0;
+    float ax, ay, az, s;
+    if (KIND == 0) {
+      ax = kt0[kxx]; ay = kt1[y]; az = kt2[kz];
+      s = st0[kxx] * st1[y] * st2[kz] * scale;
+    } else {
+      const int fy = (y <= ny) ? y : 2 * ny - y;
+      const int fz = (kz <= nz) ? kz : 2 * nz - kz;
+      const size_t oct = (size_t)(nz + 1) * (ny + 1) * (nx + 1);
+      const size_t off = ((size_t)fz * (ny + 1) + fy) * (nx + 1) + kxx;
+      ax = kap[off];
+      ay = (y <= ny) ? kap[oct + off] : -kap[oct + off];
+      az = (kz <= nz) ? kap[2 * oct + off] : -kap[2 * oct + off];
+      s = 1.f;
+    }
+    const float2 F0 = F[idx], F1 = F[CS + idx], F2 = F[2 * CS + idx];
+    const float2 cx = make_float2(ay * F2.x - az * F1.x, ay * F2.y - az * F1.y);
+    const float2 cy = make_float2(az * F0.x - ax * F2.x, az * F0.y - ax * F2.y);
+    const float2 cz = make_float2(ax * F1.x - ay * F0.x, ax * F1.y - ay * F0.y);
+    F[idx] = make_float2(-s * cx.y, s * cx.x);
+    F[CS + idx] = make_float2(-s * cy.y, s * cy.x);
+    F[2 * CS + idx] = make_float2(-s * cz.y, s * cz.x);
+  }
+  __syncthreads();
+  // ---- inverse: y[m1 + R1 m2] = sum_k2 W_R2^{-m2 k2} W_L^{-m1 k2} (sum_k1 X[k2 + R2 k1] W_R1^{-m1 k1})
+  for (int q = 0; q < 3; ++q) {
+    float2* Fq = F + q * CS;
+    float2 w[R1];
+    if (n1 < R2) {
+      const int k2 = n1;
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) w[k1] = Fq[(k2 + R2 * k1) * TC + c];
+      DFT<R1, true, float2>::run(w);
+    }
+    __syncthreads();
+    if (n1 < R2) {
+      const int k2 = n1;
+#pragma unroll
+      for (int m1 = 0; m1 < R1; ++m1) Fq[m1 * S1 + k2 * TC + c] = m1 == 0 ? w[0] : cmulc(w[m1], tw[m1 * k2]);
+    }
+    __syncthreads();
+    float2 v[R2];
+#pragma unroll
+    for (int j = 0; j < R2; ++j) v[j] = Fq[n1 * S1 + j * TC + c];
+    DFT<R2, true, float2>::run(v);
+    if (colok) {
+#pragma unroll
+      for (int m2 = 0; m2 < R2; ++m2) {
+        if (PR && m2 >= R2 / 2) continue;
+        col[q * cstride + (size_t)(n1 + R1 * m2) * zstride] = v[m2];
+      }
+    }
+  }
+}
+
+// x pass, one component at a time; the node-wise step reads the three
+// components' real rows from shared memory RS[q][p][x] (complex = rows a, b).
+template <int MODE, int R1i, int R2i, int R2o, int P>
+__global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP)
+    xpass_reg2_kernel(const XRArgs a) {
+  typedef XS<MODE, R1i, R2i, R2o> S;
+  constexpr int TP = S::TP, R1o = S::R1o, Li = S::Li, Lo = S::Lo;
+  constexpr int NT = P * TP;
+  constexpr int XL = S::C2R ? (S::PADIN ? Li / 2 : Li) : (S::PADOUT ? Lo / 2 : Lo);  // nx
+  constexpr int TT = cmax(cmax(S::C2R ? R2i * (R1i + 1) : 1, S::R2C ? R2o * (R1o + 1) : 1), S::R2C ? Lo : 1);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (a.check_done && a.ctrl->done) return;
+  float2* twi = reinterpret_cast<float2*>(smem_raw);
+  float2* two = twi + (Li > 0 ? Li : 1);
+  float2* RS = two + (Lo > 0 ? Lo : 1);  // [3][P][XL]
+  float2* T = RS + 3 * P * XL;           // [P][TT]
+  const int tid = threadIdx.x;
+  const int p = tid / TP, r = tid % TP;
+  if (S::C2R)
+    for (int i = tid; i < Li; i += NT) twi[i] = a.tw_in[i];
+  if (S::R2C)
+    for (int i = tid; i < Lo; i += NT) two[i] = a.tw_out[i];
+  const int ny = a.g.ny, nz = a.g.nz;
+  const long long N = a.g.N;
+  const int npairs = ny * nz / 2;
+  const int gp = blockIdx.x * P + p;
+  const bool pok = gp < npairs;
+  const int qa = 2 * (pok ? gp : 0);
+  const int z = qa / ny, ya = qa - z * ny;
+  float2* Tp = T + p * TT;
+
+  if constexpr (S::C2R) {
+    __syncthreads();  // twiddles
+    for (int q = 0; q < 3; ++q) {
+      const int n1 = r;
+      if (n1 < R1i) {
+        const float2* ra = a.spec_in + ((size_t)(q * nz + z) * a.in_rows + ya) * a.in_sx;
+        const float2* rb = ra + a.in_sx;
+        float2 v[R2i];
+#pragma unroll
+        for (int n2 = 0; n2 < R2i; ++n2) {
+          const int k = n1 + R1i * n2;
+          const bool lo = k <= Li / 2;
+          const int kk = lo ? k : Li - k;
+          float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+          if (pok) { A = ra[kk]; B = rb[kk]; }
+          if (kk == 0 || kk == Li / 2) { A.y = 0.f; B.y = 0.f; }
+          v[n2] = lo ? make_float2(A.x - B.y, A.y + B.x) : make_float2(A.x + B.y, B.x - A.y);
+        }
+        DFT<R2i, true, float2>::run(v);
+#pragma unroll
+        for (int k2 = 0; k2 < R2i; ++k2) Tp[k2 * (R1i + 1) + n1] = k2 == 0 ? v[0] : cmulc(v[k2], twi[n1 * k2]);
+      }
+      __syncthreads();
+      const int k2 = r;
+      if (k2 < R2i) {
+        float2 w[R1i];
+#pragma unroll
+        for (int m = 0; m < R1i; ++m) w[m] = Tp[k2 * (R1i + 1) + m];
+        DFT<R1i, true, float2>::run(w);
+#pragma unroll
+        for (int k1 = 0; k1 < S::KX; ++k1) RS[(q * P + p) * XL + k2 + R2i * k1] = w[k1];
+      }
+      __syncthreads();
+    }
+  } else {
+    // real f64 rows into RS
+    for (int idx = tid; idx < 3 * P * XL; idx += NT) {
+      const int x = idx % XL, pp2 = (idx / XL) % P, q = idx / (XL * P);
+      const int g2 = blockIdx.x * P + pp2;
+      float2 zv = make_float2(0.f, 0.f);
+      if (g2 < npairs) {
+        const size_t na = (size_t)(2 * g2) * XL + x;
+        zv = a.src_f32 ? make_float2(a.src_f32[q * N + na], a.src_f32[q * N + na + XL])
+                       : make_float2((float)a.src_f64[q * N + na], (float)a.src_f64[q * N + na + XL]);
+      }
+      RS[(q * P + pp2) * XL + x] = zv;
+    }
+    __syncthreads();
+  }
+
+  // ---- node-wise step
+  float partf = 0.f;
+  if constexpr (S::C2R) {
+    const PointParams& pp = a.pp;
+    for (int idx = tid; idx < P * XL; idx += NT) {
+      const int x = idx % XL, pp2 = idx / XL;
+      const int g2 = blockIdx.x * P + pp2;
+      if (g2 >= npairs) continue;
+      const size_t na = (size_t)(2 * g2) * XL + x, nb = na + XL;
+      float2 u[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) u[q] = RS[(q * P + pp2) * XL + x];
+      if (MODE == X_POWERLAW) {
+        const bool ia = a.mask[na], ib = a.mask[nb];
+        const float ca = a.jc ? a.jc[na] : (float)pp.jc, cb = a.jc ? a.jc[nb] : (float)pp.jc;
+        const float ra = rho_of(u[0].x, u[1].x, u[2].x, ia, ca, pp);
+        const float rb = rho_of(u[0].y, u[1].y, u[2].y, ib, cb, pp);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) u[q] = make_float2(u[q].x * ra, u[q].y * rb);
+      } else if (MODE == X_ASSEMBLE) {
+        const bool ia = a.mask[na], ib = a.mask[nb];
+        const float s = -(float)pp.inv_mu0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const float va = ia ? s * u[q].x : (a.warm_f32 ? a.warm_f32[q * N + na] : (float)a.warm[q * N + na]);
+          const float vb = ib ? s * u[q].y : (a.warm_f32 ? a.warm_f32[q * N + nb] : (float)a.warm[q * N + nb]);
+          a.hnew[q * N + na] = va;
+          a.hnew[q * N + nb] = vb;
+          u[q] = make_float2(va, vb);
+        }
+      } else if (MODE == X_MASKPAD) {
+        const bool ia = a.mask[na], ib = a.mask[nb];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) u[q] = make_float2(ia ? u[q].x : 0.f, ib ? u[q].y : 0.f);
+      } else if (MODE == X_UPDATE) {
+        // per-node |dh^{i+1} - dh^i| in FP32 (the FP32 path's own precision); the
+        // per-thread sum stays FP32, the CTA and grid sums are FP64
+        const bool ia = a.mask[na], ib = a.mask[nb];
+        float da = 0.f, db = 0.f;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const float oa = a.hold[q * N + na], ob = a.hold[q * N + nb];
+          const float he = (float)pp.hedot[q];
+          const float va = ia ? oa : he + u[q].x;
+          const float vb = ib ? ob : he + u[q].y;
+          a.hnew[q * N + na] = va;
+          a.hnew[q * N + nb] = vb;
+          const float dda = va - oa, ddb = vb - ob;
+          da += dda * dda;
+          db += ddb * ddb;
+          u[q] = make_float2(va, vb);
+        }
+        if (!ia) partf += sqrtf(da);
+        if (!ib) partf += sqrtf(db);
+      } else {  // X_TO_F64, X_CROP_F64
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          a.dst_f64[q * N + na] = (double)u[q].x;
+          a.dst_f64[q * N + nb] = (double)u[q].y;
+        }
+      }
+      if (S::R2C) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) RS[(q * P + pp2) * XL + x] = u[q];
+      }
+    }
+    __syncthreads();
+  }
+
+  if constexpr (S::R2C) {
+    constexpr int H = Lo / 2 + 1;
+    for (int q = 0; q < 3; ++q) {
+      const int n1 = r;
+      if (n1 < R1o) {
+        float2 u[R2o];
+#pragma unroll
+        for (int n2 = 0; n2 < R2o; ++n2) {
+          const int x = n1 + R1o * n2;
+          u[n2] = (x < XL) ? RS[(q * P + p) * XL + x] : make_float2(0.f, 0.f);
+        }
+        DFT<R2o, false, float2>::run(u);
+#pragma unroll
+        for (int k2 = 0; k2 < R2o; ++k2) Tp[k2 * (R1o + 1) + n1] = k2 == 0 ? u[0] : cmul(u[k2], two[n1 * k2]);
+      }
+      __syncthreads();
+      const int k2 = r;
+      float2 Zr[R1o];
+      if (k2 < R2o) {
+#pragma unroll
+        for (int m = 0; m < R1o; ++m) Zr[m] = Tp[k2 * (R1o + 1) + m];
+        DFT<R1o, false, float2>::run(Zr);
+      }
+      __syncthreads();
+      if (k2 < R2o) {
+#pragma unroll
+        for (int k1 = 0; k1 < R1o; ++k1) Tp[k2 + R2o * k1] = Zr[k1];
+      }
+      __syncthreads();
+      for (int idx = tid; idx < P * 2 * H; idx += NT) {
+        const int k = idx % H, rr = (idx / H) % 2, pp2 = idx / (2 * H);
+        const int g2 = blockIdx.x * P + pp2;
+        if (g2 >= npairs) continue;
+        const float2* zs = T + pp2 * TT;
+        const float2 Zk = zs[k], Zm = zs[(Lo - k) % Lo];
+        const float2 o = rr == 0 ? make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y))
+                                 : make_float2(0.5f * (Zk.y + Zm.y), 0.5f * (Zm.x - Zk.x));
+        const int qrow = 2 * g2 + rr;
+        const int zz = qrow / ny, yy = qrow - zz * ny;
+        a.spec_out[((size_t)(q * nz + zz) * a.out_rows + yy) * a.out_sx + k] = o;
+      }
+      __syncthreads();
+    }
+  }
+
+  if (MODE == X_UPDATE) {
+    double part = (double)partf;
+    __shared__ double red[32];
+    __shared__ int am_last;
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((tid & 31) == 0) red[tid >> 5] = part;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int i = 0; i < (NT + 31) / 32; ++i) s += red[i];
+      a.partials[blockIdx.x] = s;
+      __threadfence();
+      const unsigned prev = atomicAdd(&a.ctrl->counter, 1u);
+      am_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (am_last) {
+      __threadfence();
+      double s = 0.0;
+      for (int i = tid; i < (int)gridDim.x; i += NT) s += __ldcg(&a.partials[i]);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      __syncthreads();
+      if ((tid & 31) == 0) red[tid >> 5] = s;
+      __syncthreads();
+      if (tid == 0) {
+        double tot = 0.0;
+        for (int i = 0; i < (NT + 31) / 32; ++i) tot += red[i];
+        const double rres = tot * a.pp.inv_nout;
+        Ctrl* c = a.ctrl;
+        c->residual = rres;
+        c->iters = a.pp.iter + 1;
+        c->cur = a.out_buf;
+        const bool finite = isfinite(rres);
+        if (!finite) c->status = 6;  // SCFFT_ENONFINITE
+        c->done = (!finite || rres < a.pp.tol) ? 1 : 0;
+        c->counter = 0;
+      }
+    }
+  }
+  if (MODE == X_ASSEMBLE && blockIdx.x == 0 && tid == 0) {
+    a.ctrl->done = 0;
+    a.ctrl->iters = 0;
+    a.ctrl->cur = 0;
+    a.ctrl->counter = 0;
+    a.ctrl->residual = 0.0;
+  }
 }
 
 }  // namespace scfft

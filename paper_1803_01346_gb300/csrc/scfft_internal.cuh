@@ -99,6 +99,10 @@ cudaError_t launch_y_reg(const Launch<float>& L, bool padded, bool inverse, bool
 cudaError_t launch_z_reg(const Launch<float>& L, bool padded, bool check_done, double scale);
 cudaError_t launch_x_reg(const Launch<float>& L, XMode mode, const PointParams& pp, const double* src_f64,
                          double* dst_f64, const double* warm, int in_buf, int out_buf, bool check_done);
+// The same with FP32 source rows / FP32 warm start (used by the FP32 integrator's stages).
+cudaError_t launch_x_reg_io(const Launch<float>& L, XMode mode, const PointParams& pp, const double* src_f64,
+                            const float* src_f32, double* dst_f64, const double* warm, const float* warm_f32,
+                            int in_buf, int out_buf, bool check_done);
 
 FftPlan make_plan(int L);
 bool length_supported(int L);

@@ -259,3 +259,37 @@ def test_step_matches_integrate_and_counts_launches():
     assert s1["launches"] > s0["launches"] and s1["rhs_calls"] > s0["rhs_calls"]
     ref = O.integrate(prob, 0.0, 0.05, np.zeros((3,) + prob.grid.shape), rtol=1e-5, atol=1e-8, dt0=1e-4)
     assert rel(host(h).reshape(ref.y.shape), ref.y) < 2e-4
+
+
+def test_integrate_fp32_path_tracks_oracle():
+    """FP32 FFTs, FP32 stages, compensated FP64 state: fixed steps and an
+    adaptive run against the FP64 oracle (stated tolerance 1e-4 relative)."""
+    cfg, prob = _cube_cfg()
+    N = int(np.prod(cfg.n))
+    dts = [0.002, 0.003, 0.004, 0.004, 0.005, 0.005]
+    ctx = S.Context(cfg.n, cfg.L, n_power=cfg.n_power, rho_out=cfg.rho_out, delta_it=1e-13, max_iter=80,
+                    precision=S.PREC_F32)
+    ctx.set_geometry(cfg.mask)
+    ctx.set_field_path(cfg.knots_t, cfg.knots_he)
+    ctx.precompute_kernel()
+    h = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    t1 = float(np.sum(dts))
+    st = ctx.integrate(0.0, t1, dts[0], h, dt_fixed=dts)
+    ref = O.integrate(prob, 0.0, t1, np.zeros((3,) + prob.grid.shape), rtol=1e-6, atol=1e-9, dt0=dts[0],
+                      delta_it=1e-13, max_iter=80, dt_list=dts)
+    assert st["accepted"] == len(dts)
+    assert rel(host(h).reshape(ref.y.shape), ref.y) < 1e-4
+    # adaptive, through scfft_step
+    ctx2 = S.Context(cfg.n, cfg.L, n_power=cfg.n_power, rho_out=cfg.rho_out, delta_it=2e-5, max_iter=100,
+                     rtol=1e-4, atol=1e-7, precision=S.PREC_F32)
+    ctx2.set_geometry(cfg.mask)
+    ctx2.set_field_path(cfg.knots_t, cfg.knots_he)
+    ctx2.precompute_kernel()
+    h2 = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    warm = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    warm.view(3, N)[2] = 0.5
+    t, dt = 0.0, 1e-4
+    while t < 0.1:
+        t, dt, _ = ctx2.step(t, dt, 0.1, h2, warm)
+    ref2 = O.integrate(prob, 0.0, 0.1, np.zeros((3,) + prob.grid.shape), rtol=1e-4, atol=1e-7, dt0=1e-4)
+    assert rel(host(h2).reshape(ref2.y.shape), ref2.y) < 2e-3
