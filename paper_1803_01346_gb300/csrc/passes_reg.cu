@@ -24,7 +24,8 @@ namespace scfft {
 namespace {
 
 constexpr int kPad8 = 8;
-__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }  // row padding (complex elements) that spreads half-warps over all banks
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }  // row padding (complex elements) that spreads half-warps over all banks
 
 template <int R1, int R2> struct RegGeom {
   static constexpr int L = R1 * R2;
@@ -892,6 +893,40 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP)
   const int qa = 2 * (pok ? gp : 0);
   const int z = qa / ny, ya = qa - z * ny;
   float2* Tp = T + p * TT;
+
+  // L2 prefetch of everything this CTA reads after its first phase (components 1
+  // and 2 of the input rows, and the node-wise step's rows), so that those later
+  // phases see L2 rather than DRAM latency; it costs no registers.
+  {
+    const int row0 = 2 * blockIdx.x * P;  // first (z, y) row of this CTA
+    const int nrow = 2 * P;
+    if constexpr (S::C2R) {
+      const int lines = ((Li / 2 + 1) * 8 + 127) / 128;  // 128-byte lines per half-spectrum row
+      for (int i = tid; i < 2 * nrow * lines; i += NT) {
+        const int ln = i % lines, rr = (i / lines) % nrow, q = 1 + i / (lines * nrow);
+        const int qrow = row0 + rr;
+        if (qrow < 2 * npairs) {
+          const int zz = qrow / ny, yy = qrow - zz * ny;
+          prefetch_l2(a.spec_in + ((size_t)(q * nz + zz) * a.in_rows + yy) * a.in_sx + ln * 16);
+        }
+      }
+    }
+    const size_t nb0 = (size_t)row0 * XL;
+    const int rl = (XL * 4 + 127) / 128;  // lines per FP32 node row
+    if (MODE == X_UPDATE)
+      for (int i = tid; i < 3 * nrow * rl; i += NT) {
+        const int ln = i % rl, rr = (i / rl) % nrow, q = i / (rl * nrow);
+        if (row0 + rr < 2 * npairs) prefetch_l2(a.hold + q * N + nb0 + (size_t)rr * XL + ln * 32);
+      }
+    if (MODE == X_ASSEMBLE && a.warm)
+      for (int i = tid; i < 3 * nrow * 2 * rl; i += NT) {
+        const int ln = i % (2 * rl), rr = (i / (2 * rl)) % nrow, q = i / (2 * rl * nrow);
+        if (row0 + rr < 2 * npairs) prefetch_l2(a.warm + q * N + nb0 + (size_t)rr * XL + ln * 16);
+      }
+    if (MODE == X_UPDATE || MODE == X_ASSEMBLE || MODE == X_MASKPAD || MODE == X_POWERLAW)
+      for (int i = tid * 128; i < nrow * XL; i += NT * 128)
+        if (row0 + i / XL < 2 * npairs) prefetch_l2(a.mask + nb0 + i);
+  }
 
   if constexpr (S::C2R) {
     __syncthreads();  // twiddles
