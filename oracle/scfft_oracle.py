@@ -53,7 +53,7 @@ __all__ = [
     "rhs", "RhsResult",
     "BS23_C", "BS23_A", "BS23_B", "BS23_BHAT", "BS23_E",
     "bs23_step", "error_norm", "integrate", "IntegrateResult",
-    "magnetic_moment", "dissipation",
+    "magnetic_moment", "dissipation", "rhs_vjp", "RhsVJP",
 ]
 
 
@@ -491,3 +491,58 @@ def magnetic_moment(j: np.ndarray, grid: Grid) -> np.ndarray:
     X, Y, Z = grid.coords()
     r = np.stack(np.broadcast_arrays(X, Y, Z))
     return 0.5 * grid.dV * np.sum(_cross(r, j), axis=(1, 2, 3))
+
+
+# ----------------------------------------------------------------------------
+# Adjoint of one right-hand side with a fixed number K of Eq. 5 iterations
+# ----------------------------------------------------------------------------
+@dataclass
+class RhsVJP:
+    mu_h: np.ndarray   # (dF/dh)^T lam
+    mu_g: np.ndarray   # (dF/dg)^T lam
+    mu_jc: np.ndarray  # (dF/djc)^T lam, one value per node (zero outside Omega)
+    mu_a: np.ndarray   # (dF/da)^T lam for the applied rate a = dh_e/dt (3 values)
+
+
+def rhs_vjp(prob: Problem, t: float, h: np.ndarray, lam: np.ndarray, K: int, left: bool = False) -> RhsVJP:
+    """Reverse-mode derivative of F(h, g, jc, a) = dh^K of `rhs` (delta_it = 0,
+    max_iter = K): the forward map is, in the order of §2,
+        j = C h,  e = E(j; jc),  u = -C e / mu0,  d^0 = chi u + chib g,
+        d^{i+1} = M d^i + chib a,  M = chi + chib Phi chi C   (Eq. 5)
+    with chi the indicator of Omega and chib = 1 - chi.  The curl C (imaginary
+    odd symbol, skew cross product) and Phi (odd kernel, skew cross product, the
+    same offsets both ways after cropping) are symmetric, so
+        M^T = chi + C chi Phi chib,
+    and the transposed steps run in reverse order.  The power law's Jacobian is
+    rho (I + (n-1) jhat jhat^T) in Omega (symmetric), rho_out I outside, and
+    de/djc = -n rho j / jc in Omega (rho is proportional to jc^-n).  The warm
+    start g does not enter (the result is linear in it: mu_g = chib lam_0)."""
+    grid, mask, mat = prob.grid, prob.mask, prob.mat
+    chi = mask[None].astype(float)
+    chib = 1.0 - chi
+    Khat = prob.kernel()
+    C = lambda f: curl_s(f, grid)  # noqa: E731
+    Phi = lambda f: phi_hockney(f, grid, Khat)  # noqa: E731
+    # forward quantities the Jacobians need
+    j = C(h)
+    jn = np.sqrt(np.sum(j * j, axis=0))
+    jc = np.asarray(mat.jc, dtype=np.float64) * np.ones(jn.shape)
+    rho = (mat.e0 / jc) * (jn / jc) ** (mat.n - 1.0)
+    # iterations, in reverse
+    lam_i = lam.copy()
+    mu_a = np.zeros(3)
+    for _ in range(K):
+        mu_a += np.sum(chib * lam_i, axis=(1, 2, 3))
+        lam_i = chi * lam_i + C(chi * Phi(chib * lam_i))
+    mu_g = chib * lam_i
+    lam_u = chi * lam_i
+    lam_e = -C(lam_u) / mat.mu0
+    # power-law Jacobian transpose (Omega) / outer Ohm law (Omega_out)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        jhat = np.where(jn > 0, j / np.where(jn > 0, jn, 1.0), 0.0)
+    proj = np.sum(jhat * lam_e, axis=0)
+    lam_j_in = rho[None] * (lam_e + (mat.n - 1.0) * proj[None] * jhat)
+    lam_j = np.where(mask[None], lam_j_in, mat.rho_out * lam_e)
+    mu_jc = np.where(mask, -mat.n * rho / jc * np.sum(j * lam_e, axis=0), 0.0)
+    mu_h = C(lam_j)
+    return RhsVJP(mu_h, mu_g, mu_jc, mu_a)

@@ -371,3 +371,63 @@ def test_conducting_sphere_steady_ramp():
     assert np.abs(hd[:2][:, ~mask]).max() < 5e-3
     m20, _, _ = run(20)
     assert abs(1 - m20) < abs(1 - m16)
+
+
+# ---------------------------------------------------------------- adjoint
+def test_curl_and_phi_are_symmetric():
+    """<C a, b> = <a, C b> and <Phi a, b> = <a, Phi b> (the adjoint relies on
+    both; the curl's symbol is i k x (.) times a real even factor, Phi's kernel
+    is an odd gradient under a cross product)."""
+    g = _modes_grid()
+    a = I.random_field((3,) + g.shape, 31)
+    b = I.random_field((3,) + g.shape, 32)
+    ca, cb = O.curl_s(a, g), O.curl_s(b, g)
+    assert abs(np.sum(ca * b) - np.sum(a * cb)) < 1e-12 * np.sqrt(np.sum(ca * ca) * np.sum(b * b))
+    pa, pb = O.phi_hockney(a, g), O.phi_hockney(b, g)
+    assert abs(np.sum(pa * b) - np.sum(a * pb)) < 1e-12 * np.sqrt(np.sum(pa * pa) * np.sum(b * b))
+
+
+def _vjp_problem():
+    n, L = (12, 10, 14), (1.0, 0.8, 1.2)
+    g = O.Grid(n, L)
+    mask = I.cube(n, L, 1.0)
+    jc = I.jc_noise((n[2], n[1], n[0]), 3)
+    prob = O.Problem(g, mask, O.Material(n=7.0, rho_out=5.0, jc=jc),
+                     O.FieldPath([0, 1], [[0, 0, 0], [0.3, -0.2, 0.9]]))
+    rng = np.random.default_rng(0)
+    jr = O.curl_s(rng.standard_normal((3,) + g.shape) * 0.5, g) * mask
+    h = O.phi_hockney(jr, g) + 0.05
+    return prob, h, rng
+
+
+def test_rhs_vjp_matches_finite_differences():
+    """Reverse-mode derivative of the fixed-K rhs against central differences
+    of the rhs itself: O(eps^2) agreement for h and jc, exact for the linear
+    arguments g and dh_e/dt.  Catches a missing transpose, a wrong mask order
+    or a wrong power-law Jacobian."""
+    prob, h, rng = _vjp_problem()
+    g = prob.grid
+    gw = rng.standard_normal(h.shape) * 0.1
+    lam = rng.standard_normal(h.shape)
+    K = 3
+    v = O.rhs_vjp(prob, 0.4, h, lam, K)
+    F = lambda hh, gg, pr=prob: O.rhs(pr, 0.4, hh, gg, delta_it=0.0, max_iter=K).hdot  # noqa: E731
+    dh = rng.standard_normal(h.shape)
+    eps = 1e-4
+    fd = np.sum(lam * (F(h + eps * dh, gw) - F(h - eps * dh, gw))) / (2 * eps)
+    assert fd == pytest.approx(np.sum(v.mu_h * dh), rel=1e-8)
+    dg = rng.standard_normal(h.shape)
+    assert np.sum(lam * (F(h, gw + dg) - F(h, gw))) == pytest.approx(np.sum(v.mu_g * dg), rel=1e-10)
+    jc = prob.mat.jc
+    djc = rng.standard_normal(jc.shape) * 0.01
+
+    def Fj(jcv):
+        p2 = O.Problem(g, prob.mask, O.Material(n=7.0, rho_out=5.0, jc=jcv), prob.path, Khat=prob.kernel())
+        return F(h, gw, p2)
+    eps = 1e-3
+    fd = np.sum(lam * (Fj(jc + eps * djc) - Fj(jc - eps * djc))) / (2 * eps)
+    assert fd == pytest.approx(np.sum(v.mu_jc * djc), rel=1e-7)
+    da = np.array([0.3, -0.5, 0.2])
+    p3 = O.Problem(g, prob.mask, prob.mat, O.FieldPath([0, 1], [[0, 0, 0], list(np.array([0.3, -0.2, 0.9]) + da)]),
+                   Khat=prob.kernel())
+    assert np.sum(lam * (F(h, gw, p3) - F(h, gw))) == pytest.approx(v.mu_a @ da, rel=1e-10)
