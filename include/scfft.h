@@ -192,6 +192,23 @@ scfft_status scfft_profile(scfft_ctx* ctx, int enable);
 scfft_status scfft_profile_read(scfft_ctx* ctx, long long* counts, double* ms);
 const char* scfft_kind_name(int kind);
 
+/* Reverse-mode derivative (vector-Jacobian product) of the rhs map
+ * F(h, warm, jc, dh_e/dt) = dh/dt of scfft_rhs taken with exactly max_iter
+ * Eq. 5 iterations (no early stop; with a converged forward iteration this is
+ * the derivative of the converged map up to the residual).  The map is the
+ * chain of §2 (j = curl h, Eq. 1, Eq. 3, Eq. 5); its transpose runs the same
+ * operators backwards: the iteration's transpose is chi + curl chi Phi (1-chi)
+ * (the curl and Phi are symmetric), the power law's Jacobian is
+ * rho (I + (n-1) jhat jhat^T) in Omega and rho_out outside.
+ * h: device 3N (the point of linearisation), lam: device 3N (cotangent of
+ * dh/dt).  Outputs: mu_h device 3N; mu_g device 3N or NULL (cotangent of the
+ * warm start); mu_jc device N or NULL (cotangent of the per-node jc, 0 outside
+ * Omega); mu_a host double[3] or NULL (cotangent of dh_e/dt, summed over
+ * nodes).  The transposed passes run in FP64 or FP32 as the context's
+ * precision.  Synchronous. */
+scfft_status scfft_rhs_vjp(scfft_ctx* ctx, const double* h, const double* lam, double* mu_h, double* mu_g,
+                           double* mu_jc, double* mu_a);
+
 /* Allocation-free spectral curl: out = curl_S f, the same result as
  * scfft_curl (FP64) on the same grid and sigma_scale, for callers that cannot
  * allocate device memory when they need it (inside a region where cudaMalloc

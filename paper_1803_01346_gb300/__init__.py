@@ -30,7 +30,8 @@ _LIBNAME = "libscfft.so"
 EXPORTS = ("scfft_create", "scfft_set_geometry", "scfft_set_jc_map", "scfft_set_field_path",
            "scfft_precompute_kernel", "scfft_rhs", "scfft_curl", "scfft_phi", "scfft_integrate",
            "scfft_step", "scfft_profile", "scfft_profile_read", "scfft_kind_name",
-           "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy", "scfft_curl_noalloc")
+           "scfft_rhs_vjp", "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy",
+           "scfft_curl_noalloc")
 
 NKINDS = 14
 
@@ -108,6 +109,7 @@ def load_library(path: Optional[str] = None):
         "scfft_status_string": (ctypes.c_char_p, [I]),
         "scfft_destroy": (V, [P]),
         "scfft_curl_noalloc": (I, [ctypes.POINTER(_Grid), D, P, P, P]),
+        "scfft_rhs_vjp": (I, [P, P, P, P, P, P, ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -248,6 +250,13 @@ class Context:
         self._check(self._lib.scfft_profile_read(self._h, cnt, ms), "scfft_profile_read")
         return {self._lib.scfft_kind_name(k).decode(): (cnt[k], ms[k]) for k in range(NKINDS)}
 
+    def rhs_vjp(self, h, lam, mu_h, mu_g=None, mu_jc=None):
+        """Reverse-mode derivative of the fixed-iteration rhs; returns mu_a (3 floats)."""
+        mu_a = (ctypes.c_double * 3)()
+        self._check(self._lib.scfft_rhs_vjp(self._h, _ptr(h), _ptr(lam), _ptr(mu_h), _ptr(mu_g), _ptr(mu_jc),
+                                            mu_a), "scfft_rhs_vjp")
+        return [mu_a[0], mu_a[1], mu_a[2]]
+
     def sync(self):
         self._check(self._lib.scfft_sync(self._h), "scfft_sync")
 
@@ -255,3 +264,41 @@ class Context:
         st = _Stats()
         self._check(self._lib.scfft_get_stats(self._h, ctypes.byref(st)), "scfft_get_stats")
         return {k: getattr(st, k) for k, _ in _Stats._fields_}
+
+
+def _autograd():
+    import torch
+
+    class RhsFunction(torch.autograd.Function):
+        """dh/dt = rhs(t, h, warm[, jc]) as a differentiable torch op; the backward
+        pass is the library's hand-written reverse mode (scfft_rhs_vjp).  The
+        context must iterate Eq. 5 a fixed number of times (delta_it = 0), so that
+        forward and backward describe the same map."""
+
+        @staticmethod
+        def forward(fctx, sc, t, h, warm, jc=None):
+            if jc is not None:
+                sc.set_jc_map(jc.detach().contiguous())
+            out = torch.empty_like(h)
+            w = warm.detach().clone()
+            sc.rhs(float(t), h.detach().contiguous(), w, out)
+            fctx.sc = sc
+            fctx.has_jc = jc is not None
+            fctx.save_for_backward(h.detach())
+            return out
+
+        @staticmethod
+        def backward(fctx, lam):
+            (h,) = fctx.saved_tensors
+            mu_h = torch.empty_like(h)
+            mu_g = torch.empty_like(h)
+            mu_jc = torch.empty(h.numel() // 3, dtype=h.dtype, device=h.device) if fctx.has_jc else None
+            fctx.sc.rhs_vjp(h, lam.contiguous(), mu_h, mu_g, mu_jc)
+            return None, None, mu_h, mu_g, mu_jc
+
+    return RhsFunction
+
+
+def rhs_autograd(sc: "Context", t: float, h, warm, jc=None):
+    """Differentiable dh/dt (see RhsFunction): gradients flow to h, warm and jc."""
+    return _autograd().apply(sc, t, h, warm, jc)

@@ -56,6 +56,11 @@ struct scfft_ctx {
   double* ynew64 = nullptr;
   double* comp64 = nullptr;
   const float* last32 = nullptr;  // output of the most recent rhs (the next warm start)
+  // reverse mode: forward j, two cotangent buffers (FP64) and per-block sums of mu_a
+  double* adj = nullptr;
+  double* adj_part = nullptr;
+  double* hadj_part = nullptr;  // pinned
+  int adj_part_cap = 0;
   scfft_stats stats{};
   // profiling
   bool prof_on = false;
@@ -735,6 +740,106 @@ scfft_status bs23_step_f32(scfft_ctx* c, double* t_io, double* dt_io, double tst
   }
 }
 
+// ---------------------------------------------------------------- reverse mode of one rhs
+constexpr int kSumBlocks = 152 * 2;
+
+// per-block sums of (1 - chi) lam over the nodes, per component (deterministic: the host adds the blocks in order)
+__global__ void chib_sum_kernel(const double* __restrict__ lam, const uint8_t* __restrict__ mask, long long N,
+                                double* __restrict__ part) {
+  double s[3] = {0.0, 0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    if (!mask[i]) { s[0] += lam[i]; s[1] += lam[N + i]; s[2] += lam[2 * N + i]; }
+  __shared__ double red[3][8];
+  for (int q = 0; q < 3; ++q) {
+    double v = s[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) v += red[threadIdx.x][w];
+    part[blockIdx.x * 3 + threadIdx.x] = v;
+  }
+}
+
+// mu_g = (1 - chi) lam
+__global__ void chib_mask_kernel(const double* __restrict__ lam, const uint8_t* __restrict__ mask, long long N,
+                                 double* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const bool in = mask[i];
+    out[i] = in ? 0.0 : lam[i];
+    out[N + i] = in ? 0.0 : lam[N + i];
+    out[2 * N + i] = in ? 0.0 : lam[2 * N + i];
+  }
+}
+
+template <typename T>
+scfft_status vjp_impl(scfft_ctx* c, const double* h, const double* lam, double* mu_h, double* mu_g, double* mu_jc,
+                      double* mu_a) {
+  const long long N = c->g.N, n3 = 3 * N;
+  const int K = c->opt.max_iter;
+  if (!c->adj) CK(cudaMalloc(&c->adj, sizeof(double) * 3 * n3));
+  if (c->adj_part_cap < K + 1) {
+    cudaFree(c->adj_part);
+    if (c->hadj_part) cudaFreeHost(c->hadj_part);
+    c->adj_part = nullptr;
+    c->hadj_part = nullptr;
+    c->adj_part_cap = 0;
+    CK(cudaMalloc(&c->adj_part, sizeof(double) * 3 * kSumBlocks * (K + 1)));
+    CK(cudaHostAlloc(&c->hadj_part, sizeof(double) * 3 * kSumBlocks * (K + 1), 0));
+    c->adj_part_cap = K + 1;
+  }
+  double* jf = c->adj;
+  double* lb[2] = {c->adj + n3, c->adj + 2 * n3};
+  Launch<T> L = launch_of<T>(c);
+  PointParams pp = base_params(c);
+  // forward j = C h (the power law's Jacobian needs it)
+  CK(run(c, SCFFT_K_OTHER, [&] { return launch_x<T>(L, X_FWD_F64, pp, h, nullptr, nullptr, 0, 0, false); }));
+  CK(curl_in_U<T>(c, L, false));
+  CK(run(c, SCFFT_K_OTHER, [&] { return launch_x<T>(L, X_TO_F64, pp, nullptr, jf, nullptr, 0, 0, false); }));
+  // transposed iterations: lam_i = chi lam_{i+1} + C chi Phi (1 - chi) lam_{i+1}
+  const double* cur = lam;
+  for (int i = 0; i < K; ++i) {
+    double* nxt = lb[i & 1];
+    CK(run(c, SCFFT_K_OTHER, [&] {
+      chib_sum_kernel<<<kSumBlocks, 256, 0, c->st>>>(cur, c->mask, N, c->adj_part + (size_t)i * 3 * kSumBlocks);
+      return cudaGetLastError();
+    }));
+    CK(run(c, SCFFT_K_OTHER, [&] { return launch_x<T>(L, X_ADJ_PAD, pp, cur, nullptr, nullptr, 0, 0, false); }));
+    CK(run(c, SCFFT_K_Y_FWD_P, [&] { return launch_y<T>(L, true, false, false); }));
+    CK(run(c, SCFFT_K_Z_KERNEL, [&] { return launch_z_kernel<T>(L, false); }));
+    CK(run(c, SCFFT_K_Y_INV_P, [&] { return launch_y<T>(L, true, true, false); }));
+    CK(run(c, SCFFT_K_OTHER, [&] { return launch_x<T>(L, X_ADJ_CROP, pp, nullptr, nullptr, nullptr, 0, 0, false); }));
+    CK(curl_in_U<T>(c, L, false));
+    CK(run(c, SCFFT_K_OTHER, [&] { return launch_x<T>(L, X_ADJ_COMBINE, pp, cur, nxt, nullptr, 0, 0, false); }));
+    cur = nxt;
+  }
+  // dh^0 = chi u + (1 - chi) g:  mu_g = (1 - chi) lam_0,  lam_u = chi lam_0
+  if (mu_g)
+    CK(run(c, SCFFT_K_OTHER, [&] {
+      chib_mask_kernel<<<blocks_for(N), 256, 0, c->st>>>(cur, c->mask, N, mu_g);
+      return cudaGetLastError();
+    }));
+  // u = -C e / mu0; e = E(j); j = C h
+  CK(run(c, SCFFT_K_OTHER, [&] { return launch_x<T>(L, X_ADJ_IN, pp, cur, nullptr, nullptr, 0, 0, false); }));
+  CK(curl_in_U<T>(c, L, false));
+  CK(run(c, SCFFT_K_OTHER, [&] { return launch_x<T>(L, X_ADJ_POWERLAW, pp, jf, mu_jc, nullptr, 0, 0, false); }));
+  CK(curl_in_U<T>(c, L, false));
+  CK(run(c, SCFFT_K_OTHER, [&] { return launch_x<T>(L, X_TO_F64, pp, nullptr, mu_h, nullptr, 0, 0, false); }));
+  if (mu_a) {
+    CK(cudaMemcpyAsync(c->hadj_part, c->adj_part, sizeof(double) * 3 * kSumBlocks * K, cudaMemcpyDeviceToHost, c->st));
+  }
+  CK(cudaStreamSynchronize(c->st));
+  if (mu_a) {
+    mu_a[0] = mu_a[1] = mu_a[2] = 0.0;
+    for (int i = 0; i < K; ++i)
+      for (int b = 0; b < kSumBlocks; ++b)
+        for (int q = 0; q < 3; ++q) mu_a[q] += c->hadj_part[((size_t)i * kSumBlocks + b) * 3 + q];
+  }
+  return SCFFT_OK;
+}
+
 scfft_status step_any(scfft_ctx* c, double* t, double* dt, double tstop, double* h, double* warm, double dt_fixed,
                       int* rej) {
   return c->opt.precision == SCFFT_PREC_F32 ? bs23_step_f32(c, t, dt, tstop, h, warm, dt_fixed, rej)
@@ -817,7 +922,8 @@ void scfft_destroy(scfft_ctx* c) {
   free_work(c->wf);
   free_work(c->wd);
   cudaFree(c->ctrl); cudaFree(c->partials); cudaFree(c->mask); cudaFree(c->ib); cudaFree(c->errbits);
-  cudaFree(c->ib32); cudaFree(c->ynew64);
+  cudaFree(c->ib32); cudaFree(c->ynew64); cudaFree(c->adj); cudaFree(c->adj_part);
+  if (c->hadj_part) cudaFreeHost(c->hadj_part);
   if (c->hctrl) cudaFreeHost(c->hctrl);
   if (c->herr) cudaFreeHost(c->herr);
   for (int i = 0; i < 2; ++i) if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -970,6 +1076,15 @@ scfft_status scfft_integrate(scfft_ctx* c, double t0, double t1, double dt0, int
     stats->launches = c->stats.launches - before.launches;
   }
   return SCFFT_OK;
+}
+
+scfft_status scfft_rhs_vjp(scfft_ctx* c, const double* h, const double* lam, double* mu_h, double* mu_g, double* mu_jc,
+                           double* mu_a) {
+  if (!c || !h || !lam || !mu_h || mu_h == h || mu_h == lam) return SCFFT_EINVAL;
+  if (!c->have_geom || !c->have_kernel) return SCFFT_ESTATE;
+  c->fsal_valid = false;
+  return c->opt.precision == SCFFT_PREC_F32 ? vjp_impl<float>(c, h, lam, mu_h, mu_g, mu_jc, mu_a)
+                                            : vjp_impl<double>(c, h, lam, mu_h, mu_g, mu_jc, mu_a);
 }
 
 scfft_status scfft_sync(scfft_ctx* c) {

@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(kThreads) xpass_kernel(const XArgs<T> a) {
   for (int i = tid; i < a.Lin; i += nth) twi[i] = a.tw_in[i];
   for (int i = tid; i < a.Lout; i += nth) two[i] = a.tw_out[i];
 
-  constexpr bool kC2R = (MODE != X_FWD_F64 && MODE != X_PAD_F64);
-  constexpr bool kR2C = (MODE != X_TO_F64 && MODE != X_CROP_F64);
+  constexpr bool kC2R = (MODE != X_FWD_F64 && MODE != X_PAD_F64 && MODE != X_ADJ_PAD && MODE != X_ADJ_IN);
+  constexpr bool kR2C = (MODE != X_TO_F64 && MODE != X_CROP_F64 && MODE != X_ADJ_COMBINE);
 
   V* data;
   V* other;
@@ -153,7 +153,12 @@ __global__ void __launch_bounds__(kThreads) xpass_kernel(const XArgs<T> a) {
       const int n = idx % nx, r = (idx / nx) % R, c = idx / (nx * R);
       const int q = q0 + r;
       T v = 0;
-      if (q < nrows) v = (T)a.src_f64[(size_t)c * N + (size_t)q * nx + n];
+      if (q < nrows) {
+        const size_t node = (size_t)q * nx + n;
+        v = (T)a.src_f64[(size_t)c * N + node];
+        if (MODE == X_ADJ_PAD && a.mask[node]) v = 0;   // (1 - chi)
+        if (MODE == X_ADJ_IN && !a.mask[node]) v = 0;   // chi
+      }
       *half_of<T>(&bufA[c * CS + (r >> 1) + n * ES], r & 1) = v;
     }
     data = bufA;
@@ -162,7 +167,7 @@ __global__ void __launch_bounds__(kThreads) xpass_kernel(const XArgs<T> a) {
 
   // ---- node-wise step on the real rows held in `data`
   double part = 0.0;
-  if (MODE != X_FWD_F64 && MODE != X_PAD_F64) {
+  if (kC2R) {
     const PointParams& pp = a.pp;
     for (int idx = tid; idx < R * nx; idx += nth) {
       const int n = idx % nx, r = idx / nx;
@@ -205,6 +210,31 @@ __global__ void __launch_bounds__(kThreads) xpass_kernel(const XArgs<T> a) {
         a.hnew[node] = v0; a.hnew[N + node] = v1; a.hnew[2 * N + node] = v2;
       } else if (MODE == X_TO_F64 || MODE == X_CROP_F64) {
         a.dst_f64[node] = (double)v0; a.dst_f64[N + node] = (double)v1; a.dst_f64[2 * N + node] = (double)v2;
+      } else if (MODE == X_ADJ_CROP) {
+        if (!a.mask[node]) { v0 = 0; v1 = 0; v2 = 0; }
+      } else if (MODE == X_ADJ_COMBINE) {
+        const bool in = a.mask[node];
+        a.dst_f64[node] = (double)v0 + (in ? a.src_f64[node] : 0.0);
+        a.dst_f64[N + node] = (double)v1 + (in ? a.src_f64[N + node] : 0.0);
+        a.dst_f64[2 * N + node] = (double)v2 + (in ? a.src_f64[2 * N + node] : 0.0);
+      } else if (MODE == X_ADJ_POWERLAW) {
+        // lam_e = -(curl lam_u)/mu0; lam_j = J_e^T lam_e; J_e = rho (I + (n-1) jhat jhat^T) in Omega
+        const T s = -(T)pp.inv_mu0;
+        const T l0 = s * v0, l1 = s * v1, l2 = s * v2;
+        if (a.mask[node]) {
+          const T j0 = (T)a.src_f64[node], j1 = (T)a.src_f64[N + node], j2 = (T)a.src_f64[2 * N + node];
+          const T jcv = a.jc ? a.jc[node] : (T)pp.jc;
+          const T jn = sqrt(j0 * j0 + j1 * j1 + j2 * j2);
+          const T rho = rho_power(jn, jcv, (T)pp.n, (T)pp.e0);
+          const T jl = j0 * l0 + j1 * l1 + j2 * l2;
+          const T f = jn > 0 ? ((T)pp.n - 1) * jl / (jn * jn) : (T)0;
+          v0 = rho * (l0 + f * j0); v1 = rho * (l1 + f * j1); v2 = rho * (l2 + f * j2);
+          if (a.dst_f64) a.dst_f64[node] = (double)(-(T)pp.n * rho / jcv * jl);
+        } else {
+          const T r = (T)pp.rho_out;
+          v0 = r * l0; v1 = r * l1; v2 = r * l2;
+          if (a.dst_f64) a.dst_f64[node] = 0.0;
+        }
       }
       if (kR2C) { *p0 = v0; *p1 = v1; *p2 = v2; }
     }
@@ -508,15 +538,17 @@ template <typename T>
 cudaError_t launch_x(const Launch<T>& L, XMode mode, const PointParams& pp, const double* src_f64, double* dst_f64,
                      const double* warm, int in_buf, int out_buf, bool check_done) {
   typedef typename cplx_of<T>::type V;
+  // the FP32 forward passes use the register-resident kernels; the transposed
+  // (reverse-mode) passes use this shared-memory kernel in both precisions
   if constexpr (sizeof(T) == 4)
-    return launch_x_reg(L, mode, pp, src_f64, dst_f64, warm, in_buf, out_buf, check_done);
+    if (mode < X_ADJ_PAD) return launch_x_reg(L, mode, pp, src_f64, dst_f64, warm, in_buf, out_buf, check_done);
   XArgs<T> a{};
   const Geo& g = L.g;
   a.g = g;
-  const bool pin = (mode == X_UPDATE || mode == X_CROP_F64);
-  const bool pout = (mode == X_MASKPAD || mode == X_PAD_F64);
-  const bool c2r = !(mode == X_FWD_F64 || mode == X_PAD_F64);
-  const bool r2c = !(mode == X_TO_F64 || mode == X_CROP_F64);
+  const bool pin = (mode == X_UPDATE || mode == X_CROP_F64 || mode == X_ADJ_CROP);
+  const bool pout = (mode == X_MASKPAD || mode == X_PAD_F64 || mode == X_ADJ_PAD);
+  const bool c2r = !(mode == X_FWD_F64 || mode == X_PAD_F64 || mode == X_ADJ_PAD || mode == X_ADJ_IN);
+  const bool r2c = !(mode == X_TO_F64 || mode == X_CROP_F64 || mode == X_ADJ_COMBINE);
   a.Lin = c2r ? (pin ? 2 * g.nx : g.nx) : 0;
   a.Lout = r2c ? (pout ? 2 * g.nx : g.nx) : 0;
   a.Lmax = a.Lin > a.Lout ? a.Lin : a.Lout;
@@ -555,7 +587,8 @@ cudaError_t launch_x(const Launch<T>& L, XMode mode, const PointParams& pp, cons
     xpass_kernel<T, M><<<grid, kThreads, smem, L.st>>>(a);                                               \
     break;
     XCASE(X_FWD_F64) XCASE(X_POWERLAW) XCASE(X_ASSEMBLE) XCASE(X_MASKPAD) XCASE(X_UPDATE) XCASE(X_TO_F64)
-    XCASE(X_PAD_F64) XCASE(X_CROP_F64)
+    XCASE(X_PAD_F64) XCASE(X_CROP_F64) XCASE(X_ADJ_PAD) XCASE(X_ADJ_CROP) XCASE(X_ADJ_COMBINE) XCASE(X_ADJ_IN)
+    XCASE(X_ADJ_POWERLAW)
 #undef XCASE
   }
   return cudaGetLastError();

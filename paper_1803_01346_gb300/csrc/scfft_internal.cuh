@@ -55,7 +55,14 @@ enum XMode : int {
   X_UPDATE = 4,   // Pd -> C2R(2nx), crop -> Eq. 5 update + residual -> Hd[next]; R2C(nx) -> U
   X_TO_F64 = 5,   // U -> C2R(nx) -> real f64 rows
   X_PAD_F64 = 6,  // real f64 rows -> zero pad -> R2C(2nx) -> Pd
-  X_CROP_F64 = 7  // Pd -> C2R(2nx), crop -> real f64 rows
+  X_CROP_F64 = 7, // Pd -> C2R(2nx), crop -> real f64 rows
+  // transposed steps of the fixed-iteration rhs (reverse mode):
+  X_ADJ_PAD = 8,      // real f64 rows x (1 - chi) -> zero pad -> R2C(2nx) -> Pd
+  X_ADJ_CROP = 9,     // Pd -> C2R(2nx), crop -> x chi -> R2C(nx) -> U
+  X_ADJ_COMBINE = 10, // U -> C2R(nx) -> dst = chi * src + (.)   (f64 rows)
+  X_ADJ_IN = 11,      // real f64 rows x chi -> R2C(nx) -> U
+  X_ADJ_POWERLAW = 12 // U -> C2R(nx) -> lam_e = -(.)/mu0 -> power-law Jacobian^T (forward j in src) -> R2C(nx) -> U;
+                      //   dst (N values, optional) = d e/d jc . lam_e
 };
 
 // Scalars of the material law and the Eq. 5 update.
