@@ -53,7 +53,7 @@ __all__ = [
     "rhs", "RhsResult",
     "BS23_C", "BS23_A", "BS23_B", "BS23_BHAT", "BS23_E",
     "bs23_step", "error_norm", "integrate", "IntegrateResult",
-    "magnetic_moment", "dissipation", "rhs_vjp", "RhsVJP",
+    "magnetic_moment", "dissipation", "rhs_vjp", "RhsVJP", "integrate_adjoint", "StepAdjoint",
 ]
 
 
@@ -546,3 +546,89 @@ def rhs_vjp(prob: Problem, t: float, h: np.ndarray, lam: np.ndarray, K: int, lef
     mu_jc = np.where(mask, -mat.n * rho / jc * np.sum(j * lam_e, axis=0), 0.0)
     mu_h = C(lam_j)
     return RhsVJP(mu_h, mu_g, mu_jc, mu_a)
+
+
+# ----------------------------------------------------------------------------
+# Adjoint of fixed-step BS23 (frozen step list, fixed Eq. 5 iteration count)
+# ----------------------------------------------------------------------------
+@dataclass
+class StepAdjoint:
+    y: np.ndarray       # forward end state y_S
+    mu_y0: np.ndarray   # dJ/dy_0 for J = <lam_T, y_S>
+    mu_jc: np.ndarray   # dJ/djc (per node)
+    mu_a: np.ndarray    # dJ/d(dh_e/dt), summed over every rhs call
+
+
+def integrate_adjoint(prob: Problem, t0: float, dts: Sequence[float], y0: np.ndarray, lam_T: np.ndarray,
+                      K: int) -> StepAdjoint:
+    """Discrete adjoint of the fixed-step BS23 map y_0 -> y_S (Bogacki-Shampine
+    pair as in `integrate` with dt_list, no kinks inside the run) with each rhs
+    iterating Eq. 5 exactly K times.  The forward chain of one step is
+        Y2 = y + dt a21 k1,  k2 = F(Y2, g=k1),  Y3 = y + dt a32 k2,  k3 = F(Y3, g=k2),
+        y' = y + dt (b1 k1 + b2 k2 + b3 k3),  k4 = F(y', g=k3),  next k1 = k4 (FSAL),
+    with k1 = F(y_0, g_0) at the start and g_0 = dh_e/dt(t0) (reading R-warm);
+    the reverse sweep transposes it call by call with rhs_vjp."""
+    a21, a32 = BS23_A[1][0], BS23_A[2][1]
+    b1, b2, b3 = BS23_B[0], BS23_B[1], BS23_B[2]
+    F = lambda t, y, g: rhs(prob, t, y, g, delta_it=0.0, max_iter=K).hdot  # noqa: E731
+    g0 = np.broadcast_to(prob.path.hedot(t0)[:, None, None, None], y0.shape).copy()
+    # forward, storing y_n, k1_n and t_n
+    ys, k1s, ts = [y0.copy()], [], [t0]
+    k1 = F(t0, y0, g0)
+    y, t = y0.copy(), t0
+    for dt in dts:
+        k1s.append(k1)
+        Y2 = y + dt * a21 * k1
+        k2 = F(t + 0.5 * dt, Y2, k1)
+        Y3 = y + dt * a32 * k2
+        k3 = F(t + 0.75 * dt, Y3, k2)
+        y = y + dt * (b1 * k1 + b2 * k2 + b3 * k3)
+        k1 = F(t + dt, y, k3)
+        t = t + dt
+        ys.append(y.copy())
+        ts.append(t)
+    # reverse
+    ybar = lam_T.copy()
+    k1bar_next = np.zeros_like(y0)  # cotangent of the FSAL stage carried into the step after
+    mu_jc = np.zeros(prob.mask.shape)
+    mu_a = np.zeros(3)
+    for n in range(len(dts) - 1, -1, -1):
+        dt, yn, k1, tn = dts[n], ys[n], k1s[n], ts[n]
+        Y2 = yn + dt * a21 * k1
+        k2 = F(tn + 0.5 * dt, Y2, k1)
+        Y3 = yn + dt * a32 * k2
+        k3 = F(tn + 0.75 * dt, Y3, k2)
+        ynew = ys[n + 1]
+        k1bar = np.zeros_like(yn)
+        k2bar = np.zeros_like(yn)
+        k3bar = np.zeros_like(yn)
+        # k4 = F(y', k3)
+        v = rhs_vjp(prob, tn + dt, ynew, k1bar_next, K)
+        ybar_new = ybar + v.mu_h
+        k3bar += v.mu_g
+        mu_jc += v.mu_jc
+        mu_a += v.mu_a
+        # y' = y + dt (b1 k1 + b2 k2 + b3 k3)
+        ybar = ybar_new.copy()
+        k1bar += dt * b1 * ybar_new
+        k2bar += dt * b2 * ybar_new
+        k3bar += dt * b3 * ybar_new
+        # k3 = F(Y3, k2), Y3 = y + dt a32 k2
+        v = rhs_vjp(prob, tn + 0.75 * dt, Y3, k3bar, K)
+        ybar += v.mu_h
+        k2bar += v.mu_g + dt * a32 * v.mu_h
+        mu_jc += v.mu_jc
+        mu_a += v.mu_a
+        # k2 = F(Y2, k1), Y2 = y + dt a21 k1
+        v = rhs_vjp(prob, tn + 0.5 * dt, Y2, k2bar, K)
+        ybar += v.mu_h
+        k1bar += v.mu_g + dt * a21 * v.mu_h
+        mu_jc += v.mu_jc
+        mu_a += v.mu_a
+        k1bar_next = k1bar
+    # k1 = F(y_0, g_0)
+    v = rhs_vjp(prob, t0, ys[0], k1bar_next, K)
+    ybar += v.mu_h
+    mu_jc += v.mu_jc
+    mu_a += v.mu_a
+    return StepAdjoint(ys[-1], ybar, mu_jc, mu_a)

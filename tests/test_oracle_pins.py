@@ -431,3 +431,42 @@ def test_rhs_vjp_matches_finite_differences():
     p3 = O.Problem(g, prob.mask, prob.mat, O.FieldPath([0, 1], [[0, 0, 0], list(np.array([0.3, -0.2, 0.9]) + da)]),
                    Khat=prob.kernel())
     assert np.sum(lam * (F(h, gw, p3) - F(h, gw))) == pytest.approx(v.mu_a @ da, rel=1e-10)
+
+
+def test_step_adjoint_matches_finite_differences():
+    """Discrete adjoint of fixed-step BS23 (three steps, K = 3 iterations per
+    rhs) against central differences of the forward integrator: y_0 to
+    O(eps^2); jc and the applied rate to the accuracy the cancellation allows."""
+    n, L = (10, 12, 8), (1.0, 1.1, 0.8)
+    g = O.Grid(n, L)
+    mask = I.cube(n, L, 1.0)
+    jc = I.jc_noise((n[2], n[1], n[0]), 3)
+    path = O.FieldPath([0, 1], [[0, 0, 0], [0.3, -0.2, 0.9]])
+    prob = O.Problem(g, mask, O.Material(n=7.0, rho_out=5.0, jc=jc), path)
+    rng = np.random.default_rng(0)
+    y0 = O.phi_hockney(O.curl_s(rng.standard_normal((3,) + g.shape) * 0.5, g) * mask, g) + 0.05
+    lamT = rng.standard_normal(y0.shape)
+    dts, K = [0.002, 0.003, 0.003], 3
+    res = O.integrate_adjoint(prob, 0.1, dts, y0, lamT, K)
+
+    def J(yy, pr=prob):
+        r = O.integrate(pr, 0.1, 0.1 + sum(dts), yy, rtol=1, atol=1, dt0=dts[0], delta_it=0.0, max_iter=K,
+                        dt_list=dts)
+        return np.sum(lamT * r.y)
+
+    v = rng.standard_normal(y0.shape)
+    eps = 1e-4
+    assert (J(y0 + eps * v) - J(y0 - eps * v)) / (2 * eps) == pytest.approx(np.sum(res.mu_y0 * v), rel=1e-8)
+    dj = rng.standard_normal(jc.shape) * 0.01
+
+    def Jj(jcv):
+        return J(y0, O.Problem(g, mask, O.Material(n=7.0, rho_out=5.0, jc=jcv), path, Khat=prob.kernel()))
+    eps = 1e-3
+    assert (Jj(jc + eps * dj) - Jj(jc - eps * dj)) / (2 * eps) == pytest.approx(np.sum(res.mu_jc * dj), rel=1e-4)
+    da = np.array([0.2, -0.1, 0.3])
+
+    def Ja(d):
+        p2 = O.Problem(g, mask, prob.mat, O.FieldPath([0, 1], [[0, 0, 0], list(np.array([0.3, -0.2, 0.9]) + d)]),
+                       Khat=prob.kernel())
+        return J(y0, p2)
+    assert (Ja(1e-3 * da) - Ja(-1e-3 * da)) / 2e-3 == pytest.approx(res.mu_a @ da, rel=1e-4)
