@@ -209,6 +209,22 @@ const char* scfft_kind_name(int kind);
 scfft_status scfft_rhs_vjp(scfft_ctx* ctx, const double* h, const double* lam, double* mu_h, double* mu_g,
                            double* mu_jc, double* mu_a);
 
+/* Discrete adjoint of the fixed-step BS23 map y_0 -> y_S: steps dts[0..nsteps-1]
+ * (host) from t0, first stage k1 = rhs(y_0) with warm start dh_e/dt(t0),
+ * FSAL, each stage's warm start = the previous rhs result, every rhs taking
+ * exactly max_iter Eq. 5 iterations (delta_it is ignored during the call),
+ * dh_e/dt taken at the stage times (right derivative; steps are not clipped
+ * at kinks of the path).  For J = <lam_T, y_S> it returns mu_y0 = dJ/dy_0
+ * (device 3N), mu_jc = dJ/djc (device N or NULL), mu_a = dJ/d(dh_e/dt) summed
+ * over every rhs call (host double[3] or NULL) and y_S (device 3N or NULL).
+ * States are checkpointed every checkpoint_every steps in the forward sweep and
+ * each segment is recomputed during the reverse sweep (memory: about
+ * (14 + 2 nsteps/checkpoint_every + 2 checkpoint_every) * 3N doubles, allocated
+ * for the call).  y0, lam_T: device 3N.  Synchronous. */
+scfft_status scfft_adjoint_integrate(scfft_ctx* ctx, double t0, const double* dts, int nsteps, const double* y0,
+                                     const double* lam_T, double* y_end, double* mu_y0, double* mu_jc,
+                                     double* mu_a, int checkpoint_every);
+
 /* Allocation-free spectral curl: out = curl_S f, the same result as
  * scfft_curl (FP64) on the same grid and sigma_scale, for callers that cannot
  * allocate device memory when they need it (inside a region where cudaMalloc

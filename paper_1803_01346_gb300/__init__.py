@@ -30,7 +30,7 @@ _LIBNAME = "libscfft.so"
 EXPORTS = ("scfft_create", "scfft_set_geometry", "scfft_set_jc_map", "scfft_set_field_path",
            "scfft_precompute_kernel", "scfft_rhs", "scfft_curl", "scfft_phi", "scfft_integrate",
            "scfft_step", "scfft_profile", "scfft_profile_read", "scfft_kind_name",
-           "scfft_rhs_vjp", "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy",
+           "scfft_rhs_vjp", "scfft_adjoint_integrate", "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy",
            "scfft_curl_noalloc")
 
 NKINDS = 14
@@ -110,6 +110,7 @@ def load_library(path: Optional[str] = None):
         "scfft_destroy": (V, [P]),
         "scfft_curl_noalloc": (I, [ctypes.POINTER(_Grid), D, P, P, P]),
         "scfft_rhs_vjp": (I, [P, P, P, P, P, P, ctypes.POINTER(D)]),
+        "scfft_adjoint_integrate": (I, [P, D, P, I, P, P, P, P, P, ctypes.POINTER(D), I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -255,6 +256,15 @@ class Context:
         mu_a = (ctypes.c_double * 3)()
         self._check(self._lib.scfft_rhs_vjp(self._h, _ptr(h), _ptr(lam), _ptr(mu_h), _ptr(mu_g), _ptr(mu_jc),
                                             mu_a), "scfft_rhs_vjp")
+        return [mu_a[0], mu_a[1], mu_a[2]]
+
+    def adjoint_integrate(self, t0, dts, y0, lam_T, mu_y0, y_end=None, mu_jc=None, checkpoint_every=50):
+        """Discrete adjoint of fixed-step BS23 (see scfft.h); returns mu_a."""
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        mu_a = (ctypes.c_double * 3)()
+        self._check(self._lib.scfft_adjoint_integrate(self._h, float(t0), d.ctypes.data, len(d), _ptr(y0),
+                                                      _ptr(lam_T), _ptr(y_end), _ptr(mu_y0), _ptr(mu_jc), mu_a,
+                                                      int(checkpoint_every)), "scfft_adjoint_integrate")
         return [mu_a[0], mu_a[1], mu_a[2]]
 
     def sync(self):

@@ -1087,6 +1087,187 @@ scfft_status scfft_rhs_vjp(scfft_ctx* c, const double* h, const double* lam, dou
                                             : vjp_impl<double>(c, h, lam, mu_h, mu_g, mu_jc, mu_a);
 }
 
+// Discrete adjoint of fixed-step BS23 over a frozen step list (see scfft.h).
+namespace {
+
+struct AdjBufs {
+  double* base = nullptr;
+  double *y, *k1, *k2, *k3, *Y, *Y2, *yn, *w, *ybar, *k1b, *k2b, *k3b, *mh, *mg, *jct, *jcacc;
+  double *cpy, *cpk, *sgy, *sgk;
+};
+
+scfft_status adj_alloc(scfft_ctx* c, int ncp, int seg, AdjBufs& b) {
+  const size_t n3 = 3 * (size_t)c->g.N, N = (size_t)c->g.N;
+  const size_t total = 14 * n3 + 2 * N + 2 * (size_t)ncp * n3 + 2 * (size_t)seg * n3;
+  if (cudaMalloc(&b.base, sizeof(double) * total) != cudaSuccess) return SCFFT_ENOMEM;
+  double* p = b.base;
+  double** arr[] = {&b.y,    &b.k1,  &b.k2,  &b.k3,  &b.Y, &b.Y2, &b.yn,
+                    &b.w,    &b.ybar, &b.k1b, &b.k2b, &b.k3b, &b.mh, &b.mg};
+  for (double** a : arr) { *a = p; p += n3; }
+  b.jct = p; p += N;
+  b.jcacc = p; p += N;
+  b.cpy = p; p += (size_t)ncp * n3;
+  b.cpk = p; p += (size_t)ncp * n3;
+  b.sgy = p; p += (size_t)seg * n3;
+  b.sgk = p;
+  return SCFFT_OK;
+}
+
+// out = x + a*y over n values (out may alias x)
+cudaError_t axpy(scfft_ctx* c, double* out, const double* x, double a, const double* y, long long n) {
+  return run(c, SCFFT_K_RK, [&] {
+    combine_kernel<<<blocks_for(n), 256, 0, c->st>>>(out, x, 1.0, a, y, 0, nullptr, 0, nullptr, n);
+    return cudaGetLastError();
+  });
+}
+
+__global__ void scale_kernel(double* __restrict__ out, double a, const double* __restrict__ x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = a * x[i];
+}
+
+cudaError_t scal(scfft_ctx* c, double* out, double a, const double* x, long long n) {
+  return run(c, SCFFT_K_RK, [&] {
+    scale_kernel<<<blocks_for(n), 256, 0, c->st>>>(out, a, x, n);
+    return cudaGetLastError();
+  });
+}
+
+// k_out = F(t, Y; warm = g), leaving g untouched
+scfft_status rhs_keep(scfft_ctx* c, AdjBufs& b, double t, const double* Y, const double* g, double* out) {
+  const size_t n3 = 3 * (size_t)c->g.N;
+  CK(cudaMemcpyAsync(b.w, g, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->st));
+  return rhs_any(c, t, 0, Y, b.w, out, nullptr);
+}
+
+// forward stages of one step from (y, k1): fills k2, k3, Y (=Y3), yn (= y')
+scfft_status adj_stages(scfft_ctx* c, AdjBufs& b, double t, double dt, const double* y, const double* k1, double* Y2) {
+  const long long n3 = 3 * c->g.N;
+  CK(axpy(c, Y2, y, dt * 0.5, k1, n3));
+  CS_(rhs_keep(c, b, t + 0.5 * dt, Y2, k1, b.k2));
+  CK(axpy(c, b.Y, y, dt * 0.75, b.k2, n3));
+  CS_(rhs_keep(c, b, t + 0.75 * dt, b.Y, b.k2, b.k3));
+  CK(run(c, SCFFT_K_RK, [&] {
+    combine_kernel<<<blocks_for(n3), 256, 0, c->st>>>(b.yn, y, dt, 2.0 / 9.0, k1, 1.0 / 3.0, b.k2, 4.0 / 9.0, b.k3,
+                                                      n3);
+    return cudaGetLastError();
+  }));
+  return SCFFT_OK;
+}
+
+scfft_status adj_vjp(scfft_ctx* c, AdjBufs& b, const double* Y, const double* lam, double* mu_a_acc, bool jc) {
+  double ma[3];
+  CS_(c->opt.precision == SCFFT_PREC_F32 ? vjp_impl<float>(c, Y, lam, b.mh, b.mg, jc ? b.jct : nullptr, ma)
+                                         : vjp_impl<double>(c, Y, lam, b.mh, b.mg, jc ? b.jct : nullptr, ma));
+  for (int q = 0; q < 3; ++q) mu_a_acc[q] += ma[q];
+  if (jc) CK(axpy(c, b.jcacc, b.jcacc, 1.0, b.jct, c->g.N));
+  return SCFFT_OK;
+}
+
+scfft_status adjoint_integrate(scfft_ctx* c, double t0, const double* dts, int S, const double* y0,
+                               const double* lamT, double* y_end, double* mu_y0, double* mu_jc, double* mu_a,
+                               int C) {
+  const long long n3 = 3 * c->g.N;
+  const size_t bytes = sizeof(double) * n3;
+  const int ncp = (S + C - 1) / C;
+  AdjBufs b;
+  CS_(adj_alloc(c, ncp, C, b));
+  struct Free { double* p; ~Free() { cudaFree(p); } } guard{b.base};
+  double ma[3] = {0, 0, 0};
+  // forward: checkpoints (y_n, K1_n) every C steps
+  double g0[3];
+  hedot_at(c, t0, 0, g0);
+  CK(run(c, SCFFT_K_RK, [&] {
+    fill3_kernel<<<blocks_for(c->g.N), 256, 0, c->st>>>(b.w, g0[0], g0[1], g0[2], c->g.N);
+    return cudaGetLastError();
+  }));
+  CK(cudaMemcpyAsync(b.y, y0, bytes, cudaMemcpyDeviceToDevice, c->st));
+  CS_(rhs_any(c, t0, 0, b.y, b.w, b.k1, nullptr));
+  std::vector<double> tn(S + 1);
+  tn[0] = t0;
+  for (int n = 0; n < S; ++n) tn[n + 1] = tn[n] + dts[n];
+  for (int n = 0; n < S; ++n) {
+    if (n % C == 0) {
+      CK(cudaMemcpyAsync(b.cpy + (size_t)(n / C) * n3, b.y, bytes, cudaMemcpyDeviceToDevice, c->st));
+      CK(cudaMemcpyAsync(b.cpk + (size_t)(n / C) * n3, b.k1, bytes, cudaMemcpyDeviceToDevice, c->st));
+    }
+    CS_(adj_stages(c, b, tn[n], dts[n], b.y, b.k1, b.Y));
+    CK(cudaMemcpyAsync(b.y, b.yn, bytes, cudaMemcpyDeviceToDevice, c->st));
+    CS_(rhs_keep(c, b, tn[n + 1], b.y, b.k3, b.k1));  // FSAL: next k1 = F(y', g = k3)
+  }
+  if (y_end) CK(cudaMemcpyAsync(y_end, b.y, bytes, cudaMemcpyDeviceToDevice, c->st));
+  // reverse sweep, one checkpoint segment at a time
+  CK(cudaMemcpyAsync(b.ybar, lamT, bytes, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaMemsetAsync(b.k1b, 0, bytes, c->st));
+  CK(cudaMemsetAsync(b.jcacc, 0, sizeof(double) * c->g.N, c->st));
+  for (int m = ncp - 1; m >= 0; --m) {
+    const int n0 = m * C, n1 = std::min(S, n0 + C);
+    // recompute the segment's (y_n, K1_n)
+    CK(cudaMemcpyAsync(b.sgy, b.cpy + (size_t)m * n3, bytes, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(b.sgk, b.cpk + (size_t)m * n3, bytes, cudaMemcpyDeviceToDevice, c->st));
+    for (int n = n0; n + 1 < n1; ++n) {
+      double* yi = b.sgy + (size_t)(n - n0) * n3;
+      double* ki = b.sgk + (size_t)(n - n0) * n3;
+      CS_(adj_stages(c, b, tn[n], dts[n], yi, ki, b.Y));
+      CK(cudaMemcpyAsync(yi + n3, b.yn, bytes, cudaMemcpyDeviceToDevice, c->st));
+      CS_(rhs_keep(c, b, tn[n + 1], b.yn, b.k3, ki + n3));
+    }
+    for (int n = n1 - 1; n >= n0; --n) {
+      // reverse of step n: ybar = cotangent of y_{n+1} -> of y_n; k1b = cotangent of K1_{n+1} -> of K1_n
+      const double dt = dts[n];
+      const double* yi = b.sgy + (size_t)(n - n0) * n3;
+      const double* ki = b.sgk + (size_t)(n - n0) * n3;
+      const bool jc = mu_jc != nullptr;
+      CS_(adj_stages(c, b, tn[n], dt, yi, ki, b.Y2));  // Y2, k2, Y (= Y3), k3, yn (= y_{n+1})
+      // K1_{n+1} = F(y_{n+1}, g = k3)
+      CS_(adj_vjp(c, b, b.yn, b.k1b, ma, jc));
+      CK(axpy(c, b.ybar, b.ybar, 1.0, b.mh, n3));
+      CK(cudaMemcpyAsync(b.k3b, b.mg, bytes, cudaMemcpyDeviceToDevice, c->st));
+      // y_{n+1} = y_n + dt (b1 k1 + b2 k2 + b3 k3)
+      CK(scal(c, b.k1b, dt * 2.0 / 9.0, b.ybar, n3));
+      CK(scal(c, b.k2b, dt / 3.0, b.ybar, n3));
+      CK(axpy(c, b.k3b, b.k3b, dt * 4.0 / 9.0, b.ybar, n3));
+      // k3 = F(Y3, g = k2), Y3 = y_n + dt a32 k2
+      CS_(adj_vjp(c, b, b.Y, b.k3b, ma, jc));
+      CK(axpy(c, b.ybar, b.ybar, 1.0, b.mh, n3));
+      CK(axpy(c, b.k2b, b.k2b, dt * 0.75, b.mh, n3));
+      CK(axpy(c, b.k2b, b.k2b, 1.0, b.mg, n3));
+      // k2 = F(Y2, g = k1), Y2 = y_n + dt a21 k1
+      CS_(adj_vjp(c, b, b.Y2, b.k2b, ma, jc));
+      CK(axpy(c, b.ybar, b.ybar, 1.0, b.mh, n3));
+      CK(axpy(c, b.k1b, b.k1b, dt * 0.5, b.mh, n3));
+      CK(axpy(c, b.k1b, b.k1b, 1.0, b.mg, n3));
+    }
+  }
+  // k1 = F(y_0, g_0)
+  CS_(adj_vjp(c, b, b.cpy, b.k1b, ma, mu_jc != nullptr));
+  CK(axpy(c, b.ybar, b.ybar, 1.0, b.mh, n3));
+  CK(cudaMemcpyAsync(mu_y0, b.ybar, bytes, cudaMemcpyDeviceToDevice, c->st));
+  if (mu_jc) CK(cudaMemcpyAsync(mu_jc, b.jcacc, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (mu_a)
+    for (int q = 0; q < 3; ++q) mu_a[q] = ma[q];
+  return SCFFT_OK;
+}
+
+}  // namespace
+
+scfft_status scfft_adjoint_integrate(scfft_ctx* c, double t0, const double* dts, int nsteps, const double* y0,
+                                     const double* lam_T, double* y_end, double* mu_y0, double* mu_jc, double* mu_a,
+                                     int checkpoint_every) {
+  if (!c || !dts || nsteps < 1 || !y0 || !lam_T || !mu_y0 || checkpoint_every < 1) return SCFFT_EINVAL;
+  for (int n = 0; n < nsteps; ++n)
+    if (!(dts[n] > 0)) return SCFFT_EINVAL;
+  if (!c->have_geom || !c->have_kernel || !c->have_path) return SCFFT_ESTATE;
+  // the adjoint describes the frozen map: exactly max_iter iterations per rhs
+  const double saved = c->opt.delta_it;
+  c->opt.delta_it = 0.0;
+  c->fsal_valid = false;
+  scfft_status s = adjoint_integrate(c, t0, dts, nsteps, y0, lam_T, y_end, mu_y0, mu_jc, mu_a, checkpoint_every);
+  c->opt.delta_it = saved;
+  return s;
+}
+
 scfft_status scfft_sync(scfft_ctx* c) {
   if (!c) return SCFFT_EINVAL;
   CK(cudaStreamSynchronize(c->st));

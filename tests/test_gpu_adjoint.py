@@ -105,3 +105,24 @@ def test_autograd_rhs_matches_central_differences():
         fm = S.rhs_autograd(ctx, 0.4, ht, warm, jc - eps * dj)
     fd = float(((fp - fm) * lt).sum() / (2 * eps))
     assert fd == pytest.approx(float((jc.grad * dj).sum()), rel=1e-5)
+
+
+@pytest.mark.parametrize("prec,tol", [(S.PREC_F64, 1e-10), (S.PREC_F32, 1e-3)])
+def test_adjoint_integrate_matches_oracle(prec, tol):
+    """Checkpointed reverse sweep (checkpoints every 2 of 5 steps, so segments
+    are recomputed) against the oracle's step adjoint."""
+    K = 3
+    n, L = (16, 16, 16), (1.0, 1.0, 1.0)
+    ctx, prob, h, lam = _setup(n, L, prec, K)
+    dts = [0.002, 0.003, 0.002, 0.0025, 0.003]
+    ref = O.integrate_adjoint(prob, 0.1, dts, h, lam, K)
+    N = int(np.prod(n))
+    mu_y0 = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+    y_end = torch.empty_like(mu_y0)
+    mu_jc = torch.empty(N, dtype=torch.float64, device="cuda")
+    mu_a = ctx.adjoint_integrate(0.1, dts, dev(h), dev(lam), mu_y0, y_end=y_end, mu_jc=mu_jc, checkpoint_every=2)
+    torch.cuda.synchronize()
+    assert rel(y_end.cpu().numpy().reshape(h.shape), ref.y) < tol
+    assert rel(mu_y0.cpu().numpy().reshape(h.shape), ref.mu_y0) < tol
+    assert rel(mu_jc.cpu().numpy().reshape(ref.mu_jc.shape), ref.mu_jc) < (tol if prec == S.PREC_F64 else 1e-2)
+    assert rel(np.array(mu_a), ref.mu_a) < (tol if prec == S.PREC_F64 else 1e-2)
