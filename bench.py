@@ -218,6 +218,57 @@ def bench_reference(args, ws, rank):
     return 0
 
 
+def bench_batch(S, torch, steps: int, warmup: int):
+    """64 independent shield instances (grids 32..96^3, FP32 FFTs) advanced by
+    scfft_batch_step, each context on its own stream; compared with the same
+    instances stepped one after another."""
+    cfgs = I.batch_configs(64, seed=1803)
+    streams = [torch.cuda.Stream() for _ in cfgs]
+    inst = []
+    for c, st in zip(cfgs, streams):
+        ctx = S.Context(c.n, c.L, n_power=c.n_power, rho_out=c.rho_out, precision=S.PREC_F32, rtol=c.rtol,
+                        atol=c.atol, stream=st.cuda_stream)
+        ctx.set_geometry(c.mask)
+        ctx.set_field_path(c.knots_t, c.knots_he)
+        ctx.precompute_kernel()
+        N = int(np.prod(c.n))
+        h = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+        w = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+        rate = np.asarray(c.knots_he[1]) / c.knots_t[1]
+        for q in range(3):
+            w.view(3, N)[q] = float(rate[q])
+        inst.append((ctx, h, w, N))
+    torch.cuda.synchronize()
+    ctxs = [x[0] for x in inst]
+    t = [0.0] * len(inst)
+    dt = [1e-4] * len(inst)
+    stop = [c.t_end for c in cfgs]
+    hs = [x[1] for x in inst]
+    wsv = [x[2] for x in inst]
+    for _ in range(warmup):
+        t, dt, _ = S.batch_step(ctxs, t, dt, stop, hs, wsv)
+    torch.cuda.synchronize()
+    c0 = [x[0].stats()["rhs_calls"] for x in inst]
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        t, dt, _ = S.batch_step(ctxs, t, dt, stop, hs, wsv)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    evals = sum(x[3] * (x[0].stats()["rhs_calls"] - c) for x, c in zip(inst, c0))
+    # the same instances, one after another
+    t1 = time.perf_counter()
+    for i, (ctx, h, w, N) in enumerate(inst):
+        ti, di = t[i], dt[i]
+        for _ in range(steps):
+            ti, di, _ = ctx.step(ti, di, stop[i], h, w)
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t1
+    return {"instances": len(inst), "grids": sorted({c.n[0] for c in cfgs}), "steps": steps,
+            "instance_steps_per_s": len(inst) * steps / el, "voxel_rhs_evals_per_s": evals / el,
+            "sequential_instance_steps_per_s": len(inst) * steps / seq, "speedup_vs_sequential": seq / el,
+            "timing": "wall clock around synchronous batch calls, device synchronised on both sides"}
+
+
 def bench_ours(args, ws, rank, local):
     import torch
     import paper_1803_01346_gb300 as S
@@ -336,6 +387,7 @@ def bench_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     fp64_value = N * (ctx64.stats()["rhs_calls"] - c0) / (e4.elapsed_time(e5) * 1e-3)
 
+    batch = None if (args.no_batch or rank != 0) else bench_batch(S, torch, max(2, min(args.steps, 5)), 2)
     if rank != 0:
         return 0
     cpu = None
@@ -366,6 +418,7 @@ def bench_ours(args, ws, rank, local):
         "pass_shares": shares,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "batch": batch,
     }
     line["config"]["t_start"] = None
     print(json.dumps(line), flush=True)
@@ -379,6 +432,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":

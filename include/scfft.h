@@ -192,6 +192,18 @@ scfft_status scfft_profile(scfft_ctx* ctx, int enable);
 scfft_status scfft_profile_read(scfft_ctx* ctx, long long* counts, double* ms);
 const char* scfft_kind_name(int kind);
 
+/* Batched instances: advance nb independent contexts (one problem each: its
+ * own grid, geometry, material, applied-field path) by one accepted BS23 step
+ * each, as scfft_step does, concurrently: the contexts' steps are driven from
+ * up to 64 host threads, so the GPU overlaps the instances' kernels when each
+ * context owns its own CUDA stream (give every context a distinct stream at
+ * scfft_create).  t, dt, tstop: host arrays of nb; h, warm: host arrays of nb
+ * device pointers (3N_i doubles each).  status: host array of nb or NULL
+ * (per-instance result).  Returns the first non-OK status (all instances are
+ * attempted).  Synchronous. */
+scfft_status scfft_batch_step(scfft_ctx** ctxs, int nb, double* t, double* dt, const double* tstop, double** h,
+                              double** warm, scfft_status* status);
+
 /* Reverse-mode derivative (vector-Jacobian product) of the rhs map
  * F(h, warm, jc, dh_e/dt) = dh/dt of scfft_rhs taken with exactly max_iter
  * Eq. 5 iterations (no early stop; with a converged forward iteration this is
@@ -250,6 +262,10 @@ scfft_status scfft_sync(scfft_ctx* ctx);
 scfft_status scfft_get_stats(scfft_ctx* ctx, scfft_stats* out);
 
 const char* scfft_status_string(scfft_status s);
+
+/* Text of the CUDA error behind the most recent SCFFT_ECUDA returned by any
+ * entry point in this process ("" if none); for diagnostics. */
+const char* scfft_last_cuda_error(void);
 
 /* Free every workspace.  NULL is a no-op. */
 void scfft_destroy(scfft_ctx* ctx);

@@ -30,8 +30,8 @@ _LIBNAME = "libscfft.so"
 EXPORTS = ("scfft_create", "scfft_set_geometry", "scfft_set_jc_map", "scfft_set_field_path",
            "scfft_precompute_kernel", "scfft_rhs", "scfft_curl", "scfft_phi", "scfft_integrate",
            "scfft_step", "scfft_profile", "scfft_profile_read", "scfft_kind_name",
-           "scfft_rhs_vjp", "scfft_adjoint_integrate", "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy",
-           "scfft_curl_noalloc")
+           "scfft_rhs_vjp", "scfft_adjoint_integrate", "scfft_batch_step", "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy",
+           "scfft_curl_noalloc", "scfft_last_cuda_error")
 
 NKINDS = 14
 
@@ -42,6 +42,8 @@ def library_path() -> str:
 
 class ScfftError(RuntimeError):
     def __init__(self, code: int, what: str, msg: str):
+        if code == 3 and _lib is not None:
+            msg = f"{msg}: {_lib.scfft_last_cuda_error().decode()}"
         super().__init__(f"{what}: {msg} (status {code})")
         self.code = code
 
@@ -110,7 +112,9 @@ def load_library(path: Optional[str] = None):
         "scfft_destroy": (V, [P]),
         "scfft_curl_noalloc": (I, [ctypes.POINTER(_Grid), D, P, P, P]),
         "scfft_rhs_vjp": (I, [P, P, P, P, P, P, ctypes.POINTER(D)]),
+        "scfft_last_cuda_error": (ctypes.c_char_p, []),
         "scfft_adjoint_integrate": (I, [P, D, P, I, P, P, P, P, P, ctypes.POINTER(D), I]),
+        "scfft_batch_step": (I, [P, I, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -312,3 +316,22 @@ def _autograd():
 def rhs_autograd(sc: "Context", t: float, h, warm, jc=None):
     """Differentiable dh/dt (see RhsFunction): gradients flow to h, warm and jc."""
     return _autograd().apply(sc, t, h, warm, jc)
+
+
+def batch_step(ctxs, t, dt, tstop, h, warm):
+    """One accepted BS23 step for each of several independent contexts,
+    concurrently (scfft_batch_step).  t, dt, tstop: sequences of floats; h, warm:
+    sequences of float64 CUDA tensors.  Returns (t_new, dt_new, statuses)."""
+    lib = load_library()
+    nb = len(ctxs)
+    C = ctypes.c_void_p * nb
+    Dn = ctypes.c_double * nb
+    cs = C(*[c._h.value for c in ctxs])
+    tt, dd, ts = Dn(*t), Dn(*dt), Dn(*tstop)
+    hp = C(*[_ptr(x) for x in h])
+    wp = C(*[_ptr(x) for x in warm])
+    st = (ctypes.c_int * nb)()
+    code = lib.scfft_batch_step(cs, nb, tt, dd, ts, hp, wp, st)
+    if code not in (0,):
+        raise ScfftError(code, "scfft_batch_step", lib.scfft_status_string(code).decode())
+    return list(tt), list(dd), list(st)

@@ -6,7 +6,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "scfft.h"
@@ -73,10 +76,23 @@ struct scfft_ctx {
 
 namespace {
 
-#define CK(x)                                  \
-  do {                                         \
-    cudaError_t e_ = (x);                      \
-    if (e_ != cudaSuccess) return SCFFT_ECUDA; \
+// The most recent CUDA error behind an SCFFT_ECUDA (process wide, for diagnostics).
+std::mutex g_err_mutex;
+char g_err_text[512] = "";
+
+void note_cuda_error(cudaError_t e, int line) {
+  std::lock_guard<std::mutex> lock(g_err_mutex);
+  snprintf(g_err_text, sizeof(g_err_text), "%s (%s) at capi.cu:%d; last failed launch: %s", cudaGetErrorName(e),
+           cudaGetErrorString(e), line, last_launch_failure());
+}
+
+#define CK(x)                               \
+  do {                                      \
+    cudaError_t e_ = (x);                   \
+    if (e_ != cudaSuccess) {                \
+      note_cuda_error(e_, __LINE__);        \
+      return SCFFT_ECUDA;                   \
+    }                                       \
   } while (0)
 
 #define CS_(x)                            \
@@ -1266,6 +1282,40 @@ scfft_status scfft_adjoint_integrate(scfft_ctx* c, double t0, const double* dts,
   scfft_status s = adjoint_integrate(c, t0, dts, nsteps, y0, lam_T, y_end, mu_y0, mu_jc, mu_a, checkpoint_every);
   c->opt.delta_it = saved;
   return s;
+}
+
+scfft_status scfft_batch_step(scfft_ctx** ctxs, int nb, double* t, double* dt, const double* tstop, double** h,
+                              double** warm, scfft_status* status) {
+  if (!ctxs || nb < 1 || !t || !dt || !tstop || !h || !warm) return SCFFT_EINVAL;
+  for (int i = 0; i < nb; ++i) {
+    if (!ctxs[i] || !h[i] || !warm[i]) return SCFFT_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return SCFFT_EINVAL;  // one context is one instance
+  }
+  std::vector<scfft_status> res(nb, SCFFT_OK);
+  std::atomic<int> next(0);
+  auto worker = [&]() {
+    for (int i = next++; i < nb; i = next++) res[i] = scfft_step(ctxs[i], &t[i], &dt[i], tstop[i], h[i], warm[i], nullptr);
+  };
+  const int nth = std::min(nb, 64);
+  std::vector<std::thread> pool;
+  pool.reserve(nth - 1);
+  for (int k = 1; k < nth; ++k) pool.emplace_back(worker);
+  worker();
+  for (auto& th : pool) th.join();
+  scfft_status first = SCFFT_OK;
+  for (int i = 0; i < nb; ++i) {
+    if (status) status[i] = res[i];
+    if (first == SCFFT_OK && res[i] != SCFFT_OK) first = res[i];
+  }
+  return first;
+}
+
+const char* scfft_last_cuda_error(void) {
+  std::lock_guard<std::mutex> lock(g_err_mutex);
+  static thread_local char copy[512];
+  memcpy(copy, g_err_text, sizeof(copy));
+  return copy;
 }
 
 scfft_status scfft_sync(scfft_ctx* c) {

@@ -13,10 +13,24 @@
 // Two real rows of one component travel as the real and imaginary parts of one
 // complex pencil in the x passes (two real transforms for one complex one).
 #include <math.h>
+#include <stdio.h>
 
 #include "scfft_internal.cuh"
 
 namespace scfft {
+
+// ---------------------------------------------------------------- launch diagnostics
+static char g_launch_fail[256] = "";
+
+cudaError_t checked_launch(const char* what, dim3 grid, int block, size_t smem) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    snprintf(g_launch_fail, sizeof(g_launch_fail), "%s grid (%u,%u,%u) block %d smem %zu: %s", what, grid.x, grid.y,
+             grid.z, block, smem, cudaGetErrorString(e));
+  return e;
+}
+
+const char* last_launch_failure() { return g_launch_fail; }
 
 // ---------------------------------------------------------------- plans
 bool length_supported(int L) {
@@ -583,9 +597,9 @@ cudaError_t launch_x(const Launch<T>& L, XMode mode, const PointParams& pp, cons
   switch (mode) {
 #define XCASE(M)                                                                                         \
   case M:                                                                                                \
-    cudaFuncSetAttribute(xpass_kernel<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
+    allow_smem<xpass_kernel<T, M>>();                                                                  \
     xpass_kernel<T, M><<<grid, kThreads, smem, L.st>>>(a);                                               \
-    break;
+    return checked_launch("xpass_kernel", dim3(grid), kThreads, smem);
     XCASE(X_FWD_F64) XCASE(X_POWERLAW) XCASE(X_ASSEMBLE) XCASE(X_MASKPAD) XCASE(X_UPDATE) XCASE(X_TO_F64)
     XCASE(X_PAD_F64) XCASE(X_CROP_F64) XCASE(X_ADJ_PAD) XCASE(X_ADJ_CROP) XCASE(X_ADJ_COMBINE) XCASE(X_ADJ_IN)
     XCASE(X_ADJ_POWERLAW)
@@ -618,11 +632,13 @@ cudaError_t launch_y(const Launch<T>& L, bool padded, bool inverse, bool check_d
   dim3 grid((a.HX + a.TC - 1) / a.TC, g.nz, 3);
   const size_t smem = (size_t)(2 * Ly * (a.TC + 1) + 256) * sizeof(V);
   if (inverse) {
-    cudaFuncSetAttribute(ypass_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_smem<ypass_kernel<T, true>>();
     ypass_kernel<T, true><<<grid, kThreads, smem, L.st>>>(a);
+    return checked_launch("ypass_kernel inv", grid, kThreads, smem);
   } else {
-    cudaFuncSetAttribute(ypass_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_smem<ypass_kernel<T, false>>();
     ypass_kernel<T, false><<<grid, kThreads, smem, L.st>>>(a);
+    return checked_launch("ypass_kernel fwd", grid, kThreads, smem);
   }
   return cudaGetLastError();
 }
@@ -654,11 +670,13 @@ static cudaError_t launch_z(const Launch<T>& L, bool padded, bool check_done, do
   dim3 grid((a.HX + a.TC - 1) / a.TC, a.rows, 1);
   const size_t smem = (size_t)(2 * 3 * Lz * (a.TC + 1) + 256) * sizeof(V);
   if (padded) {
-    cudaFuncSetAttribute(zpass_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_smem<zpass_kernel<T, 1>>();
     zpass_kernel<T, 1><<<grid, kThreads, smem, L.st>>>(a);
+    return checked_launch("zpass_kernel 1", grid, kThreads, smem);
   } else {
-    cudaFuncSetAttribute(zpass_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_smem<zpass_kernel<T, 0>>();
     zpass_kernel<T, 0><<<grid, kThreads, smem, L.st>>>(a);
+    return checked_launch("zpass_kernel 0", grid, kThreads, smem);
   }
   return cudaGetLastError();
 }

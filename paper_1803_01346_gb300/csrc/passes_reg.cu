@@ -229,7 +229,7 @@ cudaError_t go_y(const Launch<float>& L, float2* base, int rows, int sx, int HX,
   constexpr int Lt = R1 * R2;
   const size_t smem = sizeof(float2) * (Lt + R2 * (R1 * TC + kPad8));
   auto k = ypass_reg_kernel<float, R1, R2, TC, INV, PIN, POUT>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_smem<ypass_reg_kernel<float, R1, R2, TC, INV, PIN, POUT>>();
   dim3 grid((HX + TC - 1) / TC, L.g.nz, 3);
   k<<<grid, TC * R1, smem, L.st>>>(base, rows, sx, HX, L.g.nz, tw, L.ctrl, chk ? 1 : 0);
   return cudaGetLastError();
@@ -242,7 +242,7 @@ cudaError_t go_z(const Launch<float>& L, float2* base, int rows, int sx, int HX,
   constexpr int CS = cmax(cmax(R2 * (R1 * TC + kPad8), R1 * (R2 * TC + kPad8)), Lt * TC);
   const size_t smem = sizeof(float2) * (Lt + 3 * CS);
   auto k = zpass_reg2_kernel<R1, R2, TC, KIND>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_smem<zpass_reg2_kernel<R1, R2, TC, KIND>>();
   dim3 grid((HX + TC - 1) / TC, rows, 1);
   const Work<float>& w = *L.w;
   k<<<grid, TC * R1, smem, L.st>>>(base, rows, sx, HX, L.g.nz, tw, w.kt[0], w.kt[1], w.kt[2], w.st[0], w.st[1],
@@ -651,7 +651,7 @@ cudaError_t go_x(const XRArgs& a, cudaStream_t st) {
   const size_t smem =
       sizeof(float2) * ((S::Li > 0 ? S::Li : 1) + (S::Lo > 0 ? S::Lo : 1) + 3 * kPairs * XL + kPairs * TT);
   auto k = xpass_reg2_kernel<MODE, R1i, R2i, R2o, kPairs>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  allow_smem<xpass_reg2_kernel<MODE, R1i, R2i, R2o, kPairs>>();
   const int npairs = a.g.ny * a.g.nz / 2;
   k<<<(npairs + kPairs - 1) / kPairs, kPairs * S::TP, smem, st>>>(a);
   return cudaGetLastError();

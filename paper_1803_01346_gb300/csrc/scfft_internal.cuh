@@ -10,6 +10,25 @@ namespace scfft {
 
 constexpr int kThreads = 256;  // every FFT pass kernel runs 256-thread CTAs
 
+// Allow a kernel the largest dynamic shared memory a CTA may use, once per
+// kernel (thread-safe static initialisation).  Raising the cap once, instead of
+// setting it to each launch's size, keeps launches from concurrent host threads
+// (batched instances of different sizes) from racing on the attribute.
+template <auto Kern> inline void allow_smem() {
+  static const cudaError_t once = [] {
+    cudaFuncAttributes fa{};
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaFuncGetAttributes(&fa, Kern);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // the cap covers dynamic shared memory only: leave room for the kernel's static arrays
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
+  }();
+  (void)once;
+}
+
 // Device-side control block of one context (one rhs at a time per context).
 struct Ctrl {
   int done;           // Eq. 5 stop reached: loop kernels of later iterations return at entry
@@ -110,6 +129,10 @@ cudaError_t launch_x_reg(const Launch<float>& L, XMode mode, const PointParams& 
 cudaError_t launch_x_reg_io(const Launch<float>& L, XMode mode, const PointParams& pp, const double* src_f64,
                             const float* src_f32, double* dst_f64, const double* warm, const float* warm_f32,
                             int in_buf, int out_buf, bool check_done);
+
+// Launch diagnostics: the last failed launch (kernel, grid, block, shared memory).
+cudaError_t checked_launch(const char* what, dim3 grid, int block, size_t smem);
+const char* last_launch_failure();
 
 FftPlan make_plan(int L);
 bool length_supported(int L);

@@ -19,7 +19,7 @@ from typing import Optional
 import numpy as np
 
 __all__ = ["node_axes", "cube", "sphere", "cylinder", "shield", "lens", "Config", "config",
-           "CONFIGS", "random_field", "jc_noise"]
+           "CONFIGS", "random_field", "jc_noise", "batch_configs"]
 
 
 def node_axes(n, L):
@@ -149,3 +149,27 @@ def random_field(shape, seed: int, scale: float = 1.0) -> np.ndarray:
 def jc_noise(shape, seed: int, amp: float = 0.05) -> np.ndarray:
     """jc = 1 + U[-amp, amp] per node (seeded)."""
     return 1.0 + np.random.default_rng(seed).uniform(-amp, amp, size=shape)
+
+
+def batch_configs(count: int = 64, seed: int = 1803) -> list:
+    """Independent shield instances for batched runs: grids drawn from
+    {32, 48, 64, 96}^3 in a cubic box of side 3.2, a hollow cylinder R 1 / 0.8,
+    height 2, cap 0.2 (the shield shortened so that it keeps a margin in the
+    cubic box), applied-field direction uniform on the sphere, ramp amplitude
+    U[0.3, 1.5] x 0.2 (jc times the wall thickness) reached at rate 1, n drawn
+    from {15, 25, 50}, rho_out = 20."""
+    rng = np.random.default_rng(seed)
+    out = []
+    L = (1.6, 1.6, 1.6)
+    for i in range(count):
+        N = int(rng.choice([32, 48, 64, 96]))
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        amp = float(rng.uniform(0.3, 1.5) * 0.2)
+        npow = float(rng.choice([15.0, 25.0, 50.0]))
+        n = (N, N, N)
+        out.append(Config(f"shield{N}_{i}", n, L, shield(n, L, 1.0, 0.8, 2.0, 0.2), npow, 20.0,
+                          [0.0, amp, amp + 1.0], [[0, 0, 0], list(amp * d), list(amp * d)],
+                          rtol=2e-4, atol=1e-6 * amp, t_end=amp + 1.0,
+                          note=f"shield instance {i}: {N}^3, n={npow}, |h_e|={amp:.3f}"))
+    return out
