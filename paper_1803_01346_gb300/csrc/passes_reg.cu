@@ -653,8 +653,18 @@ cudaError_t go_x(const XRArgs& a, cudaStream_t st) {
   auto k = xpass_reg2_kernel<MODE, R1i, R2i, R2o, kPairs>;
   allow_smem<xpass_reg2_kernel<MODE, R1i, R2i, R2o, kPairs>>();
   const int npairs = a.g.ny * a.g.nz / 2;
-  k<<<(npairs + kPairs - 1) / kPairs, kPairs * S::TP, smem, st>>>(a);
-  return cudaGetLastError();
+  const int ntiles = (npairs + kPairs - 1) / kPairs;
+  // one wave of resident CTAs (the kernel loops over tiles)
+  static const int resident = [&] {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kPairs * S::TP, smem);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return per_sm > 0 && sms > 0 ? per_sm * sms : 1024;
+  }();
+  const int grid = ntiles < resident ? ntiles : resident;
+  k<<<grid, kPairs * S::TP, smem, st>>>(a);
+  return checked_launch("xpass_reg2_kernel", dim3(grid), kPairs * S::TP, smem);
 }
 
 // Splits per unpadded length n: C2R(n) = (a, b), C2R(2n) = (c, d); the R2C
@@ -888,208 +898,239 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP)
   const int ny = a.g.ny, nz = a.g.nz;
   const long long N = a.g.N;
   const int npairs = ny * nz / 2;
-  const int gp = blockIdx.x * P + p;
-  const bool pok = gp < npairs;
-  const int qa = 2 * (pok ? gp : 0);
-  const int z = qa / ny, ya = qa - z * ny;
-  float2* Tp = T + p * TT;
-
-  // L2 prefetch of everything this CTA reads after its first phase (components 1
-  // and 2 of the input rows, and the node-wise step's rows), so that those later
-  // phases see L2 rather than DRAM latency; it costs no registers.
-  {
-    const int row0 = 2 * blockIdx.x * P;  // first (z, y) row of this CTA
-    const int nrow = 2 * P;
-    if constexpr (S::C2R) {
-      const int lines = ((Li / 2 + 1) * 8 + 127) / 128;  // 128-byte lines per half-spectrum row
-      for (int i = tid; i < 2 * nrow * lines; i += NT) {
-        const int ln = i % lines, rr = (i / lines) % nrow, q = 1 + i / (lines * nrow);
-        const int qrow = row0 + rr;
-        if (qrow < 2 * npairs) {
-          const int zz = qrow / ny, yy = qrow - zz * ny;
-          prefetch_l2(a.spec_in + ((size_t)(q * nz + zz) * a.in_rows + yy) * a.in_sx + ln * 16);
-        }
-      }
-    }
-    const size_t nb0 = (size_t)row0 * XL;
-    const int rl = (XL * 4 + 127) / 128;  // lines per FP32 node row
-    if (MODE == X_UPDATE)
-      for (int i = tid; i < 3 * nrow * rl; i += NT) {
-        const int ln = i % rl, rr = (i / rl) % nrow, q = i / (rl * nrow);
-        if (row0 + rr < 2 * npairs) prefetch_l2(a.hold + q * N + nb0 + (size_t)rr * XL + ln * 32);
-      }
-    if (MODE == X_ASSEMBLE && a.warm)
-      for (int i = tid; i < 3 * nrow * 2 * rl; i += NT) {
-        const int ln = i % (2 * rl), rr = (i / (2 * rl)) % nrow, q = i / (2 * rl * nrow);
-        if (row0 + rr < 2 * npairs) prefetch_l2(a.warm + q * N + nb0 + (size_t)rr * XL + ln * 16);
-      }
-    if (MODE == X_UPDATE || MODE == X_ASSEMBLE || MODE == X_MASKPAD || MODE == X_POWERLAW)
-      for (int i = tid * 128; i < nrow * XL; i += NT * 128)
-        if (row0 + i / XL < 2 * npairs) prefetch_l2(a.mask + nb0 + i);
-  }
-
-  if constexpr (S::C2R) {
-    __syncthreads();  // twiddles
-    for (int q = 0; q < 3; ++q) {
-      const int n1 = r;
-      if (n1 < R1i) {
-        const float2* ra = a.spec_in + ((size_t)(q * nz + z) * a.in_rows + ya) * a.in_sx;
-        const float2* rb = ra + a.in_sx;
-        float2 v[R2i];
-#pragma unroll
-        for (int n2 = 0; n2 < R2i; ++n2) {
-          const int k = n1 + R1i * n2;
-          const bool lo = k <= Li / 2;
-          const int kk = lo ? k : Li - k;
-          float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
-          if (pok) { A = ra[kk]; B = rb[kk]; }
-          if (kk == 0 || kk == Li / 2) { A.y = 0.f; B.y = 0.f; }
-          v[n2] = lo ? make_float2(A.x - B.y, A.y + B.x) : make_float2(A.x + B.y, B.x - A.y);
-        }
-        DFT<R2i, true, float2>::run(v);
-#pragma unroll
-        for (int k2 = 0; k2 < R2i; ++k2) Tp[k2 * (R1i + 1) + n1] = k2 == 0 ? v[0] : cmulc(v[k2], twi[n1 * k2]);
-      }
-      __syncthreads();
-      const int k2 = r;
-      if (k2 < R2i) {
-        float2 w[R1i];
-#pragma unroll
-        for (int m = 0; m < R1i; ++m) w[m] = Tp[k2 * (R1i + 1) + m];
-        DFT<R1i, true, float2>::run(w);
-#pragma unroll
-        for (int k1 = 0; k1 < S::KX; ++k1) RS[(q * P + p) * XL + k2 + R2i * k1] = w[k1];
-      }
-      __syncthreads();
-    }
-  } else {
-    // real f64 rows into RS
-    for (int idx = tid; idx < 3 * P * XL; idx += NT) {
-      const int x = idx % XL, pp2 = (idx / XL) % P, q = idx / (XL * P);
-      const int g2 = blockIdx.x * P + pp2;
-      float2 zv = make_float2(0.f, 0.f);
-      if (g2 < npairs) {
-        const size_t na = (size_t)(2 * g2) * XL + x;
-        zv = a.src_f32 ? make_float2(a.src_f32[q * N + na], a.src_f32[q * N + na + XL])
-                       : make_float2((float)a.src_f64[q * N + na], (float)a.src_f64[q * N + na + XL]);
-      }
-      RS[(q * P + pp2) * XL + x] = zv;
-    }
-    __syncthreads();
-  }
-
-  // ---- node-wise step
+  const int ntiles = (npairs + P - 1) / P;
   float partf = 0.f;
-  if constexpr (S::C2R) {
-    const PointParams& pp = a.pp;
-    for (int idx = tid; idx < P * XL; idx += NT) {
-      const int x = idx % XL, pp2 = idx / XL;
-      const int g2 = blockIdx.x * P + pp2;
-      if (g2 >= npairs) continue;
-      const size_t na = (size_t)(2 * g2) * XL + x, nb = na + XL;
-      float2 u[3];
-#pragma unroll
-      for (int q = 0; q < 3; ++q) u[q] = RS[(q * P + pp2) * XL + x];
-      if (MODE == X_POWERLAW) {
-        const bool ia = a.mask[na], ib = a.mask[nb];
-        const float ca = a.jc ? a.jc[na] : (float)pp.jc, cb = a.jc ? a.jc[nb] : (float)pp.jc;
-        const float ra = rho_of(u[0].x, u[1].x, u[2].x, ia, ca, pp);
-        const float rb = rho_of(u[0].y, u[1].y, u[2].y, ib, cb, pp);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) u[q] = make_float2(u[q].x * ra, u[q].y * rb);
-      } else if (MODE == X_ASSEMBLE) {
-        const bool ia = a.mask[na], ib = a.mask[nb];
-        const float s = -(float)pp.inv_mu0;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const float va = ia ? s * u[q].x : (a.warm_f32 ? a.warm_f32[q * N + na] : (float)a.warm[q * N + na]);
-          const float vb = ib ? s * u[q].y : (a.warm_f32 ? a.warm_f32[q * N + nb] : (float)a.warm[q * N + nb]);
-          a.hnew[q * N + na] = va;
-          a.hnew[q * N + nb] = vb;
-          u[q] = make_float2(va, vb);
+  // persistent CTAs: each walks tiles of P row pairs with a stride of the grid
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // prefetch the next tile's first-phase rows into L2 while this tile runs
+    if (tile + (int)gridDim.x < ntiles) {
+      const int nrow0 = 2 * (tile + (int)gridDim.x) * P;
+      if constexpr (S::C2R) {
+        const int lines = ((Li / 2 + 1) * 8 + 127) / 128;
+        for (int i = tid; i < 2 * P * lines; i += NT) {
+          const int ln = i % lines, rr = i / lines;
+          const int qrow = nrow0 + rr;
+          if (qrow < 2 * npairs) {
+            const int zz = qrow / ny, yy = qrow - zz * ny;
+            prefetch_l2(a.spec_in + ((size_t)zz * a.in_rows + yy) * a.in_sx + ln * 16);
+          }
         }
-      } else if (MODE == X_MASKPAD) {
-        const bool ia = a.mask[na], ib = a.mask[nb];
-#pragma unroll
-        for (int q = 0; q < 3; ++q) u[q] = make_float2(ia ? u[q].x : 0.f, ib ? u[q].y : 0.f);
-      } else if (MODE == X_UPDATE) {
-        // per-node |dh^{i+1} - dh^i| in FP32 (the FP32 path's own precision); the
-        // per-thread sum stays FP32, the CTA and grid sums are FP64
-        const bool ia = a.mask[na], ib = a.mask[nb];
-        float da = 0.f, db = 0.f;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const float oa = a.hold[q * N + na], ob = a.hold[q * N + nb];
-          const float he = (float)pp.hedot[q];
-          const float va = ia ? oa : he + u[q].x;
-          const float vb = ib ? ob : he + u[q].y;
-          a.hnew[q * N + na] = va;
-          a.hnew[q * N + nb] = vb;
-          const float dda = va - oa, ddb = vb - ob;
-          da += dda * dda;
-          db += ddb * ddb;
-          u[q] = make_float2(va, vb);
+      } else {
+        const int rl8 = (XL * 8 + 127) / 128;
+        for (int i = tid; i < 3 * 2 * P * rl8; i += NT) {
+          const int ln = i % rl8, rr = (i / rl8) % (2 * P), q = i / (rl8 * 2 * P);
+          if (nrow0 + rr < 2 * npairs) {
+            if (a.src_f32)
+              prefetch_l2(a.src_f32 + q * N + (size_t)(nrow0 + rr) * XL + ln * 32);
+            else
+              prefetch_l2(a.src_f64 + q * N + (size_t)(nrow0 + rr) * XL + ln * 16);
+          }
         }
-        if (!ia) partf += sqrtf(da);
-        if (!ib) partf += sqrtf(db);
-      } else {  // X_TO_F64, X_CROP_F64
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          a.dst_f64[q * N + na] = (double)u[q].x;
-          a.dst_f64[q * N + nb] = (double)u[q].y;
-        }
-      }
-      if (S::R2C) {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) RS[(q * P + pp2) * XL + x] = u[q];
       }
     }
-    __syncthreads();
-  }
+    const int gp = tile * P + p;
+    const bool pok = gp < npairs;
+    const int qa = 2 * (pok ? gp : 0);
+    const int z = qa / ny, ya = qa - z * ny;
+    float2* Tp = T + p * TT;
 
-  if constexpr (S::R2C) {
-    constexpr int H = Lo / 2 + 1;
-    for (int q = 0; q < 3; ++q) {
-      const int n1 = r;
-      if (n1 < R1o) {
-        float2 u[R2o];
-#pragma unroll
-        for (int n2 = 0; n2 < R2o; ++n2) {
-          const int x = n1 + R1o * n2;
-          u[n2] = (x < XL) ? RS[(q * P + p) * XL + x] : make_float2(0.f, 0.f);
+    // L2 prefetch of everything this CTA reads after its first phase (components 1
+    // and 2 of the input rows, and the node-wise step's rows), so that those later
+    // phases see L2 rather than DRAM latency; it costs no registers.
+    {
+      const int row0 = 2 * tile * P;  // first (z, y) row of this CTA
+      const int nrow = 2 * P;
+      if constexpr (S::C2R) {
+        const int lines = ((Li / 2 + 1) * 8 + 127) / 128;  // 128-byte lines per half-spectrum row
+        for (int i = tid; i < 2 * nrow * lines; i += NT) {
+          const int ln = i % lines, rr = (i / lines) % nrow, q = 1 + i / (lines * nrow);
+          const int qrow = row0 + rr;
+          if (qrow < 2 * npairs) {
+            const int zz = qrow / ny, yy = qrow - zz * ny;
+            prefetch_l2(a.spec_in + ((size_t)(q * nz + zz) * a.in_rows + yy) * a.in_sx + ln * 16);
+          }
         }
-        DFT<R2o, false, float2>::run(u);
-#pragma unroll
-        for (int k2 = 0; k2 < R2o; ++k2) Tp[k2 * (R1o + 1) + n1] = k2 == 0 ? u[0] : cmul(u[k2], two[n1 * k2]);
       }
-      __syncthreads();
-      const int k2 = r;
-      float2 Zr[R1o];
-      if (k2 < R2o) {
-#pragma unroll
-        for (int m = 0; m < R1o; ++m) Zr[m] = Tp[k2 * (R1o + 1) + m];
-        DFT<R1o, false, float2>::run(Zr);
+      const size_t nb0 = (size_t)row0 * XL;
+      const int rl = (XL * 4 + 127) / 128;  // lines per FP32 node row
+      if (MODE == X_UPDATE)
+        for (int i = tid; i < 3 * nrow * rl; i += NT) {
+          const int ln = i % rl, rr = (i / rl) % nrow, q = i / (rl * nrow);
+          if (row0 + rr < 2 * npairs) prefetch_l2(a.hold + q * N + nb0 + (size_t)rr * XL + ln * 32);
+        }
+      if (MODE == X_ASSEMBLE && a.warm)
+        for (int i = tid; i < 3 * nrow * 2 * rl; i += NT) {
+          const int ln = i % (2 * rl), rr = (i / (2 * rl)) % nrow, q = i / (2 * rl * nrow);
+          if (row0 + rr < 2 * npairs) prefetch_l2(a.warm + q * N + nb0 + (size_t)rr * XL + ln * 16);
+        }
+      if (MODE == X_UPDATE || MODE == X_ASSEMBLE || MODE == X_MASKPAD || MODE == X_POWERLAW)
+        for (int i = tid * 128; i < nrow * XL; i += NT * 128)
+          if (row0 + i / XL < 2 * npairs) prefetch_l2(a.mask + nb0 + i);
+    }
+
+    if constexpr (S::C2R) {
+      __syncthreads();  // twiddles
+      for (int q = 0; q < 3; ++q) {
+        const int n1 = r;
+        if (n1 < R1i) {
+          const float2* ra = a.spec_in + ((size_t)(q * nz + z) * a.in_rows + ya) * a.in_sx;
+          const float2* rb = ra + a.in_sx;
+          float2 v[R2i];
+  #pragma unroll
+          for (int n2 = 0; n2 < R2i; ++n2) {
+            const int k = n1 + R1i * n2;
+            const bool lo = k <= Li / 2;
+            const int kk = lo ? k : Li - k;
+            float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+            if (pok) { A = ra[kk]; B = rb[kk]; }
+            if (kk == 0 || kk == Li / 2) { A.y = 0.f; B.y = 0.f; }
+            v[n2] = lo ? make_float2(A.x - B.y, A.y + B.x) : make_float2(A.x + B.y, B.x - A.y);
+          }
+          DFT<R2i, true, float2>::run(v);
+  #pragma unroll
+          for (int k2 = 0; k2 < R2i; ++k2) Tp[k2 * (R1i + 1) + n1] = k2 == 0 ? v[0] : cmulc(v[k2], twi[n1 * k2]);
+        }
+        __syncthreads();
+        const int k2 = r;
+        if (k2 < R2i) {
+          float2 w[R1i];
+  #pragma unroll
+          for (int m = 0; m < R1i; ++m) w[m] = Tp[k2 * (R1i + 1) + m];
+          DFT<R1i, true, float2>::run(w);
+  #pragma unroll
+          for (int k1 = 0; k1 < S::KX; ++k1) RS[(q * P + p) * XL + k2 + R2i * k1] = w[k1];
+        }
+        __syncthreads();
       }
-      __syncthreads();
-      if (k2 < R2o) {
-#pragma unroll
-        for (int k1 = 0; k1 < R1o; ++k1) Tp[k2 + R2o * k1] = Zr[k1];
-      }
-      __syncthreads();
-      for (int idx = tid; idx < P * 2 * H; idx += NT) {
-        const int k = idx % H, rr = (idx / H) % 2, pp2 = idx / (2 * H);
-        const int g2 = blockIdx.x * P + pp2;
-        if (g2 >= npairs) continue;
-        const float2* zs = T + pp2 * TT;
-        const float2 Zk = zs[k], Zm = zs[(Lo - k) % Lo];
-        const float2 o = rr == 0 ? make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y))
-                                 : make_float2(0.5f * (Zk.y + Zm.y), 0.5f * (Zm.x - Zk.x));
-        const int qrow = 2 * g2 + rr;
-        const int zz = qrow / ny, yy = qrow - zz * ny;
-        a.spec_out[((size_t)(q * nz + zz) * a.out_rows + yy) * a.out_sx + k] = o;
+    } else {
+      // real f64 rows into RS
+      for (int idx = tid; idx < 3 * P * XL; idx += NT) {
+        const int x = idx % XL, pp2 = (idx / XL) % P, q = idx / (XL * P);
+        const int g2 = tile * P + pp2;
+        float2 zv = make_float2(0.f, 0.f);
+        if (g2 < npairs) {
+          const size_t na = (size_t)(2 * g2) * XL + x;
+          zv = a.src_f32 ? make_float2(a.src_f32[q * N + na], a.src_f32[q * N + na + XL])
+                         : make_float2((float)a.src_f64[q * N + na], (float)a.src_f64[q * N + na + XL]);
+        }
+        RS[(q * P + pp2) * XL + x] = zv;
       }
       __syncthreads();
     }
+
+    // ---- node-wise step
+    if constexpr (S::C2R) {
+      const PointParams& pp = a.pp;
+      for (int idx = tid; idx < P * XL; idx += NT) {
+        const int x = idx % XL, pp2 = idx / XL;
+        const int g2 = tile * P + pp2;
+        if (g2 >= npairs) continue;
+        const size_t na = (size_t)(2 * g2) * XL + x, nb = na + XL;
+        float2 u[3];
+  #pragma unroll
+        for (int q = 0; q < 3; ++q) u[q] = RS[(q * P + pp2) * XL + x];
+        if (MODE == X_POWERLAW) {
+          const bool ia = a.mask[na], ib = a.mask[nb];
+          const float ca = a.jc ? a.jc[na] : (float)pp.jc, cb = a.jc ? a.jc[nb] : (float)pp.jc;
+          const float ra = rho_of(u[0].x, u[1].x, u[2].x, ia, ca, pp);
+          const float rb = rho_of(u[0].y, u[1].y, u[2].y, ib, cb, pp);
+  #pragma unroll
+          for (int q = 0; q < 3; ++q) u[q] = make_float2(u[q].x * ra, u[q].y * rb);
+        } else if (MODE == X_ASSEMBLE) {
+          const bool ia = a.mask[na], ib = a.mask[nb];
+          const float s = -(float)pp.inv_mu0;
+  #pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const float va = ia ? s * u[q].x : (a.warm_f32 ? a.warm_f32[q * N + na] : (float)a.warm[q * N + na]);
+            const float vb = ib ? s * u[q].y : (a.warm_f32 ? a.warm_f32[q * N + nb] : (float)a.warm[q * N + nb]);
+            a.hnew[q * N + na] = va;
+            a.hnew[q * N + nb] = vb;
+            u[q] = make_float2(va, vb);
+          }
+        } else if (MODE == X_MASKPAD) {
+          const bool ia = a.mask[na], ib = a.mask[nb];
+  #pragma unroll
+          for (int q = 0; q < 3; ++q) u[q] = make_float2(ia ? u[q].x : 0.f, ib ? u[q].y : 0.f);
+        } else if (MODE == X_UPDATE) {
+          // per-node |dh^{i+1} - dh^i| in FP32 (the FP32 path's own precision); the
+          // per-thread sum stays FP32, the CTA and grid sums are FP64
+          const bool ia = a.mask[na], ib = a.mask[nb];
+          float da = 0.f, db = 0.f;
+  #pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const float oa = a.hold[q * N + na], ob = a.hold[q * N + nb];
+            const float he = (float)pp.hedot[q];
+            const float va = ia ? oa : he + u[q].x;
+            const float vb = ib ? ob : he + u[q].y;
+            a.hnew[q * N + na] = va;
+            a.hnew[q * N + nb] = vb;
+            const float dda = va - oa, ddb = vb - ob;
+            da += dda * dda;
+            db += ddb * ddb;
+            u[q] = make_float2(va, vb);
+          }
+          if (!ia) partf += sqrtf(da);
+          if (!ib) partf += sqrtf(db);
+        } else {  // X_TO_F64, X_CROP_F64
+  #pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            a.dst_f64[q * N + na] = (double)u[q].x;
+            a.dst_f64[q * N + nb] = (double)u[q].y;
+          }
+        }
+        if (S::R2C) {
+  #pragma unroll
+          for (int q = 0; q < 3; ++q) RS[(q * P + pp2) * XL + x] = u[q];
+        }
+      }
+      __syncthreads();
+    }
+
+    if constexpr (S::R2C) {
+      constexpr int H = Lo / 2 + 1;
+      for (int q = 0; q < 3; ++q) {
+        const int n1 = r;
+        if (n1 < R1o) {
+          float2 u[R2o];
+  #pragma unroll
+          for (int n2 = 0; n2 < R2o; ++n2) {
+            const int x = n1 + R1o * n2;
+            u[n2] = (x < XL) ? RS[(q * P + p) * XL + x] : make_float2(0.f, 0.f);
+          }
+          DFT<R2o, false, float2>::run(u);
+  #pragma unroll
+          for (int k2 = 0; k2 < R2o; ++k2) Tp[k2 * (R1o + 1) + n1] = k2 == 0 ? u[0] : cmul(u[k2], two[n1 * k2]);
+        }
+        __syncthreads();
+        const int k2 = r;
+        float2 Zr[R1o];
+        if (k2 < R2o) {
+  #pragma unroll
+          for (int m = 0; m < R1o; ++m) Zr[m] = Tp[k2 * (R1o + 1) + m];
+          DFT<R1o, false, float2>::run(Zr);
+        }
+        __syncthreads();
+        if (k2 < R2o) {
+  #pragma unroll
+          for (int k1 = 0; k1 < R1o; ++k1) Tp[k2 + R2o * k1] = Zr[k1];
+        }
+        __syncthreads();
+        for (int idx = tid; idx < P * 2 * H; idx += NT) {
+          const int k = idx % H, rr = (idx / H) % 2, pp2 = idx / (2 * H);
+          const int g2 = tile * P + pp2;
+          if (g2 >= npairs) continue;
+          const float2* zs = T + pp2 * TT;
+          const float2 Zk = zs[k], Zm = zs[(Lo - k) % Lo];
+          const float2 o = rr == 0 ? make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y))
+                                   : make_float2(0.5f * (Zk.y + Zm.y), 0.5f * (Zm.x - Zk.x));
+          const int qrow = 2 * g2 + rr;
+          const int zz = qrow / ny, yy = qrow - zz * ny;
+          a.spec_out[((size_t)(q * nz + zz) * a.out_rows + yy) * a.out_sx + k] = o;
+        }
+        __syncthreads();
+      }
+    }
+    __syncthreads();  // shared buffers are reused by the next tile
   }
 
   if (MODE == X_UPDATE) {
