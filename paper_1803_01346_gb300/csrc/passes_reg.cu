@@ -814,9 +814,13 @@ __global__ void __launch_bounds__(TC * R1) zpass_reg2_kernel(float2* __restrict_
     }
   }
   __syncthreads();
-  // ---- product on the natural-order spectra [kz][c]
+  // ---- product on the natural-order spectra [kz][c]; a fixed trip count, unrolled so
+  // the kernel-spectrum loads of several points are in flight together
   const int kxc0 = blockIdx.x * TC;
-  for (int idx = t; idx < L * TC; idx += NT) {
+  static_assert((L * TC) % NT == 0, "product loop trip count");
+#pragma unroll 8
+  for (int j = 0; j < L * TC / NT; ++j) {
+    const int idx = t + j * NT;
     const int cc = idx % TC, kz = idx / TC;
     const int kxx = kxc0 + cc < HX ? kxc0 + cc : 0;
     float ax, ay, az, s;
