@@ -38,12 +38,13 @@ import scfft_inputs as I  # noqa: E402
 WORKLOAD = "lens128"
 METRIC = "voxel-RHS evals/s at 128^3 (FP32 FFT, FP64 state)"
 UNIT = "voxel-RHS evals/s"
-# Eq. 5 iterations per right-hand side observed on the default GPU run of this
-# workload (used only to convert the reference arm's per-iteration samples).
-REF_ITERS_PER_RHS = 2.0
-# DRAM bytes per launch of the dominant kernel from the committed ncu capture
-# (profiles/); None when the kernel changed since the counters were taken.
-NCU_TRAFFIC = None
+# Eq. 5 iterations per right-hand side observed on the GPU path's runs of this
+# workload (3.3 over the first 23 steps; used only to convert the reference
+# arm's per-iteration samples to the metric's unit).
+REF_ITERS_PER_RHS = 3.3
+# DRAM bytes (read + write) per launch from the committed ncu capture
+# profiles/ncu_zpass_xupdate_lens128_fp32.md; an entry is removed when its kernel changes.
+NCU_TRAFFIC = {"z_kernel": 144443392 + 55672064, "x_update": 84949760 + 6328576}
 
 
 def _peaks():
@@ -269,6 +270,50 @@ def bench_batch(S, torch, steps: int, warmup: int):
             "timing": "wall clock around synchronous batch calls, device synchronised on both sides"}
 
 
+def bench_adjoint(S, torch, nsteps: int, checkpoint: int, K: int):
+    """Reverse mode on the lens at 96^3 with a seeded +-5% jc map (FP32 FFTs):
+    an adaptive forward run records its step sizes, then the discrete adjoint
+    of that frozen step list (checkpoints every `checkpoint` steps, K Eq. 5
+    iterations per rhs) gives d|h(bore centre)|^2 / d(jc map, y_0, dh_e/dt)."""
+    cfg = I.config("lens96")
+    N = int(np.prod(cfg.n))
+    ctx = S.Context(cfg.n, cfg.L, n_power=cfg.n_power, rho_out=cfg.rho_out, precision=S.PREC_F32,
+                    delta_it=2e-5, max_iter=K, rtol=cfg.rtol, atol=cfg.atol)
+    ctx.set_geometry(cfg.mask)
+    ctx.set_field_path(cfg.knots_t, cfg.knots_he)
+    jc = torch.from_numpy(np.ascontiguousarray(cfg.jc).reshape(-1)).cuda()
+    ctx.set_jc_map(jc)
+    ctx.precompute_kernel()
+    h = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    warm = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    warm.view(3, N)[2] = cfg.knots_he[1][2] / cfg.knots_t[1]
+    t, dt, dts = 0.0, 1e-6, []
+    for _ in range(nsteps):
+        t1, dt, _ = ctx.step(t, dt, cfg.t_end, h, warm)
+        dts.append(t1 - t)
+        t = t1
+    # objective: |h|^2 at the node nearest the bore centre
+    lam = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    c = (cfg.n[2] // 2 * cfg.n[1] + cfg.n[1] // 2) * cfg.n[0] + cfg.n[0] // 2
+    y0 = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    mu_y0 = torch.empty_like(y0)
+    y_end = torch.empty_like(y0)
+    mu_jc = torch.empty(N, dtype=torch.float64, device="cuda")
+    for q in range(3):
+        lam[q * N + c] = 2.0 * float(h[q * N + c])
+    s0 = ctx.stats()["rhs_calls"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mu_a = ctx.adjoint_integrate(0.0, dts, y0, lam, mu_y0, y_end=y_end, mu_jc=mu_jc, checkpoint_every=checkpoint)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    calls = ctx.stats()["rhs_calls"] - s0
+    return {"workload": "lens96 (jc +-5%)", "steps": nsteps, "checkpoint_every": checkpoint, "iters_per_rhs": K,
+            "seconds": el, "adjoint_steps_per_s": nsteps / el, "forward_rhs_recomputed": int(calls),
+            "grad_jc_norm": float(mu_jc.norm()), "grad_rate": mu_a,
+            "end_state_matches_forward": float((y_end - h).abs().max() / h.abs().max().clamp_min(1e-300))}
+
+
 def bench_ours(args, ws, rank, local):
     import torch
     import paper_1803_01346_gb300 as S
@@ -388,6 +433,7 @@ def bench_ours(args, ws, rank, local):
     fp64_value = N * (ctx64.stats()["rhs_calls"] - c0) / (e4.elapsed_time(e5) * 1e-3)
 
     batch = None if (args.no_batch or rank != 0) else bench_batch(S, torch, max(2, min(args.steps, 5)), 2)
+    adjoint = None if (args.no_adjoint or rank != 0) else bench_adjoint(S, torch, 100, 50, 4)
     if rank != 0:
         return 0
     cpu = None
@@ -412,13 +458,14 @@ def bench_ours(args, ws, rank, local):
                 "steps": ke},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": peak_src, "traffic": NCU_TRAFFIC,
+                     "frac": achieved / peak, "peak_source": peak_src, "traffic": NCU_TRAFFIC.get(dom),
                      "bytes_per_launch": algorithmic_bytes(dom, cfg.n, 4), "avg_launch_ms": avg_ms,
                      "launches": cnt},
         "pass_shares": shares,
         "clocks": clk,
         "cpu_baseline": cpu,
         "batch": batch,
+        "adjoint": adjoint,
     }
     line["config"]["t_start"] = None
     print(json.dumps(line), flush=True)
@@ -433,6 +480,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the reverse-mode leg")
     args = ap.parse_args()
     ws, rank, local = _dist()
     if args.impl == "reference":
