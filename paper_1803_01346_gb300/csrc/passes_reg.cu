@@ -11,25 +11,21 @@
 // L/2 rows (n2 < R2/2, skipped at load) and the inverse output keeps only the
 // first L/2 rows (k1 < R1/2 or m2 < R2/2, skipped at store).
 //
-// The z passes keep the three field components of a column in registers so
-// the spectral curl (i S(k) k x F) or the kernel-spectrum product (K^ x F,
-// Eq. 7) is applied between the forward and inverse transforms without
-// another trip through memory.  The inverse after the product uses the mirror
-// split y[m1 + R1 m2] = sum_k2 W_R2^{-m2 k2} W_L^{-m1 k2} (sum_k1 X[k2 + R2 k1] W_R1^{-m1 k1}),
-// which starts from exactly the registers the forward split ends with.
+// The z passes take the three field components of a column tile through the
+// forward transform one after another, apply the spectral curl (i S(k) k x F)
+// or the kernel-spectrum product (K^ x F, Eq. 7) on the natural-order spectra
+// in shared memory, and transform back, all in one trip through memory.  The
+// inverse uses the mirror split
+//   y[m1 + R1 m2] = sum_k2 W_R2^{-m2 k2} W_L^{-m1 k2} (sum_k1 X[k2 + R2 k1] W_R1^{-m1 k1}).
 #include "scfft_internal.cuh"
 
 namespace scfft {
 
 namespace {
 
-constexpr int kPad8 = 8;
+constexpr int kPad8 = 8;  // row padding (complex elements) that spreads half-warps over all banks
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
-__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }  // row padding (complex elements) that spreads half-warps over all banks
-
-template <int R1, int R2> struct RegGeom {
-  static constexpr int L = R1 * R2;
-};
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 template <typename V> __device__ __forceinline__ V tw_mul(V a, V w, bool inv) { return inv ? cmulc(a, w) : cmul(a, w); }
 
@@ -86,128 +82,6 @@ __global__ void __launch_bounds__(TC * R1) ypass_reg_kernel(typename cplx_of<T>:
       for (int k1 = 0; k1 < R1; ++k1) {
         if (POUT && k1 >= R1 / 2) continue;
         col[(size_t)(k2 + R2 * k1) * sx] = w[k1];
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------- z pass (3 components)
-// KIND 0: spectral curl on the unpadded grid (L = nz, no pruning).
-// KIND 1: kernel-spectrum product on the padded grid (L = 2nz, pruned in/out).
-// grid (ceil(HX/TC), rows), block TC*R1 threads.
-template <typename T, int R1, int R2, int TC, int KIND>
-__global__ void __launch_bounds__(TC * R1) zpass_reg_kernel(typename cplx_of<T>::type* __restrict__ base, int rows,
-                                                            int sx, int HX, int nzs,
-                                                            const typename cplx_of<T>::type* __restrict__ twg,
-                                                            const T* __restrict__ kt0, const T* __restrict__ kt1,
-                                                            const T* __restrict__ kt2, const T* __restrict__ st0,
-                                                            const T* __restrict__ st1, const T* __restrict__ st2,
-                                                            T scale, const T* __restrict__ kap, int nx, int ny,
-                                                            int nz, const Ctrl* ctrl, int check_done) {
-  typedef typename cplx_of<T>::type V;
-  constexpr int L = R1 * R2;
-  constexpr bool PR = (KIND == 1);         // pruned input and output
-  constexpr int S2 = R1 * TC + kPad8;      // forward transpose: [k2][n1][c]
-  constexpr int S1 = R2 * TC + kPad8;      // inverse transpose: [m1][k2][c]
-  constexpr int CSF = R2 * S2, CSI = R1 * S1;
-  constexpr int CS = CSF > CSI ? CSF : CSI;  // one component's transpose buffer
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (check_done && ctrl->done) return;
-  V* tw = reinterpret_cast<V*>(smem_raw);
-  V* sm = tw + L;
-  const int t = threadIdx.x;
-  for (int i = t; i < L; i += TC * R1) tw[i] = twg[i];
-  const int c = t % TC, n1 = t / TC;
-  const int y = blockIdx.y, kx = blockIdx.x * TC + c;
-  const bool colok = kx < HX;
-  const size_t zstride = (size_t)rows * sx;
-  const size_t cstride = (size_t)nzs * zstride;
-  V* col = base + (size_t)y * sx + kx;
-
-  // ---- forward, stage A: R2-point DFTs along n2 for the three components
-  V v[3][R2];
-#pragma unroll
-  for (int q = 0; q < 3; ++q)
-#pragma unroll
-    for (int n2 = 0; n2 < R2; ++n2) {
-      if (PR && n2 >= R2 / 2) v[q][n2] = zero_v<V>();
-      else v[q][n2] = colok ? col[q * cstride + (size_t)(n1 + R1 * n2) * zstride] : zero_v<V>();
-    }
-  __syncthreads();  // twiddles staged
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    DFT<R2, false, V>::run(v[q]);
-#pragma unroll
-    for (int k2 = 1; k2 < R2; ++k2) v[q][k2] = cmul(v[q][k2], tw[n1 * k2]);
-#pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) sm[q * CS + k2 * S2 + n1 * TC + c] = v[q][k2];
-  }
-  __syncthreads();
-  const bool actB = n1 < R2;
-  const int k2 = n1;
-  V w[3][R1];
-  if (actB) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-#pragma unroll
-      for (int m = 0; m < R1; ++m) w[q][m] = sm[q * CS + k2 * S2 + m * TC + c];
-      DFT<R1, false, V>::run(w[q]);
-    }
-    // ---- product at kz = k2 + R2 k1
-    const int kxc = colok ? kx : 0;
-#pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) {
-      const int kz = k2 + R2 * k1;
-      T ax, ay, az, s;
-      if (KIND == 0) {
-        ax = kt0[kxc]; ay = kt1[y]; az = kt2[kz];
-        s = st0[kxc] * st1[y] * st2[kz] * scale;
-      } else {
-        const int fy = (y <= ny) ? y : 2 * ny - y;
-        const int fz = (kz <= nz) ? kz : 2 * nz - kz;
-        const size_t oct = (size_t)(nz + 1) * (ny + 1) * (nx + 1);
-        const size_t off = ((size_t)fz * (ny + 1) + fy) * (nx + 1) + kxc;
-        ax = kap[off];
-        ay = (y <= ny) ? kap[oct + off] : -kap[oct + off];
-        az = (kz <= nz) ? kap[2 * oct + off] : -kap[2 * oct + off];
-        s = (T)1;
-      }
-      const V F0 = w[0][k1], F1 = w[1][k1], F2 = w[2][k1];
-      // G = i s (a x F)
-      const V cx = mk(ay * F2.x - az * F1.x, ay * F2.y - az * F1.y);
-      const V cy = mk(az * F0.x - ax * F2.x, az * F0.y - ax * F2.y);
-      const V cz = mk(ax * F1.x - ay * F0.x, ax * F1.y - ay * F0.y);
-      w[0][k1] = mk(-s * cx.y, s * cx.x);
-      w[1][k1] = mk(-s * cy.y, s * cy.x);
-      w[2][k1] = mk(-s * cz.y, s * cz.x);
-    }
-  }
-  __syncthreads();  // forward transpose buffer is free again
-  // ---- inverse, stage A': R1-point inverse DFTs along k1, twiddle, transpose
-  if (actB) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      DFT<R1, true, V>::run(w[q]);
-#pragma unroll
-      for (int m1 = 0; m1 < R1; ++m1) {
-        const V a = (m1 == 0) ? w[q][m1] : cmulc(w[q][m1], tw[m1 * k2]);
-        sm[q * CS + m1 * S1 + k2 * TC + c] = a;
-      }
-    }
-  }
-  __syncthreads();
-  // ---- inverse, stage B': R2-point inverse DFTs along k2, output rows m1 + R1 m2
-  const int m1 = n1;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-#pragma unroll
-    for (int j = 0; j < R2; ++j) v[q][j] = sm[q * CS + m1 * S1 + j * TC + c];
-    DFT<R2, true, V>::run(v[q]);
-    if (colok) {
-#pragma unroll
-      for (int m2 = 0; m2 < R2; ++m2) {
-        if (PR && m2 >= R2 / 2) continue;
-        col[q * cstride + (size_t)(m1 + R1 * m2) * zstride] = v[q][m2];
       }
     }
   }
@@ -378,263 +252,6 @@ __device__ __forceinline__ float rho_of(float jx, float jy, float jz, bool in, f
 }
 
 }  // namespace
-
-template <int MODE, int R1i, int R2i, int R2o, int P>
-__global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP)
-    xpass_reg_kernel(const XRArgs a) {
-  typedef XS<MODE, R1i, R2i, R2o> S;
-  constexpr int TP = S::TP, R1o = S::R1o, Li = S::Li, Lo = S::Lo;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (a.check_done && a.ctrl->done) return;
-  float2* twi = reinterpret_cast<float2*>(smem_raw);
-  float2* two = twi + (Li > 0 ? Li : 1);
-  float2* sm = two + (Lo > 0 ? Lo : 1);
-  const int tid = threadIdx.x, nth = P * TP;
-  const int p = tid / TP, r = tid % TP;
-  if (S::C2R)
-    for (int i = tid; i < Li; i += nth) twi[i] = a.tw_in[i];
-  if (S::R2C)
-    for (int i = tid; i < Lo; i += nth) two[i] = a.tw_out[i];
-  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-  const long long N = a.g.N;
-  const int npairs = ny * nz / 2;
-  const int gp = blockIdx.x * P + p;  // global row pair
-  const bool pok = gp < npairs;
-  const int qa = 2 * (pok ? gp : 0);  // row a (flattened z*ny + y); row b = qa + 1
-  const int z = qa / ny, ya = qa - z * ny;
-  float2* smp = sm + p * S::TB;  // this pair's shared slice
-
-  // registers carried from the C2R to the R2C: z at x = r + R2i k1
-  float2 w[3][S::C2R ? cmax(R1i, R2o) : R2o];
-
-  if constexpr (S::C2R) {
-    // ---- stage A: thread (p, n1 < R1i) builds z-spectrum entries k = n1 + R1i n2
-    float2 v[3][R2i];
-    const int n1 = r;
-    if (n1 < R1i) {
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const float2* ra = a.spec_in + ((size_t)(q * nz + z) * a.in_rows + ya) * a.in_sx;
-        const float2* rb = ra + a.in_sx;
-#pragma unroll
-        for (int n2 = 0; n2 < R2i; ++n2) {
-          const int k = n1 + R1i * n2;
-          const bool lo = k <= Li / 2;
-          const int kk = lo ? k : Li - k;
-          float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
-          if (pok) { A = ra[kk]; B = rb[kk]; }
-          if (kk == 0 || kk == Li / 2) { A.y = 0.f; B.y = 0.f; }
-          v[q][n2] = lo ? make_float2(A.x - B.y, A.y + B.x) : make_float2(A.x + B.y, B.x - A.y);
-        }
-      }
-    }
-    __syncthreads();  // twiddles staged
-    if (n1 < R1i) {
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        DFT<R2i, true, float2>::run(v[q]);
-#pragma unroll
-        for (int k2 = 0; k2 < R2i; ++k2) {
-          const float2 t = k2 == 0 ? v[q][k2] : cmulc(v[q][k2], twi[n1 * k2]);
-          smp[(q * R2i + k2) * (R1i + 1) + n1] = t;
-        }
-      }
-    }
-    __syncthreads();
-    // ---- stage B: thread (p, k2 < R2i): z at x = k2 + R2i k1
-    const int k2 = r;
-    if (k2 < R2i) {
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-#pragma unroll
-        for (int m = 0; m < R1i; ++m) w[q][m] = smp[(q * R2i + k2) * (R1i + 1) + m];
-        DFT<R1i, true, float2>::run(w[q]);
-      }
-    }
-    __syncthreads();  // transpose buffer free
-  } else {
-    // ---- real f64 rows straight into the R2C's stage-A layout
-    const int n1 = r;
-    if (n1 < R1o) {
-#pragma unroll
-      for (int q = 0; q < 3; ++q)
-#pragma unroll
-        for (int n2 = 0; n2 < R2o; ++n2) {
-          const int x = n1 + R1o * n2;
-          float2 zv = make_float2(0.f, 0.f);
-          if (pok && (!S::PADOUT || n2 < R2o / 2)) {
-            const size_t na = (size_t)qa * nx + x;
-            zv = make_float2((float)a.src_f64[q * N + na], (float)a.src_f64[q * N + na + nx]);
-          }
-          w[q][n2] = zv;
-        }
-    }
-    __syncthreads();  // twiddles staged
-  }
-
-  // ---- node-wise step on x = r + R2i k1 (C2R modes)
-  double part = 0.0;
-  if constexpr (S::C2R) {
-    const int k2 = r;
-    if (k2 < R2i && pok) {
-      const PointParams& pp = a.pp;
-#pragma unroll
-      for (int k1 = 0; k1 < S::KX; ++k1) {
-        const int x = k2 + R2i * k1;
-        const size_t na = (size_t)qa * nx + x, nb = na + nx;
-        if (MODE == X_POWERLAW) {
-          const bool ia = a.mask[na], ib = a.mask[nb];
-          const float ca = a.jc ? a.jc[na] : (float)pp.jc, cb = a.jc ? a.jc[nb] : (float)pp.jc;
-          const float ra = rho_of(w[0][k1].x, w[1][k1].x, w[2][k1].x, ia, ca, pp);
-          const float rb = rho_of(w[0][k1].y, w[1][k1].y, w[2][k1].y, ib, cb, pp);
-#pragma unroll
-          for (int q = 0; q < 3; ++q) w[q][k1] = make_float2(w[q][k1].x * ra, w[q][k1].y * rb);
-        } else if (MODE == X_ASSEMBLE) {
-          const bool ia = a.mask[na], ib = a.mask[nb];
-          const float s = -(float)pp.inv_mu0;
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            const float va = ia ? s * w[q][k1].x : (float)a.warm[q * N + na];
-            const float vb = ib ? s * w[q][k1].y : (float)a.warm[q * N + nb];
-            a.hnew[q * N + na] = va;
-            a.hnew[q * N + nb] = vb;
-            w[q][k1] = make_float2(va, vb);
-          }
-        } else if (MODE == X_MASKPAD) {
-          const bool ia = a.mask[na], ib = a.mask[nb];
-#pragma unroll
-          for (int q = 0; q < 3; ++q) w[q][k1] = make_float2(ia ? w[q][k1].x : 0.f, ib ? w[q][k1].y : 0.f);
-        } else if (MODE == X_UPDATE) {
-          const bool ia = a.mask[na], ib = a.mask[nb];
-          double da = 0.0, db = 0.0;
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            const float oa = a.hold[q * N + na], ob = a.hold[q * N + nb];
-            const float he = (float)pp.hedot[q];
-            const float va = ia ? oa : he + w[q][k1].x;
-            const float vb = ib ? ob : he + w[q][k1].y;
-            a.hnew[q * N + na] = va;
-            a.hnew[q * N + nb] = vb;
-            const double dda = (double)va - (double)oa, ddb = (double)vb - (double)ob;
-            da += dda * dda;
-            db += ddb * ddb;
-            w[q][k1] = make_float2(va, vb);
-          }
-          if (!ia) part += sqrt(da);
-          if (!ib) part += sqrt(db);
-        } else {  // X_TO_F64, X_CROP_F64
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            a.dst_f64[q * N + na] = (double)w[q][k1].x;
-            a.dst_f64[q * N + nb] = (double)w[q][k1].y;
-          }
-        }
-      }
-    }
-  }
-
-  if constexpr (S::R2C) {
-    // ---- R2C stage A': thread (p, n1' = r < R1o) holds z[n1' + R1o n2'], n2' < R2o
-    const int n1 = r;
-    if (n1 < R1o) {
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        float2 u[R2o];
-#pragma unroll
-        for (int n2 = 0; n2 < R2o; ++n2) {
-          if (S::C2R) u[n2] = (n2 < S::KX && !(S::PADOUT && n2 >= R2o / 2)) ? w[q][n2] : make_float2(0.f, 0.f);
-          else u[n2] = w[q][n2];
-        }
-        DFT<R2o, false, float2>::run(u);
-#pragma unroll
-        for (int k2 = 0; k2 < R2o; ++k2) {
-          const float2 t = k2 == 0 ? u[k2] : cmul(u[k2], two[n1 * k2]);
-          smp[(q * R2o + k2) * (R1o + 1) + n1] = t;
-        }
-      }
-    }
-    __syncthreads();
-    // ---- stage B': thread (p, k2' < R2o): Z[k2' + R2o k1']
-    float2 Zr[3][R1o];
-    const int k2 = r;
-    if (k2 < R2o) {
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-#pragma unroll
-        for (int m = 0; m < R1o; ++m) Zr[q][m] = smp[(q * R2o + k2) * (R1o + 1) + m];
-        DFT<R1o, false, float2>::run(Zr[q]);
-      }
-    }
-    __syncthreads();  // transpose buffer free
-    if (k2 < R2o) {
-#pragma unroll
-      for (int q = 0; q < 3; ++q)
-#pragma unroll
-        for (int k1 = 0; k1 < R1o; ++k1) smp[q * Lo + k2 + R2o * k1] = Zr[q][k1];
-    }
-    __syncthreads();
-    // ---- separate the two rows: A = (Z[k] + conj Z[Lo-k])/2, B = (Z[k] - conj Z[Lo-k])/(2i)
-    constexpr int H = Lo / 2 + 1;
-    for (int idx = tid; idx < P * 3 * 2 * H; idx += nth) {
-      const int k = idx % H, rr = (idx / H) % 2, q = (idx / (2 * H)) % 3, pp2 = idx / (6 * H);
-      const int g2 = blockIdx.x * P + pp2;
-      if (g2 >= npairs) continue;
-      const float2* zs = sm + pp2 * S::TB + q * Lo;
-      const float2 Zk = zs[k], Zm = zs[(Lo - k) % Lo];
-      const float2 o = rr == 0 ? make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y))
-                               : make_float2(0.5f * (Zk.y + Zm.y), 0.5f * (Zm.x - Zk.x));
-      const int qrow = 2 * g2 + rr;
-      const int zz = qrow / ny, yy = qrow - zz * ny;
-      a.spec_out[((size_t)(q * nz + zz) * a.out_rows + yy) * a.out_sx + k] = o;
-    }
-  }
-
-  if (MODE == X_UPDATE) {
-    __shared__ double red[32];
-    __shared__ int am_last;
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((tid & 31) == 0) red[tid >> 5] = part;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int i = 0; i < (nth + 31) / 32; ++i) s += red[i];
-      a.partials[blockIdx.x] = s;
-      __threadfence();
-      const unsigned prev = atomicAdd(&a.ctrl->counter, 1u);
-      am_last = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (am_last) {
-      __threadfence();
-      double s = 0.0;
-      for (int i = tid; i < (int)gridDim.x; i += nth) s += __ldcg(&a.partials[i]);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      __syncthreads();
-      if ((tid & 31) == 0) red[tid >> 5] = s;
-      __syncthreads();
-      if (tid == 0) {
-        double tot = 0.0;
-        for (int i = 0; i < (nth + 31) / 32; ++i) tot += red[i];
-        const double rres = tot * a.pp.inv_nout;
-        Ctrl* c = a.ctrl;
-        c->residual = rres;
-        c->iters = a.pp.iter + 1;
-        c->cur = a.out_buf;
-        const bool finite = isfinite(rres);
-        if (!finite) c->status = 6;  // SCFFT_ENONFINITE
-        c->done = (!finite || rres < a.pp.tol) ? 1 : 0;
-        c->counter = 0;
-      }
-    }
-  }
-  if (MODE == X_ASSEMBLE && blockIdx.x == 0 && tid == 0) {
-    a.ctrl->done = 0;
-    a.ctrl->iters = 0;
-    a.ctrl->cur = 0;
-    a.ctrl->counter = 0;
-    a.ctrl->residual = 0.0;
-  }
-}
 
 template <int MODE, int R1i, int R2i, int R2o, int P>
 __global__ void xpass_reg2_kernel(const XRArgs a);
