@@ -399,6 +399,13 @@ __global__ void __launch_bounds__(TC * R1) zpass_reg2_kernel(float2* __restrict_
   const size_t cstride = (size_t)nzs * zstride;
   float2* col = base + (size_t)y * sx + kx;
   __syncthreads();  // twiddles staged
+  // This thread's twiddles W_L^{n1 j}: stage A uses j = k2 with its own n1, and
+  // stage A' (run by the thread whose k2 equals this n1) uses j = m1, so one set
+  // of registers serves both directions for all three components.
+  constexpr int TJ = cmax(R1, R2);
+  float2 twr[TJ];
+#pragma unroll
+  for (int jj = 0; jj < TJ; ++jj) twr[jj] = tw[(n1 * jj) % L];
 
   // all three components' inputs are loaded up front (one memory latency, not three)
   constexpr int NL = PR ? R2 / 2 : R2;
@@ -416,7 +423,7 @@ __global__ void __launch_bounds__(TC * R1) zpass_reg2_kernel(float2* __restrict_
     for (int n2 = 0; n2 < R2; ++n2) v[n2] = n2 < NL ? pre[q][n2] : make_float2(0.f, 0.f);
     DFT<R2, false, float2>::run(v);
 #pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) Fq[k2 * S2 + n1 * TC + c] = k2 == 0 ? v[0] : cmul(v[k2], tw[n1 * k2]);
+    for (int k2 = 0; k2 < R2; ++k2) Fq[k2 * S2 + n1 * TC + c] = k2 == 0 ? v[0] : cmul(v[k2], twr[k2]);
     __syncthreads();
     float2 w[R1];
     if (n1 < R2) {
@@ -477,7 +484,7 @@ __global__ void __launch_bounds__(TC * R1) zpass_reg2_kernel(float2* __restrict_
     if (n1 < R2) {
       const int k2 = n1;
 #pragma unroll
-      for (int m1 = 0; m1 < R1; ++m1) Fq[m1 * S1 + k2 * TC + c] = m1 == 0 ? w[0] : cmulc(w[m1], tw[m1 * k2]);
+      for (int m1 = 0; m1 < R1; ++m1) Fq[m1 * S1 + k2 * TC + c] = m1 == 0 ? w[0] : cmulc(w[m1], twr[m1]);
     }
     __syncthreads();
     float2 v[R2];
