@@ -238,7 +238,9 @@ template <int MODE, int R1i, int R2i, int R2o> struct XS {
   static constexpr int R1o = R2i;
   static constexpr int Li = R1i * R2i;
   static constexpr int Lo = R1o * R2o;
-  static constexpr int TP = cmax(cmax(R1i, R2i), R2o);
+  // threads per row pair: a power of two, so that a pair's threads are lanes of one warp
+  static constexpr int TP0 = cmax(cmax(R1i, R2i), R2o);
+  static constexpr int TP = TP0 <= 4 ? 4 : TP0 <= 8 ? 8 : 16;
   static constexpr int KX = PADIN ? R1i / 2 : R1i;  // k1 slots that hold x < nx after the C2R
   static constexpr int TB = cmax(cmax(3 * R2i * (R1i + 1), 3 * R2o * (R1o + 1)), 3 * Lo);  // smem per pair
 };
@@ -715,7 +717,6 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP)
     }
 
     if constexpr (S::R2C) {
-      constexpr int H = Lo / 2 + 1;
       for (int q = 0; q < 3; ++q) {
         const int n1 = r;
         if (n1 < R1o) {
@@ -737,25 +738,27 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP)
           for (int m = 0; m < R1o; ++m) Zr[m] = Tp[k2 * (R1o + 1) + m];
           DFT<R1o, false, float2>::run(Zr);
         }
-        __syncthreads();
-        if (k2 < R2o) {
-  #pragma unroll
-          for (int k1 = 0; k1 < R1o; ++k1) Tp[k2 + R2o * k1] = Zr[k1];
+        // separate the two rows: A = (Z[k] + conj Z[Lo-k])/2, B = (Z[k] - conj Z[Lo-k])/(2i).
+        // Thread k2 holds Z[k2 + R2o k1]; the mirror Lo - k lives in thread R2o - k2 at
+        // register R1o - 1 - k1 (k2 > 0) or in this thread at (R1o - k1) mod R1o (k2 = 0),
+        // so a warp shuffle inside the pair's lanes replaces a trip through shared memory.
+        const int lane = tid & 31;
+        const int src = lane - k2 + (k2 == 0 ? 0 : R2o - k2);
+        float2* ra = a.spec_out + ((size_t)(q * nz + z) * a.out_rows + ya) * a.out_sx;
+        float2* rb = ra + a.out_sx;
+#pragma unroll
+        for (int k1 = 0; k1 <= R1o / 2; ++k1) {
+          const float2 sh = make_float2(__shfl_sync(0xffffffffu, Zr[R1o - 1 - k1].x, src),
+                                        __shfl_sync(0xffffffffu, Zr[R1o - 1 - k1].y, src));
+          const float2 Zk = Zr[k1];
+          const float2 Zm = k2 == 0 ? Zr[(R1o - k1) % R1o] : sh;
+          const int k = k2 + R2o * k1;
+          if (k2 < R2o && pok && k <= Lo / 2) {
+            ra[k] = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
+            rb[k] = make_float2(0.5f * (Zk.y + Zm.y), 0.5f * (Zm.x - Zk.x));
+          }
         }
-        __syncthreads();
-        for (int idx = tid; idx < P * 2 * H; idx += NT) {
-          const int k = idx % H, rr = (idx / H) % 2, pp2 = idx / (2 * H);
-          const int g2 = tile * P + pp2;
-          if (g2 >= npairs) continue;
-          const float2* zs = T + pp2 * TT;
-          const float2 Zk = zs[k], Zm = zs[(Lo - k) % Lo];
-          const float2 o = rr == 0 ? make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y))
-                                   : make_float2(0.5f * (Zk.y + Zm.y), 0.5f * (Zm.x - Zk.x));
-          const int qrow = 2 * g2 + rr;
-          const int zz = qrow / ny, yy = qrow - zz * ny;
-          a.spec_out[((size_t)(q * nz + zz) * a.out_rows + yy) * a.out_sx + k] = o;
-        }
-        __syncthreads();
+        __syncthreads();  // the next component's stage A' overwrites Tp
       }
     }
     __syncthreads();  // shared buffers are reused by the next tile
