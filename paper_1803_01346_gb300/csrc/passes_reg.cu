@@ -113,7 +113,8 @@ template <int R1, int R2, int TC, int KIND>
 cudaError_t go_z(const Launch<float>& L, float2* base, int rows, int sx, int HX, const float2* tw, double scale,
                  bool chk) {
   constexpr int Lt = R1 * R2;
-  constexpr int CS = cmax(cmax(R2 * (R1 * TC + kPad8), R1 * (R2 * TC + kPad8)), Lt * TC);
+  constexpr int CS = (R1 == R2 && KIND == 1) ? cmax(R2 * (R1 * TC + kPad8), R1 * (R2 * TC + kPad8))
+                               : cmax(cmax(R2 * (R1 * TC + kPad8), R1 * (R2 * TC + kPad8)), Lt * TC);
   const size_t smem = sizeof(float2) * (Lt + 3 * CS);
   auto k = zpass_reg2_kernel<R1, R2, TC, KIND>;
   allow_smem<zpass_reg2_kernel<R1, R2, TC, KIND>>();
@@ -372,7 +373,7 @@ cudaError_t launch_x_reg_io(const Launch<float>& L, XMode mode, const PointParam
 namespace scfft {
 
 template <int R1, int R2, int TC, int KIND>
-__global__ void __launch_bounds__(TC * R1) zpass_reg2_kernel(float2* __restrict__ base, int rows, int sx, int HX,
+__global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpass_reg2_kernel(float2* __restrict__ base, int rows, int sx, int HX,
                                                              int nzs, const float2* __restrict__ twg,
                                                              const float* __restrict__ kt0,
                                                              const float* __restrict__ kt1,
@@ -386,7 +387,8 @@ __global__ void __launch_bounds__(TC * R1) zpass_reg2_kernel(float2* __restrict_
   constexpr bool PR = (KIND == 1);
   constexpr int S2 = R1 * TC + kPad8;  // forward transpose [k2][n1][c]
   constexpr int S1 = R2 * TC + kPad8;  // inverse transpose [m1][k2][c]
-  constexpr int CS = cmax(cmax(R2 * S2, R1 * S1), L * TC);
+  constexpr bool OWN = (R1 == R2 && KIND == 1);  // own-slot product (square split, Biot-Savart kernel)
+  constexpr int CS = OWN ? cmax(R2 * S2, R1 * S1) : cmax(cmax(R2 * S2, R1 * S1), L * TC);
   constexpr int NT = TC * R1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (check_done && ctrl->done) return;
@@ -417,87 +419,208 @@ __global__ void __launch_bounds__(TC * R1) zpass_reg2_kernel(float2* __restrict_
 #pragma unroll
     for (int n2 = 0; n2 < NL; ++n2)
       pre[q][n2] = colok ? col[q * cstride + (size_t)(n1 + R1 * n2) * zstride] : make_float2(0.f, 0.f);
+  if constexpr (OWN) {
+    // Forward, one component at a time.  In stage B the thread (c, k2 = n1 < R2) reads the
+    // slots Fq[k2 S2 + m TC + c] that no other thread reads, so it writes its spectrum
+    // X_q[k2 + R2 k1] back into those same slots without a barrier ("own slots"); the
+    // last component's spectrum stays in registers.
+    float2 w2[R1];
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    float2* Fq = F + q * CS;
-    float2 v[R2];
+    for (int q = 0; q < 3; ++q) {
+      float2* Fq = F + q * CS;
+      float2 v[R2];
 #pragma unroll
-    for (int n2 = 0; n2 < R2; ++n2) v[n2] = n2 < NL ? pre[q][n2] : make_float2(0.f, 0.f);
-    DFT<R2, false, float2>::run(v);
+      for (int n2 = 0; n2 < R2; ++n2) v[n2] = n2 < NL ? pre[q][n2] : make_float2(0.f, 0.f);
+      DFT<R2, false, float2>::run(v);
 #pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) Fq[k2 * S2 + n1 * TC + c] = k2 == 0 ? v[0] : cmul(v[k2], twr[k2]);
-    __syncthreads();
-    float2 w[R1];
+      for (int k2 = 0; k2 < R2; ++k2) Fq[k2 * S2 + n1 * TC + c] = k2 == 0 ? v[0] : cmul(v[k2], twr[k2]);
+      __syncthreads();
+      if (n1 < R2) {
+        float2 w[R1];
+#pragma unroll
+        for (int m = 0; m < R1; ++m) w[m] = Fq[n1 * S2 + m * TC + c];
+        DFT<R1, false, float2>::run(w);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+          if (q < 2)
+            Fq[n1 * S2 + k1 * TC + c] = w[k1];
+          else
+            w2[k1] = w[k1];
+        }
+      }
+    }
+    // ---- product at kz = k2 + R2 k1 on the thread's own points; components 0, 1 from
+    // their own slots, component 2 in registers
     if (n1 < R2) {
+      const int k2 = n1;
+      const int kxx = colok ? kx : 0;
+      float bx0 = 0.f, by0 = 0.f, sxy = 1.f, syg = 1.f;
+      size_t oct = 0, offy = 0;
+      if (KIND == 0) {
+        bx0 = kt0[kxx];
+        by0 = kt1[y];
+        sxy = st0[kxx] * st1[y] * scale;
+      } else {
+        const int fy = (y <= ny) ? y : 2 * ny - y;
+        syg = (y <= ny) ? 1.f : -1.f;
+        oct = (size_t)(nz + 1) * (ny + 1) * (nx + 1);
+        offy = (size_t)fy * (nx + 1) + kxx;
+      }
+      float2* F0 = F + k2 * S2 + c;
+      float2* F1 = F0 + CS;
 #pragma unroll
-      for (int m = 0; m < R1; ++m) w[m] = Fq[n1 * S2 + m * TC + c];
-      DFT<R1, false, float2>::run(w);
+      for (int k1 = 0; k1 < R1; ++k1) {
+        const int kz = k2 + R2 * k1;
+        float ax, ay, az, s;
+        if (KIND == 0) {
+          ax = bx0; ay = by0; az = kt2[kz];
+          s = sxy * st2[kz];
+        } else {
+          const int fz = (kz <= nz) ? kz : 2 * nz - kz;
+          const size_t off = (size_t)fz * (ny + 1) * (nx + 1) + offy;
+          ax = kap[off];
+          ay = syg * kap[oct + off];
+          az = (kz <= nz) ? kap[2 * oct + off] : -kap[2 * oct + off];
+          s = 1.f;
+        }
+        const float2 G0 = F0[k1 * TC], G1 = F1[k1 * TC], G2 = w2[k1];
+        const float2 cx = make_float2(ay * G2.x - az * G1.x, ay * G2.y - az * G1.y);
+        const float2 cy = make_float2(az * G0.x - ax * G2.x, az * G0.y - ax * G2.y);
+        const float2 cz = make_float2(ax * G1.x - ay * G0.x, ax * G1.y - ay * G0.y);
+        F0[k1 * TC] = make_float2(-s * cx.y, s * cx.x);
+        F1[k1 * TC] = make_float2(-s * cy.y, s * cy.x);
+        w2[k1] = make_float2(-s * cz.y, s * cz.x);
+        if ((k1 & 3) == 3) asm volatile("" ::: "memory");  // at most four points' loads in flight
+      }
+    }
+    // ---- inverse: y[m1 + R1 m2] = sum_k2 W_R2^{-m2 k2} W_L^{-m1 k2} (sum_k1 X[k2 + R2 k1] W_R1^{-m1 k1}).
+    // Stage A' of component q writes transposed into buffer q once every thread has read
+    // that buffer's own slots: component 2 (in registers) right after the first barrier,
+    // component 0 after the next, component 1 after the one after.
+    __syncthreads();
+    float2 wr[R1];
+#pragma unroll
+    for (int q = 2; q < 5; ++q) {
+      const int qb = q % 3;
+      if (n1 < R2) {
+        const int k2 = n1;
+        float2* Fb = F + qb * CS;
+        if (q == 2) {
+#pragma unroll
+          for (int k1 = 0; k1 < R1; ++k1) wr[k1] = w2[k1];
+        }
+        DFT<R1, true, float2>::run(wr);
+#pragma unroll
+        for (int m1 = 0; m1 < R1; ++m1) Fb[m1 * S1 + k2 * TC + c] = m1 == 0 ? wr[0] : cmulc(wr[m1], twr[m1]);
+        if (q < 4) {  // the next component's own slots, read before the barrier that frees its buffer
+          const float2* Fn = F + (q - 2) * CS + k2 * S2 + c;
+#pragma unroll
+          for (int k1 = 0; k1 < R1; ++k1) wr[k1] = Fn[k1 * TC];
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float2* Fq = F + q * CS;
+      float2 v[R2];
+#pragma unroll
+      for (int j = 0; j < R2; ++j) v[j] = Fq[n1 * S1 + j * TC + c];
+      DFT<R2, true, float2>::run(v);
+      if (colok) {
+#pragma unroll
+        for (int m2 = 0; m2 < R2; ++m2) {
+          if (PR && m2 >= R2 / 2) continue;
+          col[q * cstride + (size_t)(n1 + R1 * m2) * zstride] = v[m2];
+        }
+      }
+    }
+  } else {
+    // R1 > R2 leaves threads idle in stage B, and the curl's spectra plus its separable
+    // factors do not fit the register budget of the own-slot form: the product runs on
+    // all threads over natural-order spectra [kz][c]
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      float2* Fq = F + q * CS;
+      float2 v[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) v[n2] = n2 < NL ? pre[q][n2] : make_float2(0.f, 0.f);
+      DFT<R2, false, float2>::run(v);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) Fq[k2 * S2 + n1 * TC + c] = k2 == 0 ? v[0] : cmul(v[k2], twr[k2]);
+      __syncthreads();
+      float2 w[R1];
+      if (n1 < R2) {
+#pragma unroll
+        for (int m = 0; m < R1; ++m) w[m] = Fq[n1 * S2 + m * TC + c];
+        DFT<R1, false, float2>::run(w);
+      }
+      __syncthreads();
+      if (n1 < R2) {
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) Fq[(n1 + R2 * k1) * TC + c] = w[k1];
+      }
     }
     __syncthreads();
-    if (n1 < R2) {
-#pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) Fq[(n1 + R2 * k1) * TC + c] = w[k1];
-    }
-  }
-  __syncthreads();
-  // ---- product on the natural-order spectra [kz][c]; a fixed trip count, unrolled so
-  // the kernel-spectrum loads of several points are in flight together
-  const int kxc0 = blockIdx.x * TC;
-  static_assert((L * TC) % NT == 0, "product loop trip count");
+    // ---- product on the natural-order spectra [kz][c]; a fixed trip count, unrolled so
+    // the kernel-spectrum loads of several points are in flight together
+    const int kxc0 = blockIdx.x * TC;
+    static_assert((L * TC) % NT == 0, "product loop trip count");
 #pragma unroll 8
-  for (int j = 0; j < L * TC / NT; ++j) {
-    const int idx = t + j * NT;
-    const int cc = idx % TC, kz = idx / TC;
-    const int kxx = kxc0 + cc < HX ? kxc0 + cc : 0;
-    float ax, ay, az, s;
-    if (KIND == 0) {
-      ax = kt0[kxx]; ay = kt1[y]; az = kt2[kz];
-      s = st0[kxx] * st1[y] * st2[kz] * scale;
-    } else {
-      const int fy = (y <= ny) ? y : 2 * ny - y;
-      const int fz = (kz <= nz) ? kz : 2 * nz - kz;
-      const size_t oct = (size_t)(nz + 1) * (ny + 1) * (nx + 1);
-      const size_t off = ((size_t)fz * (ny + 1) + fy) * (nx + 1) + kxx;
-      ax = kap[off];
-      ay = (y <= ny) ? kap[oct + off] : -kap[oct + off];
-      az = (kz <= nz) ? kap[2 * oct + off] : -kap[2 * oct + off];
-      s = 1.f;
-    }
-    const float2 F0 = F[idx], F1 = F[CS + idx], F2 = F[2 * CS + idx];
-    const float2 cx = make_float2(ay * F2.x - az * F1.x, ay * F2.y - az * F1.y);
-    const float2 cy = make_float2(az * F0.x - ax * F2.x, az * F0.y - ax * F2.y);
-    const float2 cz = make_float2(ax * F1.x - ay * F0.x, ax * F1.y - ay * F0.y);
-    F[idx] = make_float2(-s * cx.y, s * cx.x);
-    F[CS + idx] = make_float2(-s * cy.y, s * cy.x);
-    F[2 * CS + idx] = make_float2(-s * cz.y, s * cz.x);
-  }
-  __syncthreads();
-  // ---- inverse: y[m1 + R1 m2] = sum_k2 W_R2^{-m2 k2} W_L^{-m1 k2} (sum_k1 X[k2 + R2 k1] W_R1^{-m1 k1})
-  for (int q = 0; q < 3; ++q) {
-    float2* Fq = F + q * CS;
-    float2 w[R1];
-    if (n1 < R2) {
-      const int k2 = n1;
-#pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) w[k1] = Fq[(k2 + R2 * k1) * TC + c];
-      DFT<R1, true, float2>::run(w);
+    for (int j = 0; j < L * TC / NT; ++j) {
+      const int idx = t + j * NT;
+      const int cc = idx % TC, kz = idx / TC;
+      const int kxx = kxc0 + cc < HX ? kxc0 + cc : 0;
+      float ax, ay, az, s;
+      if (KIND == 0) {
+        ax = kt0[kxx]; ay = kt1[y]; az = kt2[kz];
+        s = st0[kxx] * st1[y] * st2[kz] * scale;
+      } else {
+        const int fy = (y <= ny) ? y : 2 * ny - y;
+        const int fz = (kz <= nz) ? kz : 2 * nz - kz;
+        const size_t oct = (size_t)(nz + 1) * (ny + 1) * (nx + 1);
+        const size_t off = ((size_t)fz * (ny + 1) + fy) * (nx + 1) + kxx;
+        ax = kap[off];
+        ay = (y <= ny) ? kap[oct + off] : -kap[oct + off];
+        az = (kz <= nz) ? kap[2 * oct + off] : -kap[2 * oct + off];
+        s = 1.f;
+      }
+      const float2 F0 = F[idx], F1 = F[CS + idx], F2 = F[2 * CS + idx];
+      const float2 cx = make_float2(ay * F2.x - az * F1.x, ay * F2.y - az * F1.y);
+      const float2 cy = make_float2(az * F0.x - ax * F2.x, az * F0.y - ax * F2.y);
+      const float2 cz = make_float2(ax * F1.x - ay * F0.x, ax * F1.y - ay * F0.y);
+      F[idx] = make_float2(-s * cx.y, s * cx.x);
+      F[CS + idx] = make_float2(-s * cy.y, s * cy.x);
+      F[2 * CS + idx] = make_float2(-s * cz.y, s * cz.x);
     }
     __syncthreads();
-    if (n1 < R2) {
-      const int k2 = n1;
+    // ---- inverse: y[m1 + R1 m2] = sum_k2 W_R2^{-m2 k2} W_L^{-m1 k2} (sum_k1 X[k2 + R2 k1] W_R1^{-m1 k1})
+    for (int q = 0; q < 3; ++q) {
+      float2* Fq = F + q * CS;
+      float2 w[R1];
+      if (n1 < R2) {
+        const int k2 = n1;
 #pragma unroll
-      for (int m1 = 0; m1 < R1; ++m1) Fq[m1 * S1 + k2 * TC + c] = m1 == 0 ? w[0] : cmulc(w[m1], twr[m1]);
-    }
-    __syncthreads();
-    float2 v[R2];
+        for (int k1 = 0; k1 < R1; ++k1) w[k1] = Fq[(k2 + R2 * k1) * TC + c];
+        DFT<R1, true, float2>::run(w);
+      }
+      __syncthreads();
+      if (n1 < R2) {
+        const int k2 = n1;
 #pragma unroll
-    for (int j = 0; j < R2; ++j) v[j] = Fq[n1 * S1 + j * TC + c];
-    DFT<R2, true, float2>::run(v);
-    if (colok) {
+        for (int m1 = 0; m1 < R1; ++m1) Fq[m1 * S1 + k2 * TC + c] = m1 == 0 ? w[0] : cmulc(w[m1], twr[m1]);
+      }
+      __syncthreads();
+      float2 v[R2];
 #pragma unroll
-      for (int m2 = 0; m2 < R2; ++m2) {
-        if (PR && m2 >= R2 / 2) continue;
-        col[q * cstride + (size_t)(n1 + R1 * m2) * zstride] = v[m2];
+      for (int j = 0; j < R2; ++j) v[j] = Fq[n1 * S1 + j * TC + c];
+      DFT<R2, true, float2>::run(v);
+      if (colok) {
+#pragma unroll
+        for (int m2 = 0; m2 < R2; ++m2) {
+          if (PR && m2 >= R2 / 2) continue;
+          col[q * cstride + (size_t)(n1 + R1 * m2) * zstride] = v[m2];
+        }
       }
     }
   }
