@@ -26,6 +26,12 @@ namespace {
 constexpr int kPad8 = 8;  // row padding (complex elements) that spreads half-warps over all banks
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+// 4-byte asynchronous global -> shared copy, and the wait for all of this thread's copies
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <typename V> __device__ __forceinline__ V tw_mul(V a, V w, bool inv) { return inv ? cmulc(a, w) : cmul(a, w); }
 
@@ -115,7 +121,8 @@ cudaError_t go_z(const Launch<float>& L, float2* base, int rows, int sx, int HX,
   constexpr int Lt = R1 * R2;
   constexpr int CS = (R1 == R2 && KIND == 1) ? cmax(R2 * (R1 * TC + kPad8), R1 * (R2 * TC + kPad8))
                                : cmax(cmax(R2 * (R1 * TC + kPad8), R1 * (R2 * TC + kPad8)), Lt * TC);
-  const size_t smem = sizeof(float2) * (Lt + 3 * CS);
+  // the own-slot form (square split, padded kernel) also stages K^ [3][Lt/2 + 1][TC]
+  const size_t smem = sizeof(float2) * (Lt + 3 * CS) + ((R1 == R2 && KIND == 1) ? sizeof(float) * 3 * (Lt / 2 + 1) * TC : 0);
   auto k = zpass_reg2_kernel<R1, R2, TC, KIND>;
   allow_smem<zpass_reg2_kernel<R1, R2, TC, KIND>>();
   dim3 grid((HX + TC - 1) / TC, rows, 1);
@@ -424,6 +431,21 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
     // slots Fq[k2 S2 + m TC + c] that no other thread reads, so it writes its spectrum
     // X_q[k2 + R2 k1] back into those same slots without a barrier ("own slots"); the
     // last component's spectrum stays in registers.
+    // The kernel spectrum of this tile, K^_a(kx, y, fz) for the folded kz (fz <= nz), is
+    // copied asynchronously into shared memory Ks[a][fz][c] while the forward transforms run.
+    const int NZ1 = nz + 1;
+    float* Ks = reinterpret_cast<float*>(F + 3 * CS);
+    {
+      const int fy = (y <= ny) ? y : 2 * ny - y;
+      const size_t plane = (size_t)(ny + 1) * (nx + 1);
+      const size_t oct = (size_t)NZ1 * plane;
+      const int kx0 = blockIdx.x * TC;
+      for (int i = t; i < 3 * NZ1 * TC; i += NT) {
+        const int cc = i % TC, r = i / TC, a = r / NZ1, fz = r - a * NZ1;
+        const int kxx = kx0 + cc < HX ? kx0 + cc : 0;
+        cp_async4(Ks + i, kap + a * oct + fz * plane + (size_t)fy * (nx + 1) + kxx);
+      }
+    }
     float2 w2[R1];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -434,6 +456,7 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
       DFT<R2, false, float2>::run(v);
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) Fq[k2 * S2 + n1 * TC + c] = k2 == 0 ? v[0] : cmul(v[k2], twr[k2]);
+      if (q == 2) cp_async_wait_all();  // Ks complete (visible to all after the barrier)
       __syncthreads();
       if (n1 < R2) {
         float2 w[R1];
@@ -450,47 +473,27 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
       }
     }
     // ---- product at kz = k2 + R2 k1 on the thread's own points; components 0, 1 from
-    // their own slots, component 2 in registers
+    // their own slots, component 2 in registers.  K^ is odd in ky (component y) and in
+    // kz (component z) about the fold.
     if (n1 < R2) {
       const int k2 = n1;
-      const int kxx = colok ? kx : 0;
-      float bx0 = 0.f, by0 = 0.f, sxy = 1.f, syg = 1.f;
-      size_t oct = 0, offy = 0;
-      if (KIND == 0) {
-        bx0 = kt0[kxx];
-        by0 = kt1[y];
-        sxy = st0[kxx] * st1[y] * scale;
-      } else {
-        const int fy = (y <= ny) ? y : 2 * ny - y;
-        syg = (y <= ny) ? 1.f : -1.f;
-        oct = (size_t)(nz + 1) * (ny + 1) * (nx + 1);
-        offy = (size_t)fy * (nx + 1) + kxx;
-      }
+      const float syg = (y <= ny) ? 1.f : -1.f;
       float2* F0 = F + k2 * S2 + c;
       float2* F1 = F0 + CS;
 #pragma unroll
       for (int k1 = 0; k1 < R1; ++k1) {
         const int kz = k2 + R2 * k1;
-        float ax, ay, az, s;
-        if (KIND == 0) {
-          ax = bx0; ay = by0; az = kt2[kz];
-          s = sxy * st2[kz];
-        } else {
-          const int fz = (kz <= nz) ? kz : 2 * nz - kz;
-          const size_t off = (size_t)fz * (ny + 1) * (nx + 1) + offy;
-          ax = kap[off];
-          ay = syg * kap[oct + off];
-          az = (kz <= nz) ? kap[2 * oct + off] : -kap[2 * oct + off];
-          s = 1.f;
-        }
+        const int fz = (kz <= nz) ? kz : 2 * nz - kz;
+        const float ax = Ks[fz * TC + c];
+        const float ay = syg * Ks[(NZ1 + fz) * TC + c];
+        const float az = (kz <= nz) ? Ks[(2 * NZ1 + fz) * TC + c] : -Ks[(2 * NZ1 + fz) * TC + c];
         const float2 G0 = F0[k1 * TC], G1 = F1[k1 * TC], G2 = w2[k1];
         const float2 cx = make_float2(ay * G2.x - az * G1.x, ay * G2.y - az * G1.y);
         const float2 cy = make_float2(az * G0.x - ax * G2.x, az * G0.y - ax * G2.y);
         const float2 cz = make_float2(ax * G1.x - ay * G0.x, ax * G1.y - ay * G0.y);
-        F0[k1 * TC] = make_float2(-s * cx.y, s * cx.x);
-        F1[k1 * TC] = make_float2(-s * cy.y, s * cy.x);
-        w2[k1] = make_float2(-s * cz.y, s * cz.x);
-        if ((k1 & 3) == 3) asm volatile("" ::: "memory");  // at most four points' loads in flight
+        F0[k1 * TC] = make_float2(-cx.y, cx.x);
+        F1[k1 * TC] = make_float2(-cy.y, cy.x);
+        w2[k1] = make_float2(-cz.y, cz.x);
       }
     }
     // ---- inverse: y[m1 + R1 m2] = sum_k2 W_R2^{-m2 k2} W_L^{-m1 k2} (sum_k1 X[k2 + R2 k1] W_R1^{-m1 k1}).
