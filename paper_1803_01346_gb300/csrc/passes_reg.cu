@@ -26,12 +26,6 @@ namespace {
 constexpr int kPad8 = 8;  // row padding (complex elements) that spreads half-warps over all banks
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-// 4-byte asynchronous global -> shared copy, and the wait for all of this thread's copies
-__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <typename V> __device__ __forceinline__ V tw_mul(V a, V w, bool inv) { return inv ? cmulc(a, w) : cmul(a, w); }
 
@@ -121,8 +115,7 @@ cudaError_t go_z(const Launch<float>& L, float2* base, int rows, int sx, int HX,
   constexpr int Lt = R1 * R2;
   constexpr int CS = (R1 == R2 && KIND == 1) ? cmax(R2 * (R1 * TC + kPad8), R1 * (R2 * TC + kPad8))
                                : cmax(cmax(R2 * (R1 * TC + kPad8), R1 * (R2 * TC + kPad8)), Lt * TC);
-  // the own-slot form (square split, padded kernel) also stages K^ [3][Lt/2 + 1][TC]
-  const size_t smem = sizeof(float2) * (Lt + 3 * CS) + ((R1 == R2 && KIND == 1) ? sizeof(float) * 3 * (Lt / 2 + 1) * TC : 0);
+  const size_t smem = sizeof(float2) * (Lt + 3 * CS);
   auto k = zpass_reg2_kernel<R1, R2, TC, KIND>;
   allow_smem<zpass_reg2_kernel<R1, R2, TC, KIND>>();
   dim3 grid((HX + TC - 1) / TC, rows, 1);
@@ -431,21 +424,6 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
     // slots Fq[k2 S2 + m TC + c] that no other thread reads, so it writes its spectrum
     // X_q[k2 + R2 k1] back into those same slots without a barrier ("own slots"); the
     // last component's spectrum stays in registers.
-    // The kernel spectrum of this tile, K^_a(kx, y, fz) for the folded kz (fz <= nz), is
-    // copied asynchronously into shared memory Ks[a][fz][c] while the forward transforms run.
-    const int NZ1 = nz + 1;
-    float* Ks = reinterpret_cast<float*>(F + 3 * CS);
-    {
-      const int fy = (y <= ny) ? y : 2 * ny - y;
-      const size_t plane = (size_t)(ny + 1) * (nx + 1);
-      const size_t oct = (size_t)NZ1 * plane;
-      const int kx0 = blockIdx.x * TC;
-      for (int i = t; i < 3 * NZ1 * TC; i += NT) {
-        const int cc = i % TC, r = i / TC, a = r / NZ1, fz = r - a * NZ1;
-        const int kxx = kx0 + cc < HX ? kx0 + cc : 0;
-        cp_async4(Ks + i, kap + a * oct + fz * plane + (size_t)fy * (nx + 1) + kxx);
-      }
-    }
     float2 w2[R1];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -456,7 +434,6 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
       DFT<R2, false, float2>::run(v);
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) Fq[k2 * S2 + n1 * TC + c] = k2 == 0 ? v[0] : cmul(v[k2], twr[k2]);
-      if (q == 2) cp_async_wait_all();  // Ks complete (visible to all after the barrier)
       __syncthreads();
       if (n1 < R2) {
         float2 w[R1];
@@ -473,27 +450,47 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
       }
     }
     // ---- product at kz = k2 + R2 k1 on the thread's own points; components 0, 1 from
-    // their own slots, component 2 in registers.  K^ is odd in ky (component y) and in
-    // kz (component z) about the fold.
+    // their own slots, component 2 in registers
     if (n1 < R2) {
       const int k2 = n1;
-      const float syg = (y <= ny) ? 1.f : -1.f;
+      const int kxx = colok ? kx : 0;
+      float bx0 = 0.f, by0 = 0.f, sxy = 1.f, syg = 1.f;
+      size_t oct = 0, offy = 0;
+      if (KIND == 0) {
+        bx0 = kt0[kxx];
+        by0 = kt1[y];
+        sxy = st0[kxx] * st1[y] * scale;
+      } else {
+        const int fy = (y <= ny) ? y : 2 * ny - y;
+        syg = (y <= ny) ? 1.f : -1.f;
+        oct = (size_t)(nz + 1) * (ny + 1) * (nx + 1);
+        offy = (size_t)fy * (nx + 1) + kxx;
+      }
       float2* F0 = F + k2 * S2 + c;
       float2* F1 = F0 + CS;
 #pragma unroll
       for (int k1 = 0; k1 < R1; ++k1) {
         const int kz = k2 + R2 * k1;
-        const int fz = (kz <= nz) ? kz : 2 * nz - kz;
-        const float ax = Ks[fz * TC + c];
-        const float ay = syg * Ks[(NZ1 + fz) * TC + c];
-        const float az = (kz <= nz) ? Ks[(2 * NZ1 + fz) * TC + c] : -Ks[(2 * NZ1 + fz) * TC + c];
+        float ax, ay, az, s;
+        if (KIND == 0) {
+          ax = bx0; ay = by0; az = kt2[kz];
+          s = sxy * st2[kz];
+        } else {
+          const int fz = (kz <= nz) ? kz : 2 * nz - kz;
+          const size_t off = (size_t)fz * (ny + 1) * (nx + 1) + offy;
+          ax = kap[off];
+          ay = syg * kap[oct + off];
+          az = (kz <= nz) ? kap[2 * oct + off] : -kap[2 * oct + off];
+          s = 1.f;
+        }
         const float2 G0 = F0[k1 * TC], G1 = F1[k1 * TC], G2 = w2[k1];
         const float2 cx = make_float2(ay * G2.x - az * G1.x, ay * G2.y - az * G1.y);
         const float2 cy = make_float2(az * G0.x - ax * G2.x, az * G0.y - ax * G2.y);
         const float2 cz = make_float2(ax * G1.x - ay * G0.x, ax * G1.y - ay * G0.y);
-        F0[k1 * TC] = make_float2(-cx.y, cx.x);
-        F1[k1 * TC] = make_float2(-cy.y, cy.x);
-        w2[k1] = make_float2(-cz.y, cz.x);
+        F0[k1 * TC] = make_float2(-s * cx.y, s * cx.x);
+        F1[k1 * TC] = make_float2(-s * cy.y, s * cy.x);
+        w2[k1] = make_float2(-s * cz.y, s * cz.x);
+        if ((k1 & 3) == 3) asm volatile("" ::: "memory");  // at most four points' loads in flight
       }
     }
     // ---- inverse: y[m1 + R1 m2] = sum_k2 W_R2^{-m2 k2} W_L^{-m1 k2} (sum_k1 X[k2 + R2 k1] W_R1^{-m1 k1}).
@@ -631,8 +628,10 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
 
 // x pass, one component at a time; the node-wise step reads the three
 // components' real rows from shared memory RS[q][p][x] (complex = rows a, b).
+// At most 128 registers (four CTAs per SM): the batched node-wise loads would otherwise
+// take the Eq. 5 update pass to 152 registers and three CTAs, which measured slower.
 template <int MODE, int R1i, int R2i, int R2o, int P>
-__global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP)
+__global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
     xpass_reg2_kernel(const XRArgs a) {
   typedef XS<MODE, R1i, R2i, R2o> S;
   constexpr int TP = S::TP, R1o = S::R1o, Li = S::Li, Lo = S::Lo;
@@ -774,47 +773,85 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP)
       __syncthreads();
     }
 
-    // ---- node-wise step
+    // ---- node-wise step.  All of a thread's node-wise global reads are issued first, in
+    // one unrolled batch (one memory latency per tile, not one per node pair), and the
+    // arithmetic and stores follow.
     if constexpr (S::C2R) {
       const PointParams& pp = a.pp;
-      for (int idx = tid; idx < P * XL; idx += NT) {
+      constexpr int J = (P * XL + NT - 1) / NT;  // node pairs per thread
+      constexpr bool MASKED = MODE == X_POWERLAW || MODE == X_ASSEMBLE || MODE == X_MASKPAD || MODE == X_UPDATE;
+      constexpr int NO = MODE == X_UPDATE || MODE == X_ASSEMBLE ? 3 : (MODE == X_POWERLAW ? 1 : 0);
+      bool mk[J][2];
+      float ov[J][NO > 0 ? NO : 1][2];  // hold (update), warm start (assemble), jc (power law)
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int idx = tid + j * NT;
         const int x = idx % XL, pp2 = idx / XL;
         const int g2 = tile * P + pp2;
-        if (g2 >= npairs) continue;
+        const bool ok = idx < P * XL && g2 < npairs;
         const size_t na = (size_t)(2 * g2) * XL + x, nb = na + XL;
+        mk[j][0] = mk[j][1] = false;
+#pragma unroll
+        for (int q = 0; q < (NO > 0 ? NO : 1); ++q) ov[j][q][0] = ov[j][q][1] = 0.f;
+        if (ok) {
+          if (MASKED) {
+            mk[j][0] = a.mask[na];
+            mk[j][1] = a.mask[nb];
+          }
+          if (MODE == X_UPDATE) {
+#pragma unroll
+            for (int q = 0; q < NO; ++q) {
+              ov[j][q][0] = a.hold[q * N + na];
+              ov[j][q][1] = a.hold[q * N + nb];
+            }
+          } else if (MODE == X_ASSEMBLE) {
+#pragma unroll
+            for (int q = 0; q < NO; ++q) {
+              ov[j][q][0] = a.warm_f32 ? a.warm_f32[q * N + na] : (float)a.warm[q * N + na];
+              ov[j][q][1] = a.warm_f32 ? a.warm_f32[q * N + nb] : (float)a.warm[q * N + nb];
+            }
+          } else if (MODE == X_POWERLAW) {
+            ov[j][0][0] = a.jc ? a.jc[na] : (float)pp.jc;
+            ov[j][0][1] = a.jc ? a.jc[nb] : (float)pp.jc;
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int idx = tid + j * NT;
+        const int x = idx % XL, pp2 = idx / XL;
+        const int g2 = tile * P + pp2;
+        if (!(idx < P * XL && g2 < npairs)) continue;
+        const size_t na = (size_t)(2 * g2) * XL + x, nb = na + XL;
+        const bool ia = mk[j][0], ib = mk[j][1];
         float2 u[3];
   #pragma unroll
         for (int q = 0; q < 3; ++q) u[q] = RS[(q * P + pp2) * XL + x];
         if (MODE == X_POWERLAW) {
-          const bool ia = a.mask[na], ib = a.mask[nb];
-          const float ca = a.jc ? a.jc[na] : (float)pp.jc, cb = a.jc ? a.jc[nb] : (float)pp.jc;
-          const float ra = rho_of(u[0].x, u[1].x, u[2].x, ia, ca, pp);
-          const float rb = rho_of(u[0].y, u[1].y, u[2].y, ib, cb, pp);
+          const float ra = rho_of(u[0].x, u[1].x, u[2].x, ia, ov[j][0][0], pp);
+          const float rb = rho_of(u[0].y, u[1].y, u[2].y, ib, ov[j][0][1], pp);
   #pragma unroll
           for (int q = 0; q < 3; ++q) u[q] = make_float2(u[q].x * ra, u[q].y * rb);
         } else if (MODE == X_ASSEMBLE) {
-          const bool ia = a.mask[na], ib = a.mask[nb];
           const float s = -(float)pp.inv_mu0;
   #pragma unroll
           for (int q = 0; q < 3; ++q) {
-            const float va = ia ? s * u[q].x : (a.warm_f32 ? a.warm_f32[q * N + na] : (float)a.warm[q * N + na]);
-            const float vb = ib ? s * u[q].y : (a.warm_f32 ? a.warm_f32[q * N + nb] : (float)a.warm[q * N + nb]);
+            const float va = ia ? s * u[q].x : ov[j][q][0];
+            const float vb = ib ? s * u[q].y : ov[j][q][1];
             a.hnew[q * N + na] = va;
             a.hnew[q * N + nb] = vb;
             u[q] = make_float2(va, vb);
           }
         } else if (MODE == X_MASKPAD) {
-          const bool ia = a.mask[na], ib = a.mask[nb];
   #pragma unroll
           for (int q = 0; q < 3; ++q) u[q] = make_float2(ia ? u[q].x : 0.f, ib ? u[q].y : 0.f);
         } else if (MODE == X_UPDATE) {
           // per-node |dh^{i+1} - dh^i| in FP32 (the FP32 path's own precision); the
           // per-thread sum stays FP32, the CTA and grid sums are FP64
-          const bool ia = a.mask[na], ib = a.mask[nb];
           float da = 0.f, db = 0.f;
   #pragma unroll
           for (int q = 0; q < 3; ++q) {
-            const float oa = a.hold[q * N + na], ob = a.hold[q * N + nb];
+            const float oa = ov[j][q][0], ob = ov[j][q][1];
             const float he = (float)pp.hedot[q];
             const float va = ia ? oa : he + u[q].x;
             const float vb = ib ? ob : he + u[q].y;
