@@ -118,7 +118,9 @@ cudaError_t go_z(const Launch<float>& L, float2* base, int rows, int sx, int HX,
   const size_t smem = sizeof(float2) * (Lt + 3 * CS);
   auto k = zpass_reg2_kernel<R1, R2, TC, KIND>;
   allow_smem<zpass_reg2_kernel<R1, R2, TC, KIND>>();
-  dim3 grid((HX + TC - 1) / TC, rows, 1);
+  constexpr bool PACK = (R1 == R2 && KIND == 1);  // as in the kernel's column map
+  const int nfull = HX / TC, rem = HX - nfull * TC;
+  const dim3 grid = PACK ? dim3(nfull * rows + (rows * rem + TC - 1) / TC, 1, 1) : dim3((HX + TC - 1) / TC, rows, 1);
   const Work<float>& w = *L.w;
   k<<<grid, TC * R1, smem, L.st>>>(base, rows, sx, HX, L.g.nz, tw, w.kt[0], w.kt[1], w.kt[2], w.st[0], w.st[1],
                                    w.st[2], (float)scale, w.kap, L.g.nx, L.g.ny, L.g.nz, L.ctrl, chk ? 1 : 0);
@@ -397,8 +399,33 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
   const int t = threadIdx.x;
   for (int i = t; i < L; i += NT) tw[i] = twg[i];
   const int c = t % TC, n1 = t / TC;
-  const int y = blockIdx.y, kx = blockIdx.x * TC + c;
-  const bool colok = kx < HX;
+  // Column map.  The curl's pass: grid (ceil(HX / TC), rows), TC consecutive kx of row y per
+  // CTA.  The padded pass: a 1-D grid whose regular CTAs take TC consecutive kx of one row;
+  // the kx left over when HX is not a multiple of TC (the Nyquist column kx = HX - 1 of the
+  // half spectrum) are packed TC (row, kx) pairs to a CTA and run first, so no CTA runs
+  // mostly empty columns (packing measured slower in the curl's pass).
+  constexpr bool PACK = OWN;
+  int y, kx;
+  bool colok;
+  if constexpr (PACK) {
+    const int nfull = HX / TC, rem = HX - nfull * TC;
+    const int ntail = (rows * rem + TC - 1) / TC;
+    const int b = blockIdx.x;
+    if (b >= ntail) {
+      y = (b - ntail) / nfull;
+      kx = (b - ntail - y * nfull) * TC + c;
+      colok = true;
+    } else {
+      const int e = b * TC + c;
+      colok = e < rows * rem;
+      y = colok ? e / rem : 0;
+      kx = colok ? nfull * TC + (e - y * rem) : 0;
+    }
+  } else {
+    y = blockIdx.y;
+    kx = blockIdx.x * TC + c;
+    colok = kx < HX;
+  }
   const size_t zstride = (size_t)rows * sx;
   const size_t cstride = (size_t)nzs * zstride;
   float2* col = base + (size_t)y * sx + kx;
@@ -564,18 +591,19 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
     __syncthreads();
     // ---- product on the natural-order spectra [kz][c]; a fixed trip count, unrolled so
     // the kernel-spectrum loads of several points are in flight together
-    const int kxc0 = blockIdx.x * TC;
     static_assert((L * TC) % NT == 0, "product loop trip count");
+    static_assert(NT % TC == 0, "a thread keeps its column in the product loop");
+    const int yc = y, kxx = colok ? kx : 0;  // idx % TC == c on every trip
 #pragma unroll 8
     for (int j = 0; j < L * TC / NT; ++j) {
       const int idx = t + j * NT;
-      const int cc = idx % TC, kz = idx / TC;
-      const int kxx = kxc0 + cc < HX ? kxc0 + cc : 0;
+      const int kz = idx / TC;
       float ax, ay, az, s;
       if (KIND == 0) {
-        ax = kt0[kxx]; ay = kt1[y]; az = kt2[kz];
-        s = st0[kxx] * st1[y] * st2[kz] * scale;
+        ax = kt0[kxx]; ay = kt1[yc]; az = kt2[kz];
+        s = st0[kxx] * st1[yc] * st2[kz] * scale;
       } else {
+        const int y = yc;
         const int fy = (y <= ny) ? y : 2 * ny - y;
         const int fz = (kz <= nz) ? kz : 2 * nz - kz;
         const size_t oct = (size_t)(nz + 1) * (ny + 1) * (nx + 1);
