@@ -198,6 +198,7 @@ template <typename T> scfft_status alloc_work(scfft_ctx* c) {
   CK(cudaMalloc(&w.Hd[0], sizeof(T) * 3 * N));
   CK(cudaMalloc(&w.Hd[1], sizeof(T) * 3 * N));
   CK(cudaMalloc(&w.kap, sizeof(T) * 3 * (size_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1)));
+  if constexpr (sizeof(T) == 4) CK(cudaMalloc(&w.kap4, sizeof(float4) * (size_t)(g.nx + 1) * (g.ny + 1) * (g.nz + 1)));
   const int n[3] = {g.nx, g.ny, g.nz};
   const double sig = c->opt.sigma_scale * 0.5 *
                      sqrt(pow(2 * c->L[0] / g.nx, 2) + pow(2 * c->L[1] / g.ny, 2) + pow(2 * c->L[2] / g.nz, 2));
@@ -234,7 +235,7 @@ template <typename T> scfft_status alloc_work(scfft_ctx* c) {
 }
 
 template <typename T> void free_work(Work<T>& w) {
-  cudaFree(w.U); cudaFree(w.Pd); cudaFree(w.Hd[0]); cudaFree(w.Hd[1]); cudaFree(w.jc); cudaFree(w.kap);
+  cudaFree(w.U); cudaFree(w.Pd); cudaFree(w.Hd[0]); cudaFree(w.Hd[1]); cudaFree(w.jc); cudaFree(w.kap); cudaFree(w.kap4);
   for (int a = 0; a < 3; ++a) { cudaFree(w.kt[a]); cudaFree(w.st[a]); cudaFree(w.twu[a]); cudaFree(w.twp[a]); }
   w = Work<T>();
 }

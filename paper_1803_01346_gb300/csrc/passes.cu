@@ -526,6 +526,11 @@ __global__ void scale_convert_kernel(const double* __restrict__ src, double s, f
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     dst[i] = (float)(src[i] * s);
 }
+// [3][oct] -> [oct] x float4 {a = 0, 1, 2, 0}: one 16-byte load per point in the z pass's product
+__global__ void interleave_kernel(const float* __restrict__ src, float4* __restrict__ dst, long long oct) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < oct; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = make_float4(src[i], src[oct + i], src[2 * oct + i], 0.f);
+}
 __global__ void scale_convert_kernel(const double* __restrict__ src, double s, double* dst, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     dst[i] = src[i] * s;
@@ -721,6 +726,7 @@ cudaError_t launch_kernel_spectrum(const Launch<T>& L, double Lx, double Ly, dou
     axis_transform<<<grid_for(oct), kThreads, 0, L.st>>>(a0, b0, nx + 1, ny + 1, nz, 2, c == 2);
   }
   scale_convert_kernel<<<grid_for(3 * oct), kThreads, 0, L.st>>>(B, 1.0 / (8.0 * (double)N), L.w->kap, 3 * oct);
+  if constexpr (sizeof(T) == 4) interleave_kernel<<<grid_for(oct), kThreads, 0, L.st>>>(L.w->kap, L.w->kap4, oct);
   return cudaGetLastError();
 }
 

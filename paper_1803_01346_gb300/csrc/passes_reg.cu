@@ -26,6 +26,12 @@ namespace {
 constexpr int kPad8 = 8;  // row padding (complex elements) that spreads half-warps over all banks
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+// 16-byte asynchronous global -> shared copy (L2 only), and the wait for all of this thread's copies
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <typename V> __device__ __forceinline__ V tw_mul(V a, V w, bool inv) { return inv ? cmulc(a, w) : cmul(a, w); }
 
@@ -92,7 +98,7 @@ __global__ void zpass_reg2_kernel(float2* __restrict__ base, int rows, int sx, i
                                   const float2* __restrict__ twg, const float* __restrict__ kt0,
                                   const float* __restrict__ kt1, const float* __restrict__ kt2,
                                   const float* __restrict__ st0, const float* __restrict__ st1,
-                                  const float* __restrict__ st2, float scale, const float* __restrict__ kap, int nx,
+                                  const float* __restrict__ st2, float scale, const float4* __restrict__ kap4, int nx,
                                   int ny, int nz, const Ctrl* ctrl, int check_done);
 
 // ---------------------------------------------------------------- launchers
@@ -115,7 +121,9 @@ cudaError_t go_z(const Launch<float>& L, float2* base, int rows, int sx, int HX,
   constexpr int Lt = R1 * R2;
   constexpr int CS = (R1 == R2 && KIND == 1) ? cmax(R2 * (R1 * TC + kPad8), R1 * (R2 * TC + kPad8))
                                : cmax(cmax(R2 * (R1 * TC + kPad8), R1 * (R2 * TC + kPad8)), Lt * TC);
-  const size_t smem = sizeof(float2) * (Lt + 3 * CS);
+  // the own-slot form (square split, padded kernel) also stages K^ as [Lt/2 + 1][TC] float4
+  const size_t smem = sizeof(float2) * (Lt + 3 * CS) + ((R1 == R2 && KIND == 1) ? sizeof(float4) * (Lt / 2 + 1) * TC : 0);
+  static_assert((Lt + 3 * CS) % 2 == 0, "16-byte alignment of the staged kernel spectrum");
   auto k = zpass_reg2_kernel<R1, R2, TC, KIND>;
   allow_smem<zpass_reg2_kernel<R1, R2, TC, KIND>>();
   constexpr bool PACK = (R1 == R2 && KIND == 1);  // as in the kernel's column map
@@ -123,7 +131,7 @@ cudaError_t go_z(const Launch<float>& L, float2* base, int rows, int sx, int HX,
   const dim3 grid = PACK ? dim3(nfull * rows + (rows * rem + TC - 1) / TC, 1, 1) : dim3((HX + TC - 1) / TC, rows, 1);
   const Work<float>& w = *L.w;
   k<<<grid, TC * R1, smem, L.st>>>(base, rows, sx, HX, L.g.nz, tw, w.kt[0], w.kt[1], w.kt[2], w.st[0], w.st[1],
-                                   w.st[2], (float)scale, w.kap, L.g.nx, L.g.ny, L.g.nz, L.ctrl, chk ? 1 : 0);
+                                   w.st[2], (float)scale, w.kap4, L.g.nx, L.g.ny, L.g.nz, L.ctrl, chk ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -383,7 +391,7 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
                                                              const float* __restrict__ st0,
                                                              const float* __restrict__ st1,
                                                              const float* __restrict__ st2, float scale,
-                                                             const float* __restrict__ kap, int nx, int ny, int nz,
+                                                             const float4* __restrict__ kap4, int nx, int ny, int nz,
                                                              const Ctrl* ctrl, int check_done) {
   constexpr int L = R1 * R2;
   constexpr bool PR = (KIND == 1);
@@ -451,6 +459,16 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
     // slots Fq[k2 S2 + m TC + c] that no other thread reads, so it writes its spectrum
     // X_q[k2 + R2 k1] back into those same slots without a barrier ("own slots"); the
     // last component's spectrum stays in registers.
+    // This column's kernel spectrum K^(kx, fy, fz), fz = 0..nz (the fold of kz), is copied
+    // asynchronously into shared memory Ks[fz][c] while the forward transforms run, so the
+    // product finds it there instead of waiting on L2 (the fold also halves the reads).
+    float4* Ks = reinterpret_cast<float4*>(F + 3 * CS);
+    {
+      const int fy = (y <= ny) ? y : 2 * ny - y;
+      const size_t plane = (size_t)(ny + 1) * (nx + 1);
+      const float4* src = kap4 + (size_t)fy * (nx + 1) + (colok ? kx : 0);
+      for (int fz = n1; fz <= nz; fz += R1) cp_async16(Ks + fz * TC + c, src + fz * plane);
+    }
     float2 w2[R1];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -461,6 +479,7 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
       DFT<R2, false, float2>::run(v);
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) Fq[k2 * S2 + n1 * TC + c] = k2 == 0 ? v[0] : cmul(v[k2], twr[k2]);
+      if (q == 2) cp_async_wait_all();  // Ks complete, visible to all after the barrier
       __syncthreads();
       if (n1 < R2) {
         float2 w[R1];
@@ -477,47 +496,26 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
       }
     }
     // ---- product at kz = k2 + R2 k1 on the thread's own points; components 0, 1 from
-    // their own slots, component 2 in registers
+    // their own slots, component 2 in registers.  K^ is odd in ky (component y) and in kz
+    // (component z) about the fold.
     if (n1 < R2) {
       const int k2 = n1;
-      const int kxx = colok ? kx : 0;
-      float bx0 = 0.f, by0 = 0.f, sxy = 1.f, syg = 1.f;
-      size_t oct = 0, offy = 0;
-      if (KIND == 0) {
-        bx0 = kt0[kxx];
-        by0 = kt1[y];
-        sxy = st0[kxx] * st1[y] * scale;
-      } else {
-        const int fy = (y <= ny) ? y : 2 * ny - y;
-        syg = (y <= ny) ? 1.f : -1.f;
-        oct = (size_t)(nz + 1) * (ny + 1) * (nx + 1);
-        offy = (size_t)fy * (nx + 1) + kxx;
-      }
+      const float syg = (y <= ny) ? 1.f : -1.f;
       float2* F0 = F + k2 * S2 + c;
       float2* F1 = F0 + CS;
 #pragma unroll
       for (int k1 = 0; k1 < R1; ++k1) {
         const int kz = k2 + R2 * k1;
-        float ax, ay, az, s;
-        if (KIND == 0) {
-          ax = bx0; ay = by0; az = kt2[kz];
-          s = sxy * st2[kz];
-        } else {
-          const int fz = (kz <= nz) ? kz : 2 * nz - kz;
-          const size_t off = (size_t)fz * (ny + 1) * (nx + 1) + offy;
-          ax = kap[off];
-          ay = syg * kap[oct + off];
-          az = (kz <= nz) ? kap[2 * oct + off] : -kap[2 * oct + off];
-          s = 1.f;
-        }
+        const int fz = (kz <= nz) ? kz : 2 * nz - kz;
+        const float4 K = Ks[fz * TC + c];
+        const float ax = K.x, ay = syg * K.y, az = (kz <= nz) ? K.z : -K.z;
         const float2 G0 = F0[k1 * TC], G1 = F1[k1 * TC], G2 = w2[k1];
         const float2 cx = make_float2(ay * G2.x - az * G1.x, ay * G2.y - az * G1.y);
         const float2 cy = make_float2(az * G0.x - ax * G2.x, az * G0.y - ax * G2.y);
         const float2 cz = make_float2(ax * G1.x - ay * G0.x, ax * G1.y - ay * G0.y);
-        F0[k1 * TC] = make_float2(-s * cx.y, s * cx.x);
-        F1[k1 * TC] = make_float2(-s * cy.y, s * cy.x);
-        w2[k1] = make_float2(-s * cz.y, s * cz.x);
-        if ((k1 & 3) == 3) asm volatile("" ::: "memory");  // at most four points' loads in flight
+        F0[k1 * TC] = make_float2(-cx.y, cx.x);
+        F1[k1 * TC] = make_float2(-cy.y, cy.x);
+        w2[k1] = make_float2(-cz.y, cz.x);
       }
     }
     // ---- inverse: y[m1 + R1 m2] = sum_k2 W_R2^{-m2 k2} W_L^{-m1 k2} (sum_k1 X[k2 + R2 k1] W_R1^{-m1 k1}).
@@ -606,11 +604,10 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
         const int y = yc;
         const int fy = (y <= ny) ? y : 2 * ny - y;
         const int fz = (kz <= nz) ? kz : 2 * nz - kz;
-        const size_t oct = (size_t)(nz + 1) * (ny + 1) * (nx + 1);
-        const size_t off = ((size_t)fz * (ny + 1) + fy) * (nx + 1) + kxx;
-        ax = kap[off];
-        ay = (y <= ny) ? kap[oct + off] : -kap[oct + off];
-        az = (kz <= nz) ? kap[2 * oct + off] : -kap[2 * oct + off];
+        const float4 K = kap4[((size_t)fz * (ny + 1) + fy) * (nx + 1) + kxx];
+        ax = K.x;
+        ay = (y <= ny) ? K.y : -K.y;
+        az = (kz <= nz) ? K.z : -K.z;
         s = 1.f;
       }
       const float2 F0 = F[idx], F1 = F[CS + idx], F2 = F[2 * CS + idx];

@@ -60,6 +60,7 @@ struct Work {
   T* Hd[2] = {nullptr, nullptr};  // [3][N] iterates dh^i of Eq. 5
   T* jc = nullptr;       // [N] jc map or nullptr (uniform)
   T* kap = nullptr;      // [3][nz+1][ny+1][nx+1] imaginary part of the kernel spectrum / (8N)
+  float4* kap4 = nullptr; // FP32 only: the same octant interleaved, [nz+1][ny+1][nx+1] x {a=0,1,2, 0}
   T* kt[3] = {nullptr, nullptr, nullptr};  // derivative wavenumbers (0 on Nyquist): nx/2+1, ny, nz
   T* st[3] = {nullptr, nullptr, nullptr};  // Gaussian smoothing factor per axis: nx/2+1, ny, nz
   V* twu[3] = {nullptr, nullptr, nullptr}; // twiddles W_L^m, L = nx, ny, nz
