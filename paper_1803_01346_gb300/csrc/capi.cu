@@ -30,7 +30,12 @@ struct scfft_ctx {
   Work<float> wf;
   Work<double> wd;
   Ctrl* ctrl = nullptr;        // device
+  PointParams* ppd = nullptr;  // device copy of the current rhs's PointParams
   double* partials = nullptr;  // device
+  // FP32 Eq. 5 loop as one CUDA graph: a WHILE conditional node around one iteration
+  cudaGraph_t loop_graph = nullptr;
+  cudaGraphExec_t loop_exec = nullptr;
+  bool loop_failed = false;
   uint8_t* mask = nullptr;     // device
   long long nout = 0;
   bool have_geom = false, have_kernel = false, have_path = false;
@@ -116,6 +121,7 @@ template <typename T> Launch<T> launch_of(scfft_ctx* c) {
   L.ctrl = c->ctrl;
   L.mask = c->mask;
   L.partials = c->partials;
+  L.ppd = c->ppd;
   L.st = c->st;
   return L;
 }
@@ -278,6 +284,89 @@ template <typename T> cudaError_t iteration(scfft_ctx* c, const Launch<T>& L, Po
              [&] { return launch_x<T>(L, X_UPDATE, pp, nullptr, nullptr, nullptr, i & 1, (i + 1) & 1, chk); });
 }
 
+// ---------------------------------------------------------------- Eq. 5 loop as a CUDA graph
+// The FP32 path runs the whole Eq. 5 iteration loop of one rhs as one graph launch: a WHILE
+// conditional node whose body is one iteration (the eight passes) followed by a one-thread
+// kernel that sets the loop condition from the device flags (stop reached, status,
+// iteration cap).  No iteration is queued past convergence and the host takes no part
+// in the loop.  The update pass reads its iteration index and the rhs parameters from
+// device memory, so the captured launches stay valid for every rhs of the context.
+__global__ void loop_cond_kernel(cudaGraphConditionalHandle h, Ctrl* ctrl, int max_iter) {
+  // the trip count bounds the loop by itself, whatever the update pass did
+  const unsigned trips = ++ctrl->trips;
+  const unsigned go =
+      (ctrl->done == 0 && ctrl->status == 0 && ctrl->iters < max_iter && trips < (unsigned)max_iter) ? 1u : 0u;
+  cudaGraphSetConditional(h, go);
+}
+
+constexpr int kLoopLaunches = 9;  // kernels per iteration of the graph body
+
+cudaError_t loop_body(const Launch<float>& L, const PointParams& pp, cudaGraphConditionalHandle h, int max_iter) {
+  cudaError_t e;
+  if ((e = launch_y<float>(L, false, false, false)) != cudaSuccess) return e;
+  if ((e = launch_z_curl<float>(L, false, 1.0 / (double)L.g.N)) != cudaSuccess) return e;
+  if ((e = launch_y<float>(L, false, true, false)) != cudaSuccess) return e;
+  if ((e = launch_x<float>(L, X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, false)) != cudaSuccess) return e;
+  if ((e = launch_y<float>(L, true, false, false)) != cudaSuccess) return e;
+  if ((e = launch_z_kernel<float>(L, false)) != cudaSuccess) return e;
+  if ((e = launch_y<float>(L, true, true, false)) != cudaSuccess) return e;
+  if ((e = launch_x<float>(L, X_UPDATE, pp, nullptr, nullptr, nullptr, 0, 1, false)) != cudaSuccess) return e;
+  loop_cond_kernel<<<1, 1, 0, L.st>>>(h, L.ctrl, max_iter);
+  return cudaGetLastError();
+}
+
+// Build the loop graph once per context; false (and the host-driven loop) if the driver
+// refuses any step.
+bool loop_graph_ready(scfft_ctx* c) {
+  if (c->loop_exec) return true;
+  if (c->loop_failed) return false;
+  c->loop_failed = true;  // until the build succeeds
+  // capture on a private stream: the context's stream may be the legacy default stream,
+  // which cannot be captured; the graph itself is launched on the context's stream
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  Launch<float> L = launch_of<float>(c);
+  L.st = cs;
+  const PointParams pp = base_params(c);
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaGraphConditionalHandle h{};
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphNodeParams np{};
+  cudaGraphNode_t node{};
+  if (ok) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+  }
+  if (ok) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+    if (ok) {
+      const bool launched = loop_body(L, pp, h, c->opt.max_iter) == cudaSuccess;
+      cudaGraph_t captured = nullptr;
+      ok = cudaStreamEndCapture(cs, &captured) == cudaSuccess && launched;
+    }
+  }
+  if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  cudaStreamDestroy(cs);
+  if (!ok) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();  // clear the (non-sticky) error of the refused step; the host-driven loop takes over
+    return false;
+  }
+  c->loop_graph = g;
+  c->loop_exec = ex;
+  c->loop_failed = false;
+  return true;
+}
+
 // Inputs and outputs of one rhs: FP64 arrays (public entry points, the FP64
 // integrator) or FP32 arrays (stages of the FP32 integrator).
 struct RhsIO {
@@ -322,7 +411,14 @@ scfft_status rhs_impl(scfft_ctx* c, double t, int left, const RhsIO& io, int* it
   const int maxit = c->opt.max_iter;
   const bool early = c->opt.delta_it > 0 && c->nout > 0;
   int launched = 0;
-  if (c->nout > 0) {
+  bool graphed = false;
+  if constexpr (sizeof(T) == 4) {
+    if (c->nout > 0 && maxit > 0 && !c->prof_on && loop_graph_ready(c)) {
+      CK(cudaGraphLaunch(c->loop_exec, c->st));
+      graphed = true;
+    }
+  }
+  if (c->nout > 0 && !graphed) {
     // With an early stop the host keeps one iteration queued ahead: before
     // queueing iteration i it waits for the flag copied after iteration i-2.
     // An iteration queued after convergence returns at entry (device flag), so
@@ -359,10 +455,11 @@ scfft_status rhs_impl(scfft_ctx* c, double t, int left, const RhsIO& io, int* it
     CK(run(c, SCFFT_K_FINALIZE, [&] { return launch_finalize<T>(L, io.out64, io.warm_out64); }));
   }
   c->stats.rhs_calls += 1;
-  if (iters_out || early) {
+  if (iters_out || early || graphed) {
     CK(cudaMemcpyAsync(c->hctrl + 2, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     const Ctrl hc = c->hctrl[2];
+    if (graphed) c->stats.launches += (long long)kLoopLaunches * hc.iters;
     c->stats.iterations += hc.iters;
     c->stats.last_iters = hc.iters;
     c->stats.last_residual = hc.residual;
@@ -912,7 +1009,7 @@ scfft_status scfft_create(const scfft_grid* grid, const scfft_material* mat, con
   c->opt = *opt;
   c->st = (cudaStream_t)stream;
   scfft_status s = SCFFT_OK;
-  if (cudaMalloc(&c->ctrl, sizeof(Ctrl)) != cudaSuccess ||
+  if (cudaMalloc(&c->ctrl, sizeof(Ctrl)) != cudaSuccess || cudaMalloc(&c->ppd, sizeof(PointParams)) != cudaSuccess ||
       cudaMalloc(&c->partials, sizeof(double) * (c->g.ny * c->g.nz / 2 + 8)) != cudaSuccess ||
       cudaMalloc(&c->mask, c->g.N) != cudaSuccess || cudaHostAlloc(&c->hctrl, 3 * sizeof(Ctrl), 0) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -938,7 +1035,9 @@ void scfft_destroy(scfft_ctx* c) {
   else cudaDeviceSynchronize();
   free_work(c->wf);
   free_work(c->wd);
-  cudaFree(c->ctrl); cudaFree(c->partials); cudaFree(c->mask); cudaFree(c->ib); cudaFree(c->errbits);
+  if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+  if (c->loop_graph) cudaGraphDestroy(c->loop_graph);
+  cudaFree(c->ctrl); cudaFree(c->ppd); cudaFree(c->partials); cudaFree(c->mask); cudaFree(c->ib); cudaFree(c->errbits);
   cudaFree(c->ib32); cudaFree(c->ynew64); cudaFree(c->adj); cudaFree(c->adj_part);
   if (c->hadj_part) cudaFreeHost(c->hadj_part);
   if (c->hctrl) cudaFreeHost(c->hctrl);

@@ -239,7 +239,9 @@ struct XRArgs {
   const float* jc;
   const float* hold;
   float* hnew;
+  float* hbuf[2];         // both iterate buffers: the update pass picks by the device iteration count
   PointParams pp;
+  PointParams* ppd;       // device copy of pp (written by the assemble pass, read by the update pass)
   Ctrl* ctrl;
   double* partials;
   int check_done;
@@ -361,7 +363,10 @@ cudaError_t launch_x_reg_io(const Launch<float>& L, XMode mode, const PointParam
   a.jc = L.w->jc;
   a.hold = L.w->Hd[in_buf];
   a.hnew = L.w->Hd[out_buf];
+  a.hbuf[0] = L.w->Hd[0];
+  a.hbuf[1] = L.w->Hd[1];
   a.pp = pp;
+  a.ppd = L.ppd;
   a.ctrl = L.ctrl;
   a.partials = L.partials;
   a.check_done = check_done ? 1 : 0;
@@ -687,6 +692,20 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
   constexpr int TT = cmax(cmax(S::C2R ? R2i * (R1i + 1) : 1, S::R2C ? R2o * (R1o + 1) : 1), S::R2C ? Lo : 1);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (a.check_done && a.ctrl->done) return;
+  // The update pass takes the iteration index from the device (Ctrl::iters, advanced by its
+  // own last CTA) and dh_e/dt, the stop threshold and 1/|Omega_out| from the device copy of
+  // the rhs parameters, so the same launch serves every iteration of a captured loop.
+  const float* h_old = a.hold;
+  float* h_new = a.hnew;
+  int it = 0;
+  float hef[3] = {0.f, 0.f, 0.f};
+  if (MODE == X_UPDATE) {
+    it = *reinterpret_cast<volatile const int*>(&a.ctrl->iters);
+    h_old = a.hbuf[it & 1];
+    h_new = a.hbuf[(it + 1) & 1];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) hef[q] = (float)a.ppd->hedot[q];
+  }
   float2* twi = reinterpret_cast<float2*>(smem_raw);
   float2* two = twi + (Li > 0 ? Li : 1);
   float2* RS = two + (Lo > 0 ? Lo : 1);  // [3][P][XL]
@@ -758,7 +777,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
       if (MODE == X_UPDATE)
         for (int i = tid; i < 3 * nrow * rl; i += NT) {
           const int ln = i % rl, rr = (i / rl) % nrow, q = i / (rl * nrow);
-          if (row0 + rr < 2 * npairs) prefetch_l2(a.hold + q * N + nb0 + (size_t)rr * XL + ln * 32);
+          if (row0 + rr < 2 * npairs) prefetch_l2(h_old + q * N + nb0 + (size_t)rr * XL + ln * 32);
         }
       if (MODE == X_ASSEMBLE && a.warm)
         for (int i = tid; i < 3 * nrow * 2 * rl; i += NT) {
@@ -848,8 +867,8 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
           if (MODE == X_UPDATE) {
 #pragma unroll
             for (int q = 0; q < NO; ++q) {
-              ov[j][q][0] = a.hold[q * N + na];
-              ov[j][q][1] = a.hold[q * N + nb];
+              ov[j][q][0] = h_old[q * N + na];
+              ov[j][q][1] = h_old[q * N + nb];
             }
           } else if (MODE == X_ASSEMBLE) {
 #pragma unroll
@@ -885,8 +904,8 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
           for (int q = 0; q < 3; ++q) {
             const float va = ia ? s * u[q].x : ov[j][q][0];
             const float vb = ib ? s * u[q].y : ov[j][q][1];
-            a.hnew[q * N + na] = va;
-            a.hnew[q * N + nb] = vb;
+            h_new[q * N + na] = va;
+            h_new[q * N + nb] = vb;
             u[q] = make_float2(va, vb);
           }
         } else if (MODE == X_MASKPAD) {
@@ -899,11 +918,11 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
   #pragma unroll
           for (int q = 0; q < 3; ++q) {
             const float oa = ov[j][q][0], ob = ov[j][q][1];
-            const float he = (float)pp.hedot[q];
+            const float he = hef[q];
             const float va = ia ? oa : he + u[q].x;
             const float vb = ib ? ob : he + u[q].y;
-            a.hnew[q * N + na] = va;
-            a.hnew[q * N + nb] = vb;
+            h_new[q * N + na] = va;
+            h_new[q * N + nb] = vb;
             const float dda = va - oa, ddb = vb - ob;
             da += dda * dda;
             db += ddb * ddb;
@@ -1001,19 +1020,22 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
       if (tid == 0) {
         double tot = 0.0;
         for (int i = 0; i < (NT + 31) / 32; ++i) tot += red[i];
-        const double rres = tot * a.pp.inv_nout;
+        const double rres = tot * a.ppd->inv_nout;
         Ctrl* c = a.ctrl;
         c->residual = rres;
-        c->iters = a.pp.iter + 1;
-        c->cur = a.out_buf;
+        c->iters = it + 1;
+        c->iter_total += 1;
+        c->cur = (it + 1) & 1;
         const bool finite = isfinite(rres);
         if (!finite) c->status = 6;  // SCFFT_ENONFINITE
-        c->done = (!finite || rres < a.pp.tol) ? 1 : 0;
+        c->done = (!finite || rres < a.ppd->tol) ? 1 : 0;
         c->counter = 0;
       }
     }
   }
   if (MODE == X_ASSEMBLE && blockIdx.x == 0 && tid == 0) {
+    *a.ppd = a.pp;
+    a.ctrl->trips = 0;
     a.ctrl->done = 0;
     a.ctrl->iters = 0;
     a.ctrl->cur = 0;

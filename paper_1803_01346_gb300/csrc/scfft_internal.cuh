@@ -36,11 +36,12 @@ struct Ctrl {
   int cur;            // which iterate buffer (0/1) holds the latest dh/dt
   int status;         // latched device status (scfft_status value)
   unsigned counter;   // arrival counter of the last-CTA reduction
-  unsigned pad_;
+  unsigned trips;     // trips of the graph-captured Eq. 5 loop in the current rhs (its hard bound)
   double residual;    // last Eq. 5 residual
   double err;         // last integrator error norm
   unsigned counter2;  // arrival counter of the error-norm reduction
   unsigned pad2_;
+  unsigned long long iter_total;  // Eq. 5 iterations executed since the context was created
 };
 
 // Grid geometry and strides.
@@ -106,6 +107,7 @@ struct Launch {
   Ctrl* ctrl;          // device
   const uint8_t* mask; // device [N]
   double* partials;    // device, one double per CTA of the x passes
+  PointParams* ppd;    // device copy of the current rhs's PointParams (read by the Eq. 5 update pass)
   cudaStream_t st;
 };
 

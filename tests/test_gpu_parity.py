@@ -179,6 +179,36 @@ def test_rhs_fp32_fixed_iterations_all_x_lengths(n, L):
     assert err < 2e-4, err
 
 
+def test_rhs_fp32_graph_loop_equals_host_loop():
+    """The FP32 Eq. 5 loop runs as one CUDA graph (a WHILE conditional node, one
+    iteration per trip, condition set on the device).  While profiling, the host drives
+    the same kernels one iteration at a time.  Both must give the same dh/dt bit for bit,
+    the same iteration count and the oracle's answer; the graph body counts one extra
+    kernel (the condition) per iteration, which shows that the graph really ran."""
+    n, L = (32, 32, 32), (1.0, 1.0, 1.0)
+    mask = I.lens(n, L, 0.6, 0.5, 0.1, 0.1)
+    ctx, prob = make(n, L, mask, n_power=30.0, rho_out=100.0, prec=S.PREC_F32, delta_it=2e-5, max_iter=50)
+    h = _state(prob, 31)
+    g0 = np.broadcast_to(prob.path.hedot(0.2)[:, None, None, None], h.shape).copy()
+    ref = O.rhs(prob, 0.2, h, g0, delta_it=2e-5, max_iter=50)
+    out = {}
+    for mode in ("host", "graph", "graph_again"):
+        ctx.profile(mode == "host")
+        hd = torch.empty(h.size, dtype=torch.float64, device="cuda")
+        l0 = ctx.stats()["launches"]
+        it = ctx.rhs(0.2, dev(h).reshape(-1), dev(g0).reshape(-1), hd)
+        out[mode] = (it, ctx.stats()["launches"] - l0, host(hd))
+        ctx.profile(False)
+    it_h, l_h, v_h = out["host"]
+    for mode in ("graph", "graph_again"):
+        it_g, l_g, v_g = out[mode]
+        assert it_g == it_h
+        assert l_g - l_h == it_g
+        assert np.array_equal(v_g, v_h)
+    assert abs(it_h - ref.iters) <= 1
+    assert rel(v_h.reshape(h.shape), ref.hdot) < 2e-4
+
+
 def test_rhs_fp32_error_is_stated():
     n, L = (32, 32, 32), (1.0, 1.0, 1.0)
     mask = I.sphere(n, L, 0.6)
