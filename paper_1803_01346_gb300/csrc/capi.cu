@@ -36,6 +36,10 @@ struct scfft_ctx {
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;
   bool loop_failed = false;
+  // FP32 path: Ctrl::iter_total already folded into stats, and whether graph-run rhs calls
+  // of the integrator have not been folded in yet (their statistics are read once per step)
+  unsigned long long iters_seen = 0;
+  bool graph_pending = false;
   uint8_t* mask = nullptr;     // device
   long long nout = 0;
   bool have_geom = false, have_kernel = false, have_path = false;
@@ -394,8 +398,36 @@ cudaError_t x_io(const Launch<T>& L, XMode mode, const PointParams& pp, const Rh
     return launch_x<T>(L, mode, pp, io.h64, nullptr, io.warm64, 0, 0, false);
 }
 
+// FP32 path: fold the device's iteration counter into the host statistics (graph-run
+// iterations also count their kLoopLaunches kernels here).
+void absorb_ctrl(scfft_ctx* c, const Ctrl& hc, bool graph_iters) {
+  const unsigned long long d = hc.iter_total - c->iters_seen;
+  c->iters_seen = hc.iter_total;
+  c->stats.iterations += (long long)d;
+  if (graph_iters) c->stats.launches += (long long)kLoopLaunches * (long long)d;
+  c->stats.last_iters = hc.iters;
+  c->stats.last_residual = hc.residual;
+  c->graph_pending = false;
+}
+
+// Read the device control block (synchronising the stream) and fold in the statistics of
+// graph-run rhs calls that have not been read yet; returns the latched device status.
+scfft_status flush_pending(scfft_ctx* c) {
+  if (!c->graph_pending) return SCFFT_OK;
+  CK(cudaMemcpyAsync(c->hctrl + 2, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  const Ctrl hc = c->hctrl[2];
+  absorb_ctrl(c, hc, true);
+  return (scfft_status)hc.status;
+}
+
+// defer (the FP32 integrator's stages): when the loop runs as a graph and the caller wants
+// no iteration count, return without reading the device state back; the step reads it once.
 template <typename T>
-scfft_status rhs_impl(scfft_ctx* c, double t, int left, const RhsIO& io, int* iters_out) {
+scfft_status rhs_impl(scfft_ctx* c, double t, int left, const RhsIO& io, int* iters_out, bool defer = false) {
+  if constexpr (sizeof(T) == 4) {
+    if (c->graph_pending && !(defer && !iters_out && !c->prof_on)) CS_(flush_pending(c));
+  }
   Launch<T> L = launch_of<T>(c);
   PointParams pp = base_params(c);
   hedot_at(c, t, left, pp.hedot);
@@ -455,14 +487,21 @@ scfft_status rhs_impl(scfft_ctx* c, double t, int left, const RhsIO& io, int* it
     CK(run(c, SCFFT_K_FINALIZE, [&] { return launch_finalize<T>(L, io.out64, io.warm_out64); }));
   }
   c->stats.rhs_calls += 1;
+  if (graphed && defer && !iters_out) {
+    c->graph_pending = true;
+    return SCFFT_OK;
+  }
   if (iters_out || early || graphed) {
     CK(cudaMemcpyAsync(c->hctrl + 2, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     const Ctrl hc = c->hctrl[2];
-    if (graphed) c->stats.launches += (long long)kLoopLaunches * hc.iters;
-    c->stats.iterations += hc.iters;
-    c->stats.last_iters = hc.iters;
-    c->stats.last_residual = hc.residual;
+    if constexpr (sizeof(T) == 4) {
+      absorb_ctrl(c, hc, graphed);
+    } else {
+      c->stats.iterations += hc.iters;
+      c->stats.last_iters = hc.iters;
+      c->stats.last_residual = hc.residual;
+    }
     if (iters_out) *iters_out = hc.iters;
     if (hc.status != 0) return (scfft_status)hc.status;
     if (iters_out && c->nout > 0 && maxit > 0 && !(hc.residual < pp.tol) && c->opt.delta_it > 0)
@@ -470,6 +509,7 @@ scfft_status rhs_impl(scfft_ctx* c, double t, int left, const RhsIO& io, int* it
   } else {
     c->stats.iterations += launched;
     c->stats.last_iters = launched;
+    if constexpr (sizeof(T) == 4) c->iters_seen += (unsigned long long)launched;  // no early stop: all ran
   }
   return SCFFT_OK;
 }
@@ -738,7 +778,7 @@ scfft_status rhs32(scfft_ctx* c, double t, int left, const double* h64, const fl
   io.h32 = h32;
   io.warm32 = warm32;
   io.out32 = out;
-  scfft_status s = rhs_impl<float>(c, t, left, io, nullptr);
+  scfft_status s = rhs_impl<float>(c, t, left, io, nullptr, true);
   c->last32 = out;
   return s;
 }
@@ -804,6 +844,13 @@ scfft_status bs23_step_f32(scfft_ctx* c, double* t_io, double* dt_io, double tst
         return cudaGetLastError();
       }));
       CK(cudaMemcpyAsync(c->herr, c->errbits, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+      if (c->graph_pending) {
+        const scfft_status ds = flush_pending(c);  // synchronises the stream
+        if (ds != SCFFT_OK) {
+          c->fsal_valid = false;
+          return ds;
+        }
+      }
       CK(cudaStreamSynchronize(c->st));
       unsigned bits;
       memcpy(&bits, c->herr, sizeof(unsigned));
@@ -813,6 +860,13 @@ scfft_status bs23_step_f32(scfft_ctx* c, double* t_io, double* dt_io, double tst
       if (!(en == en)) {
         c->fsal_valid = false;
         return SCFFT_ENONFINITE;
+      }
+    }
+    if (c->graph_pending) {  // fixed step: no error norm was read, read the device state here
+      const scfft_status ds = flush_pending(c);
+      if (ds != SCFFT_OK) {
+        c->fsal_valid = false;
+        return ds;
       }
     }
     if (en <= 1.0) {
@@ -1427,6 +1481,7 @@ scfft_status scfft_sync(scfft_ctx* c) {
 
 scfft_status scfft_get_stats(scfft_ctx* c, scfft_stats* out) {
   if (!c || !out) return SCFFT_EINVAL;
+  if (flush_pending(c) == SCFFT_ECUDA) return SCFFT_ECUDA;  // a latched device status is the next step's to report
   *out = c->stats;
   return SCFFT_OK;
 }
