@@ -47,7 +47,7 @@ template <typename T, int R1, int R2, int TC, bool INV, bool PIN, bool POUT>
 __global__ void __launch_bounds__(TC * R1) ypass_reg_kernel(typename cplx_of<T>::type* __restrict__ base, int rows,
                                                             int sx, int HX, int nzs,
                                                             const typename cplx_of<T>::type* __restrict__ twg,
-                                                            const Ctrl* ctrl, int check_done) {
+                                                            const Ctrl* ctrl, int check_done, int ahead) {
   typedef typename cplx_of<T>::type V;
   constexpr int L = R1 * R2;
   constexpr int S2 = R1 * TC + kPad8;  // transpose row stride
@@ -61,6 +61,17 @@ __global__ void __launch_bounds__(TC * R1) ypass_reg_kernel(typename cplx_of<T>:
   const int cz = blockIdx.z, z = blockIdx.y, kx = blockIdx.x * TC + c;
   const bool colok = kx < HX;
   V* col = base + ((size_t)(cz * nzs + z) * rows) * sx + kx;
+  if (ahead > 0) {  // prefetch into L2 the input columns of the CTA one wave of resident CTAs later
+    const int gx = gridDim.x, gy = gridDim.y;
+    const int nb = blockIdx.x + gx * (blockIdx.y + gy * blockIdx.z) + ahead;
+    if (nb < gx * gy * (int)gridDim.z) {
+      const int bx = nb % gx, zz = (nb / gx) % gy, cc = nb / (gx * gy);
+      const V* ncol = base + ((size_t)(cc * nzs + zz) * rows) * sx + bx * TC;
+      constexpr int NR = PIN ? L / 2 : L;
+      const int last = (bx * TC + TC <= HX ? TC : HX - bx * TC) - 1;
+      for (int i = t; i < 2 * NR; i += TC * R1) prefetch_l2(ncol + (size_t)(i >> 1) * sx + ((i & 1) ? last : 0));
+    }
+  }
   V v[R2];
 #pragma unroll
   for (int n2 = 0; n2 < R2; ++n2) {
@@ -104,14 +115,24 @@ __global__ void zpass_reg2_kernel(float2* __restrict__ base, int rows, int sx, i
 // ---------------------------------------------------------------- launchers
 namespace {
 
-template <int R1, int R2, int TC, bool INV, bool PIN, bool POUT>
+// PF: prefetch the next wave's input columns into L2 (measured faster on the padded passes,
+// slower on the unpadded ones, which also run narrower CTAs)
+template <int R1, int R2, int TC, bool INV, bool PIN, bool POUT, bool PF>
 cudaError_t go_y(const Launch<float>& L, float2* base, int rows, int sx, int HX, const float2* tw, bool chk) {
   constexpr int Lt = R1 * R2;
   const size_t smem = sizeof(float2) * (Lt + R2 * (R1 * TC + kPad8));
   auto k = ypass_reg_kernel<float, R1, R2, TC, INV, PIN, POUT>;
   allow_smem<ypass_reg_kernel<float, R1, R2, TC, INV, PIN, POUT>>();
   dim3 grid((HX + TC - 1) / TC, L.g.nz, 3);
-  k<<<grid, TC * R1, smem, L.st>>>(base, rows, sx, HX, L.g.nz, tw, L.ctrl, chk ? 1 : 0);
+  static const int resident = [&] {  // CTAs resident at once: the prefetch distance
+    if (!PF) return 0;
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, TC * R1, smem);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return per_sm > 0 && sms > 0 ? per_sm * sms : 0;
+  }();
+  k<<<grid, TC * R1, smem, L.st>>>(base, rows, sx, HX, L.g.nz, tw, L.ctrl, chk ? 1 : 0, resident);
   return cudaGetLastError();
 }
 
@@ -161,25 +182,25 @@ template <template <int, int> class F, typename... A> cudaError_t by_length(int 
 template <int R1, int R2> struct YFwdU {
   static cudaError_t run(const Launch<float>& L, bool chk) {
     const Geo& g = L.g;
-    return go_y<R1, R2, 16, false, false, false>(L, L.w->U, g.ny, g.sxu, g.nx / 2 + 1, L.w->twu[1], chk);
+    return go_y<R1, R2, 8, false, false, false, false>(L, L.w->U, g.ny, g.sxu, g.nx / 2 + 1, L.w->twu[1], chk);
   }
 };
 template <int R1, int R2> struct YInvU {
   static cudaError_t run(const Launch<float>& L, bool chk) {
     const Geo& g = L.g;
-    return go_y<R1, R2, 16, true, false, false>(L, L.w->U, g.ny, g.sxu, g.nx / 2 + 1, L.w->twu[1], chk);
+    return go_y<R1, R2, 8, true, false, false, false>(L, L.w->U, g.ny, g.sxu, g.nx / 2 + 1, L.w->twu[1], chk);
   }
 };
 template <int R1, int R2> struct YFwdP {
   static cudaError_t run(const Launch<float>& L, bool chk) {
     const Geo& g = L.g;
-    return go_y<R1, R2, 16, false, true, false>(L, L.w->Pd, 2 * g.ny, g.sxp, g.nx + 1, L.w->twp[1], chk);
+    return go_y<R1, R2, 16, false, true, false, true>(L, L.w->Pd, 2 * g.ny, g.sxp, g.nx + 1, L.w->twp[1], chk);
   }
 };
 template <int R1, int R2> struct YInvP {
   static cudaError_t run(const Launch<float>& L, bool chk) {
     const Geo& g = L.g;
-    return go_y<R1, R2, 16, true, false, true>(L, L.w->Pd, 2 * g.ny, g.sxp, g.nx + 1, L.w->twp[1], chk);
+    return go_y<R1, R2, 16, true, false, true, true>(L, L.w->Pd, 2 * g.ny, g.sxp, g.nx + 1, L.w->twp[1], chk);
   }
 };
 template <int R1, int R2> struct ZCurl {
