@@ -241,11 +241,16 @@ template <typename T> scfft_status alloc_work(scfft_ctx* c) {
       CK(cudaMemcpy(*dst, tw.data(), sizeof(V) * Lt, cudaMemcpyHostToDevice));
     }
   }
+  // FP32: descriptors for the TMA-fed y passes (without them the y passes load directly)
+  if constexpr (sizeof(T) == 4) {
+    if (!make_ymaps(w, g)) w.ym = nullptr;
+  }
   return SCFFT_OK;
 }
 
 template <typename T> void free_work(Work<T>& w) {
   cudaFree(w.U); cudaFree(w.Pd); cudaFree(w.Hd[0]); cudaFree(w.Hd[1]); cudaFree(w.jc); cudaFree(w.kap); cudaFree(w.kap4);
+  delete w.ym;
   for (int a = 0; a < 3; ++a) { cudaFree(w.kt[a]); cudaFree(w.st[a]); cudaFree(w.twu[a]); cudaFree(w.twp[a]); }
   w = Work<T>();
 }

@@ -219,6 +219,10 @@ template <int R1, int R2> struct ZKern {
 }  // namespace
 
 cudaError_t launch_y_reg(const Launch<float>& L, bool padded, bool inverse, bool check_done) {
+  if (L.w->ym) {
+    const cudaError_t e = launch_y_tma(L, padded, inverse, check_done);
+    if (e != cudaErrorNotSupported) return e;
+  }
   const int Ly = padded ? 2 * L.g.ny : L.g.ny;
   if (!padded) return inverse ? by_length<YInvU>(Ly, L, check_done) : by_length<YFwdU>(Ly, L, check_done);
   return inverse ? by_length<YInvP>(Ly, L, check_done) : by_length<YFwdP>(Ly, L, check_done);

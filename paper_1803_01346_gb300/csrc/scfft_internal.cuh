@@ -1,6 +1,7 @@
 // scfft_internal.cuh - device workspaces, control block and pass launchers
 // shared by the translation units of the library.
 #pragma once
+#include <cuda.h>  // CUtensorMap (types only; the encoder is fetched through the runtime)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -52,6 +53,12 @@ struct Geo {
   long long N;    // nx*ny*nz
 };
 
+// TMA descriptors of the FP32 padded y passes: the padded half spectrum Pd as read by the
+// forward pass (its first ny rows) and by the inverse pass (all 2ny rows).
+struct YMaps {
+  CUtensorMap m[2];
+};
+
 // Device workspaces of one FFT precision T.
 template <typename T>
 struct Work {
@@ -66,6 +73,7 @@ struct Work {
   T* st[3] = {nullptr, nullptr, nullptr};  // Gaussian smoothing factor per axis: nx/2+1, ny, nz
   V* twu[3] = {nullptr, nullptr, nullptr}; // twiddles W_L^m, L = nx, ny, nz
   V* twp[3] = {nullptr, nullptr, nullptr}; // twiddles, L = 2nx, 2ny, 2nz
+  YMaps* ym = nullptr;   // FP32 only: TMA descriptors of the y passes (nullptr: plain-load y passes)
 };
 
 enum XMode : int {
@@ -125,6 +133,10 @@ template <typename T> cudaError_t launch_convert(const double* src, T* dst, long
 
 // Register-resident FP32 y and z passes (passes_reg.cu); the FP32 path uses these.
 cudaError_t launch_y_reg(const Launch<float>& L, bool padded, bool inverse, bool check_done);
+// TMA-fed y passes (ypass_tma.cu): descriptors built once per workspace; the launcher returns
+// cudaErrorNotSupported when there are none or the length has no instantiation.
+bool make_ymaps(Work<float>& w, const Geo& g);
+cudaError_t launch_y_tma(const Launch<float>& L, bool padded, bool inverse, bool check_done);
 cudaError_t launch_z_reg(const Launch<float>& L, bool padded, bool check_done, double scale);
 cudaError_t launch_x_reg(const Launch<float>& L, XMode mode, const PointParams& pp, const double* src_f64,
                          double* dst_f64, const double* warm, int in_buf, int out_buf, bool check_done);
