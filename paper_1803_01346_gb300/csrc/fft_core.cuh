@@ -153,6 +153,66 @@ template <bool INV, typename V> struct DFT<16, INV, V> {
   static __device__ __forceinline__ void run(V* v) { dft_split<4, 4, INV, V>(v); }
 };
 
+// ---------------------------------------------------------------- half-zero inputs
+// DFTh<R>: the same transform when v[R/2 .. R-1] are zero (zero-padded data), without the
+// additions of those zeros.  R = P * 4 splits as in dft_split, and with n = P n2 + n1 the
+// zero inputs are exactly n2 >= 2 of every first-stage 4-point transform.
+template <int R, bool INV, typename V> struct DFTh;
+
+template <bool INV, typename V> struct DFTh<2, INV, V> {
+  static __device__ __forceinline__ void run(V* v) { v[1] = v[0]; }
+};
+
+template <bool INV, typename V> struct DFTh<4, INV, V> {
+  static __device__ __forceinline__ void run(V* v) {
+    const V a = v[0], b = v[1], ib = mul_mi<INV>(v[1]);
+    v[0] = a + b;
+    v[2] = a - b;
+    v[1] = a + ib;
+    v[3] = a - ib;
+  }
+};
+
+template <int P, bool INV, typename V>
+__device__ __forceinline__ void dft_split_h(V* v) {
+  constexpr int Q = 4, R = P * Q;
+  V y[R];
+#pragma unroll
+  for (int n1 = 0; n1 < P; ++n1) {
+    V t[Q];
+#pragma unroll
+    for (int n2 = 0; n2 < Q / 2; ++n2) t[n2] = v[P * n2 + n1];
+    DFTh<Q, INV, V>::run(t);
+#pragma unroll
+    for (int k1 = 0; k1 < Q; ++k1) y[n1 * Q + k1] = (n1 * k1 == 0) ? t[k1] : twiddle_const<V, R, INV>(t[k1], n1 * k1);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < Q; ++k1) {
+    V t[P];
+#pragma unroll
+    for (int n1 = 0; n1 < P; ++n1) t[n1] = y[n1 * Q + k1];
+    DFT<P, INV, V>::run(t);
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) v[k1 + Q * k2] = t[k2];
+  }
+}
+
+template <bool INV, typename V> struct DFTh<8, INV, V> {
+  static __device__ __forceinline__ void run(V* v) { dft_split_h<2, INV, V>(v); }
+};
+template <bool INV, typename V> struct DFTh<12, INV, V> {
+  static __device__ __forceinline__ void run(V* v) { dft_split_h<3, INV, V>(v); }
+};
+template <bool INV, typename V> struct DFTh<16, INV, V> {
+  static __device__ __forceinline__ void run(V* v) { dft_split_h<4, INV, V>(v); }
+};
+
+// DFT of v, whose upper half is known to be zero when HALF is set
+template <int R, bool INV, bool HALF, typename V> __device__ __forceinline__ void dft_maybe_half(V* v) {
+  if constexpr (HALF) DFTh<R, INV, V>::run(v);
+  else DFT<R, INV, V>::run(v);
+}
+
 // ---------------------------------------------------------------- plans
 struct FftPlan {
   int L;       // transform length

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(TC * R1) ypass_reg_kernel(typename cplx_of<T>:
     }
   }
   __syncthreads();  // twiddles staged
-  DFT<R2, INV, V>::run(v);
+  dft_maybe_half<R2, INV, PIN>(v);
 #pragma unroll
   for (int k2 = 1; k2 < R2; ++k2) v[k2] = tw_mul(v[k2], tw[n1 * k2], INV);
 #pragma unroll
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
       float2 v[R2];
 #pragma unroll
       for (int n2 = 0; n2 < R2; ++n2) v[n2] = n2 < NL ? pre[q][n2] : make_float2(0.f, 0.f);
-      DFT<R2, false, float2>::run(v);
+      dft_maybe_half<R2, false, PR>(v);
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) Fq[k2 * S2 + n1 * TC + c] = k2 == 0 ? v[0] : cmul(v[k2], twr[k2]);
       if (q == 2) cp_async_wait_all();  // Ks complete, visible to all after the barrier
@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 3 : 1) zpas
       float2 v[R2];
 #pragma unroll
       for (int n2 = 0; n2 < R2; ++n2) v[n2] = n2 < NL ? pre[q][n2] : make_float2(0.f, 0.f);
-      DFT<R2, false, float2>::run(v);
+      dft_maybe_half<R2, false, PR>(v);
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) Fq[k2 * S2 + n1 * TC + c] = k2 == 0 ? v[0] : cmul(v[k2], twr[k2]);
       __syncthreads();
@@ -980,7 +980,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
             const int x = n1 + R1o * n2;
             u[n2] = (x < XL) ? RS[(q * P + p) * XL + x] : make_float2(0.f, 0.f);
           }
-          DFT<R2o, false, float2>::run(u);
+          dft_maybe_half<R2o, false, S::PADOUT>(u);
   #pragma unroll
           for (int k2 = 0; k2 < R2o; ++k2) Tp[k2 * (R1o + 1) + n1] = k2 == 0 ? u[0] : cmul(u[k2], two[n1 * k2]);
         }

@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(TC * R1) ypass_tma_kernel(const __grid_constan
     const int kx = chunk * TC + c;
     const bool colok = kx < HX;
     float2* col = base + (size_t)plane * rows * sx + kx;
-    DFT<R2, INV, float2>::run(v);
+    dft_maybe_half<R2, INV, PIN>(v);
 #pragma unroll
     for (int k2 = 1; k2 < R2; ++k2) v[k2] = INV ? cmulc(v[k2], tw[n1 * k2]) : cmul(v[k2], tw[n1 * k2]);
 #pragma unroll
