@@ -44,7 +44,7 @@ UNIT = "voxel-RHS evals/s"
 REF_ITERS_PER_RHS = 3.3
 # DRAM bytes (read + write) per launch from the committed ncu capture
 # profiles/ncu_zpass_xupdate_lens128_fp32.md; an entry is removed when its kernel changes.
-NCU_TRAFFIC = {"z_kernel": 163764480 + 59649024, "x_update": 85066240 + 7949056}
+NCU_TRAFFIC = {"z_kernel": 163647232 + 59601920, "x_update": 85051392 + 8236544}
 
 
 def _peaks():
