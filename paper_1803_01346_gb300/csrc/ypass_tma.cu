@@ -6,8 +6,9 @@
 // Here the CTAs are persistent and a tile's input reaches shared memory as one
 // cp.async.bulk.tensor copy (a box of TC columns x the rows the transform reads), issued two
 // tiles ahead into a pair of stage buffers and completed on an mbarrier, so each SM always has
-// loads in flight while it transforms and stores the current tile.  Columns past the half
-// spectrum's last kx lie outside the tensor map and arrive as zeros.  Every wait on an
+// loads in flight while it transforms and stores the current tile.  A stage buffer whose input
+// is in registers also holds the tile's transpose, so no third buffer is needed.  Columns past
+// the half spectrum's last kx lie outside the tensor map and arrive as zeros.  Every wait on an
 // mbarrier is bounded; a wait that gives up latches SCFFT_ETIMEOUT in the device control
 // block, drains the other stage's copy (bounded again) and ends the CTA.
 #include "scfft.h"
@@ -61,9 +62,11 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 template <int R1, int R2, int TC, bool PIN> struct YT {
   static constexpr int L = R1 * R2;
   static constexpr int NRB = PIN ? L / 2 : L;     // rows in the box (the forward padded pass reads L/2)
-  static constexpr int SB = NRB * TC;             // complex elements per stage buffer
+  static constexpr int SB = NRB * TC;             // complex elements a box brings
   static constexpr int S2 = R1 * TC + kPadT;      // transpose row stride
-  static constexpr size_t smem = 128 + sizeof(float2) * (2 * SB + L + R2 * S2);
+  // a stage buffer also holds the tile's transpose once its input is in registers
+  static constexpr int SBX = ((SB > R2 * S2 ? SB : R2 * S2) + 15) / 16 * 16;
+  static constexpr size_t smem = 128 + sizeof(float2) * (2 * SBX + L);
 };
 
 // grid: persistent (at most one wave); block TC*R1 threads; tiles t = chunk + nch * plane.
@@ -73,13 +76,12 @@ __global__ void __launch_bounds__(TC * R1) ypass_tma_kernel(const __grid_constan
                                                             int nzs, const float2* __restrict__ twg, Ctrl* ctrl,
                                                             int check_done) {
   typedef YT<R1, R2, TC, PIN> S;
-  constexpr int L = S::L, SB = S::SB, S2 = S::S2, NT = TC * R1;
+  constexpr int L = S::L, SB = S::SB, SBX = S::SBX, S2 = S::S2, NT = TC * R1;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   if (check_done && ctrl->done) return;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw);         // [2]
-  float2* stage = reinterpret_cast<float2*>(smem_raw + 128);      // [2][SB], 128-byte aligned
-  float2* tw = stage + 2 * SB;                                    // [L]
-  float2* sm = tw + L;                                            // [R2][S2]
+  float2* stage = reinterpret_cast<float2*>(smem_raw + 128);      // [2][SBX], 128-byte aligned
+  float2* tw = stage + 2 * SBX;                                   // [L]
   const int t = threadIdx.x, c = t % TC, n1 = t / TC;
   const int nch = (HX + TC - 1) / TC, ntiles = nch * 3 * nzs;
   const unsigned bytes = (unsigned)(SB * sizeof(float2));
@@ -96,7 +98,7 @@ __global__ void __launch_bounds__(TC * R1) ypass_tma_kernel(const __grid_constan
       const int tile = blockIdx.x + s * gridDim.x;
       if (tile < ntiles) {
         mbar_expect_tx(&mbar[s], bytes);
-        tma_load_3d(stage + s * SB, &tmap, (tile % nch) * TC, 0, tile / nch, &mbar[s]);
+        tma_load_3d(stage + s * SBX, &tmap, (tile % nch) * TC, 0, tile / nch, &mbar[s]);
       }
     }
   }
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(TC * R1) ypass_tma_kernel(const __grid_constan
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
     const int s = it & 1;
     const bool timed_out = !mbar_wait_bounded(&mbar[s], (it >> 1) & 1);
-    const float2* st = stage + s * SB;
+    float2* st = stage + s * SBX;
     float2 v[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2)
@@ -117,14 +119,6 @@ __global__ void __launch_bounds__(TC * R1) ypass_tma_kernel(const __grid_constan
       }
       return;
     }
-    if (t == 0) {  // refill stage s two tiles ahead
-      const int nt = tile + 2 * (int)gridDim.x;
-      if (nt < ntiles) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&mbar[s], bytes);
-        tma_load_3d(stage + s * SB, &tmap, (nt % nch) * TC, 0, nt / nch, &mbar[s]);
-      }
-    }
     const int chunk = tile % nch, plane = tile / nch;
     const int kx = chunk * TC + c;
     const bool colok = kx < HX;
@@ -133,13 +127,13 @@ __global__ void __launch_bounds__(TC * R1) ypass_tma_kernel(const __grid_constan
 #pragma unroll
     for (int k2 = 1; k2 < R2; ++k2) v[k2] = INV ? cmulc(v[k2], tw[n1 * k2]) : cmul(v[k2], tw[n1 * k2]);
 #pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) sm[k2 * S2 + n1 * TC + c] = v[k2];
+    for (int k2 = 0; k2 < R2; ++k2) st[k2 * S2 + n1 * TC + c] = v[k2];  // transpose in the consumed stage
     __syncthreads();
     if (n1 < R2) {
       const int k2 = n1;
       float2 w[R1];
 #pragma unroll
-      for (int m = 0; m < R1; ++m) w[m] = sm[k2 * S2 + m * TC + c];
+      for (int m = 0; m < R1; ++m) w[m] = st[k2 * S2 + m * TC + c];
       DFT<R1, INV, float2>::run(w);
       if (colok) {
 #pragma unroll
@@ -147,6 +141,15 @@ __global__ void __launch_bounds__(TC * R1) ypass_tma_kernel(const __grid_constan
           if (POUT && k1 >= R1 / 2) continue;
           col[(size_t)(k2 + R2 * k1) * sx] = w[k1];
         }
+      }
+    }
+    __syncthreads();  // stage s is free: refill it two tiles ahead
+    if (t == 0) {
+      const int nt = tile + 2 * (int)gridDim.x;
+      if (nt < ntiles) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&mbar[s], bytes);
+        tma_load_3d(stage + s * SBX, &tmap, (nt % nch) * TC, 0, nt / nch, &mbar[s]);
       }
     }
   }
