@@ -56,6 +56,19 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def aggregate_ranks(ms: float, units: float, ws: int, device: str):
+    """Whole-job figures of a multi-rank run: the slowest rank's time and the units all
+    ranks processed (each rank runs its own replica).  Single rank: unchanged."""
+    if ws <= 1:
+        return ms, units
+    import torch
+    import torch.distributed as dist
+    tm = torch.tensor([ms, units], dtype=torch.float64, device=device)
+    dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
+    dist.all_reduce(tm[1:2], op=dist.ReduceOp.SUM)
+    return float(tm[0]), float(tm[1])
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -360,14 +373,7 @@ def bench_ours(args, ws, rank, local):
     iters = s1["iterations"] - s0["iterations"]
     launches = s1["launches"] - s0["launches"]
     units = float(N * rhs_calls)
-    t_max = ms
-    if ws > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms, units], dtype=torch.float64, device="cuda")
-        tm = tt.clone()
-        dist.all_reduce(tm[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tm[1:2], op=dist.ReduceOp.SUM)
-        t_max, units = float(tm[0]), float(tm[1])
+    t_max, units = aggregate_ranks(ms, units, ws, "cuda")
     value = units / (t_max * 1e-3)
 
     # ---- per-pass profile over the same number of steps (separate pass, events around each launch)
