@@ -42,7 +42,7 @@ typedef enum {
   SCFFT_ENOCONV = 4,   /* Eq. 5 iteration stopped at max_iter (result still written) */
   SCFFT_ESTEP = 5,     /* integrator step size fell below its floor */
   SCFFT_ENONFINITE = 6,/* NaN/Inf met in a residual or error norm */
-  SCFFT_ETIMEOUT = 7,  /* reserved: a bounded device wait gave up */
+  SCFFT_ETIMEOUT = 7,  /* a bounded device wait gave up (latched; see scfft_inject_fault) */
   SCFFT_ESTATE = 8,    /* call out of order (e.g. rhs before precompute_kernel) */
   SCFFT_ESIZE = 9      /* problem larger than a fixed, preallocated maximum */
 } scfft_status;
@@ -257,6 +257,18 @@ scfft_status scfft_curl_noalloc(const scfft_grid* grid, double sigma_scale, cons
 
 /* Wait for the stream; returns the first latched device-side status. */
 scfft_status scfft_sync(scfft_ctx* ctx);
+
+/* Fault injection for tests of the device-side timeout path; the paper has no counterpart.
+ * kind = SCFFT_FAULT_TMA_WAIT arms a one-shot fault for an FP32 context: the next TMA-fed
+ * padded y pass launched directly by the library (scfft_phi, or an rhs while profiling; not
+ * the Eq. 5 loop graph, whose launches were captured before) makes the first stage buffer of
+ * every CTA expect 16 bytes more than its copy brings, so that bounded wait gives up after
+ * about a second.  The pass then latches SCFFT_ETIMEOUT in the context (scfft_sync and later
+ * calls return it) and its output is not valid; no trap is raised, and the GPU and the other
+ * contexts stay usable.  kind = 0 disarms.  Returns SCFFT_EINVAL for an unknown kind or an
+ * FP64 context. */
+#define SCFFT_FAULT_TMA_WAIT 1
+scfft_status scfft_inject_fault(scfft_ctx* ctx, int kind);
 
 /* Counters since create (host copy). */
 scfft_status scfft_get_stats(scfft_ctx* ctx, scfft_stats* out);

@@ -18,10 +18,12 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-__all__ = ["ScfftError", "Context", "load_library", "library_path", "PREC_F64", "PREC_F32", "EXPORTS"]
+__all__ = ["ScfftError", "Context", "load_library", "library_path", "PREC_F64", "PREC_F32", "FAULT_TMA_WAIT",
+           "EXPORTS"]
 
 PREC_F64 = 0
 PREC_F32 = 1
+FAULT_TMA_WAIT = 1  # scfft_inject_fault: the next directly launched TMA-fed y pass times out (tests)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBNAME = "libscfft.so"
@@ -31,7 +33,7 @@ EXPORTS = ("scfft_create", "scfft_set_geometry", "scfft_set_jc_map", "scfft_set_
            "scfft_precompute_kernel", "scfft_rhs", "scfft_curl", "scfft_phi", "scfft_integrate",
            "scfft_step", "scfft_profile", "scfft_profile_read", "scfft_kind_name",
            "scfft_rhs_vjp", "scfft_adjoint_integrate", "scfft_batch_step", "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy",
-           "scfft_curl_noalloc", "scfft_last_cuda_error")
+           "scfft_curl_noalloc", "scfft_last_cuda_error", "scfft_inject_fault")
 
 NKINDS = 14
 
@@ -113,6 +115,7 @@ def load_library(path: Optional[str] = None):
         "scfft_curl_noalloc": (I, [ctypes.POINTER(_Grid), D, P, P, P]),
         "scfft_rhs_vjp": (I, [P, P, P, P, P, P, ctypes.POINTER(D)]),
         "scfft_last_cuda_error": (ctypes.c_char_p, []),
+        "scfft_inject_fault": (I, [P, I]),
         "scfft_adjoint_integrate": (I, [P, D, P, I, P, P, P, P, P, ctypes.POINTER(D), I]),
         "scfft_batch_step": (I, [P, I, P, P, P, P, P, P]),
     }
@@ -273,6 +276,11 @@ class Context:
 
     def sync(self):
         self._check(self._lib.scfft_sync(self._h), "scfft_sync")
+
+    def inject_fault(self, kind: int):
+        """Arm (kind = FAULT_TMA_WAIT) or disarm (0) the one-shot timeout fault; for tests of
+        the device-side timeout path only."""
+        self._check(self._lib.scfft_inject_fault(self._h, int(kind)), "scfft_inject_fault")
 
     def stats(self):
         st = _Stats()

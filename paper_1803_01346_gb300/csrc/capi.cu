@@ -36,6 +36,7 @@ struct scfft_ctx {
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;
   bool loop_failed = false;
+  int fault = 0;  // armed fault injection (scfft_inject_fault)
   // FP32 path: Ctrl::iter_total already folded into stats, and whether graph-run rhs calls
   // of the integrator have not been folded in yet (their statistics are read once per step)
   unsigned long long iters_seen = 0;
@@ -126,6 +127,7 @@ template <typename T> Launch<T> launch_of(scfft_ctx* c) {
   L.mask = c->mask;
   L.partials = c->partials;
   L.ppd = c->ppd;
+  L.fault = &c->fault;
   L.st = c->st;
   return L;
 }
@@ -339,6 +341,7 @@ bool loop_graph_ready(scfft_ctx* c) {
   }
   Launch<float> L = launch_of<float>(c);
   L.st = cs;
+  L.fault = nullptr;  // a fault is never captured into the loop graph
   const PointParams pp = base_params(c);
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ex = nullptr;
@@ -1482,6 +1485,13 @@ scfft_status scfft_sync(scfft_ctx* c) {
   CK(cudaStreamSynchronize(c->st));
   CK(cudaMemcpy(c->hctrl + 2, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
   return (scfft_status)c->hctrl[2].status;
+}
+
+scfft_status scfft_inject_fault(scfft_ctx* c, int kind) {
+  if (!c || (kind != 0 && kind != SCFFT_FAULT_TMA_WAIT)) return SCFFT_EINVAL;
+  if (kind != 0 && c->opt.precision != SCFFT_PREC_F32) return SCFFT_EINVAL;
+  c->fault = kind;
+  return SCFFT_OK;
 }
 
 scfft_status scfft_get_stats(scfft_ctx* c, scfft_stats* out) {

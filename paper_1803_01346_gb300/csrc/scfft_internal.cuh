@@ -115,7 +115,8 @@ struct Launch {
   Ctrl* ctrl;          // device
   const uint8_t* mask; // device [N]
   double* partials;    // device, one double per CTA of the x passes
-  PointParams* ppd;    // device copy of the current rhs's PointParams (read by the Eq. 5 update pass)
+  PointParams* ppd = nullptr;  // device copy of the current rhs's PointParams (read by the Eq. 5 update pass)
+  int* fault = nullptr;        // host: armed one-shot fault injection (scfft_inject_fault), or nullptr
   cudaStream_t st;
 };
 

@@ -74,7 +74,7 @@ template <int R1, int R2, int TC, bool INV, bool PIN, bool POUT>
 __global__ void __launch_bounds__(TC * R1) ypass_tma_kernel(const __grid_constant__ CUtensorMap tmap,
                                                             float2* __restrict__ base, int rows, int sx, int HX,
                                                             int nzs, const float2* __restrict__ twg, Ctrl* ctrl,
-                                                            int check_done) {
+                                                            int check_done, int inject) {
   typedef YT<R1, R2, TC, PIN> S;
   constexpr int L = S::L, SB = S::SB, SBX = S::SBX, S2 = S::S2, NT = TC * R1;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(TC * R1) ypass_tma_kernel(const __grid_constan
     for (int s = 0; s < 2; ++s) {
       const int tile = blockIdx.x + s * gridDim.x;
       if (tile < ntiles) {
-        mbar_expect_tx(&mbar[s], bytes);
+        // (inject: a test of the timeout path; stage 0 then waits for 16 bytes that never come)
+        mbar_expect_tx(&mbar[s], bytes + (s == 0 && inject ? 16u : 0u));
         tma_load_3d(stage + s * SBX, &tmap, (tile % nch) * TC, 0, tile / nch, &mbar[s]);
       }
     }
@@ -171,7 +172,9 @@ cudaError_t go_y_tma(const Launch<float>& L, const CUtensorMap& map, float2* bas
     return per_sm > 0 && sms > 0 ? per_sm * sms : 152;
   }();
   const int grid = ntiles < resident ? ntiles : resident;
-  k<<<grid, TC * R1, S::smem, L.st>>>(map, base, rows, sx, HX, L.g.nz, tw, L.ctrl, chk ? 1 : 0);
+  const int inject = (L.fault && *L.fault == SCFFT_FAULT_TMA_WAIT) ? 1 : 0;
+  if (inject) *L.fault = 0;  // one shot
+  k<<<grid, TC * R1, S::smem, L.st>>>(map, base, rows, sx, HX, L.g.nz, tw, L.ctrl, chk ? 1 : 0, inject);
   return cudaGetLastError();
 }
 
