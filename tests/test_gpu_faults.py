@@ -64,3 +64,71 @@ def test_inject_fault_rejects_unknown_kinds_and_fp64_contexts():
         ctx64.inject_fault(S.FAULT_TMA_WAIT)
     assert e.value.code == 1
     ctx64.inject_fault(0)  # disarming is always accepted
+
+
+def _state(n, L, seed, scale=0.05):
+    return torch.from_numpy(I.random_field((3,) + tuple(n[::-1]), seed, scale).ravel().copy()).cuda()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", [S.PREC_F64, S.PREC_F32])
+def test_nan_in_the_state_latches_enonfinite(prec):
+    n, L = (16, 16, 16), (1.0, 1.0, 1.0)
+    ctx = S.Context(n, L, precision=prec, delta_it=2e-5, max_iter=20)
+    ctx.set_geometry(I.cube(n, L, 1.0))
+    ctx.set_field_path([0.0, 1.0], [[0, 0, 0], [0, 0, 0.5]])
+    ctx.precompute_kernel()
+    h = _state(n, L, 3)
+    h[123] = float("nan")
+    warm = torch.zeros_like(h)
+    out = torch.empty_like(h)
+    with pytest.raises(S.ScfftError) as e:
+        ctx.rhs(0.2, h, warm, out)
+    assert e.value.code == 6
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", [S.PREC_F64, S.PREC_F32])
+def test_iteration_cap_reports_enoconv_with_the_result_written(prec):
+    import ctypes
+    n, L = (16, 16, 16), (1.0, 1.0, 1.0)
+    ctx = S.Context(n, L, n_power=20.0, rho_out=20.0, precision=prec, delta_it=1e-12, max_iter=1)
+    ctx.set_geometry(I.cube(n, L, 1.0))
+    ctx.set_field_path([0.0, 1.0], [[0, 0, 0], [0, 0, 0.5]])
+    ctx.precompute_kernel()
+    h = _state(n, L, 4)
+    warm = torch.zeros_like(h)
+    out = torch.full_like(h, float("nan"))
+    it = ctypes.c_int(0)
+    code = ctx._lib.scfft_rhs(ctx._h, 0.2, 0, ctypes.c_void_p(h.data_ptr()), ctypes.c_void_p(warm.data_ptr()),
+                              ctypes.c_void_p(out.data_ptr()), ctypes.byref(it))
+    torch.cuda.synchronize()
+    assert code == 4 and it.value == 1
+    assert bool(torch.isfinite(out).all())
+
+
+@pytest.mark.gpu
+def test_step_size_floor_reports_estep():
+    n, L = (16, 16, 16), (1.0, 1.0, 1.0)
+    ctx = S.Context(n, L, delta_it=2e-5, max_iter=20)
+    ctx.set_geometry(I.cube(n, L, 1.0))
+    ctx.set_field_path([0.0, 1.0], [[0, 0, 0], [0, 0, 0.5]])
+    ctx.precompute_kernel()
+    h = torch.zeros(3 * 16 ** 3, dtype=torch.float64, device="cuda")
+    warm = torch.zeros_like(h)
+    with pytest.raises(S.ScfftError) as e:
+        ctx.step(0.0, 1e-20, 1.0, h, warm)
+    assert e.value.code == 5
+
+
+@pytest.mark.gpu
+def test_calls_out_of_order_and_bad_sizes_are_rejected_on_the_host():
+    n, L = (16, 16, 16), (1.0, 1.0, 1.0)
+    ctx = S.Context(n, L)
+    h = torch.zeros(3 * 16 ** 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(S.ScfftError) as e:  # no geometry, kernel or field path yet
+        ctx.rhs(0.0, h, torch.zeros_like(h), torch.empty_like(h))
+    assert e.value.code == 8
+    with pytest.raises(S.ScfftError) as e:  # 20 is not a supported grid size
+        S.Context((20, 16, 16), L)
+    assert e.value.code == 1
