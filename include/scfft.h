@@ -166,6 +166,29 @@ scfft_status scfft_integrate(scfft_ctx* ctx, double t0, double t1, double dt0, i
 scfft_status scfft_step(scfft_ctx* ctx, double* t, double* dt, double tstop, double* h, double* warm,
                         int* rejected);
 
+/* Checkpoint and resume of a trajectory stepped with scfft_step (the method of lines of §2,
+ * "ode23"; the paper itself does not describe checkpoints).  A checkpoint holds the time t and
+ * proposed step dt, the state h and the Eq. 5 warm start (FP64), and the integrator state the
+ * next step would reuse: the first-stage derivative (FSAL; FP64, or FP32 on the FP32 path) and,
+ * on the FP32 path, the compensation terms of the accepted-state sums.  Resuming from it
+ * continues the trajectory with the same results, bit for bit, as the uninterrupted run.
+ *
+ * scfft_checkpoint_save: h, warm: device, 3*N doubles, the buffers the trajectory was stepped
+ * on (the FSAL stage is saved when the context's last accepted step was taken on them and ended
+ * at t; otherwise the resumed step recomputes it, as the uninterrupted run would).  buf: host,
+ * caller-owned; with buf = NULL only *size is set to the bytes needed; otherwise *size gives
+ * buf's capacity (SCFFT_EINVAL if too small) and returns the bytes written.  Synchronises the
+ * context's stream.
+ *
+ * scfft_checkpoint_load: buf/size as written by save for a context of the same grid and
+ * precision (SCFFT_EINVAL otherwise).  Writes *t, *dt, and h, warm (device, 3*N doubles,
+ * caller-owned); the next scfft_step(ctx, t, dt, .., h, warm, ..) continues the saved
+ * trajectory.  Synchronous. */
+scfft_status scfft_checkpoint_save(scfft_ctx* ctx, double t, double dt, const double* h, const double* warm,
+                                   void* buf, size_t* size);
+scfft_status scfft_checkpoint_load(scfft_ctx* ctx, const void* buf, size_t size, double* t, double* dt, double* h,
+                                   double* warm);
+
 /* Per-pass profiling: when enabled, every kernel the library launches is
  * bracketed by CUDA events on the context's stream and its elapsed time is
  * added to the counter of its pass kind.  Enabling resets the counters.

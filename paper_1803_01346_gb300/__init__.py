@@ -33,7 +33,8 @@ EXPORTS = ("scfft_create", "scfft_set_geometry", "scfft_set_jc_map", "scfft_set_
            "scfft_precompute_kernel", "scfft_rhs", "scfft_curl", "scfft_phi", "scfft_integrate",
            "scfft_step", "scfft_profile", "scfft_profile_read", "scfft_kind_name",
            "scfft_rhs_vjp", "scfft_adjoint_integrate", "scfft_batch_step", "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy",
-           "scfft_curl_noalloc", "scfft_last_cuda_error", "scfft_inject_fault")
+           "scfft_curl_noalloc", "scfft_last_cuda_error", "scfft_inject_fault", "scfft_checkpoint_save",
+           "scfft_checkpoint_load")
 
 NKINDS = 14
 
@@ -116,6 +117,8 @@ def load_library(path: Optional[str] = None):
         "scfft_rhs_vjp": (I, [P, P, P, P, P, P, ctypes.POINTER(D)]),
         "scfft_last_cuda_error": (ctypes.c_char_p, []),
         "scfft_inject_fault": (I, [P, I]),
+        "scfft_checkpoint_save": (I, [P, D, D, P, P, P, ctypes.POINTER(ctypes.c_size_t)]),
+        "scfft_checkpoint_load": (I, [P, P, ctypes.c_size_t, ctypes.POINTER(D), ctypes.POINTER(D), P, P]),
         "scfft_adjoint_integrate": (I, [P, D, P, I, P, P, P, P, P, ctypes.POINTER(D), I]),
         "scfft_batch_step": (I, [P, I, P, P, P, P, P, P]),
     }
@@ -276,6 +279,24 @@ class Context:
 
     def sync(self):
         self._check(self._lib.scfft_sync(self._h), "scfft_sync")
+
+    def checkpoint_save(self, t: float, dt: float, h, warm) -> bytes:
+        """Snapshot of the trajectory at (t, dt) on the device buffers h, warm (see scfft.h)."""
+        n = ctypes.c_size_t(0)
+        self._check(self._lib.scfft_checkpoint_save(self._h, float(t), float(dt), _ptr(h), _ptr(warm), None,
+                                                    ctypes.byref(n)), "scfft_checkpoint_save")
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(self._lib.scfft_checkpoint_save(self._h, float(t), float(dt), _ptr(h), _ptr(warm), buf,
+                                                    ctypes.byref(n)), "scfft_checkpoint_save")
+        return buf.raw[:n.value]
+
+    def checkpoint_load(self, data: bytes, h, warm):
+        """Restore a snapshot into h, warm (device) and this context; returns (t, dt)."""
+        t, dt = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        buf = ctypes.create_string_buffer(data, len(data))
+        self._check(self._lib.scfft_checkpoint_load(self._h, buf, len(data), ctypes.byref(t), ctypes.byref(dt),
+                                                    _ptr(h), _ptr(warm)), "scfft_checkpoint_load")
+        return t.value, dt.value
 
     def inject_fault(self, kind: int):
         """Arm (kind = FAULT_TMA_WAIT) or disarm (0) the one-shot timeout fault; for tests of

@@ -1212,6 +1212,104 @@ scfft_status scfft_step(scfft_ctx* c, double* t, double* dt, double tstop, doubl
   return step_any(c, t, dt, tstop, h, warm, 0.0, rejected);
 }
 
+// ---------------------------------------------------------------- checkpoint / resume
+namespace {
+struct CkptHeader {
+  char magic[8];  // "SCFFTCK1"
+  int nx, ny, nz, precision;
+  int fsal, pad_;
+  double t, dt;
+};
+
+size_t ckpt_bytes(const scfft_ctx* c) {
+  const size_t n3 = 3 * (size_t)c->g.N;
+  const bool f32 = c->opt.precision == SCFFT_PREC_F32;
+  // header, h, warm, FSAL stage, FP32-path compensation
+  return sizeof(CkptHeader) + 2 * n3 * sizeof(double) + n3 * (f32 ? sizeof(float) : sizeof(double)) +
+         (f32 ? n3 * sizeof(double) : 0);
+}
+}  // namespace
+
+scfft_status scfft_checkpoint_save(scfft_ctx* c, double t, double dt, const double* h, const double* warm, void* buf,
+                                   size_t* size) {
+  if (!c || !size) return SCFFT_EINVAL;
+  const size_t need = ckpt_bytes(c);
+  if (!buf) {
+    *size = need;
+    return SCFFT_OK;
+  }
+  if (!h || !warm || *size < need) return SCFFT_EINVAL;
+  const bool f32 = c->opt.precision == SCFFT_PREC_F32;
+  const size_t n3 = 3 * (size_t)c->g.N;
+  CK(cudaStreamSynchronize(c->st));
+  CkptHeader hd{};
+  memcpy(hd.magic, "SCFFTCK1", 8);
+  hd.nx = c->g.nx;
+  hd.ny = c->g.ny;
+  hd.nz = c->g.nz;
+  hd.precision = c->opt.precision;
+  hd.fsal = (c->fsal_valid && c->fsal_t == t && c->fsal_h == h && c->fsal_g == warm) ? 1 : 0;
+  hd.t = t;
+  hd.dt = dt;
+  char* p = static_cast<char*>(buf);
+  memcpy(p, &hd, sizeof(hd));
+  p += sizeof(hd);
+  CK(cudaMemcpy(p, h, n3 * sizeof(double), cudaMemcpyDeviceToHost));
+  p += n3 * sizeof(double);
+  CK(cudaMemcpy(p, warm, n3 * sizeof(double), cudaMemcpyDeviceToHost));
+  p += n3 * sizeof(double);
+  const size_t stage_bytes = n3 * (f32 ? sizeof(float) : sizeof(double));
+  if (hd.fsal) {
+    CK(cudaMemcpy(p, f32 ? (const void*)c->k32[0] : (const void*)c->k[0], stage_bytes, cudaMemcpyDeviceToHost));
+    if (f32) CK(cudaMemcpy(p + stage_bytes, c->comp64, n3 * sizeof(double), cudaMemcpyDeviceToHost));
+  } else {
+    memset(p, 0, stage_bytes + (f32 ? n3 * sizeof(double) : 0));
+  }
+  *size = need;
+  return SCFFT_OK;
+}
+
+scfft_status scfft_checkpoint_load(scfft_ctx* c, const void* buf, size_t size, double* t, double* dt, double* h,
+                                   double* warm) {
+  if (!c || !buf || !t || !dt || !h || !warm) return SCFFT_EINVAL;
+  if (size < ckpt_bytes(c)) return SCFFT_EINVAL;
+  CkptHeader hd;
+  memcpy(&hd, buf, sizeof(hd));
+  if (memcmp(hd.magic, "SCFFTCK1", 8) != 0 || hd.nx != c->g.nx || hd.ny != c->g.ny || hd.nz != c->g.nz ||
+      hd.precision != c->opt.precision)
+    return SCFFT_EINVAL;
+  const bool f32 = c->opt.precision == SCFFT_PREC_F32;
+  const size_t n3 = 3 * (size_t)c->g.N;
+  CK(cudaStreamSynchronize(c->st));
+  const char* p = static_cast<const char*>(buf) + sizeof(hd);
+  CK(cudaMemcpy(h, p, n3 * sizeof(double), cudaMemcpyHostToDevice));
+  p += n3 * sizeof(double);
+  CK(cudaMemcpy(warm, p, n3 * sizeof(double), cudaMemcpyHostToDevice));
+  p += n3 * sizeof(double);
+  c->fsal_valid = false;
+  if (hd.fsal) {
+    const size_t stage_bytes = n3 * (f32 ? sizeof(float) : sizeof(double));
+    if (f32) {
+      CS_(ensure_rk32(c));
+      CK(cudaMemcpy(c->k32[0], p, stage_bytes, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(c->comp64, p + stage_bytes, n3 * sizeof(double), cudaMemcpyHostToDevice));
+      c->last32 = c->k32[0];
+    } else {
+      CS_(ensure_rk(c));
+      CK(cudaMemcpy(c->k[0], p, stage_bytes, cudaMemcpyHostToDevice));
+    }
+    c->fsal_valid = true;
+    c->fsal_t = hd.t;
+    c->fsal_h = h;
+    c->fsal_g = warm;
+  }
+  *t = hd.t;
+  *dt = hd.dt;
+  c->stats.t = hd.t;
+  c->stats.dt = hd.dt;
+  return SCFFT_OK;
+}
+
 scfft_status scfft_integrate(scfft_ctx* c, double t0, double t1, double dt0, int nsnap, const double* tsnap, double* h,
                              double* snaps, double* warm, const double* dt_fixed, int nfixed, scfft_stats* stats) {
   if (!c || !h || !(t1 > t0) || !(dt0 > 0) || nsnap < 0 || (nsnap > 0 && (!tsnap || !snaps))) return SCFFT_EINVAL;
