@@ -132,3 +132,10 @@ def test_calls_out_of_order_and_bad_sizes_are_rejected_on_the_host():
     with pytest.raises(S.ScfftError) as e:  # 20 is not a supported grid size
         S.Context((20, 16, 16), L)
     assert e.value.code == 1
+    # corrupt geometry: a superconducting node within two cells of a face, or none at all
+    near_face = I.cube(n, L, 1.0)
+    near_face[1, 8, 8] = True
+    for bad in (near_face, np.zeros_like(near_face)):
+        with pytest.raises(S.ScfftError) as e:
+            ctx.set_geometry(bad)
+        assert e.value.code == 1
