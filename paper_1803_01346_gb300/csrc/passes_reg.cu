@@ -849,17 +849,29 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
         __syncthreads();
       }
     } else {
-      // real f64 rows into RS
-      for (int idx = tid; idx < 3 * P * XL; idx += NT) {
-        const int x = idx % XL, pp2 = (idx / XL) % P, q = idx / (XL * P);
-        const int g2 = tile * P + pp2;
-        float2 zv = make_float2(0.f, 0.f);
-        if (g2 < npairs) {
-          const size_t na = (size_t)(2 * g2) * XL + x;
-          zv = a.src_f32 ? make_float2(a.src_f32[q * N + na], a.src_f32[q * N + na + XL])
-                         : make_float2((float)a.src_f64[q * N + na], (float)a.src_f64[q * N + na + XL]);
+      // real rows into RS, in unrolled batches of RB loads per thread (the loads of a batch
+      // are in flight together; a plain loop would wait for each before its shared store)
+      constexpr int JT = (3 * P * XL + NT - 1) / NT, RB = 8;
+#pragma unroll 1
+      for (int j0 = 0; j0 < JT; j0 += RB) {
+        float2 zb[RB];
+#pragma unroll
+        for (int jj = 0; jj < RB; ++jj) {
+          const int idx = tid + (j0 + jj) * NT;
+          const int x = idx % XL, pp2 = (idx / XL) % P, q = idx / (XL * P);
+          const int g2 = tile * P + pp2;
+          zb[jj] = make_float2(0.f, 0.f);
+          if (j0 + jj < JT && idx < 3 * P * XL && g2 < npairs) {
+            const size_t na = (size_t)(2 * g2) * XL + x;
+            zb[jj] = a.src_f32 ? make_float2(a.src_f32[q * N + na], a.src_f32[q * N + na + XL])
+                               : make_float2((float)a.src_f64[q * N + na], (float)a.src_f64[q * N + na + XL]);
+          }
         }
-        RS[(q * P + pp2) * XL + x] = zv;
+#pragma unroll
+        for (int jj = 0; jj < RB; ++jj) {
+          const int idx = tid + (j0 + jj) * NT;
+          if (j0 + jj < JT && idx < 3 * P * XL) RS[idx] = zb[jj];  // RS[(q P + pair) XL + x]
+        }
       }
       __syncthreads();
     }
