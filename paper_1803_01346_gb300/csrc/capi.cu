@@ -725,6 +725,17 @@ __global__ void candidate32_kernel(double* __restrict__ ynew, float* __restrict_
   }
 }
 
+// |v| as a float from the high word of the double alone (exponent re-biased, the top 20
+// mantissa bits kept, so relative error below 2^-20; 0 below the float range, inf above):
+// integer work instead of an FP64-to-FP32 conversion, for the error norm's weights only.
+__device__ __forceinline__ float abs_f32_of(double v) {
+  const int hi = __double2hiint(v);
+  const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
+  if (e <= 0) return 0.f;
+  if (e >= 255) return __int_as_float(0x7f800000);
+  return __int_as_float((e << 23) | ((hi & 0xfffff) << 3));
+}
+
 // max_i |h sum_j e_j k_j| / max(rtol |y|, rtol |ynew|, atol), FP32; nonnegative
 // float bit patterns order like the floats, so an integer max combines them
 __global__ void errnorm32_kernel(const double* __restrict__ y, const double* __restrict__ yn, float h, float e1,
@@ -734,7 +745,7 @@ __global__ void errnorm32_kernel(const double* __restrict__ y, const double* __r
   float m = 0.f;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float e = h * (e1 * k1[i] + e2 * k2[i] + e3 * k3[i] + e4 * k4[i]);
-    const float w = fmaxf(fmaxf(rtol * fabsf((float)y[i]), rtol * fabsf((float)yn[i])), atol);
+    const float w = fmaxf(rtol * fmaxf(abs_f32_of(y[i]), abs_f32_of(yn[i])), atol);
     const float r = fabsf(e) / w;
     m = (r > m || r != r) ? r : m;
   }
@@ -745,25 +756,23 @@ __global__ void errnorm32_kernel(const double* __restrict__ y, const double* __r
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
-// accept: y <- y + d with Kahan compensation c
+// accept: y <- y + d with Kahan compensation c; and the caller's FP64 warm start <- the
+// latest rhs result (FP32)
 __global__ void accept32_kernel(double* __restrict__ y, double* __restrict__ c, const float* __restrict__ d,
-                                long long n) {
+                                const float* __restrict__ last, double* __restrict__ warm, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double yi = y[i];
     const double u = (double)d[i] - c[i];
     const double t = yi + u;
     c[i] = (t - yi) - u;
     y[i] = t;
+    warm[i] = (double)last[i];
   }
 }
 
 __global__ void f64_to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
-}
-__global__ void f32_to_f64_kernel(const float* __restrict__ a, double* __restrict__ b, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    b[i] = (double)a[i];
 }
 
 scfft_status ensure_rk32(scfft_ctx* c) {
@@ -879,13 +888,9 @@ scfft_status bs23_step_f32(scfft_ctx* c, double* t_io, double* dt_io, double tst
     }
     if (en <= 1.0) {
       const double tn = hits ? nxt : t + hs;
+      // the accepted state, and the caller's warm start (FP64) following the most recent rhs result
       CK(run(c, SCFFT_K_RK, [&] {
-        accept32_kernel<<<blocks, 256, 0, c->st>>>(h, c->comp64, c->d32, n3);
-        return cudaGetLastError();
-      }));
-      // the caller's warm start (FP64) follows the most recent rhs result
-      CK(run(c, SCFFT_K_RK, [&] {
-        f32_to_f64_kernel<<<blocks, 256, 0, c->st>>>(c->last32, warm, n3);
+        accept32_kernel<<<blocks, 256, 0, c->st>>>(h, c->comp64, c->d32, c->last32, warm, n3);
         return cudaGetLastError();
       }));
       c->stats.accepted += 1;
