@@ -746,7 +746,12 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
   const int npairs = ny * nz / 2;
   const int ntiles = (npairs + P - 1) / P;
   float partf = 0.f;
-  // persistent CTAs: each walks tiles of P row pairs with a stride of the grid
+  static_assert(XL % TP == 0 && 32 % TP == 0, "a row pair's nodes split evenly over its lanes, inside one warp");
+  __syncthreads();  // twiddle tables
+  // persistent CTAs: each walks tiles of P row pairs with a stride of the grid.  Inside a tile
+  // every shared-memory exchange stays within one row pair, whose TP lanes lie in one warp, so
+  // the tile needs warp barriers only and the warps of a CTA run independently of each other.
+  // Lane r of pair p owns the nodes x = r + TP j of both rows in the node-wise step.
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     // prefetch the next tile's first-phase rows into L2 while this tile runs
     if (tile + (int)gridDim.x < ntiles) {
@@ -815,7 +820,6 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
     }
 
     if constexpr (S::C2R) {
-      __syncthreads();  // twiddles
       for (int q = 0; q < 3; ++q) {
         const int n1 = r;
         if (n1 < R1i) {
@@ -836,7 +840,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
   #pragma unroll
           for (int k2 = 0; k2 < R2i; ++k2) Tp[k2 * (R1i + 1) + n1] = k2 == 0 ? v[0] : cmulc(v[k2], twi[n1 * k2]);
         }
-        __syncthreads();
+        __syncwarp();
         const int k2 = r;
         if (k2 < R2i) {
           float2 w[R1i];
@@ -846,34 +850,33 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
   #pragma unroll
           for (int k1 = 0; k1 < S::KX; ++k1) RS[(q * P + p) * XL + k2 + R2i * k1] = w[k1];
         }
-        __syncthreads();
+        __syncwarp();
       }
     } else {
-      // real rows into RS, in unrolled batches of RB loads per thread (the loads of a batch
-      // are in flight together; a plain loop would wait for each before its shared store)
-      constexpr int JT = (3 * P * XL + NT - 1) / NT, RB = 8;
+      // real rows of this lane's pair into RS, in unrolled batches of RB loads per thread (the
+      // loads of a batch are in flight together; a plain loop would wait for each before its
+      // shared store)
+      constexpr int JT = 3 * (XL / TP), RB = 8;
 #pragma unroll 1
       for (int j0 = 0; j0 < JT; j0 += RB) {
         float2 zb[RB];
 #pragma unroll
         for (int jj = 0; jj < RB; ++jj) {
-          const int idx = tid + (j0 + jj) * NT;
-          const int x = idx % XL, pp2 = (idx / XL) % P, q = idx / (XL * P);
-          const int g2 = tile * P + pp2;
+          const int j = j0 + jj, q = j / (XL / TP), x = r + TP * (j - q * (XL / TP));
           zb[jj] = make_float2(0.f, 0.f);
-          if (j0 + jj < JT && idx < 3 * P * XL && g2 < npairs) {
-            const size_t na = (size_t)(2 * g2) * XL + x;
+          if (j < JT && pok) {
+            const size_t na = (size_t)qa * XL + x;
             zb[jj] = a.src_f32 ? make_float2(a.src_f32[q * N + na], a.src_f32[q * N + na + XL])
                                : make_float2((float)a.src_f64[q * N + na], (float)a.src_f64[q * N + na + XL]);
           }
         }
 #pragma unroll
         for (int jj = 0; jj < RB; ++jj) {
-          const int idx = tid + (j0 + jj) * NT;
-          if (j0 + jj < JT && idx < 3 * P * XL) RS[idx] = zb[jj];  // RS[(q P + pair) XL + x]
+          const int j = j0 + jj, q = j / (XL / TP), x = r + TP * (j - q * (XL / TP));
+          if (j < JT) RS[(q * P + p) * XL + x] = zb[jj];
         }
       }
-      __syncthreads();
+      __syncwarp();
     }
 
     // ---- node-wise step.  All of a thread's node-wise global reads are issued first, in
@@ -881,18 +884,16 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
     // arithmetic and stores follow.
     if constexpr (S::C2R) {
       const PointParams& pp = a.pp;
-      constexpr int J = (P * XL + NT - 1) / NT;  // node pairs per thread
+      constexpr int J = XL / TP;  // node pairs per thread: x = r + TP j of the lane's own row pair
       constexpr bool MASKED = MODE == X_POWERLAW || MODE == X_ASSEMBLE || MODE == X_MASKPAD || MODE == X_UPDATE;
       constexpr int NO = MODE == X_UPDATE || MODE == X_ASSEMBLE ? 3 : (MODE == X_POWERLAW ? 1 : 0);
       bool mk[J][2];
       float ov[J][NO > 0 ? NO : 1][2];  // hold (update), warm start (assemble), jc (power law)
 #pragma unroll
       for (int j = 0; j < J; ++j) {
-        const int idx = tid + j * NT;
-        const int x = idx % XL, pp2 = idx / XL;
-        const int g2 = tile * P + pp2;
-        const bool ok = idx < P * XL && g2 < npairs;
-        const size_t na = (size_t)(2 * g2) * XL + x, nb = na + XL;
+        const int x = r + TP * j;
+        const bool ok = pok;
+        const size_t na = (size_t)qa * XL + x, nb = na + XL;
         mk[j][0] = mk[j][1] = false;
 #pragma unroll
         for (int q = 0; q < (NO > 0 ? NO : 1); ++q) ov[j][q][0] = ov[j][q][1] = 0.f;
@@ -921,11 +922,9 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
       }
 #pragma unroll
       for (int j = 0; j < J; ++j) {
-        const int idx = tid + j * NT;
-        const int x = idx % XL, pp2 = idx / XL;
-        const int g2 = tile * P + pp2;
-        if (!(idx < P * XL && g2 < npairs)) continue;
-        const size_t na = (size_t)(2 * g2) * XL + x, nb = na + XL;
+        const int x = r + TP * j, pp2 = p;
+        if (!pok) continue;
+        const size_t na = (size_t)qa * XL + x, nb = na + XL;
         const bool ia = mk[j][0], ib = mk[j][1];
         float2 u[3];
   #pragma unroll
@@ -979,7 +978,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
           for (int q = 0; q < 3; ++q) RS[(q * P + pp2) * XL + x] = u[q];
         }
       }
-      __syncthreads();
+      __syncwarp();
     }
 
     if constexpr (S::R2C) {
@@ -996,7 +995,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
   #pragma unroll
           for (int k2 = 0; k2 < R2o; ++k2) Tp[k2 * (R1o + 1) + n1] = k2 == 0 ? u[0] : cmul(u[k2], two[n1 * k2]);
         }
-        __syncthreads();
+        __syncwarp();
         const int k2 = r;
         float2 Zr[R1o];
         if (k2 < R2o) {
@@ -1024,10 +1023,10 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
             rb[k] = make_float2(0.5f * (Zk.y + Zm.y), 0.5f * (Zm.x - Zk.x));
           }
         }
-        __syncthreads();  // the next component's stage A' overwrites Tp
+        __syncwarp();  // the next component's stage A' overwrites Tp
       }
     }
-    __syncthreads();  // shared buffers are reused by the next tile
+    __syncwarp();  // the pair's shared buffers are reused by the next tile
   }
 
   if (MODE == X_UPDATE) {
