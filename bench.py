@@ -44,7 +44,7 @@ UNIT = "voxel-RHS evals/s"
 REF_ITERS_PER_RHS = 3.3
 # DRAM bytes (read + write) per launch from the committed ncu capture
 # profiles/ncu_zpass_xupdate_lens128_fp32.md; an entry is removed when its kernel changes.
-NCU_TRAFFIC = {"x_update": 84680704 + 8591104}
+NCU_TRAFFIC = {"z_kernel": 165935360 + 58314752, "x_update": 84680704 + 8591104}
 
 
 def _peaks():
