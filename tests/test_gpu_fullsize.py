@@ -1,0 +1,101 @@
+"""Full-size parity: the 128^3 lens workload that bench.py times (256^3 padded
+transforms), through the same C-ABI calls and launch configuration -- the FP32
+register passes at their full grids, and the Eq. 5 loop as one CUDA graph --
+against the FP64 oracle on every output node.
+
+The oracle needs a few seconds of host time per Eq. 5 iteration at this size, so
+the module builds its state and reference values once: five Eq. 5 iterations.
+
+Tolerance: 2e-4 of the largest oracle magnitude, the FP32 path's stated bound
+(FP32 FFT round-off of about 1e-6 amplified by the power law's exponent n = 30).
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import scfft_inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1803_01346_gb300 as S  # noqa: E402
+from paper_1803_01346_gb300 import build as B  # noqa: E402
+
+T = 0.4            # inside the field ramp: dh_e/dt = (0, 0, 1)
+ITERS = 5
+TOL32 = 2e-4
+
+
+@pytest.fixture(scope="module")
+def lens():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.build()
+    cfg = I.config("lens128")
+    g = O.Grid(cfg.n, cfg.L)
+    prob = O.Problem(g, cfg.mask, O.Material(n=cfg.n_power, rho_out=cfg.rho_out),
+                     O.FieldPath(cfg.knots_t, cfg.knots_he))
+    prob.kernel()
+    # a smooth state: a uniform field plus the field of a random current in the lens,
+    # scaled so that the largest |curl h| in the lens is 1.2 jc (the steep part of Eq. 1)
+    P = O.phi_hockney(O.curl_s(I.random_field((3,) + g.shape, 41, 0.3), g) * prob.mask[None], g)
+    jP = np.sqrt(np.sum(O.curl_s(P, g) ** 2, axis=0))[prob.mask].max()
+    h = np.array([0.05, -0.02, 0.1])[:, None, None, None] + (1.2 / jP) * P
+    g0 = np.broadcast_to(prob.path.hedot(T)[:, None, None, None], h.shape).copy()
+    ref = O.rhs(prob, T, h, g0, delta_it=0.0, max_iter=ITERS)
+    return cfg, prob, h, g0, ref
+
+
+def _ctx(cfg, delta_it, max_iter):
+    ctx = S.Context(cfg.n, cfg.L, n_power=cfg.n_power, rho_out=cfg.rho_out, precision=S.PREC_F32,
+                    delta_it=delta_it, max_iter=max_iter, rtol=cfg.rtol, atol=cfg.atol)
+    ctx.set_geometry(cfg.mask)
+    ctx.set_field_path(cfg.knots_t, cfg.knots_he)
+    ctx.precompute_kernel()
+    return ctx
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda().reshape(-1)
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def test_rhs_fp32_lens128_fixed_iterations_matches_oracle(lens):
+    """Five Eq. 5 iterations, no early stop: every pass of the right-hand side at
+    the benchmark's grid against the oracle's same five iterations."""
+    cfg, prob, h, g0, ref = lens
+    assert ref.iters == ITERS
+    ctx = _ctx(cfg, 0.0, ITERS)
+    out = torch.empty(h.size, dtype=torch.float64, device="cuda")
+    it = ctx.rhs(T, _dev(h), _dev(g0), out)
+    torch.cuda.synchronize()
+    assert it == ITERS
+    err = _rel(out.cpu().numpy().reshape(h.shape), ref.hdot)
+    assert err < TOL32, err
+
+
+def test_rhs_fp32_lens128_graph_loop_stops_with_the_oracle(lens):
+    """The Eq. 5 loop as the benchmark runs it (one CUDA graph, the stop decided on
+    the device), with the stop threshold set between the oracle's residuals after
+    iterations ITERS - 1 and ITERS (geometric mean): the device loop must stop after
+    exactly ITERS iterations, with the oracle's residual and dh/dt."""
+    cfg, prob, h, g0, ref = lens
+    r = ref.residuals
+    assert r[ITERS - 2] > 1.5 * r[ITERS - 1], r  # the threshold has room on both sides
+    hed = float(np.linalg.norm(prob.path.hedot(T)))
+    delta_it = float(np.sqrt(r[ITERS - 2] * r[ITERS - 1])) / max(hed, 1.0)
+    ctx = _ctx(cfg, delta_it, 4 * ITERS)
+    out = torch.empty(h.size, dtype=torch.float64, device="cuda")
+    it = ctx.rhs(T, _dev(h), _dev(g0), out)
+    torch.cuda.synchronize()
+    assert it == ITERS, (it, r)
+    # the residual is a mean of FP32 differences of two consecutive iterates, about
+    # 1/50000 of the largest |dh/dt| here: FP32 round-off shows at the 1e-3 level
+    st = ctx.stats()
+    assert abs(st["last_residual"] - r[-1]) < 5e-2 * r[-1], (st["last_residual"], r[-1])
+    err = _rel(out.cpu().numpy().reshape(h.shape), ref.hdot)
+    assert err < TOL32, err
