@@ -110,7 +110,7 @@ __global__ void zpass_reg2_kernel(float2* __restrict__ base, int rows, int sx, i
                                   const float* __restrict__ kt1, const float* __restrict__ kt2,
                                   const float* __restrict__ st0, const float* __restrict__ st1,
                                   const float* __restrict__ st2, float scale, const float4* __restrict__ kap4, int nx,
-                                  int ny, int nz, const Ctrl* ctrl, int check_done, int ahead);
+                                  int ny, int nz, const Ctrl* ctrl, int check_done);
 
 // ---------------------------------------------------------------- launchers
 namespace {
@@ -150,17 +150,9 @@ cudaError_t go_z(const Launch<float>& L, float2* base, int rows, int sx, int HX,
   constexpr bool PACK = (R1 == R2 && KIND == 1);  // as in the kernel's column map
   const int nfull = HX / TC, rem = HX - nfull * TC;
   const dim3 grid = PACK ? dim3(nfull * rows + (rows * rem + TC - 1) / TC, 1, 1) : dim3((HX + TC - 1) / TC, rows, 1);
-  static const int resident = [&] {  // CTAs resident at once: the prefetch distance
-    int per_sm = 0, dev = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, TC * R1, smem);
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return per_sm > 0 && sms > 0 ? per_sm * sms : 0;
-  }();
   const Work<float>& w = *L.w;
   k<<<grid, TC * R1, smem, L.st>>>(base, rows, sx, HX, L.g.nz, tw, w.kt[0], w.kt[1], w.kt[2], w.st[0], w.st[1],
-                                   w.st[2], (float)scale, w.kap4, L.g.nx, L.g.ny, L.g.nz, L.ctrl, chk ? 1 : 0,
-                                   resident);
+                                   w.st[2], (float)scale, w.kap4, L.g.nx, L.g.ny, L.g.nz, L.ctrl, chk ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -288,7 +280,6 @@ template <int MODE, int R1i, int R2i, int R2o> struct XS {
   static constexpr int TP0 = cmax(cmax(R1i, R2i), R2o);
   static constexpr int TP = TP0 <= 4 ? 4 : TP0 <= 8 ? 8 : 16;
   static constexpr int KX = PADIN ? R1i / 2 : R1i;  // k1 slots that hold x < nx after the C2R
-  static constexpr int TB = cmax(cmax(3 * R2i * (R1i + 1), 3 * R2o * (R1o + 1)), 3 * Lo);  // smem per pair
 };
 
 __device__ __forceinline__ float rho_of(float jx, float jy, float jz, bool in, float jcv, const PointParams& pp) {
@@ -430,7 +421,7 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 4 : 1) zpas
                                                              const float* __restrict__ st1,
                                                              const float* __restrict__ st2, float scale,
                                                              const float4* __restrict__ kap4, int nx, int ny, int nz,
-                                                             const Ctrl* ctrl, int check_done, int ahead) {
+                                                             const Ctrl* ctrl, int check_done) {
   constexpr int L = R1 * R2;
   constexpr bool PR = (KIND == 1);
   constexpr int S2 = R1 * TC + kPad8;  // forward transpose [k2][n1][c]
@@ -475,20 +466,8 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 4 : 1) zpas
   const size_t zstride = (size_t)rows * sx;
   const size_t cstride = (size_t)nzs * zstride;
   float2* col = base + (size_t)y * sx + kx;
-  if constexpr (PACK) {  // prefetch into L2 the input columns of the CTA one wave of resident CTAs later
-    const int nfull = HX / TC, rem = HX - nfull * TC;
-    const int ntail = (rows * rem + TC - 1) / TC;
-    const int nb = (int)blockIdx.x + ahead;
-    constexpr int NZ = (R2 / 2) * R1;
-    if (ahead > 0 && nb >= ntail && nb < (int)gridDim.x && c == 0) {
-      const int yb = (nb - ntail) / nfull;
-      const float2* ncol = base + (size_t)yb * sx + (nb - ntail - yb * nfull) * TC;
-      for (int i = n1; i < 3 * NZ; i += R1) {
-        const int q = i / NZ, zz = i - q * NZ;
-        prefetch_l2(ncol + q * cstride + (size_t)zz * zstride);
-      }
-    }
-  }
+  // (an L2 prefetch of the input columns of the CTA one wave later paid at three CTAs per SM;
+  // at four it measured 2% slower and is gone)
   __syncthreads();  // twiddles staged
   // This thread's twiddles W_L^{n1 j}: stage A uses j = k2 with its own n1, and
   // stage A' (run by the thread whose k2 equals this n1) uses j = m1, so one set
