@@ -89,6 +89,8 @@ typedef struct {
   int last_iters;          /* iterations of the most recent rhs */
   double last_residual;    /* its final Eq. 5 residual */
   double t, dt;            /* integrator time and proposed step */
+  long long h2d_bytes;     /* host -> device bytes copied by scfft_step_host */
+  long long d2h_bytes;     /* device -> host bytes copied by scfft_step_host */
 } scfft_stats;
 
 /* Create a context for one grid.  stream: a cudaStream_t (NULL = legacy
@@ -165,6 +167,18 @@ scfft_status scfft_integrate(scfft_ctx* ctx, double t0, double t1, double dt0, i
  * NULL (rejected trials).  Synchronous (reads the error norm). */
 scfft_status scfft_step(scfft_ctx* ctx, double* t, double* dt, double tstop, double* h, double* warm,
                         int* rejected);
+
+/* scfft_step with the state kept in host memory: h_host, warm_host (host, 3*N doubles each,
+ * in/out; page-locked memory makes the copies fast) are copied into h, warm (device, 3*N
+ * doubles, caller-owned: the buffers scfft_step would take), the step runs on those, and the
+ * new h and warm are copied back before the call returns.  h is copied in on every call; warm
+ * only when the step reads it, i.e. always on the FP64 path and on the FP32 path unless the
+ * step continues the context's own trajectory on these device buffers (FSAL, as in
+ * scfft_step), whose warm start the context then holds itself.  The bytes copied are added to
+ * scfft_stats.h2d_bytes / d2h_bytes.  Statuses as scfft_step; on an error nothing is copied
+ * back.  Synchronous. */
+scfft_status scfft_step_host(scfft_ctx* ctx, double* t, double* dt, double tstop, double* h_host,
+                             double* warm_host, double* h, double* warm, int* rejected);
 
 /* Checkpoint and resume of a trajectory stepped with scfft_step (the method of lines of §2,
  * "ode23"; the paper itself does not describe checkpoints).  A checkpoint holds the time t and

@@ -34,7 +34,7 @@ EXPORTS = ("scfft_create", "scfft_set_geometry", "scfft_set_jc_map", "scfft_set_
            "scfft_step", "scfft_profile", "scfft_profile_read", "scfft_kind_name",
            "scfft_rhs_vjp", "scfft_adjoint_integrate", "scfft_batch_step", "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy",
            "scfft_curl_noalloc", "scfft_last_cuda_error", "scfft_inject_fault", "scfft_checkpoint_save",
-           "scfft_checkpoint_load")
+           "scfft_checkpoint_load", "scfft_step_host")
 
 NKINDS = 14
 
@@ -78,7 +78,8 @@ class _Stats(ctypes.Structure):
                 ("iterations", ctypes.c_longlong),
                 ("accepted", ctypes.c_longlong), ("rejected", ctypes.c_longlong),
                 ("last_iters", ctypes.c_int), ("last_residual", ctypes.c_double),
-                ("t", ctypes.c_double), ("dt", ctypes.c_double)]
+                ("t", ctypes.c_double), ("dt", ctypes.c_double),
+                ("h2d_bytes", ctypes.c_longlong), ("d2h_bytes", ctypes.c_longlong)]
 
 
 _lib = None
@@ -106,6 +107,7 @@ def load_library(path: Optional[str] = None):
         "scfft_phi": (I, [P, P, P]),
         "scfft_integrate": (I, [P, D, D, D, I, P, P, P, P, P, I, ctypes.POINTER(_Stats)]),
         "scfft_step": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), D, P, P, ctypes.POINTER(I)]),
+        "scfft_step_host": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), D, P, P, P, P, ctypes.POINTER(I)]),
         "scfft_profile": (I, [P, I]),
         "scfft_profile_read": (I, [P, P, P]),
         "scfft_kind_name": (ctypes.c_char_p, [I]),
@@ -249,6 +251,20 @@ class Context:
         tt, dd, rj = ctypes.c_double(t), ctypes.c_double(dt), ctypes.c_int(0)
         self._check(self._lib.scfft_step(self._h, ctypes.byref(tt), ctypes.byref(dd), float(tstop), _ptr(h),
                                          _ptr(warm), ctypes.byref(rj)), "scfft_step")
+        return tt.value, dd.value, rj.value
+
+    def step_host(self, t: float, dt: float, tstop: float, h_host, warm_host, h, warm):
+        """One accepted BS23 step with the state in host memory (h_host, warm_host: CPU
+        tensors, pinned for speed), run on the device buffers h, warm; returns
+        (t_new, dt_next, rejected_trials)."""
+        import torch
+        for a in (h_host, warm_host):
+            if a.device.type != "cpu" or a.dtype != torch.float64 or not a.is_contiguous():
+                raise ValueError("h_host, warm_host: contiguous float64 CPU tensors")
+        tt, dd, rj = ctypes.c_double(t), ctypes.c_double(dt), ctypes.c_int(0)
+        self._check(self._lib.scfft_step_host(self._h, ctypes.byref(tt), ctypes.byref(dd), float(tstop),
+                                              ctypes.c_void_p(h_host.data_ptr()), ctypes.c_void_p(warm_host.data_ptr()),
+                                              _ptr(h), _ptr(warm), ctypes.byref(rj)), "scfft_step_host")
         return tt.value, dd.value, rj.value
 
     def profile(self, enable: bool = True):

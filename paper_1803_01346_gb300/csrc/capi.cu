@@ -1217,6 +1217,26 @@ scfft_status scfft_step(scfft_ctx* c, double* t, double* dt, double tstop, doubl
   return step_any(c, t, dt, tstop, h, warm, 0.0, rejected);
 }
 
+scfft_status scfft_step_host(scfft_ctx* c, double* t, double* dt, double tstop, double* h_host, double* warm_host,
+                             double* h, double* warm, int* rejected) {
+  if (!c || !t || !dt || !h_host || !warm_host || !h || !warm || !(*dt > 0) || !(tstop > *t)) return SCFFT_EINVAL;
+  if (!c->have_geom || !c->have_kernel || !c->have_path) return SCFFT_ESTATE;
+  const size_t bytes = sizeof(double) * 3 * (size_t)c->g.N;
+  // the FP32 step reads the caller's warm start only when it starts a trajectory (FSAL below)
+  const bool continues = c->fsal_valid && c->fsal_t == *t && c->fsal_h == h && c->fsal_g == warm;
+  const bool reads_warm = c->opt.precision != SCFFT_PREC_F32 || !continues;
+  CK(cudaMemcpyAsync(h, h_host, bytes, cudaMemcpyHostToDevice, c->st));
+  if (reads_warm) CK(cudaMemcpyAsync(warm, warm_host, bytes, cudaMemcpyHostToDevice, c->st));
+  c->stats.h2d_bytes += (long long)(reads_warm ? 2 : 1) * (long long)bytes;
+  const scfft_status s = step_any(c, t, dt, tstop, h, warm, 0.0, rejected);
+  if (s != SCFFT_OK) return s;
+  CK(cudaMemcpyAsync(h_host, h, bytes, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaMemcpyAsync(warm_host, warm, bytes, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  c->stats.d2h_bytes += 2 * (long long)bytes;
+  return SCFFT_OK;
+}
+
 // ---------------------------------------------------------------- checkpoint / resume
 namespace {
 struct CkptHeader {
@@ -1355,6 +1375,8 @@ scfft_status scfft_integrate(scfft_ctx* c, double t0, double t1, double dt0, int
     stats->rhs_calls = c->stats.rhs_calls - before.rhs_calls;
     stats->iterations = c->stats.iterations - before.iterations;
     stats->launches = c->stats.launches - before.launches;
+    stats->h2d_bytes = c->stats.h2d_bytes - before.h2d_bytes;
+    stats->d2h_bytes = c->stats.d2h_bytes - before.d2h_bytes;
   }
   return SCFFT_OK;
 }

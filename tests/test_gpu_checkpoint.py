@@ -1,6 +1,7 @@
 """Checkpoint and resume through the C ABI: a trajectory saved after a few steps and resumed
 (in a fresh context, into fresh buffers) continues bit for bit like the uninterrupted run,
-on both paths; snapshots of another grid or precision are refused."""
+on both paths; snapshots of another grid or precision are refused.  The host-buffer step
+(scfft_step_host) follows the device API's trajectory bit for bit."""
 
 import numpy as np
 import pytest
@@ -65,3 +66,36 @@ def test_snapshots_of_another_grid_or_precision_are_refused():
         with pytest.raises(S.ScfftError) as e:
             other.checkpoint_load(snap, hh, torch.zeros_like(hh))
         assert e.value.code == 1
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", [S.PREC_F64, S.PREC_F32])
+def test_step_host_matches_step_bit_for_bit(prec):
+    """scfft_step_host (state and warm start in page-locked host memory) follows the device
+    API's trajectory bit for bit and copies what it states: h in and h, warm out on every
+    step; warm in on the first step of a trajectory, and on every step of the FP64 path
+    (whose stages read it)."""
+    n3 = 3 * int(np.prod(N_GRID))
+    k = 4
+    a = _ctx(prec)
+    h = torch.zeros(n3, dtype=torch.float64, device="cuda")
+    warm = torch.zeros_like(h)
+    warm.view(3, -1)[2] = 0.5
+    h_host = h.cpu().pin_memory()
+    w_host = warm.cpu().pin_memory()
+    t_ref, dt_ref = _steps(a, 0.0, 1e-3, h, warm, k)
+
+    b = _ctx(prec)
+    hd = torch.full_like(h, float("nan"))
+    wd = torch.full_like(h, float("nan"))
+    t, dt = 0.0, 1e-3
+    for _ in range(k):
+        t, dt, _ = b.step_host(t, dt, 2.0, h_host, w_host, hd, wd)
+    assert (t, dt) == (t_ref, dt_ref)
+    assert np.array_equal(h_host.numpy(), h.cpu().numpy())
+    assert np.array_equal(w_host.numpy(), warm.cpu().numpy())
+    st, nb = b.stats(), n3 * 8
+    assert st["d2h_bytes"] == 2 * k * nb
+    assert st["h2d_bytes"] == (2 * k * nb if prec == S.PREC_F64 else (k + 1) * nb)
+    with pytest.raises(ValueError):
+        b.step_host(t, dt, 2.0, hd, w_host, hd, wd)  # device tensor where a host one belongs
