@@ -148,6 +148,7 @@ cudaError_t go_z(const Launch<float>& L, float2* base, int rows, int sx, int HX,
   auto k = zpass_reg2_kernel<R1, R2, TC, KIND>;
   allow_smem<zpass_reg2_kernel<R1, R2, TC, KIND>>();
   constexpr bool PACK = (R1 == R2 && KIND == 1);  // as in the kernel's column map
+  if (KIND == 1 && Lt != 2 * L.g.nz) return cudaErrorInvalidValue;  // the padded pass folds kz about Lt/2
   const int nfull = HX / TC, rem = HX - nfull * TC;
   const dim3 grid = PACK ? dim3(nfull * rows + (rows * rem + TC - 1) / TC, 1, 1) : dim3((HX + TC - 1) / TC, rows, 1);
   const Work<float>& w = *L.w;
@@ -527,7 +528,7 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 4 : 1) zpas
       const int fy = (y <= ny) ? y : 2 * ny - y;
       const size_t plane = (size_t)(ny + 1) * (nx + 1);
       const float4* src = kap4 + (size_t)fy * (nx + 1) + (colok ? kx : 0);
-      for (int fz = n1; fz <= nz; fz += R1) cp_async16(Ks + fz * TC + c, src + fz * plane);
+      for (int fz = n1; fz <= L / 2; fz += R1) cp_async16(Ks + fz * TC + c, src + fz * plane);
     }
     cp_async_wait_all();
     __syncthreads();  // Ks complete and visible
@@ -542,9 +543,9 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 4 : 1) zpas
 #pragma unroll
       for (int k1 = 0; k1 < R1; ++k1) {
         const int kz = k2 + R2 * k1;
-        const int fz = (kz <= nz) ? kz : 2 * nz - kz;
+        const int fz = (kz <= L / 2) ? kz : L - kz;  // L = 2 nz: a constant, so most folds resolve at compile time
         const float4 K = Ks[fz * TC + c];
-        const float ax = K.x, ay = syg * K.y, az = (kz <= nz) ? K.z : -K.z;
+        const float ax = K.x, ay = syg * K.y, az = (kz <= L / 2) ? K.z : -K.z;
         const float2 G0 = F0[k1 * TC], G1 = F1[k1 * TC], G2 = w2[k1];
         const float2 cx = make_float2(ay * G2.x - az * G1.x, ay * G2.y - az * G1.y);
         const float2 cy = make_float2(az * G0.x - ax * G2.x, az * G0.y - ax * G2.y);
