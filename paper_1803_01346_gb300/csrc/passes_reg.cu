@@ -724,10 +724,12 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
   float2* T = RS + 3 * P * XL;           // [P][TT]
   const int tid = threadIdx.x;
   const int p = tid / TP, r = tid % TP;
+  // twiddle tables laid out [k2][n1] (entry k2 R + n1 holds W^{n1 k2}), so that the lanes n1 of
+  // a pair read consecutive words in the first stage instead of a stride of k2 (bank conflicts)
   if (S::C2R)
-    for (int i = tid; i < Li; i += NT) twi[i] = a.tw_in[i];
+    for (int i = tid; i < Li; i += NT) twi[i] = a.tw_in[(i % R1i) * (i / R1i)];
   if (S::R2C)
-    for (int i = tid; i < Lo; i += NT) two[i] = a.tw_out[i];
+    for (int i = tid; i < Lo; i += NT) two[i] = a.tw_out[(i % R1o) * (i / R1o)];
   const int ny = a.g.ny, nz = a.g.nz;
   const long long N = a.g.N;
   const int npairs = ny * nz / 2;
@@ -825,7 +827,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
           }
           DFT<R2i, true, float2>::run(v);
   #pragma unroll
-          for (int k2 = 0; k2 < R2i; ++k2) Tp[k2 * (R1i + 1) + n1] = k2 == 0 ? v[0] : cmulc(v[k2], twi[n1 * k2]);
+          for (int k2 = 0; k2 < R2i; ++k2) Tp[k2 * (R1i + 1) + n1] = k2 == 0 ? v[0] : cmulc(v[k2], twi[k2 * R1i + n1]);
         }
         __syncwarp();
         const int k2 = r;
@@ -980,7 +982,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
           }
           dft_maybe_half<R2o, false, S::PADOUT>(u);
   #pragma unroll
-          for (int k2 = 0; k2 < R2o; ++k2) Tp[k2 * (R1o + 1) + n1] = k2 == 0 ? u[0] : cmul(u[k2], two[n1 * k2]);
+          for (int k2 = 0; k2 < R2o; ++k2) Tp[k2 * (R1o + 1) + n1] = k2 == 0 ? u[0] : cmul(u[k2], two[k2 * R1o + n1]);
         }
         __syncwarp();
         const int k2 = r;
