@@ -44,7 +44,7 @@ UNIT = "voxel-RHS evals/s"
 REF_ITERS_PER_RHS = 2.9
 # DRAM bytes (read + write) per launch from the committed ncu capture
 # profiles/ncu_zpass_xupdate_lens128_fp32.md; an entry is removed when its kernel changes.
-NCU_TRAFFIC = {"z_kernel": 161649152 + 57520384}
+NCU_TRAFFIC = {"z_kernel": 161649152 + 57520384, "x_update": 84624128 + 8733696}
 
 
 def _peaks():
