@@ -168,7 +168,8 @@ scfft_status scfft_integrate(scfft_ctx* ctx, double t0, double t1, double dt0, i
 scfft_status scfft_step(scfft_ctx* ctx, double* t, double* dt, double tstop, double* h, double* warm,
                         int* rejected);
 
-/* scfft_step with the state kept in host memory: h_host, warm_host (host, 3*N doubles each,
+/* scfft_step (one BS23 step of the method of lines of §2) with the state kept in host memory:
+ * h_host, warm_host (host, 3*N doubles each,
  * in/out; page-locked memory makes the copies fast) are copied into h, warm (device, 3*N
  * doubles, caller-owned: the buffers scfft_step would take), the step runs on those, and the
  * new h and warm are copied back before the call returns.  h is copied in on every call; warm
