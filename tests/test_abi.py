@@ -53,4 +53,6 @@ def test_create_rejects_bad_arguments_on_host(lib):
     bad_o = S._Options(7, 2e-5, 100, 1.0, 2e-4, 1e-6)
     assert lib.scfft_create(ctypes.byref(g), ctypes.byref(m), ctypes.byref(bad_o), None, ctypes.byref(out)) == 1
     assert lib.scfft_rhs(None, 0.0, 0, None, None, None, None) == 1
+    t, dt = ctypes.c_double(0.0), ctypes.c_double(1e-3)
+    assert lib.scfft_step_host(None, ctypes.byref(t), ctypes.byref(dt), 1.0, None, None, None, None, None) == 1
     lib.scfft_destroy(None)

@@ -45,3 +45,19 @@ def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
     c.begin()
     c.end()
     assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_algorithmic_bytes_of_the_padded_z_pass_and_one_eq5_iteration():
+    """The roofline's numerator, counted from the layouts: the padded z pass reads and writes
+    the N_z non-zero planes of the padded half spectrum (3 components x (N_x+1) x 2N_y x N_z
+    complex FP32) and reads the kernel spectrum's octant (3 x (N_x+1)(N_y+1)(N_z+1) floats);
+    the eight passes of one Eq. 5 iteration at 128^3 move 0.893 GB."""
+    b = _bench()
+    n = (128, 128, 128)
+    p_all = 3 * 129 * 256 * 128 * 8
+    assert b.algorithmic_bytes("z_kernel", n, 4) == 2 * p_all + 3 * 129 ** 3 * 4 == 228_659_724
+    u = 3 * 65 * 128 * 128 * 8
+    assert b.algorithmic_bytes("z_curl", n, 4) == 2 * u
+    passes = ("x_update", "y_fwd_unpadded", "z_curl", "y_inv_unpadded", "x_maskpad", "y_fwd_padded",
+              "z_kernel", "y_inv_padded")
+    assert abs(sum(b.algorithmic_bytes(k, n, 4) for k in passes) - 0.8935e9) < 1e6
