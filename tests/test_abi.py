@@ -56,3 +56,34 @@ def test_create_rejects_bad_arguments_on_host(lib):
     t, dt = ctypes.c_double(0.0), ctypes.c_double(1e-3)
     assert lib.scfft_step_host(None, ctypes.byref(t), ctypes.byref(dt), 1.0, None, None, None, None, None) == 1
     lib.scfft_destroy(None)
+
+
+def test_every_entry_point_validates_before_any_cuda_call(lib):
+    """A null context (or null arrays) gives SCFFT_EINVAL from every entry point without a
+    GPU: each validates its arguments before it touches CUDA."""
+    d = ctypes.c_double(0.0)
+    sz = ctypes.c_size_t(0)
+    calls = {
+        "scfft_set_geometry": (None, None),
+        "scfft_set_jc_map": (None, None),
+        "scfft_set_field_path": (None, None),
+        "scfft_precompute_kernel": (None,),
+        "scfft_curl": (None, None, None),
+        "scfft_phi": (None, None, None),
+        "scfft_step": (None, ctypes.byref(d), ctypes.byref(d), 1.0, None, None, None),
+        "scfft_checkpoint_save": (None, 0.0, 1e-3, None, None, None, ctypes.byref(sz)),
+        "scfft_checkpoint_load": (None, None, 0, ctypes.byref(d), ctypes.byref(d), None, None),
+        "scfft_integrate": (None, 0.0, 1.0, 1e-3, 0, None, None, None, None, None, 0, None),
+        "scfft_rhs_vjp": (None, None, None, None, None, None, None),
+        "scfft_adjoint_integrate": (None, 0.0, None, 1, None, None, None, None, None, None, 4),
+        "scfft_batch_step": (None, 1, None, None, None, None, None, None),
+        "scfft_sync": (None,),
+        "scfft_inject_fault": (None, 0),
+        "scfft_get_stats": (None, None),
+        "scfft_profile": (None, 1),
+        "scfft_profile_read": (None, None, None),
+    }
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == 1, name
+    g = S._Grid(16, 16, 16, 1.0, 1.0, 1.0)
+    assert lib.scfft_curl_noalloc(ctypes.byref(g), 1.0, None, None, None) == 1
