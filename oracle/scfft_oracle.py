@@ -298,6 +298,26 @@ class FieldPath:
                 v = v + self.sin_amp * w * math.cos(w * (t - self.sin_t0)) * np.asarray(self.sin_dir, float)
         return v
 
+    def hedot_jacobian(self, t: float, left: bool = False) -> np.ndarray:
+        """d(dh_e/dt)(t) / d(path parameters), shape (3, 3K + 1): the parameters are the
+        knot amplitudes he[k][a] (knot-major, 3 per knot) and sin_amp.  On the linear
+        piece (t_s, t_{s+1}) that holds t (on the side `left` picks at a kink) the rate
+        (he_{s+1} - he_s) / (t_{s+1} - t_s) gives +-1/(t_{s+1} - t_s); inside the sine
+        window the rate sin_amp w cos(w (t - sin_t0)) sin_dir gives w cos(.) sin_dir."""
+        K = len(self.t)
+        J = np.zeros((3, 3 * K + 1))
+        s = self._seg(t, left)
+        if s >= 0:
+            w = 1.0 / (float(self.t[s + 1]) - float(self.t[s]))
+            for a in range(3):
+                J[a, 3 * (s + 1) + a] += w
+                J[a, 3 * s + a] -= w
+        inside = (self.sin_t0 < t <= self.sin_t1) if left else (self.sin_t0 <= t < self.sin_t1)
+        if inside and self.sin_period > 0:
+            w = 2 * math.pi / self.sin_period
+            J[:, 3 * K] = w * math.cos(w * (t - self.sin_t0)) * np.asarray(self.sin_dir, float)
+        return J
+
     def kinks(self):
         ks = list(np.asarray(self.t, float))
         if self.sin_amp != 0.0:
@@ -413,6 +433,7 @@ class IntegrateResult:
     rhs_calls: int
     iters: list
     dts: list
+    ts: list = field(default_factory=list)  # end time of every accepted step
 
 
 def integrate(prob: Problem, t0: float, t1: float, y0: np.ndarray, rtol: float, atol: float,
@@ -446,6 +467,7 @@ def integrate(prob: Problem, t0: float, t1: float, y0: np.ndarray, rtol: float, 
     snaps = []
     acc = rej = 0
     dts = []
+    tends = []
     si = 0
     step = 0
     while t < t1 and step < max_steps:
@@ -468,6 +490,7 @@ def integrate(prob: Problem, t0: float, t1: float, y0: np.ndarray, rtol: float, 
             y = ynew
             acc += 1
             dts.append(h_step)
+            tends.append(t)
             if end_left:
                 k1 = f(t, y, False)
             else:
@@ -480,7 +503,7 @@ def integrate(prob: Problem, t0: float, t1: float, y0: np.ndarray, rtol: float, 
         else:
             rej += 1
             dt = h_step * max(0.2, 0.9 * en ** (-1.0 / 3.0))
-    return IntegrateResult(t, y, snaps, acc, rej, state["calls"], state["iters"], dts)
+    return IntegrateResult(t, y, snaps, acc, rej, state["calls"], state["iters"], dts, tends)
 
 
 # ----------------------------------------------------------------------------
@@ -556,79 +579,106 @@ class StepAdjoint:
     y: np.ndarray       # forward end state y_S
     mu_y0: np.ndarray   # dJ/dy_0 for J = <lam_T, y_S>
     mu_jc: np.ndarray   # dJ/djc (per node)
-    mu_a: np.ndarray    # dJ/d(dh_e/dt), summed over every rhs call
+    mu_a: np.ndarray    # dJ/d(dh_e/dt), summed over every rhs call (and the first warm start)
+    mu_path: np.ndarray  # dJ/d(path parameters): knot amplitudes (3 per knot) and sin_amp
 
 
 def integrate_adjoint(prob: Problem, t0: float, dts: Sequence[float], y0: np.ndarray, lam_T: np.ndarray,
-                      K: int) -> StepAdjoint:
-    """Discrete adjoint of the fixed-step BS23 map y_0 -> y_S (Bogacki-Shampine
-    pair as in `integrate` with dt_list, no kinks inside the run) with each rhs
-    iterating Eq. 5 exactly K times.  The forward chain of one step is
-        Y2 = y + dt a21 k1,  k2 = F(Y2, g=k1),  Y3 = y + dt a32 k2,  k3 = F(Y3, g=k2),
-        y' = y + dt (b1 k1 + b2 k2 + b3 k3),  k4 = F(y', g=k3),  next k1 = k4 (FSAL),
-    with k1 = F(y_0, g_0) at the start and g_0 = dh_e/dt(t0) (reading R-warm);
-    the reverse sweep transposes it call by call with rhs_vjp."""
+                      K: int, ts: Optional[Sequence[float]] = None) -> StepAdjoint:
+    """Discrete adjoint of the fixed-step BS23 map y_0 -> y_S of `integrate` (Bogacki-
+    Shampine pair, dt_list mode) with each rhs iterating Eq. 5 exactly K times.  The
+    step times are ts (S + 1 values), or t0 + cumulative dts.  The forward chain of
+    step n (t = t_n, dt = t_{n+1} - t_n) is
+        Y2 = y + dt a21 k1,  k2 = F(t + dt/2, Y2; g=k1),  Y3 = y + dt a32 k2,
+        k3 = F(t + 3dt/4, Y3; g=k2),  y' = y + dt (b1 k1 + b2 k2 + b3 k3),
+        k4 = F(t_{n+1}, y'; g=k3)  (the left derivative of h_e when t_{n+1} is a kink),
+        next k1 = k4 (FSAL), or, when t_{n+1} is a kink, next k1 = F(t_{n+1}, y'; g=k4)
+        with the right derivative,
+    with k1 = F(t_0, y_0; g_0) at the start and g_0 = dh_e/dt(t_0) (reading R-warm);
+    F(t, h; g) depends on t only through the applied rate a = dh_e/dt(t).  The reverse
+    sweep transposes it call by call with rhs_vjp; each call's cotangent of a (and that
+    of g_0, summed over the nodes) maps to the path parameters through
+    FieldPath.hedot_jacobian at that call's time and side."""
     a21, a32 = BS23_A[1][0], BS23_A[2][1]
     b1, b2, b3 = BS23_B[0], BS23_B[1], BS23_B[2]
-    F = lambda t, y, g: rhs(prob, t, y, g, delta_it=0.0, max_iter=K).hdot  # noqa: E731
-    g0 = np.broadcast_to(prob.path.hedot(t0)[:, None, None, None], y0.shape).copy()
-    # forward, storing y_n, k1_n and t_n
-    ys, k1s, ts = [y0.copy()], [], [t0]
-    k1 = F(t0, y0, g0)
-    y, t = y0.copy(), t0
-    for dt in dts:
-        k1s.append(k1)
+    if ts is None:
+        ts = [t0]
+        for dt in dts:
+            ts.append(ts[-1] + dt)
+    ts = [float(v) for v in ts]
+    S = len(ts) - 1
+    kinks = set(prob.path.kinks())
+    ends_on_kink = [ts[n + 1] in kinks for n in range(S)]
+    F = lambda t, y, g, left=False: rhs(prob, t, y, g, delta_it=0.0, max_iter=K, left=left).hdot  # noqa: E731
+    g0 = np.broadcast_to(prob.path.hedot(ts[0])[:, None, None, None], y0.shape).copy()
+
+    def stages(n, y, k1):
+        t, dt = ts[n], ts[n + 1] - ts[n]
         Y2 = y + dt * a21 * k1
         k2 = F(t + 0.5 * dt, Y2, k1)
         Y3 = y + dt * a32 * k2
         k3 = F(t + 0.75 * dt, Y3, k2)
-        y = y + dt * (b1 * k1 + b2 * k2 + b3 * k3)
-        k1 = F(t + dt, y, k3)
-        t = t + dt
+        ynew = y + dt * (b1 * k1 + b2 * k2 + b3 * k3)
+        k4 = F(ts[n + 1], ynew, k3, left=ends_on_kink[n])
+        return Y2, k2, Y3, k3, ynew, k4
+
+    # forward, storing y_n and k1_n
+    ys, k1s = [y0.copy()], []
+    k1 = F(ts[0], y0, g0)
+    y = y0.copy()
+    for n in range(S):
+        k1s.append(k1)
+        _, _, _, _, y, k4 = stages(n, y, k1)
+        k1 = F(ts[n + 1], y, k4) if ends_on_kink[n] else k4
         ys.append(y.copy())
-        ts.append(t)
     # reverse
-    ybar = lam_T.copy()
-    k1bar_next = np.zeros_like(y0)  # cotangent of the FSAL stage carried into the step after
+    P = 3 * len(prob.path.t) + 1
+    mu_path = np.zeros(P)
     mu_jc = np.zeros(prob.mask.shape)
     mu_a = np.zeros(3)
-    for n in range(len(dts) - 1, -1, -1):
-        dt, yn, k1, tn = dts[n], ys[n], k1s[n], ts[n]
-        Y2 = yn + dt * a21 * k1
-        k2 = F(tn + 0.5 * dt, Y2, k1)
-        Y3 = yn + dt * a32 * k2
-        k3 = F(tn + 0.75 * dt, Y3, k2)
-        ynew = ys[n + 1]
-        k1bar = np.zeros_like(yn)
-        k2bar = np.zeros_like(yn)
-        k3bar = np.zeros_like(yn)
-        # k4 = F(y', k3)
-        v = rhs_vjp(prob, tn + dt, ynew, k1bar_next, K)
-        ybar_new = ybar + v.mu_h
+
+    def back(t, left, Y, lam):
+        v = rhs_vjp(prob, t, Y, lam, K, left=left)
+        nonlocal mu_jc, mu_a, mu_path
+        mu_jc = mu_jc + v.mu_jc
+        mu_a = mu_a + v.mu_a
+        mu_path = mu_path + prob.path.hedot_jacobian(t, left).T @ v.mu_a
+        return v
+
+    ybar = lam_T.copy()
+    k1bar_next = np.zeros_like(y0)  # cotangent of the next step's first stage
+    for n in range(S - 1, -1, -1):
+        t, dt = ts[n], ts[n + 1] - ts[n]
+        Y2, k2, Y3, k3, ynew, k4 = stages(n, ys[n], k1s[n])
+        k1bar = np.zeros_like(y0)
+        k2bar = np.zeros_like(y0)
+        k3bar = np.zeros_like(y0)
+        if ends_on_kink[n]:
+            # next k1 = F(t_{n+1}, y'; g=k4) (right derivative), k4 = F(t_{n+1}, y'; g=k3) (left)
+            v = back(ts[n + 1], False, ynew, k1bar_next)
+            ybar = ybar + v.mu_h
+            v = back(ts[n + 1], True, ynew, v.mu_g)
+        else:
+            v = back(ts[n + 1], False, ynew, k1bar_next)
+        ybar = ybar + v.mu_h
         k3bar += v.mu_g
-        mu_jc += v.mu_jc
-        mu_a += v.mu_a
         # y' = y + dt (b1 k1 + b2 k2 + b3 k3)
-        ybar = ybar_new.copy()
-        k1bar += dt * b1 * ybar_new
-        k2bar += dt * b2 * ybar_new
-        k3bar += dt * b3 * ybar_new
-        # k3 = F(Y3, k2), Y3 = y + dt a32 k2
-        v = rhs_vjp(prob, tn + 0.75 * dt, Y3, k3bar, K)
-        ybar += v.mu_h
+        k1bar += dt * b1 * ybar
+        k2bar += dt * b2 * ybar
+        k3bar += dt * b3 * ybar
+        # k3 = F(t + 3dt/4, Y3; g=k2), Y3 = y + dt a32 k2
+        v = back(t + 0.75 * dt, False, Y3, k3bar)
+        ybar = ybar + v.mu_h
         k2bar += v.mu_g + dt * a32 * v.mu_h
-        mu_jc += v.mu_jc
-        mu_a += v.mu_a
-        # k2 = F(Y2, k1), Y2 = y + dt a21 k1
-        v = rhs_vjp(prob, tn + 0.5 * dt, Y2, k2bar, K)
-        ybar += v.mu_h
+        # k2 = F(t + dt/2, Y2; g=k1), Y2 = y + dt a21 k1
+        v = back(t + 0.5 * dt, False, Y2, k2bar)
+        ybar = ybar + v.mu_h
         k1bar += v.mu_g + dt * a21 * v.mu_h
-        mu_jc += v.mu_jc
-        mu_a += v.mu_a
         k1bar_next = k1bar
-    # k1 = F(y_0, g_0)
-    v = rhs_vjp(prob, t0, ys[0], k1bar_next, K)
-    ybar += v.mu_h
-    mu_jc += v.mu_jc
-    mu_a += v.mu_a
-    return StepAdjoint(ys[-1], ybar, mu_jc, mu_a)
+    # k1 = F(t_0, y_0; g_0) with g_0 = dh_e/dt(t_0) at every node
+    v = back(ts[0], False, ys[0], k1bar_next)
+    ybar = ybar + v.mu_h
+    mg0 = np.sum(v.mu_g, axis=(1, 2, 3))
+    mu_a = mu_a + mg0
+    mu_path = mu_path + prob.path.hedot_jacobian(ts[0], False).T @ mg0
+    return StepAdjoint(ys[-1], ybar, mu_jc, mu_a, mu_path)
