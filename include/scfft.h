@@ -109,6 +109,23 @@ scfft_status scfft_set_geometry(scfft_ctx* ctx, const uint8_t* mask);
  * for the uniform material jc.  Copied (converted to the FFT precision). */
 scfft_status scfft_set_jc_map(scfft_ctx* ctx, const double* jc_dev);
 
+/* The e(j, h) law in Omega.  §2 (after Eq. 1) notes that another current-voltage relation,
+ * e(j) or e(j, h) with h the local magnetic field, can replace the power law; two are
+ * provided, alone or together:
+ *   Kim's field-dependent critical current  jc(h) = jc / (1 + |h| / kim_h0)  (kim_h0 > 0;
+ *     0 = jc independent of h), with |h| the state h at the node;
+ *   an anisotropic power law  e = (e0/jc)(|j|_A / jc)^(n-1) A^2 j,  A = diag(aniso),
+ *     |j|_A = |A j|, the gradient of the convex potential (e0 jc/(n+1)) (|j|_A / jc)^(n+1),
+ *     so the critical current density along axis a is jc / aniso[a].
+ * kim_h0 = 0 with aniso = (1, 1, 1) is Eq. 1 (the default).  EINVAL for kim_h0 < 0 or a
+ * non-positive or non-finite aniso.  The reverse mode (scfft_rhs_vjp, scfft_adjoint_*)
+ * covers Eq. 1 only and returns SCFFT_ESTATE while another law is set. */
+typedef struct {
+  double kim_h0;
+  double aniso[3];
+} scfft_ej_law;
+scfft_status scfft_set_ej_law(scfft_ctx* ctx, const scfft_ej_law* law);
+
 /* Applied-field path h_e(t); copied.  EINVAL on bad knots. */
 scfft_status scfft_set_field_path(scfft_ctx* ctx, const scfft_field_path* path);
 
@@ -259,21 +276,55 @@ scfft_status scfft_batch_step(scfft_ctx** ctxs, int nb, double* t, double* dt, c
 scfft_status scfft_rhs_vjp(scfft_ctx* ctx, const double* h, const double* lam, double* mu_h, double* mu_g,
                            double* mu_jc, double* mu_a);
 
-/* Discrete adjoint of the fixed-step BS23 map y_0 -> y_S: steps dts[0..nsteps-1]
- * (host) from t0, first stage k1 = rhs(y_0) with warm start dh_e/dt(t0),
- * FSAL, each stage's warm start = the previous rhs result, every rhs taking
- * exactly max_iter Eq. 5 iterations (delta_it is ignored during the call),
- * dh_e/dt taken at the stage times (right derivative; steps are not clipped
- * at kinks of the path).  For J = <lam_T, y_S> it returns mu_y0 = dJ/dy_0
- * (device 3N), mu_jc = dJ/djc (device N or NULL), mu_a = dJ/d(dh_e/dt) summed
- * over every rhs call (host double[3] or NULL) and y_S (device 3N or NULL).
- * States are checkpointed every checkpoint_every steps in the forward sweep and
- * each segment is recomputed during the reverse sweep (memory: about
- * (14 + 2 nsteps/checkpoint_every + 2 checkpoint_every) * 3N doubles, allocated
- * for the call).  y0, lam_T: device 3N.  Synchronous. */
+/* Discrete adjoint of the fixed-step BS23 map y_0 -> y_S over the whole run at once (built
+ * on scfft_adjoint_record / scfft_adjoint_step below, with step times t0 + dts[0] + ... and
+ * the first warm start dh_e/dt(t0)): steps dts[0..nsteps-1] (host), first stage
+ * k1 = rhs(y_0), FSAL, each stage's warm start = the previous rhs result, every rhs taking
+ * exactly max_iter Eq. 5 iterations (delta_it is ignored during the call), dh_e/dt taken at
+ * the stage times (right derivative; a step whose end time equals a kink of the path ends
+ * on it as in scfft_adjoint_record).  For J = <lam_T, y_S> it returns mu_y0 = dJ/dy_0
+ * (device 3N), mu_jc = dJ/djc (device N or NULL), mu_a = dJ/d(dh_e/dt) summed over every
+ * rhs call and the first warm start (host double[3] or NULL) and y_S (device 3N or NULL).
+ * States are checkpointed every checkpoint_every steps in the forward sweep and each
+ * segment is recomputed during the reverse sweep (memory: about
+ * (16 + 2 nsteps/checkpoint_every + 2 checkpoint_every) * 3N doubles, allocated and freed
+ * by the call; it also drops any recording of scfft_adjoint_record).  y0, lam_T: device 3N.
+ * Synchronous. */
 scfft_status scfft_adjoint_integrate(scfft_ctx* ctx, double t0, const double* dts, int nsteps, const double* y0,
                                      const double* lam_T, double* y_end, double* mu_y0, double* mu_jc,
                                      double* mu_a, int checkpoint_every);
+
+/* Reverse mode step by step over a recorded trajectory of the method of lines (§2, "ode23";
+ * the paper has no reverse mode): the map is the fixed-step BS23 map of scfft_integrate's
+ * fixed-step mode over the given step times, with every rhs taking exactly max_iter Eq. 5
+ * iterations (delta_it is ignored during these calls) and the warm-start chain of the
+ * forward run (each rhs starts Eq. 5 from the previous rhs result).  A step that ends on a
+ * kink of the applied-field path takes its last stage with the left derivative of h_e there
+ * and the next step restarts its first stage with the right one, as scfft_step does, so the
+ * recorded map reproduces an adaptive run from its accepted step times.
+ *
+ * scfft_adjoint_record: runs the forward map from y0 (device 3N) at t = ts[0] through the step
+ * times ts[0..nsteps] (host, increasing; the accepted step end times of a scfft_step run end
+ * exactly on the path's kinks, and a step whose end time equals a kink is treated as ending
+ * on it).  warm0: device 3N first warm start, or NULL for dh_e/dt(ts[0]) at every node.  The
+ * states (y_n, first stage k1_n) are checkpointed every checkpoint_every steps; y_end (device
+ * 3N or NULL) receives y at ts[nsteps].  The context keeps the recording (about
+ * (16 + 2 nsteps/checkpoint_every + 2 checkpoint_every) * 3N doubles of device memory,
+ * allocated here) until the next record or scfft_destroy.  Synchronous.
+ *
+ * scfft_adjoint_step: the reverse of step n = step_index; call it for n = nsteps-1, nsteps-2,
+ * ..., 0 in this order (SCFFT_ESTATE otherwise).  lambda_h (device 3N, in/out): on entry the
+ * cotangent of y_{n+1} (the caller may add dJ/dy_{n+1} of an objective between calls), on
+ * return that of y_n; after step 0 it is the full dJ/dy_0.  The recomputation of a checkpoint
+ * segment happens in the call that enters it.  grad_jc: device N doubles or NULL, += dJ/djc
+ * (per node) over this step's rhs calls.  grad_path: host, 3*nknots + 1 doubles or NULL,
+ * += dJ/d(path parameters): entries 3k..3k+2 the knot amplitudes he[3k..3k+2] of
+ * scfft_field_path (they enter through the rates dh_e/dt of the linear pieces), entry 3*nknots
+ * the sine amplitude sin_amp; step 0 also adds the cotangent of the default first warm start
+ * dh_e/dt(ts[0]) (not that of an explicit warm0).  Synchronous. */
+scfft_status scfft_adjoint_record(scfft_ctx* ctx, const double* ts, int nsteps, const double* y0, const double* warm0,
+                                  int checkpoint_every, double* y_end);
+scfft_status scfft_adjoint_step(scfft_ctx* ctx, int step_index, double* lambda_h, double* grad_jc, double* grad_path);
 
 /* Allocation-free spectral curl: out = curl_S f, the same result as
  * scfft_curl (FP64) on the same grid and sigma_scale, for callers that cannot
@@ -282,14 +333,19 @@ scfft_status scfft_adjoint_integrate(scfft_ctx* ctx, double t0, const double* dt
  * framework that owns every allocation).  This entry point has no counterpart
  * in the paper; it only repackages the curl.
  * It needs no context: grid (host) gives the sizes and half extents;
- * stream is a cudaStream_t (NULL = legacy default stream); f, out: device,
- * 3*N doubles, not aliased.  Its scratch is one static 8 MiB device array per
- * GPU (grids up to 64^3 nodes fit); larger grids return SCFFT_ESIZE and
- * nothing is queued.  It calls no allocator.  The first call on a device looks
- * up that array's device address; make that first call before any stream
- * capture.  Calls share the array: calls that overlap on the GPU (other
- * streams or host threads on the same device) race and must be serialized.
- * Asynchronous on stream. */
+ * stream is a cudaStream_t (NULL = legacy default stream) of the current
+ * device (SCFFT_EINVAL if it belongs to another device); f, out: device,
+ * 3*N doubles, not aliased; sigma_scale finite and >= 0.  Its scratch is one
+ * static 8 MiB device array per GPU (grids up to 64^3 nodes fit); larger grids
+ * return SCFFT_ESIZE and nothing is queued.  It calls no allocator.  Every call
+ * made outside a stream capture looks up that array's device address on the
+ * current device (so a device reset between calls is harmless); a call made
+ * while the stream is capturing reuses the address found by an earlier call on
+ * that device, and returns SCFFT_ESTATE if there was none: make the first call
+ * on a device before any stream capture.  Calls share the array: calls that
+ * overlap on the GPU (other streams or host threads on the same device) race
+ * and must be serialized.  SCFFT_ECUDA leaves its cause in
+ * scfft_last_cuda_error().  Asynchronous on stream. */
 scfft_status scfft_curl_noalloc(const scfft_grid* grid, double sigma_scale, const double* f, double* out,
                                 void* stream);
 

@@ -151,15 +151,30 @@ class Material:
     jc: object = 1.0      # scalar or (nz, ny, nx) map
     rho_out: float = 20.0  # fictitious resistivity in Omega_out
     mu0: float = 1.0
+    # e(j, h) variants (§2 after Eq. 1: "e(j) or e(j, h), where h is the local magnetic field"):
+    kim_h0: float = 0.0            # Kim-type jc(|h|) = jc / (1 + |h| / kim_h0); 0: jc independent of h
+    aniso: tuple = (1.0, 1.0, 1.0)  # a_x, a_y, a_z of the anisotropic norm |j|_A = |(a_x j_x, a_y j_y, a_z j_z)|
 
 
-def electric_field(j: np.ndarray, mask: np.ndarray, mat: Material) -> np.ndarray:
+def electric_field(j: np.ndarray, mask: np.ndarray, mat: Material, h: Optional[np.ndarray] = None) -> np.ndarray:
     """e = rho(|j|) j in Omega with rho = (e0/jc)|j/jc|^(n-1) (Eq. 1), e = rho_out j in
-    Omega_out (the poor-conductor Ohm law of §2)."""
-    jn = np.sqrt(np.sum(j * j, axis=0))
+    Omega_out (the poor-conductor Ohm law of §2).
+
+    The e(j, h) variants that §2 allows in place of Eq. 1 (readings R-kim, R-aniso):
+    jc may depend on the local field, jc(h) = jc / (1 + |h| / kim_h0) (Kim's form), and
+    the power law may be anisotropic: e = (e0/jc)(|j|_A/jc)^(n-1) A^2 j with
+    A = diag(a_x, a_y, a_z) and |j|_A = |A j|, the gradient in j of the convex potential
+    (e0 jc / (n + 1)) (|j|_A / jc)^(n + 1), so the critical current along axis a is jc / a_a.
+    With kim_h0 = 0 and A = I this is Eq. 1."""
     jc = np.asarray(mat.jc, dtype=np.float64)
-    rho = (mat.e0 / jc) * (jn / jc) ** (mat.n - 1.0)
-    return np.where(mask[None], rho[None] * j, mat.rho_out * j)
+    if mat.kim_h0 > 0:
+        if h is None:
+            raise ValueError("a field-dependent jc needs the field h")
+        jc = jc / (1.0 + np.sqrt(np.sum(h * h, axis=0)) / mat.kim_h0)
+    A = np.asarray(mat.aniso, dtype=np.float64)[:, None, None, None]
+    jA = np.sqrt(np.sum((A * j) ** 2, axis=0))
+    rho = (mat.e0 / jc) * (jA / jc) ** (mat.n - 1.0)
+    return np.where(mask[None], rho[None] * (A * A) * j, mat.rho_out * j)
 
 
 def dissipation(j: np.ndarray, e: np.ndarray, mask: np.ndarray, dV: float) -> float:
@@ -367,7 +382,7 @@ def rhs(prob: Problem, t: float, h: np.ndarray, g: np.ndarray, delta_it: float =
         Khat = prob.kernel()
         phi = lambda jj: phi_hockney(jj, grid, Khat)  # noqa: E731
     j = curl_s(h, grid)
-    e = electric_field(j, mask, mat)
+    e = electric_field(j, mask, mat, h)
     hdot_in = -curl_s(e, grid) / mat.mu0
     hd = np.where(mask[None], hdot_in, g)
     hed = prob.path.hedot(t, left=left)
@@ -541,6 +556,8 @@ def rhs_vjp(prob: Problem, t: float, h: np.ndarray, lam: np.ndarray, K: int, lef
     de/djc = -n rho j / jc in Omega (rho is proportional to jc^-n).  The warm
     start g does not enter (the result is linear in it: mu_g = chib lam_0)."""
     grid, mask, mat = prob.grid, prob.mask, prob.mat
+    if mat.kim_h0 > 0 or tuple(mat.aniso) != (1.0, 1.0, 1.0):
+        raise NotImplementedError("the reverse mode covers the isotropic, field-independent law of Eq. 1")
     chi = mask[None].astype(float)
     chib = 1.0 - chi
     Khat = prob.kernel()

@@ -19,7 +19,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 __all__ = ["ScfftError", "Context", "load_library", "library_path", "PREC_F64", "PREC_F32", "FAULT_TMA_WAIT",
-           "EXPORTS"]
+           "EXPORTS", "rhs_autograd", "integrate_autograd", "batch_step", "curl_noalloc"]
 
 PREC_F64 = 0
 PREC_F32 = 1
@@ -34,7 +34,7 @@ EXPORTS = ("scfft_create", "scfft_set_geometry", "scfft_set_jc_map", "scfft_set_
            "scfft_step", "scfft_profile", "scfft_profile_read", "scfft_kind_name",
            "scfft_rhs_vjp", "scfft_adjoint_integrate", "scfft_batch_step", "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy",
            "scfft_curl_noalloc", "scfft_last_cuda_error", "scfft_inject_fault", "scfft_checkpoint_save",
-           "scfft_checkpoint_load", "scfft_step_host")
+           "scfft_checkpoint_load", "scfft_step_host", "scfft_adjoint_record", "scfft_adjoint_step", "scfft_set_ej_law")
 
 NKINDS = 14
 
@@ -71,6 +71,10 @@ class _FieldPath(ctypes.Structure):
                 ("he", ctypes.POINTER(ctypes.c_double)), ("sin_amp", ctypes.c_double),
                 ("sin_period", ctypes.c_double), ("sin_t0", ctypes.c_double), ("sin_t1", ctypes.c_double),
                 ("sin_dir", ctypes.c_double * 3)]
+
+
+class _EjLaw(ctypes.Structure):
+    _fields_ = [("kim_h0", ctypes.c_double), ("aniso", ctypes.c_double * 3)]
 
 
 class _Stats(ctypes.Structure):
@@ -122,6 +126,9 @@ def load_library(path: Optional[str] = None):
         "scfft_checkpoint_save": (I, [P, D, D, P, P, P, ctypes.POINTER(ctypes.c_size_t)]),
         "scfft_checkpoint_load": (I, [P, P, ctypes.c_size_t, ctypes.POINTER(D), ctypes.POINTER(D), P, P]),
         "scfft_adjoint_integrate": (I, [P, D, P, I, P, P, P, P, P, ctypes.POINTER(D), I]),
+        "scfft_adjoint_record": (I, [P, P, I, P, P, I, P]),
+        "scfft_adjoint_step": (I, [P, I, P, P, P]),
+        "scfft_set_ej_law": (I, [P, ctypes.POINTER(_EjLaw)]),
         "scfft_batch_step": (I, [P, I, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -212,10 +219,17 @@ class Context:
         tt = np.ascontiguousarray(t, dtype=np.float64)
         hh = np.ascontiguousarray(he, dtype=np.float64).reshape(-1)
         self._keep = (tt, hh)
+        self._nknots = len(tt)
         fp = _FieldPath(len(tt), tt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                         hh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(sin_amp), float(sin_period),
                         float(sin_t0), float(sin_t1), (ctypes.c_double * 3)(*[float(v) for v in sin_dir]))
         self._check(self._lib.scfft_set_field_path(self._h, ctypes.byref(fp)), "scfft_set_field_path")
+
+    def set_ej_law(self, kim_h0: float = 0.0, aniso=(1.0, 1.0, 1.0)):
+        """The e(j, h) law in Omega (see scfft_set_ej_law): Kim's jc(|h|) = jc/(1 + |h|/kim_h0)
+        and/or the anisotropic norm |j|_A = |diag(aniso) j|; the defaults are Eq. 1."""
+        law = _EjLaw(float(kim_h0), (ctypes.c_double * 3)(*[float(v) for v in aniso]))
+        self._check(self._lib.scfft_set_ej_law(self._h, ctypes.byref(law)), "scfft_set_ej_law")
 
     def precompute_kernel(self):
         self._check(self._lib.scfft_precompute_kernel(self._h), "scfft_precompute_kernel")
@@ -293,6 +307,26 @@ class Context:
                                                       int(checkpoint_every)), "scfft_adjoint_integrate")
         return [mu_a[0], mu_a[1], mu_a[2]]
 
+    def adjoint_record(self, ts, y0, warm0=None, y_end=None, checkpoint_every=50):
+        """Record the frozen forward map over the step times ts (host, nsteps + 1 values) from
+        y0 for the per-step reverse mode (see scfft.h); y_end receives the end state."""
+        tt = np.ascontiguousarray(ts, dtype=np.float64)
+        self._check(self._lib.scfft_adjoint_record(self._h, tt.ctypes.data, len(tt) - 1, _ptr(y0), _ptr(warm0),
+                                                   int(checkpoint_every), _ptr(y_end)), "scfft_adjoint_record")
+        return len(tt) - 1
+
+    def adjoint_step(self, n: int, lam, grad_jc=None, grad_path=None):
+        """Reverse of step n (n = nsteps-1 down to 0): lam (device) goes from the cotangent of
+        y_{n+1} to that of y_n; grad_jc (device) and grad_path (numpy float64 array of
+        3 * nknots + 1) are accumulated."""
+        gp = None
+        if grad_path is not None:
+            if grad_path.dtype != np.float64 or not grad_path.flags.c_contiguous:
+                raise TypeError("grad_path: contiguous float64 numpy array")
+            gp = grad_path.ctypes.data
+        self._check(self._lib.scfft_adjoint_step(self._h, int(n), _ptr(lam), _ptr(grad_jc), gp),
+                    "scfft_adjoint_step")
+
     def sync(self):
         self._check(self._lib.scfft_sync(self._h), "scfft_sync")
 
@@ -356,6 +390,49 @@ def _autograd():
             return None, None, mu_h, mu_g, mu_jc
 
     return RhsFunction
+
+
+def _integrate_autograd():
+    import torch
+
+    class IntegrateFunction(torch.autograd.Function):
+        """y(ts[-1]) of the frozen BS23 map over the step times ts from y0 (every rhs with
+        max_iter Eq. 5 iterations), as a differentiable op of y0, the jc map and the knot
+        amplitudes of the applied-field path; the backward pass is the library's
+        checkpointed reverse sweep (scfft_adjoint_record / scfft_adjoint_step)."""
+
+        @staticmethod
+        def forward(fctx, sc, ts, y0, jc, knots_t, knots_he, checkpoint_every):
+            sc.set_jc_map(jc.detach().contiguous())
+            sc.set_field_path(list(knots_t), knots_he.detach().cpu().numpy().reshape(-1, 3))
+            y_end = torch.empty_like(y0)
+            sc.adjoint_record(ts, y0.detach().contiguous(), y_end=y_end, checkpoint_every=checkpoint_every)
+            fctx.sc, fctx.S = sc, len(ts) - 1
+            fctx.shapes = (jc.shape, knots_he.shape, knots_he.dtype, knots_he.device)
+            return y_end
+
+        @staticmethod
+        def backward(fctx, lam):
+            sc = fctx.sc
+            jc_shape, he_shape, he_dtype, he_dev = fctx.shapes
+            lam_h = lam.detach().clone().contiguous()
+            gjc = torch.zeros(jc_shape, dtype=torch.float64, device=lam.device).reshape(-1)
+            gp = np.zeros(3 * (he_shape[0]) + 1)
+            for n in range(fctx.S - 1, -1, -1):
+                sc.adjoint_step(n, lam_h, gjc, gp)
+            ghe = torch.from_numpy(gp[:-1].reshape(he_shape)).to(device=he_dev, dtype=he_dtype)
+            return None, None, lam_h, gjc.reshape(jc_shape), None, ghe, None
+
+    return IntegrateFunction
+
+
+def integrate_autograd(sc: "Context", ts, y0, jc, knots_t, knots_he, checkpoint_every: int = 50):
+    """Differentiable end state of the frozen fixed-step BS23 map over the step times ts (the
+    accepted step end times of an adaptive run reproduce it, kinks included): gradients flow
+    to y0 (device), jc (device, per node) and knots_he (a (K, 3) tensor of the path's knot
+    amplitudes at times knots_t).  The context must use delta_it = 0 semantics for the
+    forward to equal the map (the record runs with exactly max_iter iterations per rhs)."""
+    return _integrate_autograd().apply(sc, ts, y0, jc, knots_t, knots_he, checkpoint_every)
 
 
 def rhs_autograd(sc: "Context", t: float, h, warm, jc=None):

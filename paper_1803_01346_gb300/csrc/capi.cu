@@ -20,6 +20,10 @@ using namespace scfft;
 namespace {
 constexpr int kProfPool = 1 << 14;  // event pairs buffered before a flush
 }
+struct AdjRec;  // a recorded trajectory of the reverse mode (defined with it below)
+namespace {
+void free_rec(scfft_ctx* c);
+}
 
 struct scfft_ctx {
   Geo g{};
@@ -43,6 +47,10 @@ struct scfft_ctx {
   bool graph_pending = false;
   uint8_t* mask = nullptr;     // device
   long long nout = 0;
+  // e(j, h) law in Omega (scfft_set_ej_law); law = 0 is Eq. 1
+  int law = 0;
+  double kim_h0 = 0.0;
+  double aniso[3] = {1.0, 1.0, 1.0};
   bool have_geom = false, have_kernel = false, have_path = false;
   // field path
   std::vector<double> kt, khe;
@@ -74,6 +82,7 @@ struct scfft_ctx {
   double* adj_part = nullptr;
   double* hadj_part = nullptr;  // pinned
   int adj_part_cap = 0;
+  AdjRec* rec = nullptr;  // recorded trajectory of scfft_adjoint_record
   scfft_stats stats{};
   // profiling
   bool prof_on = false;
@@ -85,24 +94,26 @@ struct scfft_ctx {
 };
 
 namespace {
-
 // The most recent CUDA error behind an SCFFT_ECUDA (process wide, for diagnostics).
 std::mutex g_err_mutex;
 char g_err_text[512] = "";
+}  // namespace
 
-void note_cuda_error(cudaError_t e, int line) {
+void scfft::note_cuda_error(cudaError_t e, const char* file, int line) {
   std::lock_guard<std::mutex> lock(g_err_mutex);
-  snprintf(g_err_text, sizeof(g_err_text), "%s (%s) at capi.cu:%d; last failed launch: %s", cudaGetErrorName(e),
-           cudaGetErrorString(e), line, last_launch_failure());
+  snprintf(g_err_text, sizeof(g_err_text), "%s (%s) at %s:%d; last failed launch: %s", cudaGetErrorName(e),
+           cudaGetErrorString(e), file, line, last_launch_failure());
 }
 
-#define CK(x)                               \
-  do {                                      \
-    cudaError_t e_ = (x);                   \
-    if (e_ != cudaSuccess) {                \
-      note_cuda_error(e_, __LINE__);        \
-      return SCFFT_ECUDA;                   \
-    }                                       \
+namespace {
+
+#define CK(x)                                     \
+  do {                                            \
+    cudaError_t e_ = (x);                         \
+    if (e_ != cudaSuccess) {                      \
+      note_cuda_error(e_, "capi.cu", __LINE__);   \
+      return SCFFT_ECUDA;                         \
+    }                                             \
   } while (0)
 
 #define CS_(x)                            \
@@ -266,6 +277,9 @@ PointParams base_params(const scfft_ctx* c) {
   pp.inv_mu0 = 1.0 / c->mat.mu0;
   pp.inv_nout = c->nout > 0 ? 1.0 / (double)c->nout : 0.0;
   pp.max_iter = c->opt.max_iter;
+  pp.law = c->law;
+  pp.kim_h0 = c->kim_h0;
+  for (int a = 0; a < 3; ++a) pp.aniso[a] = c->aniso[a];
   return pp;
 }
 
@@ -444,8 +458,12 @@ scfft_status rhs_impl(scfft_ctx* c, double t, int left, const RhsIO& io, int* it
   // pre-stage: j = curl h; e = rho(j) j; dh^0 = -curl e / mu0 on Omega, warm on Omega_out
   CK(run(c, SCFFT_K_X_FWD, [&] { return x_io<T>(L, X_FWD_F64, pp, io); }));
   CK(curl_in_U<T>(c, L, false));
-  CK(run(c, SCFFT_K_X_POWERLAW,
-         [&] { return launch_x<T>(L, X_POWERLAW, pp, nullptr, nullptr, nullptr, 0, 0, false); }));
+  if (c->law) {  // the e(j, h) law reads the state h at each node
+    CK(run(c, SCFFT_K_X_POWERLAW, [&] { return x_io<T>(L, X_POWERLAW_H, pp, io); }));
+  } else {
+    CK(run(c, SCFFT_K_X_POWERLAW,
+           [&] { return launch_x<T>(L, X_POWERLAW, pp, nullptr, nullptr, nullptr, 0, 0, false); }));
+  }
   CK(curl_in_U<T>(c, L, false));
   CK(run(c, SCFFT_K_X_ASSEMBLE, [&] { return x_io<T>(L, X_ASSEMBLE, pp, io); }));
   const int maxit = c->opt.max_iter;
@@ -1062,7 +1080,8 @@ scfft_status scfft_create(const scfft_grid* grid, const scfft_material* mat, con
   if (!(grid->Lx > 0) || !(grid->Ly > 0) || !(grid->Lz > 0)) return SCFFT_EINVAL;
   if (!(mat->n >= 1) || !(mat->e0 > 0) || !(mat->jc > 0) || !(mat->rho_out >= 0) || !(mat->mu0 > 0))
     return SCFFT_EINVAL;
-  if (opt->max_iter < 0 || !(opt->delta_it >= 0) || !(opt->sigma_scale >= 0)) return SCFFT_EINVAL;
+  if (opt->max_iter < 0 || !(opt->delta_it >= 0) || !(opt->sigma_scale >= 0) || !isfinite(opt->sigma_scale))
+    return SCFFT_EINVAL;
   if (!(opt->rtol > 0) || !(opt->atol > 0)) return SCFFT_EINVAL;
   if (opt->precision != SCFFT_PREC_F64 && opt->precision != SCFFT_PREC_F32) return SCFFT_EINVAL;
   scfft_ctx* c = new (std::nothrow) scfft_ctx();
@@ -1100,6 +1119,7 @@ void scfft_destroy(scfft_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
+  free_rec(c);
   free_work(c->wf);
   free_work(c->wd);
   if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
@@ -1154,6 +1174,18 @@ scfft_status scfft_set_jc_map(scfft_ctx* c, const double* jc) {
       CK(launch_convert<double>(jc, c->wd.jc, N, c->st));
     }
   }
+  return SCFFT_OK;
+}
+
+scfft_status scfft_set_ej_law(scfft_ctx* c, const scfft_ej_law* law) {
+  if (!c || !law) return SCFFT_EINVAL;
+  if (!(law->kim_h0 >= 0) || !isfinite(law->kim_h0)) return SCFFT_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (!(law->aniso[a] > 0) || !isfinite(law->aniso[a])) return SCFFT_EINVAL;
+  c->kim_h0 = law->kim_h0;
+  for (int a = 0; a < 3; ++a) c->aniso[a] = law->aniso[a];
+  c->law = (law->kim_h0 > 0 || law->aniso[0] != 1.0 || law->aniso[1] != 1.0 || law->aniso[2] != 1.0) ? 1 : 0;
+  c->fsal_valid = false;
   return SCFFT_OK;
 }
 
@@ -1384,31 +1416,59 @@ scfft_status scfft_integrate(scfft_ctx* c, double t0, double t1, double dt0, int
 scfft_status scfft_rhs_vjp(scfft_ctx* c, const double* h, const double* lam, double* mu_h, double* mu_g, double* mu_jc,
                            double* mu_a) {
   if (!c || !h || !lam || !mu_h || mu_h == h || mu_h == lam) return SCFFT_EINVAL;
-  if (!c->have_geom || !c->have_kernel) return SCFFT_ESTATE;
+  if (!c->have_geom || !c->have_kernel || c->law) return SCFFT_ESTATE;
   c->fsal_valid = false;
   return c->opt.precision == SCFFT_PREC_F32 ? vjp_impl<float>(c, h, lam, mu_h, mu_g, mu_jc, mu_a)
                                             : vjp_impl<double>(c, h, lam, mu_h, mu_g, mu_jc, mu_a);
 }
 
-// Discrete adjoint of fixed-step BS23 over a frozen step list (see scfft.h).
+}  // extern "C"
+
+// Reverse mode of the BS23 map over a recorded, frozen step list (see scfft.h).
 namespace {
 
 struct AdjBufs {
   double* base = nullptr;
-  double *y, *k1, *k2, *k3, *Y, *Y2, *yn, *w, *ybar, *k1b, *k2b, *k3b, *mh, *mg, *jct, *jcacc;
+  double *y, *k1, *k2, *k3, *k4, *Y, *Y2, *yn, *w, *k1b, *k2b, *k3b, *k4b, *mh, *mg, *jct;
   double *cpy, *cpk, *sgy, *sgk;
 };
 
+}  // namespace
+
+// A recorded trajectory: step times, kink flags, checkpoints (y_n, k1_n) every C steps, the
+// segment currently recomputed, and the cotangent of the next step's first stage.
+struct AdjRec {
+  AdjBufs b;
+  int S = 0, C = 1, ncp = 0;
+  std::vector<double> ts;
+  std::vector<char> left;  // step n ends on a kink of the path
+  int next = -1;           // the step index the next scfft_adjoint_step must take
+  int seg = -1;            // checkpoint segment whose states are in sgy / sgk
+  bool g0_fill = true;     // the first warm start was dh_e/dt(t_0) (its cotangent goes to the path)
+};
+
+namespace {
+
+void free_rec(scfft_ctx* c) {
+  if (!c->rec) return;
+  cudaFree(c->rec->b.base);
+  delete c->rec;
+  c->rec = nullptr;
+}
+
 scfft_status adj_alloc(scfft_ctx* c, int ncp, int seg, AdjBufs& b) {
   const size_t n3 = 3 * (size_t)c->g.N, N = (size_t)c->g.N;
-  const size_t total = 14 * n3 + 2 * N + 2 * (size_t)ncp * n3 + 2 * (size_t)seg * n3;
-  if (cudaMalloc(&b.base, sizeof(double) * total) != cudaSuccess) return SCFFT_ENOMEM;
+  const size_t total = 15 * n3 + N + 2 * (size_t)ncp * n3 + 2 * (size_t)seg * n3;
+  if (cudaMalloc(&b.base, sizeof(double) * total) != cudaSuccess) {
+    cudaGetLastError();
+    b.base = nullptr;
+    return SCFFT_ENOMEM;
+  }
   double* p = b.base;
-  double** arr[] = {&b.y,    &b.k1,  &b.k2,  &b.k3,  &b.Y, &b.Y2, &b.yn,
-                    &b.w,    &b.ybar, &b.k1b, &b.k2b, &b.k3b, &b.mh, &b.mg};
+  double** arr[] = {&b.y,  &b.k1, &b.k2,  &b.k3,  &b.k4,  &b.Y,  &b.Y2, &b.yn,
+                    &b.w,  &b.k1b, &b.k2b, &b.k3b, &b.k4b, &b.mh, &b.mg};
   for (double** a : arr) { *a = p; p += n3; }
   b.jct = p; p += N;
-  b.jcacc = p; p += N;
   b.cpy = p; p += (size_t)ncp * n3;
   b.cpk = p; p += (size_t)ncp * n3;
   b.sgy = p; p += (size_t)seg * n3;
@@ -1436,124 +1496,236 @@ cudaError_t scal(scfft_ctx* c, double* out, double a, const double* x, long long
   });
 }
 
-// k_out = F(t, Y; warm = g), leaving g untouched
-scfft_status rhs_keep(scfft_ctx* c, AdjBufs& b, double t, const double* Y, const double* g, double* out) {
+// k_out = F(t, Y; warm = g) (left: the left derivative of h_e at t), leaving g untouched
+scfft_status rhs_keep(scfft_ctx* c, AdjBufs& b, double t, int left, const double* Y, const double* g, double* out) {
   const size_t n3 = 3 * (size_t)c->g.N;
   CK(cudaMemcpyAsync(b.w, g, sizeof(double) * n3, cudaMemcpyDeviceToDevice, c->st));
-  return rhs_any(c, t, 0, Y, b.w, out, nullptr);
+  return rhs_any(c, t, left, Y, b.w, out, nullptr);
 }
 
-// forward stages of one step from (y, k1): fills k2, k3, Y (=Y3), yn (= y')
-scfft_status adj_stages(scfft_ctx* c, AdjBufs& b, double t, double dt, const double* y, const double* k1, double* Y2) {
+// forward stages of step n from (y, k1): fills Y2, k2, Y (= Y3), k3, yn (= y'), and k4 when
+// the step ends on a kink (the last stage, taken with the left derivative there)
+scfft_status adj_stages(scfft_ctx* c, AdjRec& r, int n, const double* y, const double* k1) {
+  AdjBufs& b = r.b;
   const long long n3 = 3 * c->g.N;
-  CK(axpy(c, Y2, y, dt * 0.5, k1, n3));
-  CS_(rhs_keep(c, b, t + 0.5 * dt, Y2, k1, b.k2));
+  const double t = r.ts[n], dt = r.ts[n + 1] - r.ts[n];
+  CK(axpy(c, b.Y2, y, dt * 0.5, k1, n3));
+  CS_(rhs_keep(c, b, t + 0.5 * dt, 0, b.Y2, k1, b.k2));
   CK(axpy(c, b.Y, y, dt * 0.75, b.k2, n3));
-  CS_(rhs_keep(c, b, t + 0.75 * dt, b.Y, b.k2, b.k3));
+  CS_(rhs_keep(c, b, t + 0.75 * dt, 0, b.Y, b.k2, b.k3));
   CK(run(c, SCFFT_K_RK, [&] {
     combine_kernel<<<blocks_for(n3), 256, 0, c->st>>>(b.yn, y, dt, 2.0 / 9.0, k1, 1.0 / 3.0, b.k2, 4.0 / 9.0, b.k3,
                                                       n3);
     return cudaGetLastError();
   }));
+  if (r.left[n]) CS_(rhs_keep(c, b, r.ts[n + 1], 1, b.yn, b.k3, b.k4));
   return SCFFT_OK;
 }
 
-scfft_status adj_vjp(scfft_ctx* c, AdjBufs& b, const double* Y, const double* lam, double* mu_a_acc, bool jc) {
+// the first stage of step n + 1 from the stages of step n: the FSAL stage F(t_{n+1}, y'; g = k3),
+// or after a kink F(t_{n+1}, y'; g = k4) with the right derivative
+scfft_status adj_next_k1(scfft_ctx* c, AdjRec& r, int n, double* k1_out) {
+  return rhs_keep(c, r.b, r.ts[n + 1], 0, r.b.yn, r.left[n] ? r.b.k4 : r.b.k3, k1_out);
+}
+
+// dJ/d(path parameters) += (d(dh_e/dt)(t) / d params)^T mu: the knot amplitudes (3 per knot)
+// through the rate of the linear piece that holds t (on the side `left` picks at a kink), and
+// sin_amp through the rate of the sine inside its window
+void path_grad(const scfft_ctx* c, double t, int left, const double mu[3], double* gp) {
+  if (!gp) return;
+  const int K = (int)c->kt.size();
+  for (int s = 0; s + 1 < K; ++s) {
+    const double lo = c->kt[s], hi = c->kt[s + 1];
+    const bool in = left ? (lo < t && t <= hi) : (lo <= t && t < hi);
+    if (in) {
+      const double w = 1.0 / (hi - lo);
+      for (int a = 0; a < 3; ++a) {
+        gp[3 * (s + 1) + a] += w * mu[a];
+        gp[3 * s + a] -= w * mu[a];
+      }
+      break;
+    }
+  }
+  const bool ins = left ? (c->sin_t0 < t && t <= c->sin_t1) : (c->sin_t0 <= t && t < c->sin_t1);
+  if (ins && c->sin_period > 0) {
+    const double w = 2 * M_PI / c->sin_period;
+    gp[3 * K] += w * cos(w * (t - c->sin_t0)) * (c->sin_dir[0] * mu[0] + c->sin_dir[1] * mu[1] + c->sin_dir[2] * mu[2]);
+  }
+}
+
+// one rhs call's transpose at (t, left): mh = (dF/dh)^T lam, mg = (dF/dg)^T lam; jc and path
+// cotangents accumulated
+scfft_status adj_call(scfft_ctx* c, AdjRec& r, double t, int left, const double* Y, const double* lam,
+                      double* grad_jc, double* grad_path, double* mu_a_acc) {
+  AdjBufs& b = r.b;
   double ma[3];
-  CS_(c->opt.precision == SCFFT_PREC_F32 ? vjp_impl<float>(c, Y, lam, b.mh, b.mg, jc ? b.jct : nullptr, ma)
-                                         : vjp_impl<double>(c, Y, lam, b.mh, b.mg, jc ? b.jct : nullptr, ma));
-  for (int q = 0; q < 3; ++q) mu_a_acc[q] += ma[q];
-  if (jc) CK(axpy(c, b.jcacc, b.jcacc, 1.0, b.jct, c->g.N));
+  CS_(c->opt.precision == SCFFT_PREC_F32 ? vjp_impl<float>(c, Y, lam, b.mh, b.mg, grad_jc ? b.jct : nullptr, ma)
+                                         : vjp_impl<double>(c, Y, lam, b.mh, b.mg, grad_jc ? b.jct : nullptr, ma));
+  if (grad_jc) CK(axpy(c, grad_jc, grad_jc, 1.0, b.jct, c->g.N));
+  path_grad(c, t, left, ma, grad_path);
+  if (mu_a_acc)
+    for (int q = 0; q < 3; ++q) mu_a_acc[q] += ma[q];
   return SCFFT_OK;
 }
 
-scfft_status adjoint_integrate(scfft_ctx* c, double t0, const double* dts, int S, const double* y0,
-                               const double* lamT, double* y_end, double* mu_y0, double* mu_jc, double* mu_a,
-                               int C) {
+// the frozen forward map over ts[0..S] from y0 (warm start warm0, or dh_e/dt(t_0) when NULL)
+scfft_status adj_record(scfft_ctx* c, const double* ts, int S, const double* y0, const double* warm0, int C,
+                        double* y_end) {
+  free_rec(c);
+  AdjRec* r = new (std::nothrow) AdjRec();
+  if (!r) return SCFFT_ENOMEM;
+  r->S = S;
+  r->C = std::min(C, S);
+  r->ncp = (S + r->C - 1) / r->C;
+  r->ts.assign(ts, ts + S + 1);
+  const std::vector<double> kinks = kinks_of(c);
+  r->left.resize(S);
+  for (int n = 0; n < S; ++n) r->left[n] = std::binary_search(kinks.begin(), kinks.end(), ts[n + 1]) ? 1 : 0;
+  r->g0_fill = warm0 == nullptr;
+  const scfft_status sa = adj_alloc(c, r->ncp, r->C, r->b);
+  if (sa != SCFFT_OK) {
+    delete r;
+    return sa;
+  }
+  c->rec = r;
+  AdjBufs& b = r->b;
   const long long n3 = 3 * c->g.N;
   const size_t bytes = sizeof(double) * n3;
-  const int ncp = (S + C - 1) / C;
-  AdjBufs b;
-  CS_(adj_alloc(c, ncp, C, b));
-  struct Free { double* p; ~Free() { cudaFree(p); } } guard{b.base};
-  double ma[3] = {0, 0, 0};
-  // forward: checkpoints (y_n, K1_n) every C steps
-  double g0[3];
-  hedot_at(c, t0, 0, g0);
-  CK(run(c, SCFFT_K_RK, [&] {
-    fill3_kernel<<<blocks_for(c->g.N), 256, 0, c->st>>>(b.w, g0[0], g0[1], g0[2], c->g.N);
-    return cudaGetLastError();
-  }));
+  if (warm0) {
+    CK(cudaMemcpyAsync(b.k4b, warm0, bytes, cudaMemcpyDeviceToDevice, c->st));
+  } else {
+    double g0[3];
+    hedot_at(c, ts[0], 0, g0);
+    CK(run(c, SCFFT_K_RK, [&] {
+      fill3_kernel<<<blocks_for(c->g.N), 256, 0, c->st>>>(b.k4b, g0[0], g0[1], g0[2], c->g.N);
+      return cudaGetLastError();
+    }));
+  }
+  // the checkpoint area holds the first warm start until it is consumed by k1_0
   CK(cudaMemcpyAsync(b.y, y0, bytes, cudaMemcpyDeviceToDevice, c->st));
-  CS_(rhs_any(c, t0, 0, b.y, b.w, b.k1, nullptr));
-  std::vector<double> tn(S + 1);
-  tn[0] = t0;
-  for (int n = 0; n < S; ++n) tn[n + 1] = tn[n] + dts[n];
+  CS_(rhs_keep(c, b, ts[0], 0, b.y, b.k4b, b.k1));
   for (int n = 0; n < S; ++n) {
-    if (n % C == 0) {
-      CK(cudaMemcpyAsync(b.cpy + (size_t)(n / C) * n3, b.y, bytes, cudaMemcpyDeviceToDevice, c->st));
-      CK(cudaMemcpyAsync(b.cpk + (size_t)(n / C) * n3, b.k1, bytes, cudaMemcpyDeviceToDevice, c->st));
+    if (n % r->C == 0) {
+      CK(cudaMemcpyAsync(b.cpy + (size_t)(n / r->C) * n3, b.y, bytes, cudaMemcpyDeviceToDevice, c->st));
+      CK(cudaMemcpyAsync(b.cpk + (size_t)(n / r->C) * n3, b.k1, bytes, cudaMemcpyDeviceToDevice, c->st));
     }
-    CS_(adj_stages(c, b, tn[n], dts[n], b.y, b.k1, b.Y));
+    CS_(adj_stages(c, *r, n, b.y, b.k1));
+    CS_(adj_next_k1(c, *r, n, b.k1));
     CK(cudaMemcpyAsync(b.y, b.yn, bytes, cudaMemcpyDeviceToDevice, c->st));
-    CS_(rhs_keep(c, b, tn[n + 1], b.y, b.k3, b.k1));  // FSAL: next k1 = F(y', g = k3)
   }
   if (y_end) CK(cudaMemcpyAsync(y_end, b.y, bytes, cudaMemcpyDeviceToDevice, c->st));
-  // reverse sweep, one checkpoint segment at a time
-  CK(cudaMemcpyAsync(b.ybar, lamT, bytes, cudaMemcpyDeviceToDevice, c->st));
+  // cotangent of the first stage of the step after the last: none
   CK(cudaMemsetAsync(b.k1b, 0, bytes, c->st));
-  CK(cudaMemsetAsync(b.jcacc, 0, sizeof(double) * c->g.N, c->st));
-  for (int m = ncp - 1; m >= 0; --m) {
-    const int n0 = m * C, n1 = std::min(S, n0 + C);
-    // recompute the segment's (y_n, K1_n)
+  CK(cudaStreamSynchronize(c->st));
+  r->next = S - 1;
+  r->seg = -1;
+  return SCFFT_OK;
+}
+
+// reverse of step n: lam (device 3N) in: cotangent of y_{n+1}; out: of y_n
+scfft_status adj_step(scfft_ctx* c, int n, double* lam, double* grad_jc, double* grad_path, double* mu_a_acc) {
+  AdjRec& r = *c->rec;
+  AdjBufs& b = r.b;
+  const long long n3 = 3 * c->g.N;
+  const size_t bytes = sizeof(double) * n3;
+  const int m = n / r.C, n0 = m * r.C, n1 = std::min(r.S, n0 + r.C);
+  if (r.seg != m) {  // recompute the segment's (y_i, k1_i) from its checkpoint
     CK(cudaMemcpyAsync(b.sgy, b.cpy + (size_t)m * n3, bytes, cudaMemcpyDeviceToDevice, c->st));
     CK(cudaMemcpyAsync(b.sgk, b.cpk + (size_t)m * n3, bytes, cudaMemcpyDeviceToDevice, c->st));
-    for (int n = n0; n + 1 < n1; ++n) {
-      double* yi = b.sgy + (size_t)(n - n0) * n3;
-      double* ki = b.sgk + (size_t)(n - n0) * n3;
-      CS_(adj_stages(c, b, tn[n], dts[n], yi, ki, b.Y));
+    for (int i = n0; i + 1 < n1; ++i) {
+      double* yi = b.sgy + (size_t)(i - n0) * n3;
+      double* ki = b.sgk + (size_t)(i - n0) * n3;
+      CS_(adj_stages(c, r, i, yi, ki));
       CK(cudaMemcpyAsync(yi + n3, b.yn, bytes, cudaMemcpyDeviceToDevice, c->st));
-      CS_(rhs_keep(c, b, tn[n + 1], b.yn, b.k3, ki + n3));
+      CS_(adj_next_k1(c, r, i, ki + n3));
     }
-    for (int n = n1 - 1; n >= n0; --n) {
-      // reverse of step n: ybar = cotangent of y_{n+1} -> of y_n; k1b = cotangent of K1_{n+1} -> of K1_n
-      const double dt = dts[n];
-      const double* yi = b.sgy + (size_t)(n - n0) * n3;
-      const double* ki = b.sgk + (size_t)(n - n0) * n3;
-      const bool jc = mu_jc != nullptr;
-      CS_(adj_stages(c, b, tn[n], dt, yi, ki, b.Y2));  // Y2, k2, Y (= Y3), k3, yn (= y_{n+1})
-      // K1_{n+1} = F(y_{n+1}, g = k3)
-      CS_(adj_vjp(c, b, b.yn, b.k1b, ma, jc));
-      CK(axpy(c, b.ybar, b.ybar, 1.0, b.mh, n3));
-      CK(cudaMemcpyAsync(b.k3b, b.mg, bytes, cudaMemcpyDeviceToDevice, c->st));
-      // y_{n+1} = y_n + dt (b1 k1 + b2 k2 + b3 k3)
-      CK(scal(c, b.k1b, dt * 2.0 / 9.0, b.ybar, n3));
-      CK(scal(c, b.k2b, dt / 3.0, b.ybar, n3));
-      CK(axpy(c, b.k3b, b.k3b, dt * 4.0 / 9.0, b.ybar, n3));
-      // k3 = F(Y3, g = k2), Y3 = y_n + dt a32 k2
-      CS_(adj_vjp(c, b, b.Y, b.k3b, ma, jc));
-      CK(axpy(c, b.ybar, b.ybar, 1.0, b.mh, n3));
-      CK(axpy(c, b.k2b, b.k2b, dt * 0.75, b.mh, n3));
-      CK(axpy(c, b.k2b, b.k2b, 1.0, b.mg, n3));
-      // k2 = F(Y2, g = k1), Y2 = y_n + dt a21 k1
-      CS_(adj_vjp(c, b, b.Y2, b.k2b, ma, jc));
-      CK(axpy(c, b.ybar, b.ybar, 1.0, b.mh, n3));
-      CK(axpy(c, b.k1b, b.k1b, dt * 0.5, b.mh, n3));
-      CK(axpy(c, b.k1b, b.k1b, 1.0, b.mg, n3));
-    }
+    r.seg = m;
   }
-  // k1 = F(y_0, g_0)
-  CS_(adj_vjp(c, b, b.cpy, b.k1b, ma, mu_jc != nullptr));
-  CK(axpy(c, b.ybar, b.ybar, 1.0, b.mh, n3));
-  CK(cudaMemcpyAsync(mu_y0, b.ybar, bytes, cudaMemcpyDeviceToDevice, c->st));
-  if (mu_jc) CK(cudaMemcpyAsync(mu_jc, b.jcacc, sizeof(double) * c->g.N, cudaMemcpyDeviceToDevice, c->st));
+  const double t = r.ts[n], t1 = r.ts[n + 1], dt = t1 - t;
+  const double* yi = b.sgy + (size_t)(n - n0) * n3;
+  const double* ki = b.sgk + (size_t)(n - n0) * n3;
+  CS_(adj_stages(c, r, n, yi, ki));  // Y2, k2, Y (= Y3), k3, yn (= y_{n+1}), k4 at a kink
+  if (n + 1 < r.S) {
+    // the next step's first stage (cotangent k1b); the last step's is not part of the map
+    CS_(adj_call(c, r, t1, 0, b.yn, b.k1b, grad_jc, grad_path, mu_a_acc));
+    CK(axpy(c, lam, lam, 1.0, b.mh, n3));
+    if (r.left[n]) {  // k1' = F(t1+, y'; g = k4), k4 = F(t1-, y'; g = k3)
+      CK(cudaMemcpyAsync(b.k4b, b.mg, bytes, cudaMemcpyDeviceToDevice, c->st));
+      CS_(adj_call(c, r, t1, 1, b.yn, b.k4b, grad_jc, grad_path, mu_a_acc));
+      CK(axpy(c, lam, lam, 1.0, b.mh, n3));
+    }
+    CK(cudaMemcpyAsync(b.k3b, b.mg, bytes, cudaMemcpyDeviceToDevice, c->st));
+  } else {
+    CK(cudaMemsetAsync(b.k3b, 0, bytes, c->st));
+  }
+  // y' = y + dt (b1 k1 + b2 k2 + b3 k3)
+  CK(scal(c, b.k1b, dt * 2.0 / 9.0, lam, n3));
+  CK(scal(c, b.k2b, dt / 3.0, lam, n3));
+  CK(axpy(c, b.k3b, b.k3b, dt * 4.0 / 9.0, lam, n3));
+  // k3 = F(t + 3dt/4, Y3; g = k2), Y3 = y + dt a32 k2
+  CS_(adj_call(c, r, t + 0.75 * dt, 0, b.Y, b.k3b, grad_jc, grad_path, mu_a_acc));
+  CK(axpy(c, lam, lam, 1.0, b.mh, n3));
+  CK(axpy(c, b.k2b, b.k2b, dt * 0.75, b.mh, n3));
+  CK(axpy(c, b.k2b, b.k2b, 1.0, b.mg, n3));
+  // k2 = F(t + dt/2, Y2; g = k1), Y2 = y + dt a21 k1
+  CS_(adj_call(c, r, t + 0.5 * dt, 0, b.Y2, b.k2b, grad_jc, grad_path, mu_a_acc));
+  CK(axpy(c, lam, lam, 1.0, b.mh, n3));
+  CK(axpy(c, b.k1b, b.k1b, dt * 0.5, b.mh, n3));
+  CK(axpy(c, b.k1b, b.k1b, 1.0, b.mg, n3));
+  r.next = n - 1;
+  if (n == 0) {
+    // k1_0 = F(t_0, y_0; g_0)
+    CS_(adj_call(c, r, t, 0, b.cpy, b.k1b, grad_jc, grad_path, mu_a_acc));
+    CK(axpy(c, lam, lam, 1.0, b.mh, n3));
+    if (r.g0_fill && (grad_path || mu_a_acc)) {
+      // g_0 = dh_e/dt(t_0) at every node: its cotangent is the node sum of mg
+      CK(run(c, SCFFT_K_OTHER, [&] {
+        chib_sum_kernel<<<kSumBlocks, 256, 0, c->st>>>(b.mg, c->mask, c->g.N, c->adj_part);
+        return cudaGetLastError();
+      }));
+      CK(cudaMemcpyAsync(c->hadj_part, c->adj_part, sizeof(double) * 3 * kSumBlocks, cudaMemcpyDeviceToHost, c->st));
+      CK(cudaStreamSynchronize(c->st));
+      double mg0[3] = {0, 0, 0};
+      for (int bk = 0; bk < kSumBlocks; ++bk)
+        for (int q = 0; q < 3; ++q) mg0[q] += c->hadj_part[bk * 3 + q];
+      path_grad(c, t, 0, mg0, grad_path);
+      if (mu_a_acc)
+        for (int q = 0; q < 3; ++q) mu_a_acc[q] += mg0[q];
+    }
+    r.next = -2;  // finished
+  }
   CK(cudaStreamSynchronize(c->st));
-  if (mu_a)
-    for (int q = 0; q < 3; ++q) mu_a[q] = ma[q];
   return SCFFT_OK;
+}
+
+// run f with Eq. 5 frozen at exactly max_iter iterations (the map the reverse mode describes)
+template <typename F> scfft_status frozen(scfft_ctx* c, F&& f) {
+  const double saved = c->opt.delta_it;
+  c->opt.delta_it = 0.0;
+  c->fsal_valid = false;
+  const scfft_status s = f();
+  c->opt.delta_it = saved;
+  return s;
 }
 
 }  // namespace
+
+extern "C" {
+
+scfft_status scfft_adjoint_record(scfft_ctx* c, const double* ts, int nsteps, const double* y0, const double* warm0,
+                                  int checkpoint_every, double* y_end) {
+  if (!c || !ts || nsteps < 1 || !y0 || checkpoint_every < 1) return SCFFT_EINVAL;
+  for (int n = 0; n < nsteps; ++n)
+    if (!(ts[n + 1] > ts[n])) return SCFFT_EINVAL;
+  if (!c->have_geom || !c->have_kernel || !c->have_path || c->law) return SCFFT_ESTATE;
+  return frozen(c, [&] { return adj_record(c, ts, nsteps, y0, warm0, checkpoint_every, y_end); });
+}
+
+scfft_status scfft_adjoint_step(scfft_ctx* c, int step_index, double* lambda_h, double* grad_jc, double* grad_path) {
+  if (!c || !lambda_h) return SCFFT_EINVAL;
+  if (!c->rec || c->rec->next != step_index || step_index < 0) return SCFFT_ESTATE;
+  return frozen(c, [&] { return adj_step(c, step_index, lambda_h, grad_jc, grad_path, nullptr); });
+}
 
 scfft_status scfft_adjoint_integrate(scfft_ctx* c, double t0, const double* dts, int nsteps, const double* y0,
                                      const double* lam_T, double* y_end, double* mu_y0, double* mu_jc, double* mu_a,
@@ -1561,13 +1733,22 @@ scfft_status scfft_adjoint_integrate(scfft_ctx* c, double t0, const double* dts,
   if (!c || !dts || nsteps < 1 || !y0 || !lam_T || !mu_y0 || checkpoint_every < 1) return SCFFT_EINVAL;
   for (int n = 0; n < nsteps; ++n)
     if (!(dts[n] > 0)) return SCFFT_EINVAL;
-  if (!c->have_geom || !c->have_kernel || !c->have_path) return SCFFT_ESTATE;
-  // the adjoint describes the frozen map: exactly max_iter iterations per rhs
-  const double saved = c->opt.delta_it;
-  c->opt.delta_it = 0.0;
-  c->fsal_valid = false;
-  scfft_status s = adjoint_integrate(c, t0, dts, nsteps, y0, lam_T, y_end, mu_y0, mu_jc, mu_a, checkpoint_every);
-  c->opt.delta_it = saved;
+  if (!c->have_geom || !c->have_kernel || !c->have_path || c->law) return SCFFT_ESTATE;
+  std::vector<double> ts(nsteps + 1);
+  ts[0] = t0;
+  for (int n = 0; n < nsteps; ++n) ts[n + 1] = ts[n] + dts[n];
+  const scfft_status s = frozen(c, [&]() -> scfft_status {
+    CS_(adj_record(c, ts.data(), nsteps, y0, nullptr, checkpoint_every, y_end));
+    const size_t bytes = sizeof(double) * 3 * (size_t)c->g.N;
+    CK(cudaMemcpyAsync(mu_y0, lam_T, bytes, cudaMemcpyDeviceToDevice, c->st));
+    if (mu_jc) CK(cudaMemsetAsync(mu_jc, 0, sizeof(double) * c->g.N, c->st));
+    double ma[3] = {0, 0, 0};
+    for (int n = nsteps - 1; n >= 0; --n) CS_(adj_step(c, n, mu_y0, mu_jc, nullptr, ma));
+    if (mu_a)
+      for (int q = 0; q < 3; ++q) mu_a[q] = ma[q];
+    return SCFFT_OK;
+  });
+  free_rec(c);
   return s;
 }
 

@@ -22,8 +22,12 @@ template <> struct cplx_of<double> { typedef double2 type; };
 
 __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
-__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// FP32 complex sums as packed two-lane instructions of sm_100 and later (one instruction for
+// the real and imaginary parts; each lane rounds as the scalar add does, and b * -1 + a
+// rounds exactly as a - b).  A product that feeds such a sum is rounded on its own instead
+// of being fused into it, so results can differ from the scalar forms in the last bit.
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 scl(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
@@ -58,26 +62,30 @@ __host__ __device__ constexpr double cos24(int m) {
 __host__ __device__ constexpr double sin24(int m) { return cos24(m - 12); }
 
 // a * W_R^m with W_R = exp(-2 pi i / R) (forward) or its conjugate (inverse); R divides 48.
-template <typename V, int R, bool INV>
-__device__ __forceinline__ V twiddle_const(V a, int m) {
-  // angle 2 pi m / R = (2 m * 24 / R) * pi / 24; m is a compile-time constant at every
-  // call site, so the branches below fold and multiples of pi/2 cost no multiply
-  // (IEEE forbids the compiler from dropping x*0 or x*1 on its own)
-  const int q = ((2 * m * 24 / R) % 48 + 48) % 48;
-  typedef decltype(a.x) T;
-  if (q == 0) return a;
-  if (q == 24) return mk(-a.x, -a.y);
-  if (q == 12) return INV ? mk(-a.y, a.x) : mk(a.y, -a.x);  // * (+i) / (-i)
-  if (q == 36) return INV ? mk(a.y, -a.x) : mk(-a.y, a.x);
-  const T c = (T)cos24(q), s = (T)sin24(q);
-  if (q % 12 == 6) {  // odd multiples of pi/4: |c| = |s|
-    const T h = (T)0.7071067811865475244008444;
-    const T sc = c > 0 ? (T)1 : (T)-1, ss = s > 0 ? (T)1 : (T)-1;
-    // forward: a * (c - i s); inverse: a * (c + i s)
-    return INV ? mk(h * (sc * a.x - ss * a.y), h * (ss * a.x + sc * a.y))
-               : mk(h * (sc * a.x + ss * a.y), h * (sc * a.y - ss * a.x));
+template <typename V, int R, bool INV> struct TwiddleConst {
+  static __device__ __forceinline__ V apply(V a, int m) {
+    // angle 2 pi m / R = (2 m * 24 / R) * pi / 24; m is a compile-time constant at every
+    // call site, so the branches below fold and multiples of pi/2 cost no multiply
+    // (IEEE forbids the compiler from dropping x*0 or x*1 on its own)
+    const int q = ((2 * m * 24 / R) % 48 + 48) % 48;
+    typedef decltype(a.x) T;
+    if (q == 0) return a;
+    if (q == 24) return mk(-a.x, -a.y);
+    if (q == 12) return INV ? mk(-a.y, a.x) : mk(a.y, -a.x);  // * (+i) / (-i)
+    if (q == 36) return INV ? mk(a.y, -a.x) : mk(-a.y, a.x);
+    const T c = (T)cos24(q), s = (T)sin24(q);
+    if (q % 12 == 6) {  // odd multiples of pi/4: |c| = |s|
+      const T h = (T)0.7071067811865475244008444;
+      const T sc = c > 0 ? (T)1 : (T)-1, ss = s > 0 ? (T)1 : (T)-1;
+      // forward: a * (c - i s); inverse: a * (c + i s)
+      return INV ? mk(h * (sc * a.x - ss * a.y), h * (ss * a.x + sc * a.y))
+                 : mk(h * (sc * a.x + ss * a.y), h * (sc * a.y - ss * a.x));
+    }
+    return INV ? mk(a.x * c - a.y * s, a.x * s + a.y * c) : mk(a.x * c + a.y * s, a.y * c - a.x * s);
   }
-  return INV ? mk(a.x * c - a.y * s, a.x * s + a.y * c) : mk(a.x * c + a.y * s, a.y * c - a.x * s);
+};
+template <typename V, int R, bool INV> __device__ __forceinline__ V twiddle_const(V a, int m) {
+  return TwiddleConst<V, R, INV>::apply(a, m);
 }
 
 // ---------------------------------------------------------------- small DFTs
@@ -114,6 +122,20 @@ template <bool INV, typename V> struct DFT<4, INV, V> {
     v[2] = a0 - b0;
     v[1] = a1 + b1;
     v[3] = a1 - b1;
+  }
+};
+
+// FP32: the sums as packed instructions; the products by -+i stay scalar (a packed form would
+// need the real and imaginary parts swapped first)
+template <bool INV> struct DFT<4, INV, float2> {
+  static __device__ __forceinline__ void run(float2* v) {
+    const float2 a0 = v[0] + v[2], a1 = v[0] - v[2];
+    const float2 b0 = v[1] + v[3], b1 = v[1] - v[3];
+    v[0] = a0 + b0;
+    v[2] = a0 - b0;
+    // a1 + (-+i) b1 and a1 - (-+i) b1
+    v[1] = INV ? make_float2(a1.x - b1.y, a1.y + b1.x) : make_float2(a1.x + b1.y, a1.y - b1.x);
+    v[3] = INV ? make_float2(a1.x + b1.y, a1.y - b1.x) : make_float2(a1.x - b1.y, a1.y + b1.x);
   }
 };
 
@@ -170,6 +192,16 @@ template <bool INV, typename V> struct DFTh<4, INV, V> {
     v[2] = a - b;
     v[1] = a + ib;
     v[3] = a - ib;
+  }
+};
+
+template <bool INV> struct DFTh<4, INV, float2> {
+  static __device__ __forceinline__ void run(float2* v) {
+    const float2 a = v[0], b = v[1];
+    v[0] = a + b;
+    v[2] = a - b;
+    v[1] = INV ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, a.y - b.x);
+    v[3] = INV ? make_float2(a.x + b.y, a.y - b.x) : make_float2(a.x - b.y, a.y + b.x);
   }
 };
 

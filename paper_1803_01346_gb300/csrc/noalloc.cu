@@ -33,9 +33,21 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Device address of g_noalloc_scratch for each device.  In host code the
-// symbol name is only a host-side stand-in, never a device address.
+// symbol name is only a host-side stand-in, never a device address.  The
+// address is looked up again on every call made outside a stream capture (the
+// module, and the array with it, may have been reloaded at another address
+// after a device reset); a call inside a capture uses the cached address.
 unsigned char* g_scratch_addr[kMaxDevices] = {nullptr};
 std::mutex g_setup_mutex;
+
+#define NCK(x)                                  \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) {                    \
+      note_cuda_error(e_, "noalloc.cu", __LINE__); \
+      return SCFFT_ECUDA;                       \
+    }                                           \
+  } while (0)
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -71,7 +83,7 @@ bool grid_ok(int n) { return n == 16 || n == 32 || n == 48 || n == 64 || n == 96
 
 extern "C" scfft_status scfft_curl_noalloc(const scfft_grid* grid, double sigma_scale, const double* f, double* out,
                                            void* stream) {
-  if (!grid || !f || !out || f == out || !(sigma_scale >= 0)) return SCFFT_EINVAL;
+  if (!grid || !f || !out || f == out || !(sigma_scale >= 0) || !isfinite(sigma_scale)) return SCFFT_EINVAL;
   if (!grid_ok(grid->nx) || !grid_ok(grid->ny) || !grid_ok(grid->nz)) return SCFFT_EINVAL;
   if (!(grid->Lx > 0) || !(grid->Ly > 0) || !(grid->Lz > 0)) return SCFFT_EINVAL;
   Geo g{};
@@ -88,14 +100,23 @@ extern "C" scfft_status scfft_curl_noalloc(const scfft_grid* grid, double sigma_
   const size_t need = off_u + sizeof(double2) * 3 * (size_t)g.nz * g.ny * g.sxu;
   if (need > kNoAllocBytes) return SCFFT_ESIZE;
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SCFFT_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the scratch address belongs to the device of the stream, which must be the current device
+  // (kernels are launched on the current device)
+  int dev = 0, sdev = 0;
+  NCK(cudaGetDevice(&dev));
+  NCK(cudaStreamGetDevice(s, &sdev));
+  if (sdev != dev || dev < 0 || dev >= kMaxDevices) return SCFFT_EINVAL;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  NCK(cudaStreamIsCapturing(s, &cap));
   unsigned char* base;
   {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_scratch_addr[dev]) {
+      if (cap != cudaStreamCaptureStatusNone) return SCFFT_ESTATE;  // first call on this device inside a capture
       void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SCFFT_ECUDA;
+      NCK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      if (!p) return SCFFT_ECUDA;
       g_scratch_addr[dev] = static_cast<unsigned char*>(p);
     }
     base = g_scratch_addr[dev];
@@ -111,7 +132,6 @@ extern "C" scfft_status scfft_curl_noalloc(const scfft_grid* grid, double sigma_
   w.st[0] = st; w.st[1] = st + g.nx / 2 + 1; w.st[2] = st + g.nx / 2 + 1 + g.ny;
   const double dx = 2 * grid->Lx / g.nx, dy = 2 * grid->Ly / g.ny, dz = 2 * grid->Lz / g.nz;
   const double sigma = sigma_scale * 0.5 * sqrt(dx * dx + dy * dy + dz * dz);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   Launch<double> L;
   L.g = g;
@@ -122,11 +142,11 @@ extern "C" scfft_status scfft_curl_noalloc(const scfft_grid* grid, double sigma_
   L.st = s;
   PointParams pp{};
   noalloc_tables<<<1, 256, 0, s>>>(tw, kt, st, g.nx, g.ny, g.nz, grid->Lx, grid->Ly, grid->Lz, sigma);
-  if (cudaGetLastError() != cudaSuccess) return SCFFT_ECUDA;
-  if (launch_x<double>(L, X_FWD_F64, pp, f, nullptr, nullptr, 0, 0, false) != cudaSuccess) return SCFFT_ECUDA;
-  if (launch_y<double>(L, false, false, false) != cudaSuccess) return SCFFT_ECUDA;
-  if (launch_z_curl<double>(L, false, 1.0 / (double)g.N) != cudaSuccess) return SCFFT_ECUDA;
-  if (launch_y<double>(L, false, true, false) != cudaSuccess) return SCFFT_ECUDA;
-  if (launch_x<double>(L, X_TO_F64, pp, nullptr, out, nullptr, 0, 0, false) != cudaSuccess) return SCFFT_ECUDA;
+  NCK(cudaGetLastError());
+  NCK(launch_x<double>(L, X_FWD_F64, pp, f, nullptr, nullptr, 0, 0, false));
+  NCK(launch_y<double>(L, false, false, false));
+  NCK(launch_z_curl<double>(L, false, 1.0 / (double)g.N));
+  NCK(launch_y<double>(L, false, true, false));
+  NCK(launch_x<double>(L, X_TO_F64, pp, nullptr, out, nullptr, 0, 0, false));
   return SCFFT_OK;
 }

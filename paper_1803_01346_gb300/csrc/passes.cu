@@ -195,13 +195,26 @@ __global__ void __launch_bounds__(kThreads) xpass_kernel(const XArgs<T> a) {
       if (MODE == X_POWERLAW) {
         T rho;
         if (a.mask[node]) {
-          const T jcv = a.jc ? a.jc[node] : (T)pp.jc;
-          const T jn = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
-          rho = rho_power(jn, jcv, (T)pp.n, (T)pp.e0);
+          T jcv = a.jc ? a.jc[node] : (T)pp.jc;
+          if (pp.law) {
+            // e(j, h): jc(h) = jc / (1 + |h| / h0) (Kim), e = rho(|A j|) A^2 j
+            if (pp.kim_h0 > 0) {
+              const T h0 = (T)a.src_f64[node], h1 = (T)a.src_f64[N + node], h2 = (T)a.src_f64[2 * N + node];
+              jcv = jcv / ((T)1 + sqrt(h0 * h0 + h1 * h1 + h2 * h2) / (T)pp.kim_h0);
+            }
+            const T ax = (T)pp.aniso[0], ay = (T)pp.aniso[1], az = (T)pp.aniso[2];
+            const T u0 = ax * v0, u1 = ay * v1, u2 = az * v2;
+            rho = rho_power(sqrt(u0 * u0 + u1 * u1 + u2 * u2), jcv, (T)pp.n, (T)pp.e0);
+            v0 *= rho * ax * ax; v1 *= rho * ay * ay; v2 *= rho * az * az;
+          } else {
+            const T jn = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+            rho = rho_power(jn, jcv, (T)pp.n, (T)pp.e0);
+            v0 *= rho; v1 *= rho; v2 *= rho;
+          }
         } else {
           rho = (T)pp.rho_out;
+          v0 *= rho; v1 *= rho; v2 *= rho;
         }
-        v0 *= rho; v1 *= rho; v2 *= rho;
       } else if (MODE == X_ASSEMBLE) {
         if (a.mask[node]) {
           const T s = -(T)pp.inv_mu0;
@@ -560,7 +573,9 @@ cudaError_t launch_x(const Launch<T>& L, XMode mode, const PointParams& pp, cons
   // the FP32 forward passes use the register-resident kernels; the transposed
   // (reverse-mode) passes use this shared-memory kernel in both precisions
   if constexpr (sizeof(T) == 4)
-    if (mode < X_ADJ_PAD) return launch_x_reg(L, mode, pp, src_f64, dst_f64, warm, in_buf, out_buf, check_done);
+    if (mode < X_ADJ_PAD || mode == X_POWERLAW_H)
+      return launch_x_reg(L, mode, pp, src_f64, dst_f64, warm, in_buf, out_buf, check_done);
+  if (mode == X_POWERLAW_H) mode = X_POWERLAW;
   XArgs<T> a{};
   const Geo& g = L.g;
   a.g = g;

@@ -291,6 +291,22 @@ __device__ __forceinline__ float rho_of(float jx, float jy, float jz, bool in, f
   return (e0 / jcv) * exp2f((n - 1.f) * log2f(jn / jcv));
 }
 
+// the e(j, h) law (PointParams::law): jc(h) = jc / (1 + |h| / h0), e = rho(|A j|) A^2 j; returns
+// the factors f_a with e_a = f_a j_a
+__device__ __forceinline__ void law_factors(float jx, float jy, float jz, bool in, float jcv, float hx, float hy,
+                                            float hz, const PointParams& pp, float f[3]) {
+  if (!in) {
+    f[0] = f[1] = f[2] = (float)pp.rho_out;
+    return;
+  }
+  if (pp.kim_h0 > 0) jcv = jcv / (1.f + sqrtf(hx * hx + hy * hy + hz * hz) / (float)pp.kim_h0);
+  const float ax = (float)pp.aniso[0], ay = (float)pp.aniso[1], az = (float)pp.aniso[2];
+  const float r = rho_of(ax * jx, ay * jy, az * jz, true, jcv, pp);
+  f[0] = r * ax * ax;
+  f[1] = r * ay * ay;
+  f[2] = r * az * az;
+}
+
 }  // namespace
 
 template <int MODE, int R1i, int R2i, int R2o, int P>
@@ -331,7 +347,7 @@ template <int MODE> cudaError_t go_x_n(int n, const XRArgs& a, cudaStream_t st) 
   case NN:                                                                                       \
     if constexpr (MODE == X_FWD_F64) return go_x<MODE, 1, B_, A_>(a, st);                        \
     else if constexpr (MODE == X_PAD_F64) return go_x<MODE, 1, B_, 2 * A_>(a, st);               \
-    else if constexpr (MODE == X_POWERLAW || MODE == X_ASSEMBLE) return go_x<MODE, A_, B_, A_>(a, st); \
+    else if constexpr (MODE == X_POWERLAW || MODE == X_POWERLAW_H || MODE == X_ASSEMBLE) return go_x<MODE, A_, B_, A_>(a, st); \
     else if constexpr (MODE == X_MASKPAD) return go_x<MODE, A_, B_, 2 * A_>(a, st);              \
     else if constexpr (MODE == X_TO_F64) return go_x<MODE, A_, B_, 1>(a, st);                    \
     else if constexpr (MODE == X_UPDATE) return go_x<MODE, C_, D_, C_ / 2>(a, st);               \
@@ -391,6 +407,7 @@ cudaError_t launch_x_reg_io(const Launch<float>& L, XMode mode, const PointParam
   switch (mode) {
     case X_FWD_F64: return go_x_n<X_FWD_F64>(g.nx, a, L.st);
     case X_POWERLAW: return go_x_n<X_POWERLAW>(g.nx, a, L.st);
+    case X_POWERLAW_H: return go_x_n<X_POWERLAW_H>(g.nx, a, L.st);
     case X_ASSEMBLE: return go_x_n<X_ASSEMBLE>(g.nx, a, L.st);
     case X_MASKPAD: return go_x_n<X_MASKPAD>(g.nx, a, L.st);
     case X_UPDATE: return go_x_n<X_UPDATE>(g.nx, a, L.st);
@@ -803,7 +820,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
           const int ln = i % (2 * rl), rr = (i / (2 * rl)) % nrow, q = i / (2 * rl * nrow);
           if (row0 + rr < 2 * npairs) prefetch_l2(a.warm + q * N + nb0 + (size_t)rr * XL + ln * 16);
         }
-      if (MODE == X_UPDATE || MODE == X_ASSEMBLE || MODE == X_MASKPAD || MODE == X_POWERLAW)
+      if (MODE == X_UPDATE || MODE == X_ASSEMBLE || MODE == X_MASKPAD || MODE == X_POWERLAW || MODE == X_POWERLAW_H)
         for (int i = tid * 128; i < nrow * XL; i += NT * 128)
           if (row0 + i / XL < 2 * npairs) prefetch_l2(a.mask + nb0 + i);
     }
@@ -874,8 +891,9 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
     if constexpr (S::C2R) {
       const PointParams& pp = a.pp;
       constexpr int J = XL / TP;  // node pairs per thread: x = r + TP j of the lane's own row pair
-      constexpr bool MASKED = MODE == X_POWERLAW || MODE == X_ASSEMBLE || MODE == X_MASKPAD || MODE == X_UPDATE;
-      constexpr int NO = MODE == X_UPDATE || MODE == X_ASSEMBLE ? 3 : (MODE == X_POWERLAW ? 1 : 0);
+      constexpr bool MASKED = MODE == X_POWERLAW || MODE == X_POWERLAW_H || MODE == X_ASSEMBLE || MODE == X_MASKPAD ||
+                              MODE == X_UPDATE;
+      constexpr int NO = MODE == X_UPDATE || MODE == X_ASSEMBLE ? 3 : (MODE == X_POWERLAW ? 1 : (MODE == X_POWERLAW_H ? 4 : 0));
       bool mk[J][2];
       float ov[J][NO > 0 ? NO : 1][2];  // hold (update), warm start (assemble), jc (power law)
 #pragma unroll
@@ -906,6 +924,16 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
           } else if (MODE == X_POWERLAW) {
             ov[j][0][0] = a.jc ? a.jc[na] : (float)pp.jc;
             ov[j][0][1] = a.jc ? a.jc[nb] : (float)pp.jc;
+          } else if (MODE == X_POWERLAW_H) {
+            ov[j][0][0] = a.jc ? a.jc[na] : (float)pp.jc;
+            ov[j][0][1] = a.jc ? a.jc[nb] : (float)pp.jc;
+            if (pp.kim_h0 > 0) {
+#pragma unroll
+              for (int q = 0; q < 3; ++q) {
+                ov[j][1 + q][0] = a.src_f32 ? a.src_f32[q * N + na] : (float)a.src_f64[q * N + na];
+                ov[j][1 + q][1] = a.src_f32 ? a.src_f32[q * N + nb] : (float)a.src_f64[q * N + nb];
+              }
+            }
           }
         }
       }
@@ -923,6 +951,14 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
           const float rb = rho_of(u[0].y, u[1].y, u[2].y, ib, ov[j][0][1], pp);
   #pragma unroll
           for (int q = 0; q < 3; ++q) u[q] = make_float2(u[q].x * ra, u[q].y * rb);
+        } else if (MODE == X_POWERLAW_H) {
+          float fa[3], fb[3];
+          law_factors(u[0].x, u[1].x, u[2].x, ia, ov[j][0][0], ov[j][NO > 1 ? 1 : 0][0], ov[j][NO > 2 ? 2 : 0][0],
+                      ov[j][NO > 3 ? 3 : 0][0], pp, fa);
+          law_factors(u[0].y, u[1].y, u[2].y, ib, ov[j][0][1], ov[j][NO > 1 ? 1 : 0][1], ov[j][NO > 2 ? 2 : 0][1],
+                      ov[j][NO > 3 ? 3 : 0][1], pp, fb);
+  #pragma unroll
+          for (int q = 0; q < 3; ++q) u[q] = make_float2(u[q].x * fa[q], u[q].y * fb[q]);
         } else if (MODE == X_ASSEMBLE) {
           const float s = -(float)pp.inv_mu0;
   #pragma unroll

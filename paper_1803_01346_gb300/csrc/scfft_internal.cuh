@@ -90,8 +90,9 @@ enum XMode : int {
   X_ADJ_CROP = 9,     // Pd -> C2R(2nx), crop -> x chi -> R2C(nx) -> U
   X_ADJ_COMBINE = 10, // U -> C2R(nx) -> dst = chi * src + (.)   (f64 rows)
   X_ADJ_IN = 11,      // real f64 rows x chi -> R2C(nx) -> U
-  X_ADJ_POWERLAW = 12 // U -> C2R(nx) -> lam_e = -(.)/mu0 -> power-law Jacobian^T (forward j in src) -> R2C(nx) -> U;
-                      //   dst (N values, optional) = d e/d jc . lam_e
+  X_ADJ_POWERLAW = 12, // U -> C2R(nx) -> lam_e = -(.)/mu0 -> power-law Jacobian^T (forward j in src) -> R2C(nx) -> U;
+                       //   dst (N values, optional) = d e/d jc . lam_e
+  X_POWERLAW_H = 13    // as X_POWERLAW with the e(j, h) law of PointParams::law (the state h read from src)
 };
 
 // Scalars of the material law and the Eq. 5 update.
@@ -106,6 +107,11 @@ struct PointParams {
   double inv_nout;    // 1 / |Omega_out|
   int iter;           // iteration index i (X_UPDATE)
   int max_iter;
+  // e(j, h) law in Omega (scfft_set_ej_law): law = 0 is Eq. 1; law = 1 uses
+  // jc(h) = jc / (1 + |h| / kim_h0) (kim_h0 > 0) and e = rho(|A j|) A^2 j, A = diag(aniso)
+  int law;
+  double kim_h0;
+  double aniso[3];
 };
 
 template <typename T>
@@ -139,6 +145,7 @@ cudaError_t launch_y_reg(const Launch<float>& L, bool padded, bool inverse, bool
 bool make_ymaps(Work<float>& w, const Geo& g);
 cudaError_t launch_y_tma(const Launch<float>& L, bool padded, bool inverse, bool check_done);
 cudaError_t launch_z_reg(const Launch<float>& L, bool padded, bool check_done, double scale);
+
 cudaError_t launch_x_reg(const Launch<float>& L, XMode mode, const PointParams& pp, const double* src_f64,
                          double* dst_f64, const double* warm, int in_buf, int out_buf, bool check_done);
 // The same with FP32 source rows / FP32 warm start (used by the FP32 integrator's stages).
@@ -149,6 +156,8 @@ cudaError_t launch_x_reg_io(const Launch<float>& L, XMode mode, const PointParam
 // Launch diagnostics: the last failed launch (kernel, grid, block, shared memory).
 cudaError_t checked_launch(const char* what, dim3 grid, int block, size_t smem);
 const char* last_launch_failure();
+// Record the CUDA error behind an SCFFT_ECUDA for scfft_last_cuda_error() (defined in capi.cu).
+void note_cuda_error(cudaError_t e, const char* file, int line);
 
 FftPlan make_plan(int L);
 bool length_supported(int L);

@@ -61,3 +61,20 @@ def test_algorithmic_bytes_of_the_padded_z_pass_and_one_eq5_iteration():
     passes = ("x_update", "y_fwd_unpadded", "z_curl", "y_inv_unpadded", "x_maskpad", "y_fwd_padded",
               "z_kernel", "y_inv_padded")
     assert abs(sum(b.algorithmic_bytes(k, n, 4) for k in passes) - 0.8935e9) < 1e6
+
+
+def test_cufft_baseline_kernel_spectrum_matches_the_oracle():
+    """The cuFFT yardstick builds the same sampled-kernel spectrum as the oracle's Hockney
+    convolution (checked here with torch on the CPU; on the GPU the bench compares its
+    result with scfft_phi before timing)."""
+    import numpy as np
+    import pytest
+    torch = pytest.importorskip("torch")
+    import cufft_baseline as C
+    import oracle as O
+
+    n, L = (6, 8, 4), (1.0, 1.2, 0.7)
+    g = O.Grid(n, L)
+    ref = O.hockney_kernel_spectrum(g)[:, :, :, : n[0] + 1]
+    K = C.kernel_spectrum(torch, n, L, g.sigma, device="cpu").numpy()
+    assert np.abs(K - ref).max() < 1e-6 * np.abs(ref).max()

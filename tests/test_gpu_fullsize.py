@@ -6,8 +6,9 @@ against the FP64 oracle on every output node.
 The oracle needs a few seconds of host time per Eq. 5 iteration at this size, so
 the module builds its state and reference values once: five Eq. 5 iterations.
 
-Tolerance: 2e-4 of the largest oracle magnitude, the FP32 path's stated bound
-(FP32 FFT round-off of about 1e-6 amplified by the power law's exponent n = 30).
+Tolerance: per component of dh/dt, max |GPU - oracle| / max |oracle| below TOL32
+(about three times the error observed on GB300: FP32 FFT round-off of about 1e-6
+amplified by the power law's exponent n = 30).
 """
 
 import numpy as np
@@ -24,7 +25,7 @@ from paper_1803_01346_gb300 import build as B  # noqa: E402
 
 T = 0.4            # inside the field ramp: dh_e/dt = (0, 0, 1)
 ITERS = 5
-TOL32 = 2e-4
+TOL32 = (6e-6, 6e-6, 6e-6)  # observed on GB300: 1.5e-6, 1.9e-6, 1.8e-6
 
 
 @pytest.fixture(scope="module")
@@ -64,6 +65,12 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
+def _check3(name, a, b):
+    e = [_rel(a[q], b[q]) for q in range(3)]
+    print(f"[fp32 error] {name}: " + " ".join(f"{v:.2e}" for v in e))
+    assert all(v < bd for v, bd in zip(e, TOL32)), (name, e)
+
+
 def test_rhs_fp32_lens128_fixed_iterations_matches_oracle(lens):
     """Five Eq. 5 iterations, no early stop: every pass of the right-hand side at
     the benchmark's grid against the oracle's same five iterations."""
@@ -74,8 +81,7 @@ def test_rhs_fp32_lens128_fixed_iterations_matches_oracle(lens):
     it = ctx.rhs(T, _dev(h), _dev(g0), out)
     torch.cuda.synchronize()
     assert it == ITERS
-    err = _rel(out.cpu().numpy().reshape(h.shape), ref.hdot)
-    assert err < TOL32, err
+    _check3("lens128 fixed", out.cpu().numpy().reshape(h.shape), ref.hdot)
 
 
 def test_rhs_fp32_lens128_graph_loop_stops_with_the_oracle(lens):
@@ -97,5 +103,4 @@ def test_rhs_fp32_lens128_graph_loop_stops_with_the_oracle(lens):
     # 1/50000 of the largest |dh/dt| here: FP32 round-off shows at the 1e-3 level
     st = ctx.stats()
     assert abs(st["last_residual"] - r[-1]) < 5e-2 * r[-1], (st["last_residual"], r[-1])
-    err = _rel(out.cpu().numpy().reshape(h.shape), ref.hdot)
-    assert err < TOL32, err
+    _check3("lens128 graph loop", out.cpu().numpy().reshape(h.shape), ref.hdot)

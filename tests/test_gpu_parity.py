@@ -42,6 +42,19 @@ def rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
+def rel3(a, b):
+    """Per-component relative error of a (3, ...) field: max |a_q - b_q| / max |b_q|."""
+    return [rel(a[q], b[q]) for q in range(3)]
+
+
+def check3(name, a, b, bounds):
+    """Assert the per-component error of the FP32 path against its stated bounds."""
+    e = rel3(a, b)
+    print(f"[fp32 error] {name}: " + " ".join(f"{v:.2e}" for v in e))
+    assert all(v < bd for v, bd in zip(e, bounds)), (name, e, bounds)
+    return e
+
+
 def make(n, L, mask, n_power=20.0, rho_out=20.0, prec=S.PREC_F64, delta_it=0.0, max_iter=3, path=None,
          jc_map=None, sigma_scale=1.0, rtol=2e-4, atol=1e-6):
     ctx = S.Context(n, L, n_power=n_power, rho_out=rho_out, precision=prec, delta_it=delta_it,
@@ -58,6 +71,13 @@ def make(n, L, mask, n_power=20.0, rho_out=20.0, prec=S.PREC_F64, delta_it=0.0, 
                      O.FieldPath(t, he))
     return ctx, prob
 
+
+# FP32 path: per-component bounds of max |GPU - oracle| / max |oracle| (about three times
+# the errors observed on GB300, printed by check3 under pytest -s)
+# (observed: curl and Phi <= 2.9e-7 per component, rhs with 3 Eq. 5 iterations <= 2.1e-6)
+CURL32 = (1e-6, 1e-6, 1e-6)
+PHI32 = (1e-6, 1e-6, 1e-6)
+RHS32 = (6e-6, 6e-6, 6e-6)
 
 GRIDS = [((16, 16, 16), (1.0, 1.0, 1.0)),
          ((48, 32, 16), (1.2, 0.9, 0.8)),     # ragged column tiles (25 and 17 spectral columns)
@@ -100,7 +120,7 @@ def test_curl_fp32_matches_oracle(n, L):
     ctx = S.Context(n, L, precision=S.PREC_F32)
     out = torch.empty(f.size, dtype=torch.float64, device="cuda")
     ctx.curl(dev(f).reshape(-1), out)
-    assert rel(host(out).reshape(f.shape), O.curl_s(f, g)) < 2e-5
+    check3(f"curl {n}", host(out).reshape(f.shape), O.curl_s(f, g), CURL32)
 
 
 @pytest.mark.parametrize("n,L", GRIDS32)
@@ -111,7 +131,7 @@ def test_phi_fp32_matches_oracle(n, L):
     ctx.precompute_kernel()
     out = torch.empty(j.size, dtype=torch.float64, device="cuda")
     ctx.phi(dev(j).reshape(-1), out)
-    assert rel(host(out).reshape(j.shape), O.phi_hockney(j, g)) < 2e-5
+    check3(f"phi {n}", host(out).reshape(j.shape), O.phi_hockney(j, g), PHI32)
 
 
 def test_phi_fp64_matches_direct_sum():
@@ -175,8 +195,7 @@ def test_rhs_fp32_fixed_iterations_all_x_lengths(n, L):
     hd = torch.empty(h.size, dtype=torch.float64, device="cuda")
     it = ctx.rhs(0.4, dev(h).reshape(-1), dev(g0).reshape(-1), hd)
     assert it == 3
-    err = rel(host(hd).reshape(h.shape), ref.hdot)
-    assert err < 2e-4, err
+    check3(f"rhs {n}", host(hd).reshape(h.shape), ref.hdot, RHS32)
 
 
 def test_rhs_fp32_graph_loop_equals_host_loop():
@@ -206,7 +225,7 @@ def test_rhs_fp32_graph_loop_equals_host_loop():
         assert l_g - l_h == it_g
         assert np.array_equal(v_g, v_h)
     assert abs(it_h - ref.iters) <= 1
-    assert rel(v_h.reshape(h.shape), ref.hdot) < 2e-4
+    check3("rhs lens32 early stop", v_h.reshape(h.shape), ref.hdot, RHS32)
 
 
 def test_rhs_fp32_error_is_stated():
@@ -218,8 +237,7 @@ def test_rhs_fp32_error_is_stated():
     ref = O.rhs(prob, 0.4, h, g0, delta_it=0.0, max_iter=3)
     hd = torch.empty(h.size, dtype=torch.float64, device="cuda")
     ctx.rhs(0.4, dev(h).reshape(-1), dev(g0).reshape(-1), hd)
-    err = rel(host(hd).reshape(h.shape), ref.hdot)
-    assert err < 2e-4, err
+    check3("rhs sphere32", host(hd).reshape(h.shape), ref.hdot, RHS32)
 
 
 def _cube_cfg():
@@ -323,3 +341,55 @@ def test_integrate_fp32_path_tracks_oracle():
         t, dt, _ = ctx2.step(t, dt, 0.1, h2, warm)
     ref2 = O.integrate(prob, 0.0, 0.1, np.zeros((3,) + prob.grid.shape), rtol=1e-4, atol=1e-7, dt0=1e-4)
     assert rel(host(h2).reshape(ref2.y.shape), ref2.y) < 2e-3
+
+
+@pytest.mark.parametrize("prec", [S.PREC_F64, S.PREC_F32])
+def test_rhs_ej_law_kim_and_anisotropy_matches_oracle(prec):
+    """The e(j, h) law of §2 (after Eq. 1) in place of the power law: Kim's jc(|h|) with the
+    anisotropic norm |A j|, through the x pass that reads the state h at every node."""
+    n, L = (32, 48, 32), (1.0, 1.2, 0.9)
+    mask = I.cube(n, L, 0.6 * min(L) * 2)
+    ctx, prob = make(n, L, mask, n_power=25.0, prec=prec, max_iter=3)
+    ctx.set_ej_law(kim_h0=0.3, aniso=(1.0, 0.7, 1.5))
+    prob.mat.kim_h0 = 0.3
+    prob.mat.aniso = (1.0, 0.7, 1.5)
+    h = _state(prob, 51)
+    g0 = I.random_field(h.shape, 52, 0.1)
+    ref = O.rhs(prob, 0.4, h, g0, delta_it=0.0, max_iter=3)
+    hd = torch.empty(h.size, dtype=torch.float64, device="cuda")
+    assert ctx.rhs(0.4, dev(h).reshape(-1), dev(g0).reshape(-1), hd) == 3
+    if prec == S.PREC_F64:
+        assert rel(host(hd).reshape(h.shape), ref.hdot) < 1e-10
+    else:
+        check3("rhs e(j,h) law", host(hd).reshape(h.shape), ref.hdot, RHS32)
+    # the reverse mode covers Eq. 1 only
+    mu = torch.empty_like(hd)
+    with pytest.raises(S.ScfftError) as ei:
+        ctx.rhs_vjp(dev(h).reshape(-1), hd, mu)
+    assert ei.value.code == 8
+    # back to Eq. 1: the plain power law again
+    ctx.set_ej_law()
+    prob.mat.kim_h0, prob.mat.aniso = 0.0, (1.0, 1.0, 1.0)
+    ref1 = O.rhs(prob, 0.4, h, g0, delta_it=0.0, max_iter=3)
+    ctx.rhs(0.4, dev(h).reshape(-1), dev(g0).reshape(-1), hd)
+    assert rel(host(hd).reshape(h.shape), ref1.hdot) < (1e-10 if prec == S.PREC_F64 else 6e-6)
+
+
+def test_integrate_ej_law_fixed_steps_fp64_matches_oracle():
+    """Fixed-step BS23 with the Kim / anisotropic law (Eq. 5 iterated to its fixed point)."""
+    cfg, prob = _cube_cfg()
+    prob.mat.kim_h0 = 0.2
+    prob.mat.aniso = (1.2, 1.0, 0.8)
+    dts = [0.002, 0.003, 0.004]
+    ctx = S.Context(cfg.n, cfg.L, n_power=cfg.n_power, rho_out=cfg.rho_out, delta_it=1e-13, max_iter=80)
+    ctx.set_geometry(cfg.mask)
+    ctx.set_field_path(cfg.knots_t, cfg.knots_he)
+    ctx.set_ej_law(kim_h0=0.2, aniso=(1.2, 1.0, 0.8))
+    ctx.precompute_kernel()
+    N = int(np.prod(cfg.n))
+    h = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+    t1 = float(np.sum(dts))
+    ctx.integrate(0.0, t1, dts[0], h, dt_fixed=dts)
+    ref = O.integrate(prob, 0.0, t1, np.zeros((3,) + prob.grid.shape), rtol=1e-6, atol=1e-9, dt0=dts[0],
+                      delta_it=1e-13, max_iter=80, dt_list=dts)
+    assert rel(host(h).reshape(ref.y.shape), ref.y) < 1e-10

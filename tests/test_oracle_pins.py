@@ -686,3 +686,61 @@ def test_step_adjoint_path_gradient_across_a_kink():
     pp.Khat = pm.Khat = prob.kernel()
     fd = (np.sum(lamT * run(pp).y) - np.sum(lamT * run(pm).y)) / (2 * eps)
     assert fd == pytest.approx(res.mu_path[9], rel=1e-6)
+
+
+# ---------------------------------------------------------------- e(j, h) variants
+def test_ej_variants_are_the_gradient_of_a_convex_potential():
+    """§2 after Eq. 1 allows e(j) or e(j, h) in place of the power law.  The variants here:
+    Kim's jc(|h|) = jc / (1 + |h|/h0) and an anisotropic norm |j|_A = |A j|.  e must be the
+    gradient in j of U = (e0 jc(h) / (n + 1)) (|j|_A / jc(h))^(n + 1) (checked by central
+    differences of U, which catches a wrong power of A or of jc), dissipate (e.j >= 0), reduce
+    to Eq. 1 for h0 = 0 and A = I, and give |e| = e0 at |j| = jc(h) in the isotropic case."""
+    rng = np.random.default_rng(21)
+    j = rng.standard_normal((3, 2, 3, 4)) * 0.6
+    h = rng.standard_normal((3, 2, 3, 4)) * 0.4
+    mask = np.ones((2, 3, 4), bool)
+    mat = O.Material(n=9.0, e0=1.3, jc=1.1, kim_h0=0.7, aniso=(1.0, 0.8, 1.6))
+    A = np.array(mat.aniso)[:, None, None, None]
+    jch = mat.jc / (1.0 + np.sqrt(np.sum(h * h, axis=0)) / mat.kim_h0)
+
+    def U(jj):
+        jA = np.sqrt(np.sum((A * jj) ** 2, axis=0))
+        return mat.e0 * jch / (mat.n + 1) * (jA / jch) ** (mat.n + 1)
+
+    e = O.electric_field(j, mask, mat, h)
+    eps = 1e-6
+    for q in range(3):
+        dj = np.zeros_like(j)
+        dj[q] = eps
+        fd = (U(j + dj) - U(j - dj)) / (2 * eps)
+        assert np.allclose(fd, e[q], rtol=1e-6, atol=1e-12)
+    assert np.all(np.sum(e * j, axis=0) >= 0)
+    iso = O.Material(n=9.0, e0=1.3, jc=1.1)
+    assert np.array_equal(O.electric_field(j, mask, iso, h), O.electric_field(j, mask, iso))
+    kim = O.Material(n=9.0, e0=1.3, jc=1.1, kim_h0=0.7)
+    unit = j / np.sqrt(np.sum(j * j, axis=0)) * jch
+    assert np.allclose(np.sqrt(np.sum(O.electric_field(unit, mask, kim, h) ** 2, axis=0)), 1.3, rtol=1e-12)
+
+
+def test_kim_law_slows_the_penetration_of_a_uniform_rate():
+    """Omega = box, n = 1 (Ohm's law with rho = e0/jc(h)): a Kim jc lowers the
+    conductivity where |h| is large, so a Fourier mode of h decays faster there; with a
+    uniform background field B the rate is exactly that of Ohm's law with
+    rho = (e0/jc)(1 + |h|/h0) at |h| ~ B (the mode is small), giving the closed form
+    dh/dt = -(e0/jc)(1 + B/h0) S^2 |k|^2 h' for the mode h' (to first order in its amplitude)."""
+    g = O.Grid((12, 10, 8), (1.0, 0.8, 1.2))
+    X, Y, Z = g.coords()
+    k = np.array([math.pi * 1 / g.L[0], math.pi * 2 / g.L[1], math.pi * 1 / g.L[2]])
+    a = np.cross(k, [0.3, -0.2, 0.9])
+    ph = k[0] * X + k[1] * Y + k[2] * Z
+    amp = 1e-7
+    mode = np.stack([amp * a[i] * np.sin(ph + 0.2) for i in range(3)])
+    B = np.array([0.0, 0.0, 2.0])[:, None, None, None]
+    h0 = 0.5
+    prob = O.Problem(g, np.ones(g.shape, bool), O.Material(n=1.0, kim_h0=h0),
+                     O.FieldPath([0.0, 1.0], [[0, 0, 0], [0, 0, 0.0]]))
+    r = O.rhs(prob, 0.5, B + mode, np.zeros_like(mode))
+    k2 = float(k @ k)
+    S2 = math.exp(-g.sigma ** 2 * k2)
+    expect = -(1.0 + 2.0 / h0) * S2 * k2 * mode
+    assert np.abs(r.hdot - expect).max() < 1e-5 * np.abs(expect).max()

@@ -57,3 +57,32 @@ def test_curl_noalloc_rejects_grids_beyond_its_maximum():
     f = torch.zeros(3 * 128 ** 3, dtype=torch.float64, device="cuda")
     out = torch.zeros_like(f)
     assert lib.scfft_curl_noalloc(ctypes.byref(grid), 1.0, f.data_ptr(), out.data_ptr(), None) == 9
+
+
+def test_curl_noalloc_near_its_maximum_on_a_side_stream():
+    # 64^3 nodes fill most of the 8 MiB scratch; the call runs on a non-default stream
+    lib = S.load_library()
+    n, L = (64, 64, 64), (1.6, 1.6, 1.6)
+    N = n[0] * n[1] * n[2]
+    grid = S._Grid(n[0], n[1], n[2], L[0], L[1], L[2])
+    ctx = S.Context(n, L)
+    side = torch.cuda.Stream()
+    for seed in (23, 24):
+        f = torch.from_numpy(I.random_field(3 * N, seed)).cuda()
+        ref = torch.empty_like(f)
+        ctx.curl(f, ref)
+        torch.cuda.synchronize()
+        out = torch.full_like(f, float("nan"))
+        code = lib.scfft_curl_noalloc(ctypes.byref(grid), 1.0, f.data_ptr(), out.data_ptr(),
+                                      ctypes.c_void_p(side.cuda_stream))
+        assert code == 0
+        side.synchronize()
+        assert _rel(out, ref) < 1e-12
+
+
+def test_curl_noalloc_rejects_a_non_finite_sigma():
+    lib = S.load_library()
+    grid = S._Grid(16, 16, 16, 1.0, 1.0, 1.0)
+    f = torch.zeros(3 * 16 ** 3, dtype=torch.float64, device="cuda")
+    out = torch.zeros_like(f)
+    assert lib.scfft_curl_noalloc(ctypes.byref(grid), float("inf"), f.data_ptr(), out.data_ptr(), None) == 1
