@@ -109,6 +109,18 @@ scfft_status scfft_set_geometry(scfft_ctx* ctx, const uint8_t* mask);
  * for the uniform material jc.  Copied (converted to the FFT precision). */
 scfft_status scfft_set_jc_map(scfft_ctx* ctx, const double* jc_dev);
 
+/* The discrete curl of the right-hand side (j = curl h of Eq. 4, -curl e of Eq. 3 and the
+ * curl of dh^i in Eq. 5).  SCFFT_CURL_SPECTRAL (the default) takes the derivatives in Fourier
+ * space with the Gaussian smoothing of §2 (the paper's choice).  SCFFT_CURL_FD is a local
+ * alternative the paper does not use: second-order central differences on the periodic grid,
+ * (f(i+1) - f(i-1)) / (2 d_a), no smoothing; the unpadded grid's FFT passes then drop out of
+ * every rhs.  scfft_curl keeps the spectral curl either way.  The reverse mode covers the
+ * spectral curl only (SCFFT_ESTATE otherwise).  EINVAL for another kind; ENOMEM if the
+ * stencil's buffer (3N values) cannot be allocated.  Synchronises the stream. */
+#define SCFFT_CURL_SPECTRAL 0
+#define SCFFT_CURL_FD 1
+scfft_status scfft_set_curl(scfft_ctx* ctx, int kind);
+
 /* The e(j, h) law in Omega.  §2 (after Eq. 1) notes that another current-voltage relation,
  * e(j) or e(j, h) with h the local magnetic field, can replace the power law; two are
  * provided, alone or together:
@@ -185,6 +197,22 @@ scfft_status scfft_integrate(scfft_ctx* ctx, double t0, double t1, double dt0, i
 scfft_status scfft_step(scfft_ctx* ctx, double* t, double* dt, double tstop, double* h, double* warm,
                         int* rejected);
 
+/* Up to nsteps accepted BS23 steps (the pair, error control and kink handling of scfft_step,
+ * the method of lines of §2) without the host between steps.  On the FP32 path the whole
+ * sequence is one CUDA graph launch: a WHILE node over trials whose body computes on the
+ * device the trial step, dh_e/dt and the Eq. 5 stop threshold at its stage times, the stage
+ * states, the three stage right-hand sides (each with its Eq. 5 loop as a nested WHILE node),
+ * the error norm and the step controller, and applies an accepted step.  The graph is built
+ * on the first call for the buffers h, warm and rebuilt when they or a setting change.  The
+ * call returns after nsteps accepted steps, or when t reaches tstop or the next kink of the
+ * path (the step that reaches it ends there, as in scfft_step), whichever comes first.  On
+ * the FP64 path, and while profiling, the host drives the same steps.  Results equal
+ * scfft_step's up to the rounding of the device's cos and pow in the path rate and the step
+ * controller.  h, warm: device, 3*N doubles, in/out; steps_done: host int* or NULL (accepted
+ * steps taken).  Statuses as scfft_step.  Synchronous. */
+scfft_status scfft_advance(scfft_ctx* ctx, double* t, double* dt, double tstop, int nsteps, double* h, double* warm,
+                           int* steps_done);
+
 /* scfft_step (one BS23 step of the method of lines of §2) with the state kept in host memory:
  * h_host, warm_host (host, 3*N doubles each,
  * in/out; page-locked memory makes the copies fast) are copied into h, warm (device, 3*N
@@ -247,15 +275,18 @@ scfft_status scfft_profile(scfft_ctx* ctx, int enable);
 scfft_status scfft_profile_read(scfft_ctx* ctx, long long* counts, double* ms);
 const char* scfft_kind_name(int kind);
 
-/* Batched instances: advance nb independent contexts (one problem each: its
- * own grid, geometry, material, applied-field path) by one accepted BS23 step
- * each, as scfft_step does, concurrently: the contexts' steps are driven from
- * up to 64 host threads, so the GPU overlaps the instances' kernels when each
- * context owns its own CUDA stream (give every context a distinct stream at
- * scfft_create).  t, dt, tstop: host arrays of nb; h, warm: host arrays of nb
- * device pointers (3N_i doubles each).  status: host array of nb or NULL
- * (per-instance result).  Returns the first non-OK status (all instances are
- * attempted).  Synchronous. */
+/* Batched instances: advance nb independent contexts (one problem each: its own grid,
+ * geometry, material, applied-field path) by one accepted BS23 step each, as scfft_step does.
+ * When every context computes in FP32 (and none is profiling), one CUDA graph launch advances
+ * them all: the graph holds each instance's trial loop (the device-resident step of
+ * scfft_advance) as a WHILE node of its own, side by side, so the instances run concurrently
+ * on the GPU with no host involvement between their kernels; the graph is kept and reused
+ * while the batch (contexts, buffers, settings) stays the same.  Otherwise the contexts'
+ * steps are driven from up to 64 host threads (give every context a distinct stream at
+ * scfft_create so that the GPU overlaps them).  t, dt, tstop: host arrays of nb; h, warm: host
+ * arrays of nb device pointers (3N_i doubles each).  status: host array of nb or NULL
+ * (per-instance result).  Returns the first non-OK status (all instances are attempted).
+ * Synchronous. */
 scfft_status scfft_batch_step(scfft_ctx** ctxs, int nb, double* t, double* dt, const double* tstop, double** h,
                               double** warm, scfft_status* status);
 

@@ -48,7 +48,7 @@ from scipy.special import erf
 
 __all__ = [
     "Grid", "Material", "FieldPath", "Problem",
-    "wavenumbers", "curl_s", "div_s", "electric_field",
+    "wavenumbers", "curl_s", "div_s", "curl_fd", "div_fd", "electric_field",
     "grad_green_sigma", "phi_direct", "phi_hockney", "hockney_kernel_spectrum",
     "rhs", "RhsResult",
     "BS23_C", "BS23_A", "BS23_B", "BS23_BHAT", "BS23_E",
@@ -139,6 +139,31 @@ def div_s(f: np.ndarray, grid: Grid) -> np.ndarray:
     Dx, Dy, Dz, S = _symbols(grid)
     F = np.fft.fftn(f, axes=(1, 2, 3))
     return np.real(np.fft.ifftn((Dx * F[0] + Dy * F[1] + Dz * F[2]) * S))
+
+
+def _dfd(f: np.ndarray, axis: int, d: float) -> np.ndarray:
+    """Second-order central difference (f[i+1] - f[i-1]) / (2 d) along an array axis of the
+    periodic grid."""
+    return (np.roll(f, -1, axis=axis) - np.roll(f, 1, axis=axis)) / (2.0 * d)
+
+
+def curl_fd(f: np.ndarray, grid: Grid) -> np.ndarray:
+    """Local-stencil curl (reading R-fd, an alternative to the smoothed spectral derivatives of
+    §2): second-order central differences on the periodic grid, no smoothing.  f has shape
+    (3, nz, ny, nx): array axis 2 is y, 1 is z, 3 is x."""
+    dx, dy, dz = grid.d
+    fx, fy, fz = f[0], f[1], f[2]
+    return np.stack([
+        _dfd(fz, 1, dy) - _dfd(fy, 0, dz),
+        _dfd(fx, 0, dz) - _dfd(fz, 2, dx),
+        _dfd(fy, 2, dx) - _dfd(fx, 1, dy),
+    ])
+
+
+def div_fd(f: np.ndarray, grid: Grid) -> np.ndarray:
+    """Divergence with the same central differences as curl_fd."""
+    dx, dy, dz = grid.d
+    return _dfd(f[0], 2, dx) + _dfd(f[1], 1, dy) + _dfd(f[2], 0, dz)
 
 
 # ----------------------------------------------------------------------------
@@ -347,11 +372,18 @@ class Problem:
     mat: Material
     path: FieldPath
     Khat: Optional[np.ndarray] = None
+    curl: str = "spectral"    # "spectral" (§2: smoothed spectral derivatives) or "fd" (reading R-fd)
 
     def kernel(self):
         if self.Khat is None:
             self.Khat = hockney_kernel_spectrum(self.grid)
         return self.Khat
+
+    def curl_op(self) -> Callable:
+        """The discrete curl of Eqs. 3-5 for this problem."""
+        if self.curl == "fd":
+            return lambda f: curl_fd(f, self.grid)
+        return lambda f: curl_s(f, self.grid)
 
 
 # ----------------------------------------------------------------------------
@@ -381,9 +413,10 @@ def rhs(prob: Problem, t: float, h: np.ndarray, g: np.ndarray, delta_it: float =
     if phi is None:
         Khat = prob.kernel()
         phi = lambda jj: phi_hockney(jj, grid, Khat)  # noqa: E731
-    j = curl_s(h, grid)
+    C = prob.curl_op()
+    j = C(h)
     e = electric_field(j, mask, mat, h)
-    hdot_in = -curl_s(e, grid) / mat.mu0
+    hdot_in = -C(e) / mat.mu0
     hd = np.where(mask[None], hdot_in, g)
     hed = prob.path.hedot(t, left=left)
     tol = delta_it * max(float(np.linalg.norm(hed)), 1.0)
@@ -394,7 +427,7 @@ def rhs(prob: Problem, t: float, h: np.ndarray, g: np.ndarray, delta_it: float =
     if nout == 0:  # Omega fills the box: Eq. 5 has nothing to iterate on
         return RhsResult(hd, 0, True, 0.0, res)
     for i in range(max_iter):
-        jdot_in = curl_s(hd, grid) * mask[None]
+        jdot_in = C(hd) * mask[None]
         P = phi(jdot_in)
         new = np.where(mask[None], hd, hed[:, None, None, None] + P)
         r = float(np.sum(np.sqrt(np.sum((new - hd) ** 2, axis=0))[out]) / nout)
@@ -561,7 +594,7 @@ def rhs_vjp(prob: Problem, t: float, h: np.ndarray, lam: np.ndarray, K: int, lef
     chi = mask[None].astype(float)
     chib = 1.0 - chi
     Khat = prob.kernel()
-    C = lambda f: curl_s(f, grid)  # noqa: E731
+    C = prob.curl_op()  # both curls are symmetric operators (odd symbols under a cross product)
     Phi = lambda f: phi_hockney(f, grid, Khat)  # noqa: E731
     # forward quantities the Jacobians need
     j = C(h)

@@ -24,6 +24,8 @@ __all__ = ["ScfftError", "Context", "load_library", "library_path", "PREC_F64", 
 PREC_F64 = 0
 PREC_F32 = 1
 FAULT_TMA_WAIT = 1  # scfft_inject_fault: the next directly launched TMA-fed y pass times out (tests)
+CURL_SPECTRAL = 0   # scfft_set_curl: smoothed spectral derivatives (§2)
+CURL_FD = 1         # scfft_set_curl: second-order central differences
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBNAME = "libscfft.so"
@@ -34,7 +36,8 @@ EXPORTS = ("scfft_create", "scfft_set_geometry", "scfft_set_jc_map", "scfft_set_
            "scfft_step", "scfft_profile", "scfft_profile_read", "scfft_kind_name",
            "scfft_rhs_vjp", "scfft_adjoint_integrate", "scfft_batch_step", "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy",
            "scfft_curl_noalloc", "scfft_last_cuda_error", "scfft_inject_fault", "scfft_checkpoint_save",
-           "scfft_checkpoint_load", "scfft_step_host", "scfft_adjoint_record", "scfft_adjoint_step", "scfft_set_ej_law")
+           "scfft_checkpoint_load", "scfft_step_host", "scfft_adjoint_record", "scfft_adjoint_step", "scfft_set_ej_law", "scfft_set_curl",
+           "scfft_advance")
 
 NKINDS = 14
 
@@ -129,6 +132,8 @@ def load_library(path: Optional[str] = None):
         "scfft_adjoint_record": (I, [P, P, I, P, P, I, P]),
         "scfft_adjoint_step": (I, [P, I, P, P, P]),
         "scfft_set_ej_law": (I, [P, ctypes.POINTER(_EjLaw)]),
+        "scfft_set_curl": (I, [P, I]),
+        "scfft_advance": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), D, I, P, P, ctypes.POINTER(I)]),
         "scfft_batch_step": (I, [P, I, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -225,6 +230,10 @@ class Context:
                         float(sin_t0), float(sin_t1), (ctypes.c_double * 3)(*[float(v) for v in sin_dir]))
         self._check(self._lib.scfft_set_field_path(self._h, ctypes.byref(fp)), "scfft_set_field_path")
 
+    def set_curl(self, kind: int):
+        """CURL_SPECTRAL (§2) or CURL_FD (central differences) for the curls of the rhs."""
+        self._check(self._lib.scfft_set_curl(self._h, int(kind)), "scfft_set_curl")
+
     def set_ej_law(self, kim_h0: float = 0.0, aniso=(1.0, 1.0, 1.0)):
         """The e(j, h) law in Omega (see scfft_set_ej_law): Kim's jc(|h|) = jc/(1 + |h|/kim_h0)
         and/or the anisotropic norm |j|_A = |diag(aniso) j|; the defaults are Eq. 1."""
@@ -266,6 +275,14 @@ class Context:
         self._check(self._lib.scfft_step(self._h, ctypes.byref(tt), ctypes.byref(dd), float(tstop), _ptr(h),
                                          _ptr(warm), ctypes.byref(rj)), "scfft_step")
         return tt.value, dd.value, rj.value
+
+    def advance(self, t: float, dt: float, tstop: float, nsteps: int, h, warm):
+        """Up to nsteps accepted BS23 steps without the host between steps (one CUDA graph
+        launch on the FP32 path); returns (t_new, dt_next, steps_taken)."""
+        tt, dd, nd = ctypes.c_double(t), ctypes.c_double(dt), ctypes.c_int(0)
+        self._check(self._lib.scfft_advance(self._h, ctypes.byref(tt), ctypes.byref(dd), float(tstop), int(nsteps),
+                                            _ptr(h), _ptr(warm), ctypes.byref(nd)), "scfft_advance")
+        return tt.value, dd.value, nd.value
 
     def step_host(self, t: float, dt: float, tstop: float, h_host, warm_host, h, warm):
         """One accepted BS23 step with the state in host memory (h_host, warm_host: CPU

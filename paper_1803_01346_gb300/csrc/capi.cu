@@ -20,7 +20,9 @@ using namespace scfft;
 namespace {
 constexpr int kProfPool = 1 << 14;  // event pairs buffered before a flush
 }
-struct AdjRec;  // a recorded trajectory of the reverse mode (defined with it below)
+struct AdjRec;   // a recorded trajectory of the reverse mode (defined with it below)
+struct StepDev;  // device state of scfft_advance (defined with it below)
+struct PathDev;  // the applied-field path on the device
 namespace {
 void free_rec(scfft_ctx* c);
 }
@@ -47,6 +49,9 @@ struct scfft_ctx {
   bool graph_pending = false;
   uint8_t* mask = nullptr;     // device
   long long nout = 0;
+  // curls of the rhs: SCFFT_CURL_SPECTRAL (§2) or SCFFT_CURL_FD (scfft_set_curl)
+  int curl_kind = SCFFT_CURL_SPECTRAL;
+  double dcell[3]{};  // cell sizes dx, dy, dz
   // e(j, h) law in Omega (scfft_set_ej_law); law = 0 is Eq. 1
   int law = 0;
   double kim_h0 = 0.0;
@@ -83,6 +88,20 @@ struct scfft_ctx {
   double* hadj_part = nullptr;  // pinned
   int adj_part_cap = 0;
   AdjRec* rec = nullptr;  // recorded trajectory of scfft_adjoint_record
+  // device-resident stepping (scfft_advance): step state, path, per-stage rhs parameters and
+  // the step graph (rebuilt when the buffers it was built on or any setting change)
+  StepDev* sdev = nullptr;     // device
+  StepDev* hsdev = nullptr;    // pinned host mirror
+  PathDev* pathd = nullptr;    // device
+  PointParams* ppsd = nullptr; // device, 3 stages
+  cudaGraph_t step_graph = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  const double* step_h = nullptr;
+  const double* step_warm = nullptr;
+  float* step_k[4] = {nullptr, nullptr, nullptr, nullptr};
+  unsigned long long step_epoch = 0;
+  unsigned long long epoch = 1;  // bumped by every setting the step graph bakes in
+  bool path_dirty = true;
   scfft_stats stats{};
   // profiling
   bool prof_on = false;
@@ -264,6 +283,7 @@ template <typename T> scfft_status alloc_work(scfft_ctx* c) {
 template <typename T> void free_work(Work<T>& w) {
   cudaFree(w.U); cudaFree(w.Pd); cudaFree(w.Hd[0]); cudaFree(w.Hd[1]); cudaFree(w.jc); cudaFree(w.kap); cudaFree(w.kap4);
   delete w.ym;
+  cudaFree(w.Jd);
   for (int a = 0; a < 3; ++a) { cudaFree(w.kt[a]); cudaFree(w.st[a]); cudaFree(w.twu[a]); cudaFree(w.twp[a]); }
   w = Work<T>();
 }
@@ -295,18 +315,37 @@ template <typename T> cudaError_t curl_in_U(scfft_ctx* c, const Launch<T>& L, bo
 }
 
 // One iteration of Eq. 5 (the i-th): U holds R2C_x of dh^i on entry and of dh^{i+1} on exit.
+// The masked stencil curl of the iterate and the zero-padded R2C of it (local-stencil curl option).
+template <typename T> cudaError_t fd_maskpad(scfft_ctx* c, const Launch<T>& L, const PointParams& pp, bool chk) {
+  cudaError_t e;
+  if ((e = run(c, SCFFT_K_Z_CURL, [&] { return launch_fd_curl_mask<T>(L, L.w->Jd, c->dcell, chk); })) != cudaSuccess)
+    return e;
+  return run(c, SCFFT_K_X_MASKPAD, [&] {
+    if constexpr (sizeof(T) == 4)
+      return launch_x_reg_io(L, X_PAD_F64, pp, nullptr, L.w->Jd, nullptr, nullptr, nullptr, 0, 0, chk);
+    else
+      return launch_x<T>(L, X_PAD_F64, pp, L.w->Jd, nullptr, nullptr, 0, 0, chk);
+  });
+}
+
 template <typename T> cudaError_t iteration(scfft_ctx* c, const Launch<T>& L, PointParams pp, int i, bool chk) {
   cudaError_t e;
-  if ((e = curl_in_U<T>(c, L, chk)) != cudaSuccess) return e;
-  if ((e = run(c, SCFFT_K_X_MASKPAD,
-               [&] { return launch_x<T>(L, X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, chk); })) != cudaSuccess)
-    return e;
+  const bool fd = c->curl_kind == SCFFT_CURL_FD;
+  if (fd) {
+    if ((e = fd_maskpad<T>(c, L, pp, chk)) != cudaSuccess) return e;
+  } else {
+    if ((e = curl_in_U<T>(c, L, chk)) != cudaSuccess) return e;
+    if ((e = run(c, SCFFT_K_X_MASKPAD,
+                 [&] { return launch_x<T>(L, X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, chk); })) != cudaSuccess)
+      return e;
+  }
   if ((e = run(c, SCFFT_K_Y_FWD_P, [&] { return launch_y<T>(L, true, false, chk); })) != cudaSuccess) return e;
   if ((e = run(c, SCFFT_K_Z_KERNEL, [&] { return launch_z_kernel<T>(L, chk); })) != cudaSuccess) return e;
   if ((e = run(c, SCFFT_K_Y_INV_P, [&] { return launch_y<T>(L, true, true, chk); })) != cudaSuccess) return e;
   pp.iter = i;
-  return run(c, SCFFT_K_X_UPDATE,
-             [&] { return launch_x<T>(L, X_UPDATE, pp, nullptr, nullptr, nullptr, i & 1, (i + 1) & 1, chk); });
+  return run(c, SCFFT_K_X_UPDATE, [&] {
+    return launch_x<T>(L, fd ? X_UPDATE_FD : X_UPDATE, pp, nullptr, nullptr, nullptr, i & 1, (i + 1) & 1, chk);
+  });
 }
 
 // ---------------------------------------------------------------- Eq. 5 loop as a CUDA graph
@@ -324,18 +363,28 @@ __global__ void loop_cond_kernel(cudaGraphConditionalHandle h, Ctrl* ctrl, int m
   cudaGraphSetConditional(h, go);
 }
 
-constexpr int kLoopLaunches = 9;  // kernels per iteration of the graph body
+constexpr int kLoopLaunches = 9;    // kernels per iteration of the graph body
+constexpr int kLoopLaunchesFd = 7;  // the same with the local-stencil curl
 
-cudaError_t loop_body(const Launch<float>& L, const PointParams& pp, cudaGraphConditionalHandle h, int max_iter) {
+cudaError_t loop_body(const Launch<float>& L, const PointParams& pp, cudaGraphConditionalHandle h, int max_iter,
+                      bool fd, const double* dcell) {
   cudaError_t e;
-  if ((e = launch_y<float>(L, false, false, false)) != cudaSuccess) return e;
-  if ((e = launch_z_curl<float>(L, false, 1.0 / (double)L.g.N)) != cudaSuccess) return e;
-  if ((e = launch_y<float>(L, false, true, false)) != cudaSuccess) return e;
-  if ((e = launch_x<float>(L, X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, false)) != cudaSuccess) return e;
+  if (fd) {
+    if ((e = launch_fd_curl_mask<float>(L, L.w->Jd, dcell, false)) != cudaSuccess) return e;
+    if ((e = launch_x_reg_io(L, X_PAD_F64, pp, nullptr, L.w->Jd, nullptr, nullptr, nullptr, 0, 0, false)) !=
+        cudaSuccess)
+      return e;
+  } else {
+    if ((e = launch_y<float>(L, false, false, false)) != cudaSuccess) return e;
+    if ((e = launch_z_curl<float>(L, false, 1.0 / (double)L.g.N)) != cudaSuccess) return e;
+    if ((e = launch_y<float>(L, false, true, false)) != cudaSuccess) return e;
+    if ((e = launch_x<float>(L, X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, false)) != cudaSuccess) return e;
+  }
   if ((e = launch_y<float>(L, true, false, false)) != cudaSuccess) return e;
   if ((e = launch_z_kernel<float>(L, false)) != cudaSuccess) return e;
   if ((e = launch_y<float>(L, true, true, false)) != cudaSuccess) return e;
-  if ((e = launch_x<float>(L, X_UPDATE, pp, nullptr, nullptr, nullptr, 0, 1, false)) != cudaSuccess) return e;
+  if ((e = launch_x<float>(L, fd ? X_UPDATE_FD : X_UPDATE, pp, nullptr, nullptr, nullptr, 0, 1, false)) != cudaSuccess)
+    return e;
   loop_cond_kernel<<<1, 1, 0, L.st>>>(h, L.ctrl, max_iter);
   return cudaGetLastError();
 }
@@ -375,7 +424,8 @@ bool loop_graph_ready(scfft_ctx* c) {
     cudaGraph_t body = np.conditional.phGraph_out[0];
     ok = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
     if (ok) {
-      const bool launched = loop_body(L, pp, h, c->opt.max_iter) == cudaSuccess;
+      const bool launched =
+          loop_body(L, pp, h, c->opt.max_iter, c->curl_kind == SCFFT_CURL_FD, c->dcell) == cudaSuccess;
       cudaGraph_t captured = nullptr;
       ok = cudaStreamEndCapture(cs, &captured) == cudaSuccess && launched;
     }
@@ -426,7 +476,8 @@ void absorb_ctrl(scfft_ctx* c, const Ctrl& hc, bool graph_iters) {
   const unsigned long long d = hc.iter_total - c->iters_seen;
   c->iters_seen = hc.iter_total;
   c->stats.iterations += (long long)d;
-  if (graph_iters) c->stats.launches += (long long)kLoopLaunches * (long long)d;
+  if (graph_iters)
+    c->stats.launches += (long long)(c->curl_kind == SCFFT_CURL_FD ? kLoopLaunchesFd : kLoopLaunches) * (long long)d;
   c->stats.last_iters = hc.iters;
   c->stats.last_residual = hc.residual;
   c->graph_pending = false;
@@ -456,16 +507,29 @@ scfft_status rhs_impl(scfft_ctx* c, double t, int left, const RhsIO& io, int* it
   const double hn = sqrt(pp.hedot[0] * pp.hedot[0] + pp.hedot[1] * pp.hedot[1] + pp.hedot[2] * pp.hedot[2]);
   pp.tol = c->opt.delta_it * (hn > 1.0 ? hn : 1.0);
   // pre-stage: j = curl h; e = rho(j) j; dh^0 = -curl e / mu0 on Omega, warm on Omega_out
-  CK(run(c, SCFFT_K_X_FWD, [&] { return x_io<T>(L, X_FWD_F64, pp, io); }));
-  CK(curl_in_U<T>(c, L, false));
-  if (c->law) {  // the e(j, h) law reads the state h at each node
-    CK(run(c, SCFFT_K_X_POWERLAW, [&] { return x_io<T>(L, X_POWERLAW_H, pp, io); }));
+  if (c->curl_kind == SCFFT_CURL_FD) {
+    // two stencil passes: e (into the second iterate buffer, free here), then dh^0
+    T* ebuf = L.w->Hd[1];
+    CK(run(c, SCFFT_K_X_POWERLAW, [&] {
+      if constexpr (sizeof(T) == 4) return launch_fd_efield<T>(L, pp, io.h64, io.h32, c->dcell, ebuf);
+      else return launch_fd_efield<T>(L, pp, io.h64, nullptr, c->dcell, ebuf);
+    }));
+    CK(run(c, SCFFT_K_X_ASSEMBLE, [&] {
+      if constexpr (sizeof(T) == 4) return launch_fd_assemble<T>(L, pp, ebuf, io.warm64, io.warm32, c->dcell);
+      else return launch_fd_assemble<T>(L, pp, ebuf, io.warm64, nullptr, c->dcell);
+    }));
   } else {
-    CK(run(c, SCFFT_K_X_POWERLAW,
-           [&] { return launch_x<T>(L, X_POWERLAW, pp, nullptr, nullptr, nullptr, 0, 0, false); }));
+    CK(run(c, SCFFT_K_X_FWD, [&] { return x_io<T>(L, X_FWD_F64, pp, io); }));
+    CK(curl_in_U<T>(c, L, false));
+    if (c->law) {  // the e(j, h) law reads the state h at each node
+      CK(run(c, SCFFT_K_X_POWERLAW, [&] { return x_io<T>(L, X_POWERLAW_H, pp, io); }));
+    } else {
+      CK(run(c, SCFFT_K_X_POWERLAW,
+             [&] { return launch_x<T>(L, X_POWERLAW, pp, nullptr, nullptr, nullptr, 0, 0, false); }));
+    }
+    CK(curl_in_U<T>(c, L, false));
+    CK(run(c, SCFFT_K_X_ASSEMBLE, [&] { return x_io<T>(L, X_ASSEMBLE, pp, io); }));
   }
-  CK(curl_in_U<T>(c, L, false));
-  CK(run(c, SCFFT_K_X_ASSEMBLE, [&] { return x_io<T>(L, X_ASSEMBLE, pp, io); }));
   const int maxit = c->opt.max_iter;
   const bool early = c->opt.delta_it > 0 && c->nout > 0;
   int launched = 0;
@@ -939,6 +1003,467 @@ scfft_status bs23_step_f32(scfft_ctx* c, double* t_io, double* dt_io, double tst
   }
 }
 
+// ---------------------------------------------------------------- device-resident stepping
+// scfft_advance runs up to K accepted BS23 steps of the FP32 path as one CUDA graph launch:
+// a WHILE conditional node over trials whose body computes, on the device, the trial step and
+// the rhs parameters of its three stages (dh_e/dt of the path and the Eq. 5 stop threshold at
+// each stage time), the stage states, the three stage rhs (each with its Eq. 5 loop as a
+// nested WHILE node), the candidate, the error norm, and the step controller (accept or
+// reject, the next step size), then applies an accepted step.  The host reads the step state
+// back once, after the launch.
+}  // namespace
+
+struct PathDev {
+  int nk;
+  int pad_;
+  double kt[64];
+  double khe[3 * 64];
+  double sin_amp, sin_period, sin_t0, sin_t1;
+  double sin_dir[3];
+};
+
+struct StepDev {
+  double t, dt, tlim, hs;      // time, proposed step, stop of this launch, trial step
+  double delta_it;             // Eq. 5 tolerance
+  double rtol, atol;
+  int hits, end_left;          // the trial ends on tlim; tlim is a kink (left derivative there)
+  int tlim_kink;
+  int accepted;                // the last trial was accepted
+  int steps, target;           // accepted steps so far, wanted
+  int trials, max_trials;
+  int status;                  // scfft_status of a device-side failure
+  unsigned errbits;            // error norm (float bits; integer max of nonnegative floats)
+};
+
+namespace {
+
+// dh_e/dt at t on the device (the host's hedot_at, term by term)
+__device__ void hedot_dev(const PathDev* p, double t, int left, double out[3]) {
+  out[0] = out[1] = out[2] = 0.0;
+  for (int s = 0; s + 1 < p->nk; ++s) {
+    const double lo = p->kt[s], hi = p->kt[s + 1];
+    const bool in = left ? (lo < t && t <= hi) : (lo <= t && t < hi);
+    if (in) {
+      for (int a = 0; a < 3; ++a) out[a] = (p->khe[3 * (s + 1) + a] - p->khe[3 * s + a]) / (hi - lo);
+      break;
+    }
+  }
+  if (p->sin_amp != 0) {
+    const bool in = left ? (p->sin_t0 < t && t <= p->sin_t1) : (p->sin_t0 <= t && t < p->sin_t1);
+    if (in) {
+      const double w = 2 * M_PI / p->sin_period;
+      const double v = p->sin_amp * w * cos(w * (t - p->sin_t0));
+      for (int a = 0; a < 3; ++a) out[a] += v * p->sin_dir[a];
+    }
+  }
+}
+
+__global__ void step_begin_kernel(StepDev* sd, const PathDev* path, PointParams base, PointParams* pps) {
+  const double t = sd->t;
+  double hs = fmin(sd->dt, sd->tlim - t);
+  const int hits = hs == sd->tlim - t;
+  if (!(hs > 1e-14 * fmax(1.0, fabs(t)))) {
+    sd->status = SCFFT_ESTEP;
+    hs = 0.0;
+  }
+  sd->hs = hs;
+  sd->hits = hits;
+  sd->end_left = hits && sd->tlim_kink;
+  sd->errbits = 0u;
+  sd->trials += 1;
+  const double ts[3] = {t + 0.5 * hs, t + 0.75 * hs, hits ? sd->tlim : t + hs};
+  const int left[3] = {0, 0, sd->end_left};
+  for (int s = 0; s < 3; ++s) {
+    PointParams pp = base;
+    hedot_dev(path, ts[s], left[s], pp.hedot);
+    const double hn = sqrt(pp.hedot[0] * pp.hedot[0] + pp.hedot[1] * pp.hedot[1] + pp.hedot[2] * pp.hedot[2]);
+    pp.tol = sd->delta_it * (hn > 1.0 ? hn : 1.0);
+    pps[s] = pp;
+  }
+}
+
+__global__ void combine32d_kernel(float* __restrict__ out, const double* __restrict__ y, const StepDev* sd, float c1,
+                                  const float* __restrict__ k1, float c2, const float* __restrict__ k2, long long n) {
+  const float h = (float)sd->hs;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    float s = c1 * k1[i];
+    if (k2) s += c2 * k2[i];
+    out[i] = (float)y[i] + h * s;
+  }
+}
+
+__global__ void candidate32d_kernel(double* __restrict__ ynew, float* __restrict__ d, const double* __restrict__ y,
+                                    const StepDev* sd, float b1, const float* __restrict__ k1, float b2,
+                                    const float* __restrict__ k2, float b3, const float* __restrict__ k3, long long n) {
+  const float h = (float)sd->hs;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float di = h * (b1 * k1[i] + b2 * k2[i] + b3 * k3[i]);
+    d[i] = di;
+    ynew[i] = y[i] + (double)di;
+  }
+}
+
+__global__ void errnorm32d_kernel(const double* __restrict__ y, const double* __restrict__ yn, StepDev* sd, float e1,
+                                  const float* __restrict__ k1, float e2, const float* __restrict__ k2, float e3,
+                                  const float* __restrict__ k3, float e4, const float* __restrict__ k4, float rtol,
+                                  float atol, long long n) {
+  const float h = (float)sd->hs;
+  float m = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float e = h * (e1 * k1[i] + e2 * k2[i] + e3 * k3[i] + e4 * k4[i]);
+    const float w = fmaxf(rtol * fmaxf(abs_f32_of(y[i]), abs_f32_of(yn[i])), atol);
+    const float r = fabsf(e) / w;
+    m = (r > m || r != r) ? r : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float q = __shfl_xor_sync(0xffffffffu, m, o);
+    m = (q > m || q != q) ? q : m;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(&sd->errbits, __float_as_uint(m));
+}
+
+// accept or reject the trial, propose the next step (the host controller's rule), and set
+// the trial loop's condition
+__global__ void step_end_kernel(StepDev* sd, const Ctrl* ctrl, cudaGraphConditionalHandle h) {
+  const double en = (double)__uint_as_float(sd->errbits);
+  if (sd->status == 0 && ctrl->status != 0) sd->status = ctrl->status;
+  if (sd->status == 0 && !(en == en)) sd->status = SCFFT_ENONFINITE;
+  sd->accepted = 0;
+  if (sd->status == 0) {
+    const double hs = sd->hs;
+    if (en <= 1.0) {
+      sd->accepted = 1;
+      sd->t = sd->hits ? sd->tlim : sd->t + hs;
+      const double fac = en == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(en, -1.0 / 3.0)));
+      sd->dt = hs * fac;
+      sd->steps += 1;
+    } else {
+      sd->dt = hs * fmax(0.2, 0.9 * pow(en, -1.0 / 3.0));
+    }
+  }
+  const bool go = sd->status == 0 && sd->steps < sd->target && !(sd->accepted && sd->hits) &&
+                  sd->trials < sd->max_trials;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// an accepted trial: y <- y + d (Kahan), the caller's warm start <- the last rhs result, and the
+// first stage of the next step <- the last stage (FSAL)
+__global__ void accept32d_kernel(double* __restrict__ y, double* __restrict__ c, const float* __restrict__ d,
+                                 const float* __restrict__ last, double* __restrict__ warm, float* __restrict__ k0,
+                                 const StepDev* sd, long long n) {
+  if (!sd->accepted) return;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double yi = y[i];
+    const double u = (double)d[i] - c[i];
+    const double t = yi + u;
+    c[i] = (t - yi) - u;
+    y[i] = t;
+    const float l = last[i];
+    warm[i] = (double)l;
+    k0[i] = l;
+  }
+}
+
+__global__ void set_cond_kernel(cudaGraphConditionalHandle h) { cudaGraphSetConditional(h, 1u); }
+
+// Add a WHILE node running the Eq. 5 loop body at the current point of the capture on cs;
+// its body is captured on cs2.  The handle is set to 1 by a kernel just before the node (a
+// default value applies only at the start of each top-level launch).
+bool capture_eq5_loop(scfft_ctx* c, cudaStream_t cs, cudaStream_t cs2, const PointParams& pp) {
+  cudaGraphConditionalHandle hh{};
+  cudaStreamCaptureStatus stc;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(cs, &stc, nullptr, &g, &deps, nullptr, &nd) != cudaSuccess ||
+      stc != cudaStreamCaptureStatusActive)
+    return false;
+  if (cudaGraphConditionalHandleCreate(&hh, g, 0, 0) != cudaSuccess) return false;
+  set_cond_kernel<<<1, 1, 0, cs>>>(hh);
+  if (cudaGetLastError() != cudaSuccess) return false;
+  if (cudaStreamGetCaptureInfo(cs, &stc, nullptr, &g, &deps, nullptr, &nd) != cudaSuccess) return false;
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = hh;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node{};
+  if (cudaGraphAddNode(&node, g, deps, nullptr, nd, &np) != cudaSuccess) return false;
+  if (cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+    return false;
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  if (cudaStreamBeginCaptureToGraph(cs2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return false;
+  Launch<float> L2 = launch_of<float>(c);
+  L2.st = cs2;
+  L2.fault = nullptr;
+  const bool ok = loop_body(L2, pp, hh, c->opt.max_iter, c->curl_kind == SCFFT_CURL_FD, c->dcell) == cudaSuccess;
+  cudaGraph_t captured = nullptr;
+  return cudaStreamEndCapture(cs2, &captured) == cudaSuccess && ok;
+}
+
+// One stage rhs of the FP32 path captured on cs: the pre-stage passes with the stage's
+// parameters read from the device (pps), the Eq. 5 loop, and the result into out.
+bool capture_stage(scfft_ctx* c, cudaStream_t cs, cudaStream_t cs2, const PointParams* pps, const double* h64,
+                   const float* h32, const float* warm32, float* out) {
+  Launch<float> L = launch_of<float>(c);
+  L.st = cs;
+  L.fault = nullptr;
+  L.pps = pps;
+  const PointParams pp = base_params(c);
+  if (c->curl_kind == SCFFT_CURL_FD) {
+    if (launch_fd_efield<float>(L, pp, h64, h32, c->dcell, L.w->Hd[1]) != cudaSuccess) return false;
+    if (launch_fd_assemble<float>(L, pp, L.w->Hd[1], nullptr, warm32, c->dcell) != cudaSuccess) return false;
+  } else {
+    if (launch_x_reg_io(L, X_FWD_F64, pp, h64, h32, nullptr, nullptr, nullptr, 0, 0, false) != cudaSuccess) return false;
+    if (launch_y<float>(L, false, false, false) != cudaSuccess) return false;
+    if (launch_z_curl<float>(L, false, 1.0 / (double)L.g.N) != cudaSuccess) return false;
+    if (launch_y<float>(L, false, true, false) != cudaSuccess) return false;
+    const cudaError_t e = c->law ? launch_x_reg_io(L, X_POWERLAW_H, pp, h64, h32, nullptr, nullptr, nullptr, 0, 0, false)
+                                 : launch_x<float>(L, X_POWERLAW, pp, nullptr, nullptr, nullptr, 0, 0, false);
+    if (e != cudaSuccess) return false;
+    if (launch_y<float>(L, false, false, false) != cudaSuccess) return false;
+    if (launch_z_curl<float>(L, false, 1.0 / (double)L.g.N) != cudaSuccess) return false;
+    if (launch_y<float>(L, false, true, false) != cudaSuccess) return false;
+    if (launch_x_reg_io(L, X_ASSEMBLE, pp, nullptr, nullptr, nullptr, nullptr, warm32, 0, 0, false) != cudaSuccess)
+      return false;
+  }
+  if (c->nout > 0 && c->opt.max_iter > 0 && !capture_eq5_loop(c, cs, cs2, pp)) return false;
+  const long long n3 = 3 * c->g.N;
+  finalize_f32_kernel<<<(int)std::min<long long>((n3 + 255) / 256, 152 * 8), 256, 0, cs>>>(c->wf.Hd[0], c->wf.Hd[1],
+                                                                                          c->ctrl, out, n3);
+  return cudaGetLastError() == cudaSuccess;
+}
+
+// Add the trial loop of context c for the state buffers h, warm (FP32 path) to graph g as a
+// WHILE node with no dependencies; false if the driver refuses any part.
+bool add_step_loop(scfft_ctx* c, cudaGraph_t g, double* h, double* warm) {
+  cudaStream_t cs = nullptr, cs2 = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&cs2, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cs) cudaStreamDestroy(cs);
+    cudaGetLastError();
+    return false;
+  }
+  const long long n3 = 3 * c->g.N;
+  const int blocks = blocks_for(n3);
+  float** k = c->k32;
+  const float a21 = 0.5f, a32 = 0.75f, b1 = 2.0f / 9.0f, b2 = 1.0f / 3.0f, b3 = 4.0f / 9.0f;
+  const float e1 = (float)(2.0 / 9.0 - 7.0 / 24.0), e2 = (float)(1.0 / 3.0 - 0.25),
+              e3 = (float)(4.0 / 9.0 - 1.0 / 3.0), e4 = -0.125f;
+  cudaGraphConditionalHandle hw{};
+  bool ok = cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphNodeParams np{};
+  cudaGraphNode_t node{};
+  if (ok) {
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hw;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+  }
+  if (ok) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+    if (ok) {
+      bool good = true;
+      step_begin_kernel<<<1, 1, 0, cs>>>(c->sdev, c->pathd, base_params(c), c->ppsd);
+      good = good && cudaGetLastError() == cudaSuccess;
+      // stage 2: the warm start is the most recent rhs result, kept in k[3]
+      combine32d_kernel<<<blocks, 256, 0, cs>>>(c->ytmp32, h, c->sdev, a21, k[0], 0.f, nullptr, n3);
+      good = good && cudaGetLastError() == cudaSuccess &&
+             capture_stage(c, cs, cs2, c->ppsd + 0, nullptr, c->ytmp32, k[3], k[1]);
+      combine32d_kernel<<<blocks, 256, 0, cs>>>(c->ytmp32, h, c->sdev, 0.f, k[0], a32, k[1], n3);
+      good = good && cudaGetLastError() == cudaSuccess &&
+             capture_stage(c, cs, cs2, c->ppsd + 1, nullptr, c->ytmp32, k[1], k[2]);
+      candidate32d_kernel<<<blocks, 256, 0, cs>>>(c->ynew64, c->d32, h, c->sdev, b1, k[0], b2, k[1], b3, k[2], n3);
+      good = good && cudaGetLastError() == cudaSuccess &&
+             capture_stage(c, cs, cs2, c->ppsd + 2, c->ynew64, nullptr, k[2], k[3]);
+      errnorm32d_kernel<<<blocks, 256, 0, cs>>>(h, c->ynew64, c->sdev, e1, k[0], e2, k[1], e3, k[2], e4, k[3],
+                                                 (float)c->opt.rtol, (float)c->opt.atol, n3);
+      step_end_kernel<<<1, 1, 0, cs>>>(c->sdev, c->ctrl, hw);
+      accept32d_kernel<<<blocks, 256, 0, cs>>>(h, c->comp64, c->d32, k[3], warm, k[0], c->sdev, n3);
+      good = good && cudaGetLastError() == cudaSuccess;
+      cudaGraph_t captured = nullptr;
+      ok = cudaStreamEndCapture(cs, &captured) == cudaSuccess && good;
+    }
+  }
+  cudaStreamDestroy(cs);
+  cudaStreamDestroy(cs2);
+  if (!ok) cudaGetLastError();
+  return ok;
+}
+
+// the step graph of one context for the buffers h, warm
+bool build_step_graph(scfft_ctx* c, double* h, double* warm) {
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  if (c->step_graph) cudaGraphDestroy(c->step_graph);
+  c->step_exec = nullptr;
+  c->step_graph = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess && add_step_loop(c, g, h, warm);
+  if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  if (!ok) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return false;
+  }
+  c->step_graph = g;
+  c->step_exec = ex;
+  c->step_h = h;
+  c->step_warm = warm;
+  for (int i = 0; i < 4; ++i) c->step_k[i] = c->k32[i];
+  c->step_epoch = c->epoch;
+  return true;
+}
+
+// kernels launched per trial of the step graph outside the Eq. 5 loops
+int step_graph_launches(const scfft_ctx* c) {
+  const int pre = c->curl_kind == SCFFT_CURL_FD ? 2 : 9;
+  return 3 * (pre + 2) + 2 + 1 + 1 + 1 + 1;  // stages (+ cond set, finalize), combines, candidate, norm, end, accept
+}
+
+// Everything before the graph launch of scfft_advance on the context's stream: step state,
+// path, the first stage (computed unless FSAL), the buffer roles the graph was built on.
+// need_graph: the context's own step graph must be (re)built for h, warm.
+scfft_status advance_prologue(scfft_ctx* c, double t, double dt, double tstop, int nsteps, double* h, double* warm,
+                              bool* need_graph) {
+  CS_(ensure_rk32(c));
+  const long long n3 = 3 * c->g.N;
+  const int blocks = blocks_for(n3);
+  if (!c->sdev) {
+    if (cudaMalloc(&c->sdev, sizeof(StepDev)) != cudaSuccess || cudaMalloc(&c->pathd, sizeof(PathDev)) != cudaSuccess ||
+        cudaMalloc(&c->ppsd, 3 * sizeof(PointParams)) != cudaSuccess ||
+        cudaHostAlloc(&c->hsdev, sizeof(StepDev), 0) != cudaSuccess) {
+      cudaGetLastError();
+      return SCFFT_ENOMEM;
+    }
+  }
+  if (c->path_dirty) {
+    PathDev p{};
+    p.nk = (int)c->kt.size();
+    for (int i = 0; i < p.nk; ++i) p.kt[i] = c->kt[i];
+    for (int i = 0; i < 3 * p.nk; ++i) p.khe[i] = c->khe[i];
+    p.sin_amp = c->sin_amp;
+    p.sin_period = c->sin_period;
+    p.sin_t0 = c->sin_t0;
+    p.sin_t1 = c->sin_t1;
+    for (int a = 0; a < 3; ++a) p.sin_dir[a] = c->sin_dir[a];
+    CK(cudaMemcpy(c->pathd, &p, sizeof(p), cudaMemcpyHostToDevice));
+    c->path_dirty = false;
+  }
+  if (c->graph_pending) CS_(flush_pending(c));
+  const std::vector<double> kinks = kinks_of(c);
+  double tlim = tstop;
+  for (double v : kinks)
+    if (v > t && v < tlim) tlim = v;
+  const bool tlim_kink = tlim < tstop || std::binary_search(kinks.begin(), kinks.end(), tlim);
+  // the first stage: reused (FSAL) or computed here, as scfft_step does
+  if (!(c->fsal_valid && c->fsal_t == t && c->fsal_h == h && c->fsal_g == warm)) {
+    CK(run(c, SCFFT_K_RK, [&] {
+      f64_to_f32_kernel<<<blocks, 256, 0, c->st>>>(warm, c->g32, n3);
+      return cudaGetLastError();
+    }));
+    CK(cudaMemsetAsync(c->comp64, 0, sizeof(double) * n3, c->st));
+    CS_(rhs32(c, t, 0, h, nullptr, c->g32, c->k32[0]));
+    if (c->graph_pending) CS_(flush_pending(c));
+  }
+  // the graph keeps its own buffer roles: first stage in step_k[0], most recent rhs result in step_k[3]
+  if (c->step_k[0] && c->k32[0] != c->step_k[0]) {
+    CK(cudaMemcpyAsync(c->step_k[0], c->k32[0], sizeof(float) * n3, cudaMemcpyDeviceToDevice, c->st));
+    if (c->last32 == c->k32[0]) c->last32 = c->step_k[0];
+    for (int i = 0; i < 4; ++i) c->k32[i] = c->step_k[i];
+  }
+  if (c->last32 != c->k32[3]) {
+    CK(cudaMemcpyAsync(c->k32[3], c->last32, sizeof(float) * n3, cudaMemcpyDeviceToDevice, c->st));
+    c->last32 = c->k32[3];
+  }
+  *need_graph = !c->step_exec || c->step_h != h || c->step_warm != warm || c->step_epoch != c->epoch;
+  StepDev sd{};
+  sd.t = t;
+  sd.dt = dt;
+  sd.tlim = tlim;
+  sd.tlim_kink = tlim_kink ? 1 : 0;
+  sd.delta_it = c->opt.delta_it;
+  sd.rtol = c->opt.rtol;
+  sd.atol = c->opt.atol;
+  sd.target = nsteps;
+  sd.max_trials = 100 * nsteps + 100;
+  *c->hsdev = sd;
+  CK(cudaMemcpyAsync(c->sdev, c->hsdev, sizeof(StepDev), cudaMemcpyHostToDevice, c->st));
+  return SCFFT_OK;
+}
+
+// the read-back of the step state, queued on stream st after the graph
+cudaError_t advance_readback(scfft_ctx* c, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(c->hsdev, c->sdev, sizeof(StepDev), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->hctrl + 2, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+  return e;
+}
+
+// after the read-back has completed: statistics, time, step size, FSAL
+scfft_status advance_epilogue(scfft_ctx* c, double* t_io, double* dt_io, double* h, double* warm, int* done) {
+  const StepDev r = *c->hsdev;
+  absorb_ctrl(c, c->hctrl[2], true);
+  c->stats.rhs_calls += 3LL * r.trials;
+  c->stats.launches += (long long)step_graph_launches(c) * r.trials;
+  c->stats.accepted += r.steps;
+  c->stats.rejected += r.trials - r.steps;
+  c->last32 = c->k32[3];
+  *done = r.steps;
+  if (r.status != 0) {
+    c->fsal_valid = false;
+    return (scfft_status)r.status;
+  }
+  *t_io = r.t;
+  *dt_io = r.dt;
+  c->stats.t = r.t;
+  c->stats.dt = r.dt;
+  const bool kink_end = r.accepted && r.hits && r.end_left;
+  c->fsal_valid = r.steps > 0 ? !kink_end : c->fsal_valid;
+  if (c->fsal_valid) {
+    c->fsal_t = r.t;
+    c->fsal_h = h;
+    c->fsal_g = warm;
+  }
+  return SCFFT_OK;
+}
+
+scfft_status advance_f32(scfft_ctx* c, double* t_io, double* dt_io, double tstop, int nsteps, double* h,
+                         double* warm, int* done) {
+  bool need_graph = false;
+  CS_(advance_prologue(c, *t_io, *dt_io, tstop, nsteps, h, warm, &need_graph));
+  if (need_graph && !build_step_graph(c, h, warm)) return SCFFT_ECUDA;
+  CK(cudaGraphLaunch(c->step_exec, c->st));
+  CK(advance_readback(c, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return advance_epilogue(c, t_io, dt_io, h, warm, done);
+}
+
+// One graph over a batch of FP32 contexts: every instance's trial loop as a WHILE node of its
+// own, side by side with no dependencies, so one launch advances all instances concurrently.
+struct BatchGraph {
+  std::vector<scfft_ctx*> ctx;
+  std::vector<const double*> h, warm;
+  std::vector<unsigned long long> epoch;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaEvent_t done = nullptr;
+  std::vector<cudaEvent_t> ready;
+};
+std::mutex g_batch_mutex;
+BatchGraph* g_batch = nullptr;  // the last batch graph (rebuilt when the batch changes)
+
+void free_batch_graph(BatchGraph* b) {
+  if (!b) return;
+  if (b->ex) cudaGraphExecDestroy(b->ex);
+  if (b->g) cudaGraphDestroy(b->g);
+  if (b->done) cudaEventDestroy(b->done);
+  for (cudaEvent_t e : b->ready) cudaEventDestroy(e);
+  delete b;
+}
+
 // ---------------------------------------------------------------- reverse mode of one rhs
 constexpr int kSumBlocks = 152 * 2;
 
@@ -1091,6 +1616,7 @@ scfft_status scfft_create(const scfft_grid* grid, const scfft_material* mat, con
   c->g.sxp = round_up(grid->nx + 1, 8);
   c->g.N = (long long)grid->nx * grid->ny * grid->nz;
   c->L[0] = grid->Lx; c->L[1] = grid->Ly; c->L[2] = grid->Lz;
+  c->dcell[0] = 2 * grid->Lx / grid->nx; c->dcell[1] = 2 * grid->Ly / grid->ny; c->dcell[2] = 2 * grid->Lz / grid->nz;
   c->mat = *mat;
   c->opt = *opt;
   c->st = (cudaStream_t)stream;
@@ -1120,6 +1646,17 @@ void scfft_destroy(scfft_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   free_rec(c);
+  {  // a batch graph built on this context is dropped with it
+    std::lock_guard<std::mutex> lock(g_batch_mutex);
+    if (g_batch && std::find(g_batch->ctx.begin(), g_batch->ctx.end(), c) != g_batch->ctx.end()) {
+      free_batch_graph(g_batch);
+      g_batch = nullptr;
+    }
+  }
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  if (c->step_graph) cudaGraphDestroy(c->step_graph);
+  cudaFree(c->sdev); cudaFree(c->pathd); cudaFree(c->ppsd);
+  if (c->hsdev) cudaFreeHost(c->hsdev);
   free_work(c->wf);
   free_work(c->wd);
   if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
@@ -1152,6 +1689,7 @@ scfft_status scfft_set_geometry(scfft_ctx* c, const uint8_t* mask) {
   c->nout = g.N - nin;
   c->have_geom = true;
   c->fsal_valid = false;
+  c->epoch++;
   return SCFFT_OK;
 }
 
@@ -1159,6 +1697,7 @@ scfft_status scfft_set_jc_map(scfft_ctx* c, const double* jc) {
   if (!c) return SCFFT_EINVAL;
   const long long N = c->g.N;
   c->fsal_valid = false;
+  c->epoch++;
   if (c->opt.precision == SCFFT_PREC_F32) {
     cudaFree(c->wf.jc);
     c->wf.jc = nullptr;
@@ -1177,6 +1716,31 @@ scfft_status scfft_set_jc_map(scfft_ctx* c, const double* jc) {
   return SCFFT_OK;
 }
 
+scfft_status scfft_set_curl(scfft_ctx* c, int kind) {
+  if (!c || (kind != SCFFT_CURL_SPECTRAL && kind != SCFFT_CURL_FD)) return SCFFT_EINVAL;
+  if (kind == c->curl_kind) return SCFFT_OK;
+  if (kind == SCFFT_CURL_FD) {
+    const size_t bytes = (c->opt.precision == SCFFT_PREC_F32 ? sizeof(float) : sizeof(double)) * 3 * (size_t)c->g.N;
+    void** jd = c->opt.precision == SCFFT_PREC_F32 ? (void**)&c->wf.Jd : (void**)&c->wd.Jd;
+    if (!*jd && cudaMalloc(jd, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *jd = nullptr;
+      return SCFFT_ENOMEM;
+    }
+  }
+  CK(cudaStreamSynchronize(c->st));
+  // the Eq. 5 loop graph holds the launches of one curl kind: rebuilt on the next rhs
+  if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+  if (c->loop_graph) cudaGraphDestroy(c->loop_graph);
+  c->loop_exec = nullptr;
+  c->loop_graph = nullptr;
+  c->loop_failed = false;
+  c->curl_kind = kind;
+  c->fsal_valid = false;
+  c->epoch++;
+  return SCFFT_OK;
+}
+
 scfft_status scfft_set_ej_law(scfft_ctx* c, const scfft_ej_law* law) {
   if (!c || !law) return SCFFT_EINVAL;
   if (!(law->kim_h0 >= 0) || !isfinite(law->kim_h0)) return SCFFT_EINVAL;
@@ -1186,6 +1750,7 @@ scfft_status scfft_set_ej_law(scfft_ctx* c, const scfft_ej_law* law) {
   for (int a = 0; a < 3; ++a) c->aniso[a] = law->aniso[a];
   c->law = (law->kim_h0 > 0 || law->aniso[0] != 1.0 || law->aniso[1] != 1.0 || law->aniso[2] != 1.0) ? 1 : 0;
   c->fsal_valid = false;
+  c->epoch++;
   return SCFFT_OK;
 }
 
@@ -1203,6 +1768,8 @@ scfft_status scfft_set_field_path(scfft_ctx* c, const scfft_field_path* p) {
   for (int a = 0; a < 3; ++a) c->sin_dir[a] = p->sin_dir[a];
   c->have_path = true;
   c->fsal_valid = false;
+  c->path_dirty = true;
+  c->epoch++;
   return SCFFT_OK;
 }
 
@@ -1222,6 +1789,7 @@ scfft_status scfft_precompute_kernel(scfft_ctx* c) {
   if (e != cudaSuccess || e2 != cudaSuccess) return SCFFT_ECUDA;
   c->have_kernel = true;
   c->fsal_valid = false;
+  c->epoch++;
   return SCFFT_OK;
 }
 
@@ -1247,6 +1815,29 @@ scfft_status scfft_step(scfft_ctx* c, double* t, double* dt, double tstop, doubl
   if (!c || !t || !dt || !h || !warm || !(*dt > 0) || !(tstop > *t)) return SCFFT_EINVAL;
   if (!c->have_geom || !c->have_kernel || !c->have_path) return SCFFT_ESTATE;
   return step_any(c, t, dt, tstop, h, warm, 0.0, rejected);
+}
+
+scfft_status scfft_advance(scfft_ctx* c, double* t, double* dt, double tstop, int nsteps, double* h, double* warm,
+                           int* steps_done) {
+  if (!c || !t || !dt || !h || !warm || !(*dt > 0) || !(tstop > *t) || nsteps < 1) return SCFFT_EINVAL;
+  if (!c->have_geom || !c->have_kernel || !c->have_path) return SCFFT_ESTATE;
+  int done = 0;
+  scfft_status s = SCFFT_OK;
+  if (c->opt.precision == SCFFT_PREC_F32 && !c->prof_on) {
+    s = advance_f32(c, t, dt, tstop, nsteps, h, warm, &done);
+  } else {  // FP64 path, or profiling (per-launch events): the host drives the steps
+    const std::vector<double> kinks = kinks_of(c);
+    double tlim = tstop;
+    for (double v : kinks)
+      if (v > *t && v < tlim) tlim = v;
+    while (done < nsteps && *t < tlim) {
+      s = step_any(c, t, dt, tlim, h, warm, 0.0, nullptr);
+      if (s != SCFFT_OK) break;
+      ++done;
+    }
+  }
+  if (steps_done) *steps_done = done;
+  return s;
 }
 
 scfft_status scfft_step_host(scfft_ctx* c, double* t, double* dt, double tstop, double* h_host, double* warm_host,
@@ -1416,7 +2007,7 @@ scfft_status scfft_integrate(scfft_ctx* c, double t0, double t1, double dt0, int
 scfft_status scfft_rhs_vjp(scfft_ctx* c, const double* h, const double* lam, double* mu_h, double* mu_g, double* mu_jc,
                            double* mu_a) {
   if (!c || !h || !lam || !mu_h || mu_h == h || mu_h == lam) return SCFFT_EINVAL;
-  if (!c->have_geom || !c->have_kernel || c->law) return SCFFT_ESTATE;
+  if (!c->have_geom || !c->have_kernel || c->law || c->curl_kind != SCFFT_CURL_SPECTRAL) return SCFFT_ESTATE;
   c->fsal_valid = false;
   return c->opt.precision == SCFFT_PREC_F32 ? vjp_impl<float>(c, h, lam, mu_h, mu_g, mu_jc, mu_a)
                                             : vjp_impl<double>(c, h, lam, mu_h, mu_g, mu_jc, mu_a);
@@ -1717,7 +2308,8 @@ scfft_status scfft_adjoint_record(scfft_ctx* c, const double* ts, int nsteps, co
   if (!c || !ts || nsteps < 1 || !y0 || checkpoint_every < 1) return SCFFT_EINVAL;
   for (int n = 0; n < nsteps; ++n)
     if (!(ts[n + 1] > ts[n])) return SCFFT_EINVAL;
-  if (!c->have_geom || !c->have_kernel || !c->have_path || c->law) return SCFFT_ESTATE;
+  if (!c->have_geom || !c->have_kernel || !c->have_path || c->law || c->curl_kind != SCFFT_CURL_SPECTRAL)
+    return SCFFT_ESTATE;
   return frozen(c, [&] { return adj_record(c, ts, nsteps, y0, warm0, checkpoint_every, y_end); });
 }
 
@@ -1733,7 +2325,8 @@ scfft_status scfft_adjoint_integrate(scfft_ctx* c, double t0, const double* dts,
   if (!c || !dts || nsteps < 1 || !y0 || !lam_T || !mu_y0 || checkpoint_every < 1) return SCFFT_EINVAL;
   for (int n = 0; n < nsteps; ++n)
     if (!(dts[n] > 0)) return SCFFT_EINVAL;
-  if (!c->have_geom || !c->have_kernel || !c->have_path || c->law) return SCFFT_ESTATE;
+  if (!c->have_geom || !c->have_kernel || !c->have_path || c->law || c->curl_kind != SCFFT_CURL_SPECTRAL)
+    return SCFFT_ESTATE;
   std::vector<double> ts(nsteps + 1);
   ts[0] = t0;
   for (int n = 0; n < nsteps; ++n) ts[n + 1] = ts[n] + dts[n];
@@ -1752,15 +2345,88 @@ scfft_status scfft_adjoint_integrate(scfft_ctx* c, double t0, const double* dts,
   return s;
 }
 
+namespace {
+
+// One accepted step of every FP32 instance by one launch of the batch graph (see BatchGraph).
+scfft_status batch_graph_step(scfft_ctx** ctxs, int nb, double* t, double* dt, const double* tstop, double** h,
+                              double** warm, std::vector<scfft_status>& res) {
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  for (int i = 0; i < nb; ++i) {
+    bool need = false;
+    if (!(dt[i] > 0) || !(tstop[i] > t[i])) return SCFFT_EINVAL;
+    if (!ctxs[i]->have_geom || !ctxs[i]->have_kernel || !ctxs[i]->have_path) return SCFFT_ESTATE;
+    CS_(advance_prologue(ctxs[i], t[i], dt[i], tstop[i], 1, h[i], warm[i], &need));
+  }
+  BatchGraph* b = g_batch;
+  bool same = b && (int)b->ctx.size() == nb;
+  for (int i = 0; same && i < nb; ++i)
+    same = b->ctx[i] == ctxs[i] && b->h[i] == h[i] && b->warm[i] == warm[i] && b->epoch[i] == ctxs[i]->epoch &&
+           ctxs[i]->k32[0] == ctxs[i]->step_k[0];
+  if (!same) {
+    free_batch_graph(g_batch);
+    g_batch = nullptr;
+    b = new (std::nothrow) BatchGraph();
+    if (!b) return SCFFT_ENOMEM;
+    bool ok = cudaGraphCreate(&b->g, 0) == cudaSuccess && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) ==
+                                                              cudaSuccess;
+    for (int i = 0; ok && i < nb; ++i) {
+      scfft_ctx* c = ctxs[i];
+      ok = add_step_loop(c, b->g, h[i], warm[i]);
+      for (int q = 0; q < 4; ++q) c->step_k[q] = c->k32[q];
+      b->ctx.push_back(c);
+      b->h.push_back(h[i]);
+      b->warm.push_back(warm[i]);
+      b->epoch.push_back(c->epoch);
+      cudaEvent_t e = nullptr;
+      ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+      b->ready.push_back(e);
+    }
+    if (ok) ok = cudaGraphInstantiate(&b->ex, b->g, 0) == cudaSuccess;
+    if (!ok) {
+      free_batch_graph(b);
+      cudaGetLastError();
+      return SCFFT_ECUDA;
+    }
+    g_batch = b;
+  }
+  cudaStream_t s0 = ctxs[0]->st;
+  for (int i = 0; i < nb; ++i) {
+    CK(cudaEventRecord(b->ready[i], ctxs[i]->st));
+    CK(cudaStreamWaitEvent(s0, b->ready[i], 0));
+  }
+  CK(cudaGraphLaunch(b->ex, s0));
+  for (int i = 0; i < nb; ++i) CK(advance_readback(ctxs[i], s0));
+  CK(cudaStreamSynchronize(s0));
+  for (int i = 0; i < nb; ++i) {
+    int done = 0;
+    res[i] = advance_epilogue(ctxs[i], &t[i], &dt[i], h[i], warm[i], &done);
+  }
+  return SCFFT_OK;
+}
+
+}  // namespace
+
 scfft_status scfft_batch_step(scfft_ctx** ctxs, int nb, double* t, double* dt, const double* tstop, double** h,
                               double** warm, scfft_status* status) {
   if (!ctxs || nb < 1 || !t || !dt || !tstop || !h || !warm) return SCFFT_EINVAL;
+  bool graphable = true;
   for (int i = 0; i < nb; ++i) {
     if (!ctxs[i] || !h[i] || !warm[i]) return SCFFT_EINVAL;
     for (int j = 0; j < i; ++j)
       if (ctxs[j] == ctxs[i]) return SCFFT_EINVAL;  // one context is one instance
+    graphable = graphable && ctxs[i]->opt.precision == SCFFT_PREC_F32 && !ctxs[i]->prof_on;
   }
   std::vector<scfft_status> res(nb, SCFFT_OK);
+  if (graphable) {
+    const scfft_status s = batch_graph_step(ctxs, nb, t, dt, tstop, h, warm, res);
+    if (s != SCFFT_OK) return s;
+    scfft_status first = SCFFT_OK;
+    for (int i = 0; i < nb; ++i) {
+      if (status) status[i] = res[i];
+      if (first == SCFFT_OK && res[i] != SCFFT_OK) first = res[i];
+    }
+    return first;
+  }
   std::atomic<int> next(0);
   auto worker = [&]() {
     for (int i = next++; i < nb; i = next++) res[i] = scfft_step(ctxs[i], &t[i], &dt[i], tstop[i], h[i], warm[i], nullptr);

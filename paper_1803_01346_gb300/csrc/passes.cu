@@ -573,9 +573,10 @@ cudaError_t launch_x(const Launch<T>& L, XMode mode, const PointParams& pp, cons
   // the FP32 forward passes use the register-resident kernels; the transposed
   // (reverse-mode) passes use this shared-memory kernel in both precisions
   if constexpr (sizeof(T) == 4)
-    if (mode < X_ADJ_PAD || mode == X_POWERLAW_H)
+    if (mode < X_ADJ_PAD || mode == X_POWERLAW_H || mode == X_UPDATE_FD)
       return launch_x_reg(L, mode, pp, src_f64, dst_f64, warm, in_buf, out_buf, check_done);
   if (mode == X_POWERLAW_H) mode = X_POWERLAW;
+  if (mode == X_UPDATE_FD) mode = X_UPDATE;  // its R2C output is not read by the stencil curl
   XArgs<T> a{};
   const Geo& g = L.g;
   a.g = g;

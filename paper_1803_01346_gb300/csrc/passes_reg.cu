@@ -260,6 +260,7 @@ struct XRArgs {
   float* hbuf[2];         // both iterate buffers: the update pass picks by the device iteration count
   PointParams pp;
   PointParams* ppd;       // device copy of pp (written by the assemble pass, read by the update pass)
+  const PointParams* pps; // device source of that copy, or nullptr (pp is copied)
   Ctrl* ctrl;
   double* partials;
   int check_done;
@@ -271,8 +272,8 @@ namespace {
 
 template <int MODE, int R1i, int R2i, int R2o> struct XS {
   static constexpr bool C2R = !(MODE == X_FWD_F64 || MODE == X_PAD_F64);
-  static constexpr bool R2C = !(MODE == X_TO_F64 || MODE == X_CROP_F64);
-  static constexpr bool PADIN = (MODE == X_UPDATE || MODE == X_CROP_F64);   // C2R length 2nx, keep x < nx
+  static constexpr bool R2C = !(MODE == X_TO_F64 || MODE == X_CROP_F64 || MODE == X_UPDATE_FD);
+  static constexpr bool PADIN = (MODE == X_UPDATE || MODE == X_UPDATE_FD || MODE == X_CROP_F64);  // C2R length 2nx, keep x < nx
   static constexpr bool PADOUT = (MODE == X_MASKPAD || MODE == X_PAD_F64);  // R2C length 2nx, input x < nx
   static constexpr int R1o = R2i;
   static constexpr int Li = R1i * R2i;
@@ -351,6 +352,7 @@ template <int MODE> cudaError_t go_x_n(int n, const XRArgs& a, cudaStream_t st) 
     else if constexpr (MODE == X_MASKPAD) return go_x<MODE, A_, B_, 2 * A_>(a, st);              \
     else if constexpr (MODE == X_TO_F64) return go_x<MODE, A_, B_, 1>(a, st);                    \
     else if constexpr (MODE == X_UPDATE) return go_x<MODE, C_, D_, C_ / 2>(a, st);               \
+    else if constexpr (MODE == X_UPDATE_FD) return go_x<MODE, C_, D_, 1>(a, st);                 \
     else return go_x<MODE, C_, D_, 1>(a, st);
   switch (n) {
     XN(16, 4, 4, 8, 4)
@@ -377,7 +379,7 @@ cudaError_t launch_x_reg_io(const Launch<float>& L, XMode mode, const PointParam
   const Geo& g = L.g;
   XRArgs a{};
   a.g = g;
-  const bool pin = (mode == X_UPDATE || mode == X_CROP_F64);
+  const bool pin = (mode == X_UPDATE || mode == X_UPDATE_FD || mode == X_CROP_F64);
   const bool pout = (mode == X_MASKPAD || mode == X_PAD_F64);
   a.spec_in = pin ? L.w->Pd : L.w->U;
   a.in_rows = pin ? 2 * g.ny : g.ny;
@@ -400,6 +402,7 @@ cudaError_t launch_x_reg_io(const Launch<float>& L, XMode mode, const PointParam
   a.hbuf[1] = L.w->Hd[1];
   a.pp = pp;
   a.ppd = L.ppd;
+  a.pps = L.pps;
   a.ctrl = L.ctrl;
   a.partials = L.partials;
   a.check_done = check_done ? 1 : 0;
@@ -411,6 +414,7 @@ cudaError_t launch_x_reg_io(const Launch<float>& L, XMode mode, const PointParam
     case X_ASSEMBLE: return go_x_n<X_ASSEMBLE>(g.nx, a, L.st);
     case X_MASKPAD: return go_x_n<X_MASKPAD>(g.nx, a, L.st);
     case X_UPDATE: return go_x_n<X_UPDATE>(g.nx, a, L.st);
+    case X_UPDATE_FD: return go_x_n<X_UPDATE_FD>(g.nx, a, L.st);
     case X_TO_F64: return go_x_n<X_TO_F64>(g.nx, a, L.st);
     case X_PAD_F64: return go_x_n<X_PAD_F64>(g.nx, a, L.st);
     case X_CROP_F64: return go_x_n<X_CROP_F64>(g.nx, a, L.st);
@@ -716,6 +720,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
     xpass_reg2_kernel(const XRArgs a) {
   typedef XS<MODE, R1i, R2i, R2o> S;
   constexpr int TP = S::TP, R1o = S::R1o, Li = S::Li, Lo = S::Lo;
+  constexpr bool UPD = (MODE == X_UPDATE || MODE == X_UPDATE_FD);  // the Eq. 5 update
   constexpr int NT = P * TP;
   constexpr int XL = S::C2R ? (S::PADIN ? Li / 2 : Li) : (S::PADOUT ? Lo / 2 : Lo);  // nx
   constexpr int TT = cmax(cmax(S::C2R ? R2i * (R1i + 1) : 1, S::R2C ? R2o * (R1o + 1) : 1), S::R2C ? Lo : 1);
@@ -728,7 +733,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
   float* h_new = a.hnew;
   int it = 0;
   float hef[3] = {0.f, 0.f, 0.f};
-  if (MODE == X_UPDATE) {
+  if (UPD) {
     it = *reinterpret_cast<volatile const int*>(&a.ctrl->iters);
     h_old = a.hbuf[it & 1];
     h_new = a.hbuf[(it + 1) & 1];
@@ -810,7 +815,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
       }
       const size_t nb0 = (size_t)row0 * XL;
       const int rl = (XL * 4 + 127) / 128;  // lines per FP32 node row
-      if (MODE == X_UPDATE)
+      if (UPD)
         for (int i = tid; i < 3 * nrow * rl; i += NT) {
           const int ln = i % rl, rr = (i / rl) % nrow, q = i / (rl * nrow);
           if (row0 + rr < 2 * npairs) prefetch_l2(h_old + q * N + nb0 + (size_t)rr * XL + ln * 32);
@@ -820,7 +825,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
           const int ln = i % (2 * rl), rr = (i / (2 * rl)) % nrow, q = i / (2 * rl * nrow);
           if (row0 + rr < 2 * npairs) prefetch_l2(a.warm + q * N + nb0 + (size_t)rr * XL + ln * 16);
         }
-      if (MODE == X_UPDATE || MODE == X_ASSEMBLE || MODE == X_MASKPAD || MODE == X_POWERLAW || MODE == X_POWERLAW_H)
+      if (UPD || MODE == X_ASSEMBLE || MODE == X_MASKPAD || MODE == X_POWERLAW || MODE == X_POWERLAW_H)
         for (int i = tid * 128; i < nrow * XL; i += NT * 128)
           if (row0 + i / XL < 2 * npairs) prefetch_l2(a.mask + nb0 + i);
     }
@@ -892,8 +897,8 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
       const PointParams& pp = a.pp;
       constexpr int J = XL / TP;  // node pairs per thread: x = r + TP j of the lane's own row pair
       constexpr bool MASKED = MODE == X_POWERLAW || MODE == X_POWERLAW_H || MODE == X_ASSEMBLE || MODE == X_MASKPAD ||
-                              MODE == X_UPDATE;
-      constexpr int NO = MODE == X_UPDATE || MODE == X_ASSEMBLE ? 3 : (MODE == X_POWERLAW ? 1 : (MODE == X_POWERLAW_H ? 4 : 0));
+                              UPD;
+      constexpr int NO = UPD || MODE == X_ASSEMBLE ? 3 : (MODE == X_POWERLAW ? 1 : (MODE == X_POWERLAW_H ? 4 : 0));
       bool mk[J][2];
       float ov[J][NO > 0 ? NO : 1][2];  // hold (update), warm start (assemble), jc (power law)
 #pragma unroll
@@ -909,7 +914,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
             mk[j][0] = a.mask[na];
             mk[j][1] = a.mask[nb];
           }
-          if (MODE == X_UPDATE) {
+          if (UPD) {
 #pragma unroll
             for (int q = 0; q < NO; ++q) {
               ov[j][q][0] = h_old[q * N + na];
@@ -972,7 +977,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
         } else if (MODE == X_MASKPAD) {
   #pragma unroll
           for (int q = 0; q < 3; ++q) u[q] = make_float2(ia ? u[q].x : 0.f, ib ? u[q].y : 0.f);
-        } else if (MODE == X_UPDATE) {
+        } else if (UPD) {
           // per-node |dh^{i+1} - dh^i| in FP32 (the FP32 path's own precision); the
           // per-thread sum stays FP32, the CTA and grid sums are FP64
           float da = 0.f, db = 0.f;
@@ -1054,7 +1059,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
     __syncwarp();  // the pair's shared buffers are reused by the next tile
   }
 
-  if (MODE == X_UPDATE) {
+  if (UPD) {
     double part = (double)partf;
     __shared__ double red[32];
     __shared__ int am_last;
@@ -1095,7 +1100,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
     }
   }
   if (MODE == X_ASSEMBLE && blockIdx.x == 0 && tid == 0) {
-    *a.ppd = a.pp;
+    *a.ppd = a.pps ? *a.pps : a.pp;
     a.ctrl->trips = 0;
     a.ctrl->done = 0;
     a.ctrl->iters = 0;

@@ -74,6 +74,7 @@ struct Work {
   V* twu[3] = {nullptr, nullptr, nullptr}; // twiddles W_L^m, L = nx, ny, nz
   V* twp[3] = {nullptr, nullptr, nullptr}; // twiddles, L = 2nx, 2ny, 2nz
   YMaps* ym = nullptr;   // FP32 only: TMA descriptors of the y passes (nullptr: plain-load y passes)
+  T* Jd = nullptr;       // [3][N] masked stencil curl of the iterate (local-stencil curl option only)
 };
 
 enum XMode : int {
@@ -92,7 +93,8 @@ enum XMode : int {
   X_ADJ_IN = 11,      // real f64 rows x chi -> R2C(nx) -> U
   X_ADJ_POWERLAW = 12, // U -> C2R(nx) -> lam_e = -(.)/mu0 -> power-law Jacobian^T (forward j in src) -> R2C(nx) -> U;
                        //   dst (N values, optional) = d e/d jc . lam_e
-  X_POWERLAW_H = 13    // as X_POWERLAW with the e(j, h) law of PointParams::law (the state h read from src)
+  X_POWERLAW_H = 13,   // as X_POWERLAW with the e(j, h) law of PointParams::law (the state h read from src)
+  X_UPDATE_FD = 14     // as X_UPDATE without the R2C of the new iterate (the stencil curl reads it as is)
 };
 
 // Scalars of the material law and the Eq. 5 update.
@@ -122,6 +124,8 @@ struct Launch {
   const uint8_t* mask; // device [N]
   double* partials;    // device, one double per CTA of the x passes
   PointParams* ppd = nullptr;  // device copy of the current rhs's PointParams (read by the Eq. 5 update pass)
+  const PointParams* pps = nullptr;  // device source of that copy (the assembly pass reads it instead of its
+                                     // argument when set: rhs parameters computed on the device)
   int* fault = nullptr;        // host: armed one-shot fault injection (scfft_inject_fault), or nullptr
   cudaStream_t st;
 };
@@ -152,6 +156,13 @@ cudaError_t launch_x_reg(const Launch<float>& L, XMode mode, const PointParams& 
 cudaError_t launch_x_reg_io(const Launch<float>& L, XMode mode, const PointParams& pp, const double* src_f64,
                             const float* src_f32, double* dst_f64, const double* warm, const float* warm_f32,
                             int in_buf, int out_buf, bool check_done);
+
+// Local-stencil curl option (fd_curl.cu): d = cell sizes (dx, dy, dz).
+template <typename T> cudaError_t launch_fd_efield(const Launch<T>& L, const PointParams& pp, const double* h64,
+                                                   const float* h32, const double* d, T* out);
+template <typename T> cudaError_t launch_fd_assemble(const Launch<T>& L, const PointParams& pp, const T* e,
+                                                     const double* warm64, const float* warm32, const double* d);
+template <typename T> cudaError_t launch_fd_curl_mask(const Launch<T>& L, T* out, const double* d, bool check_done);
 
 // Launch diagnostics: the last failed launch (kernel, grid, block, shared memory).
 cudaError_t checked_launch(const char* what, dim3 grid, int block, size_t smem);

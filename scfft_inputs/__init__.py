@@ -18,8 +18,8 @@ from typing import Optional
 
 import numpy as np
 
-__all__ = ["node_axes", "cube", "sphere", "cylinder", "shield", "lens", "Config", "config",
-           "CONFIGS", "random_field", "jc_noise", "batch_configs"]
+__all__ = ["node_axes", "cube", "sphere", "cylinder", "shield", "lens", "biconical_lens", "disk_region",
+           "Config", "config", "CONFIGS", "random_field", "jc_noise", "batch_configs", "shield_case_path"]
 
 
 def node_axes(n, L):
@@ -70,6 +70,35 @@ def lens(n, L, R: float, height: float, bore: float, slit: float) -> np.ndarray:
     hole = r2 < bore * bore
     cut = (np.abs(Y) < 0.5 * slit) & (X > 0)
     return body & ~hole & ~cut
+
+
+def biconical_lens(n, L, R: float, height: float, r_mid: float, r_face: float, slit: float) -> np.ndarray:
+    """Cylinder r <= R, |z| <= height/2 with a coaxial biconical hole whose radius grows
+    linearly from r_mid at z = 0 to r_face at |z| = height/2, and a radial slit |y| < slit/2,
+    x > 0 from the hole to the outer surface (the lens shape of §3; its dimensions are
+    readings, the paper gives them only in a figure)."""
+    Z, Y, X = _zyx(n, L)
+    r = np.sqrt(X * X + Y * Y)
+    body = (r <= R) & (np.abs(Z) <= 0.5 * height)
+    hole = r < r_mid + (r_face - r_mid) * np.abs(Z) / (0.5 * height)
+    cut = (np.abs(Y) < 0.5 * slit) & (X > 0)
+    return body & ~hole & ~cut
+
+
+def disk_region(n, L, z_center: float, thickness: float, radius: float) -> np.ndarray:
+    """Nodes of the coaxial disk r <= radius, |z - z_center| <= thickness/2 (an averaging zone)."""
+    Z, Y, X = _zyx(n, L)
+    return (X * X + Y * Y <= radius * radius) & (np.abs(Z - z_center) <= 0.5 * thickness) & (X * 0 == 0)
+
+
+def shield_case_path(case: str, tau: float = 0.09):
+    """Applied-field knots of the shield experiment of §3: case A ramps along the axis to tau,
+    then perpendicular (h_e = (t - tau, 0, tau)); case B the same ramps in the inverse order."""
+    if case == "A":
+        return [0.0, tau, 2 * tau], [[0, 0, 0], [0, 0, tau], [tau, 0, tau]]
+    if case == "B":
+        return [0.0, tau, 2 * tau], [[0, 0, 0], [tau, 0, 0], [tau, 0, tau]]
+    raise KeyError(case)
 
 
 @dataclass

@@ -7,7 +7,9 @@ then integrates each instance alone over the step sizes the GPU chose, with
 Eq. 5 iterated to its fixed point on both sides (delta_it = 1e-13), and the
 states agree element by element: <= 1e-10 (FP64 path), <= 1e-4 (FP32 path,
 the FP32 fixed-step bound of test_gpu_parity).  A second check: the batch gives
-bit for bit the results of stepping the same instances one after another."""
+bit for bit the results of stepping the same instances one after another with the same
+device-resident step (scfft_advance), and those of the host-driven scfft_step up to the
+rounding of the step controller's pow (FP32 contexts run the batch as one CUDA graph)."""
 
 import numpy as np
 import pytest
@@ -96,11 +98,17 @@ def test_batch_step_equals_individual_steps(prec):
         t, dt, st = S.batch_step([a[0] for a in A], t, dt, stop, [a[1] for a in A], [a[2] for a in A])
         assert all(v == 0 for v in st)
     torch.cuda.synchronize()
-    for (ctx, h, w), c, tb in zip(Bv, cfgs, t):
+    C = [_make(c, prec, s, delta_it=2e-5, max_iter=100) for c, s in zip(cfgs, streams)]
+    for (ctx, h, w), (ctx2, h2, w2), c, tb in zip(Bv, C, cfgs, t):
         tt, d = 0.0, 1e-4
-        for _ in range(3):
-            tt, d, _ = ctx.step(tt, d, c.t_end, h, w)
+        for _ in range(3):  # the same device-resident step, one instance at a time
+            tt, d, _ = ctx.advance(tt, d, c.t_end, 1, h, w)
         assert tt == tb
+        tt, d = 0.0, 1e-4
+        for _ in range(3):  # the host-driven step: the same up to the rounding of pow in the controller
+            tt, d, _ = ctx2.step(tt, d, c.t_end, h2, w2)
+        assert tt == pytest.approx(tb, rel=1e-12)
     torch.cuda.synchronize()
-    for a, b in zip(A, Bv):
+    for a, b, c2 in zip(A, Bv, C):
         assert torch.equal(a[1], b[1])
+        assert float((a[1] - c2[1]).abs().max() / c2[1].abs().max()) < 1e-9

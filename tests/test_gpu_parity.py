@@ -393,3 +393,73 @@ def test_integrate_ej_law_fixed_steps_fp64_matches_oracle():
     ref = O.integrate(prob, 0.0, t1, np.zeros((3,) + prob.grid.shape), rtol=1e-6, atol=1e-9, dt0=dts[0],
                       delta_it=1e-13, max_iter=80, dt_list=dts)
     assert rel(host(h).reshape(ref.y.shape), ref.y) < 1e-10
+
+
+# ---------------------------------------------------------------- local-stencil curl option
+def _fd_ctx(n, L, mask, prec, **kw):
+    ctx, prob = make(n, L, mask, prec=prec, **kw)
+    ctx.set_curl(S.CURL_FD)
+    prob.curl = "fd"
+    return ctx, prob
+
+
+@pytest.mark.parametrize("n,L", [((16, 32, 48), (0.8, 1.0, 1.2)), ((48, 32, 16), (1.2, 0.9, 0.8))])
+@pytest.mark.parametrize("prec", [S.PREC_F64, S.PREC_F32])
+def test_rhs_stencil_curl_matches_oracle(n, L, prec):
+    """Central-difference curls (the pre-stage's two stencil passes, the masked stencil curl
+    of every Eq. 5 iterate) against the oracle's curl_fd, fixed iteration count."""
+    mask = I.cube(n, L, 0.6 * min(L) * 2)
+    ctx, prob = _fd_ctx(n, L, mask, prec, n_power=20.0, max_iter=3)
+    h = _state(prob, 61)
+    g0 = I.random_field(h.shape, 62, 0.1)
+    ref = O.rhs(prob, 0.4, h, g0, delta_it=0.0, max_iter=3)
+    hd = torch.empty(h.size, dtype=torch.float64, device="cuda")
+    assert ctx.rhs(0.4, dev(h).reshape(-1), dev(g0).reshape(-1), hd) == 3
+    if prec == S.PREC_F64:
+        assert rel(host(hd).reshape(h.shape), ref.hdot) < 1e-10
+    else:
+        check3(f"rhs stencil curl {n}", host(hd).reshape(h.shape), ref.hdot, RHS32)
+
+
+def test_rhs_stencil_curl_graph_loop_and_early_stop():
+    """FP32 with the stencil curl: the Eq. 5 loop as one CUDA graph gives the host-driven
+    loop's result bit for bit and stops with the oracle (lens 32^3, jc map, delta_it 2e-5)."""
+    n, L = (32, 32, 32), (1.0, 1.0, 1.0)
+    mask = I.lens(n, L, 0.6, 0.5, 0.1, 0.1)
+    jc = I.jc_noise((32, 32, 32), 5)
+    ctx, prob = _fd_ctx(n, L, mask, S.PREC_F32, n_power=30.0, rho_out=100.0, delta_it=2e-5, max_iter=50, jc_map=jc)
+    h = _state(prob, 63)
+    g0 = np.broadcast_to(prob.path.hedot(0.2)[:, None, None, None], h.shape).copy()
+    ref = O.rhs(prob, 0.2, h, g0, delta_it=2e-5, max_iter=50)
+    out = {}
+    for mode in ("host", "graph"):
+        ctx.profile(mode == "host")
+        hd = torch.empty(h.size, dtype=torch.float64, device="cuda")
+        it = ctx.rhs(0.2, dev(h).reshape(-1), dev(g0).reshape(-1), hd)
+        out[mode] = (it, host(hd))
+        ctx.profile(False)
+    assert out["graph"][0] == out["host"][0]
+    assert np.array_equal(out["graph"][1], out["host"][1])
+    assert abs(out["host"][0] - ref.iters) <= 1
+    check3("rhs stencil curl lens32 early stop", out["host"][1].reshape(h.shape), ref.hdot, RHS32)
+
+
+def test_integrate_stencil_curl_fixed_steps_matches_oracle():
+    """Fixed-step BS23 with the stencil curl, Eq. 5 iterated to its fixed point: FP64 and FP32."""
+    cfg, prob = _cube_cfg()
+    prob.curl = "fd"
+    dts = [0.002, 0.003, 0.004, 0.004]
+    t1 = float(np.sum(dts))
+    ref = O.integrate(prob, 0.0, t1, np.zeros((3,) + prob.grid.shape), rtol=1e-6, atol=1e-9, dt0=dts[0],
+                      delta_it=1e-13, max_iter=80, dt_list=dts)
+    N = int(np.prod(cfg.n))
+    for prec, tol in ((S.PREC_F64, 1e-10), (S.PREC_F32, 1e-4)):
+        ctx = S.Context(cfg.n, cfg.L, n_power=cfg.n_power, rho_out=cfg.rho_out, delta_it=1e-13, max_iter=80,
+                        precision=prec)
+        ctx.set_geometry(cfg.mask)
+        ctx.set_field_path(cfg.knots_t, cfg.knots_he)
+        ctx.set_curl(S.CURL_FD)
+        ctx.precompute_kernel()
+        h = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
+        ctx.integrate(0.0, t1, dts[0], h, dt_fixed=dts)
+        assert rel(host(h).reshape(ref.y.shape), ref.y) < tol, prec

@@ -744,3 +744,65 @@ def test_kim_law_slows_the_penetration_of_a_uniform_rate():
     S2 = math.exp(-g.sigma ** 2 * k2)
     expect = -(1.0 + 2.0 / h0) * S2 * k2 * mode
     assert np.abs(r.hdot - expect).max() < 1e-5 * np.abs(expect).max()
+
+
+# ---------------------------------------------------------------- local-stencil curl (reading R-fd)
+def test_curl_fd_single_modes_closed_form():
+    """Central differences act on a Fourier mode sin(k x + p) as multiplication of its
+    derivative by sin(k d)/(k d): the curl of (A sin(ky y + p1), B sin(kz z + p2),
+    C sin(kx x + p3)) is (-B s(kz) cos(kz z + p2), -C s(kx) cos(kx x + p3), -A s(ky) cos(ky y + p1))
+    with s(k_a) = sin(k_a d_a)/d_a.  Catches a wrong stencil sign, axis, spacing or a
+    one-sided difference."""
+    g = _modes_grid()
+    X, Y, Z = g.coords()
+    kx, ky, kz = math.pi * 2 / g.L[0], math.pi * 3 / g.L[1], math.pi * 4 / g.L[2]
+    A, B, C, p1, p2, p3 = 0.7, -1.3, 0.4, 0.3, 1.1, -0.5
+    z0 = 0 * X + 0 * Y + 0 * Z
+    h = np.stack([A * np.sin(ky * Y + p1) + z0, B * np.sin(kz * Z + p2) + z0, C * np.sin(kx * X + p3) + z0])
+    s = lambda k, d: math.sin(k * d) / d  # noqa: E731
+    ex = np.stack([-B * s(kz, g.d[2]) * np.cos(kz * Z + p2) + z0,
+                   -C * s(kx, g.d[0]) * np.cos(kx * X + p3) + z0,
+                   -A * s(ky, g.d[1]) * np.cos(ky * Y + p1) + z0])
+    assert np.abs(O.curl_fd(h, g) - ex).max() < 1e-12 * max(kx, ky, kz)
+
+
+def test_curl_fd_is_divergence_free_and_symmetric():
+    """div_FD curl_FD = 0 to round-off (the central differences commute), and the curl is a
+    symmetric operator, <C a, b> = <a, C b>, which the reverse mode relies on."""
+    g = _modes_grid()
+    a = I.random_field((3,) + g.shape, 31)
+    b = I.random_field((3,) + g.shape, 32)
+    c = O.curl_fd(a, g)
+    assert np.abs(O.div_fd(c, g)).max() < 1e-12 * np.abs(c).max()
+    assert np.sum(c * b) == pytest.approx(np.sum(a * O.curl_fd(b, g)), rel=1e-12)
+
+
+def test_sphere_screening_with_the_stencil_curl():
+    """The sphere of the screening pin with the local-stencil curl: the stencil does not
+    reach past the neighbouring nodes, so the interior field stays exactly zero, and the
+    screening surface lies within one and a half cells of the voxel surface (the stencil's
+    half-width, against about two sigma for the smoothed spectral curl); the exterior field
+    beyond 1.5 cells is the ideal-screening field of the measured moment within 3% of h_e
+    (the stencil follows the staircase of the voxel surface, whose near field is less
+    dipolar than that of the smoothed current: 1.6% at 16^3, 2.5% at 24^3; a Phi of the
+    wrong sign leaves 13%)."""
+    for N in (16, 24):
+        L, R, he = (1.0, 1.0, 1.0), 0.5, 0.01
+        g = O.Grid((N, N, N), L)
+        mask = I.sphere(g.n, L, R)
+        prob = O.Problem(g, mask, O.Material(n=20.0, rho_out=20.0),
+                         O.FieldPath([0.0, 0.01], [[0, 0, 0], [0, 0, he]]), curl="fd")
+        h = O.integrate(prob, 0.0, 0.05, np.zeros((3,) + g.shape), rtol=1e-3, atol=1e-7, dt0=1e-4).y
+        X, Y, Z = g.coords()
+        r = np.sqrt(X * X + Y * Y + Z * Z) + 0 * X
+        assert np.abs(h[:, r < R / 3]).max() < 1e-12 * he
+        m = O.magnetic_moment(O.curl_fd(h, g) * mask[None], g)
+        Rs = (abs(m[2]) / (2 * math.pi * he)) ** (1 / 3)
+        assert m[2] < 0 and 0.5 < (R - Rs) / g.d[0] < 1.5
+        rv = np.stack(np.broadcast_arrays(X, Y, Z))
+        rs = np.maximum(r, 1e-9)
+        mr = np.sum(m[:, None, None, None] * rv, axis=0)
+        ideal = np.array([0.0, 0.0, he])[:, None, None, None] + \
+            (3 * rv * mr / rs ** 5 - m[:, None, None, None] / rs ** 3) / (4 * math.pi)
+        far = (r > R + 1.5 * g.d[0]) & (np.abs(X) < 0.9) & (np.abs(Y) < 0.9) & (np.abs(Z) < 0.9)
+        assert np.abs(h - ideal)[:, far].max() < 3e-2 * he
