@@ -533,11 +533,21 @@ def bench_ours(args, ws, rank, local):
     fixed_it = 8
     c32f = make_ctx(S, cfg, S.PREC_F32, delta_it=0.0, max_iter=fixed_it)
     c64f = make_ctx(S, cfg, S.PREC_F64, delta_it=0.0, max_iter=fixed_it)
+    cdff = make_ctx(S, cfg, S.PREC_DF64, delta_it=0.0, max_iter=fixed_it)
+    odf = torch.empty_like(h)
     c32f.rhs(state[0], hA, warm.clone(), o32)
+    # (NVTX ranges: every pass of these calls does work, so ncu can pick any launch in them)
+    torch.cuda.nvtx.range_push("fp64_fixed_iterations")
     c64f.rhs(state[0], hA, warm.clone(), o64)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.nvtx.range_push("df64_fixed_iterations")
+    cdff.rhs(state[0], hA, warm.clone(), odf)
+    torch.cuda.nvtx.range_pop()
     fp32_err = per_comp(o32, o64)
     fp32_err["iterations"] = fixed_it
-    del c32f, c64f
+    df64_err = per_comp(odf, o64)
+    df64_err["iterations"] = fixed_it
+    del c32f, c64f, cdff
     st64 = [state[0], state[1], h.clone(), warm.clone()]
     torch.cuda.synchronize()
     c0 = ctx64.stats()["rhs_calls"]
@@ -548,6 +558,26 @@ def bench_ours(args, ws, rank, local):
     e5.record(stream)
     torch.cuda.synchronize()
     fp64_value = N * (ctx64.stats()["rhs_calls"] - c0) / (e4.elapsed_time(e5) * 1e-3)
+    fp64_ms_per_step = e4.elapsed_time(e5) / k64
+    del ctx64
+    # the double-float path (FP64-equivalent transforms on the FP32 pipes) over the same steps
+    cdf = make_ctx(S, cfg, S.PREC_DF64)
+    stdf = [state[0], state[1], h.clone(), warm.clone()]
+    torch.cuda.synchronize()
+    d0 = cdf.stats()
+    e10, e11 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e10.record(stream)
+    run_steps(cdf, stdf, k64)
+    e11.record(stream)
+    torch.cuda.synchronize()
+    d1 = cdf.stats()
+    df64 = {"value": N * (d1["rhs_calls"] - d0["rhs_calls"]) / (e10.elapsed_time(e11) * 1e-3), "unit": UNIT,
+            "steps": k64, "ms_per_step": e10.elapsed_time(e11) / k64, "fp64_ms_per_step": fp64_ms_per_step,
+            "speedup_vs_fp64": fp64_ms_per_step / (e10.elapsed_time(e11) / k64),
+            "iters_per_rhs": (d1["iterations"] - d0["iterations"]) / max(1, d1["rhs_calls"] - d0["rhs_calls"]),
+            "error_vs_fp64": df64_err,
+            "what": "SCFFT_PREC_DF64: double-float FFT passes (hi + lo FP32), node-wise law and stages in FP64"}
+    del cdf, stdf
 
     # the local-stencil curl option: its own trajectory from the virgin state (a state of the
     # spectral trajectory is not one of the stencil's: its unsmoothed curl at the voxel
@@ -571,7 +601,27 @@ def bench_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         f1 = cfd.stats()
         fd_ms = e6.elapsed_time(e7)
+        # the cost of one rhs at a fixed count of 5 Eq. 5 iterations on the headline's mid-ramp
+        # state, spectral against stencil curl (the same work per call, whatever the trajectory)
+        per_rhs = {}
+        for kind in (S.CURL_SPECTRAL, S.CURL_FD):
+            cx = make_ctx(S, cfg, S.PREC_F32, delta_it=0.0, max_iter=5)
+            cx.set_curl(kind)
+            ox = torch.empty_like(h)
+            wx = warm.clone()
+            for _ in range(3):
+                cx.rhs(state[0], h, wx, ox)
+            torch.cuda.synchronize()
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            for _ in range(10):
+                cx.rhs(state[0], h, wx, ox)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            per_rhs["spectral" if kind == S.CURL_SPECTRAL else "stencil"] = ea.elapsed_time(eb) / 10
+            del cx
         fd = {"curl": "second-order central differences (stencil passes, no unpadded FFTs)",
+              "ms_per_rhs_5_iterations": per_rhs,
               "value": N * (f1["rhs_calls"] - f0["rhs_calls"]) / (fd_ms * 1e-3), "unit": UNIT,
               "ms_per_step": fd_ms / max(nf, 1), "steps": nf, "t_start": tf, "steps_before_t_start": npre,
               "rhs_per_step": (f1["rhs_calls"] - f0["rhs_calls"]) / max(nf, 1),
@@ -606,7 +656,8 @@ def bench_ours(args, ws, rank, local):
                    "parallelism": f"replicas x{ws}"},
         "virgin_state": virgin,
         "host_stepped": host_stepped,
-        "fp64_path": {"value": fp64_value, "unit": UNIT, "steps": k64},
+        "fp64_path": {"value": fp64_value, "unit": UNIT, "steps": k64, "ms_per_step": fp64_ms_per_step},
+        "df64_path": df64,
         "fp32_error_vs_fp64": fp32_err,
         "fp32_error_vs_fp64_early_stop": fp32_err_stop,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e_h2d, "d2h_bytes_per_step": e2e_d2h,

@@ -47,10 +47,17 @@ typedef enum {
   SCFFT_ESIZE = 9      /* problem larger than a fixed, preallocated maximum */
 } scfft_status;
 
-/* Arithmetic of the FFTs and pointwise steps.  The integrator state, its stage
- * sums, error norm and step control are FP64 in both modes. */
+/* Arithmetic of the FFTs and pointwise steps.  The integrator state and its step control
+ * are FP64 in every mode.
+ *   SCFFT_PREC_F64   FP64 transforms; FP64 stage sums.
+ *   SCFFT_PREC_F32   FP32 transforms and stages, FP64 state with compensated sums.
+ *   SCFFT_PREC_DF64  double-float transforms (each value an unevaluated sum of two FP32
+ *                    numbers, a 48-bit significand, FP32's exponent range: FP64-equivalent
+ *                    accuracy on the FP32 pipes); the node-wise law in FP64; FP64 stage sums.
+ *                    Its buffers, entry points and results are those of SCFFT_PREC_F64. */
 #define SCFFT_PREC_F64 0
 #define SCFFT_PREC_F32 1
+#define SCFFT_PREC_DF64 2
 
 typedef struct {
   int nx, ny, nz;      /* nodes per axis */
@@ -63,7 +70,7 @@ typedef struct {
 } scfft_material;
 
 typedef struct {
-  int precision;       /* SCFFT_PREC_F64 or SCFFT_PREC_F32 */
+  int precision;       /* SCFFT_PREC_F64, SCFFT_PREC_F32 or SCFFT_PREC_DF64 */
   double delta_it;     /* Eq. 5 stop tolerance (§2 uses 2e-5); 0 = never stop early */
   int max_iter;        /* iteration cap of Eq. 5 (>= 0) */
   double sigma_scale;  /* multiplies sigma = half the cell diagonal (§2); 1 = paper */

@@ -18,11 +18,12 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-__all__ = ["ScfftError", "Context", "load_library", "library_path", "PREC_F64", "PREC_F32", "FAULT_TMA_WAIT",
+__all__ = ["ScfftError", "Context", "load_library", "library_path", "PREC_F64", "PREC_F32", "PREC_DF64", "FAULT_TMA_WAIT",
            "EXPORTS", "rhs_autograd", "integrate_autograd", "batch_step", "curl_noalloc"]
 
 PREC_F64 = 0
 PREC_F32 = 1
+PREC_DF64 = 2  # double-float FFT passes (FP64-equivalent accuracy on the FP32 pipes)
 FAULT_TMA_WAIT = 1  # scfft_inject_fault: the next directly launched TMA-fed y pass times out (tests)
 CURL_SPECTRAL = 0   # scfft_set_curl: smoothed spectral derivatives (§2)
 CURL_FD = 1         # scfft_set_curl: second-order central differences

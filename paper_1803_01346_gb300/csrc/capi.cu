@@ -35,6 +35,7 @@ struct scfft_ctx {
   cudaStream_t st = nullptr;
   Work<float> wf;
   Work<double> wd;
+  Work<dfloat> wq;  // double-float FFT passes (SCFFT_PREC_DF64)
   Ctrl* ctrl = nullptr;        // device
   PointParams* ppd = nullptr;  // device copy of the current rhs's PointParams
   double* partials = nullptr;  // device
@@ -148,6 +149,15 @@ bool grid_ok(int n) { return n == 16 || n == 32 || n == 48 || n == 64 || n == 96
 template <typename T> Work<T>& work(scfft_ctx* c);
 template <> Work<float>& work<float>(scfft_ctx* c) { return c->wf; }
 template <> Work<double>& work<double>(scfft_ctx* c) { return c->wd; }
+template <> Work<dfloat>& work<dfloat>(scfft_ctx* c) { return c->wq; }
+
+// Calls f with a value of the context's FFT element type: float (SCFFT_PREC_F32), double
+// (SCFFT_PREC_F64) or dfloat (SCFFT_PREC_DF64).
+template <typename F> auto by_prec(const scfft_ctx* c, F&& f) {
+  if (c->opt.precision == SCFFT_PREC_F32) return f(float{});
+  if (c->opt.precision == SCFFT_PREC_DF64) return f(dfloat{});
+  return f(double{});
+}
 
 template <typename T> Launch<T> launch_of(scfft_ctx* c) {
   Launch<T> L;
@@ -324,7 +334,7 @@ template <typename T> cudaError_t fd_maskpad(scfft_ctx* c, const Launch<T>& L, c
     if constexpr (sizeof(T) == 4)
       return launch_x_reg_io(L, X_PAD_F64, pp, nullptr, L.w->Jd, nullptr, nullptr, nullptr, 0, 0, chk);
     else
-      return launch_x<T>(L, X_PAD_F64, pp, L.w->Jd, nullptr, nullptr, 0, 0, chk);
+      return launch_x_pad_rows<T>(L, pp, L.w->Jd, chk);
   });
 }
 
@@ -610,7 +620,7 @@ scfft_status rhs_any(scfft_ctx* c, double t, int left, const double* h, double* 
   io.warm64 = warm;
   io.out64 = hdot;
   io.warm_out64 = warm;
-  return c->opt.precision == SCFFT_PREC_F32 ? rhs_impl<float>(c, t, left, io, it) : rhs_impl<double>(c, t, left, io, it);
+  return by_prec(c, [&](auto z) { return rhs_impl<decltype(z)>(c, t, left, io, it); });
 }
 
 template <typename T> scfft_status curl_impl(scfft_ctx* c, const double* f, double* out) {
@@ -1608,7 +1618,8 @@ scfft_status scfft_create(const scfft_grid* grid, const scfft_material* mat, con
   if (opt->max_iter < 0 || !(opt->delta_it >= 0) || !(opt->sigma_scale >= 0) || !isfinite(opt->sigma_scale))
     return SCFFT_EINVAL;
   if (!(opt->rtol > 0) || !(opt->atol > 0)) return SCFFT_EINVAL;
-  if (opt->precision != SCFFT_PREC_F64 && opt->precision != SCFFT_PREC_F32) return SCFFT_EINVAL;
+  if (opt->precision != SCFFT_PREC_F64 && opt->precision != SCFFT_PREC_F32 && opt->precision != SCFFT_PREC_DF64)
+    return SCFFT_EINVAL;
   scfft_ctx* c = new (std::nothrow) scfft_ctx();
   if (!c) return SCFFT_ENOMEM;
   c->g.nx = grid->nx; c->g.ny = grid->ny; c->g.nz = grid->nz;
@@ -1630,7 +1641,7 @@ scfft_status scfft_create(const scfft_grid* grid, const scfft_material* mat, con
       cudaHostAlloc(&c->herr, sizeof(unsigned long long), 0) != cudaSuccess) {
     s = SCFFT_ENOMEM;
   }
-  if (s == SCFFT_OK) s = (opt->precision == SCFFT_PREC_F32) ? alloc_work<float>(c) : alloc_work<double>(c);
+  if (s == SCFFT_OK) s = by_prec(c, [&](auto z) { return alloc_work<decltype(z)>(c); });
   if (s == SCFFT_OK && cudaMemset(c->ctrl, 0, sizeof(Ctrl)) != cudaSuccess) s = SCFFT_ECUDA;
   if (s != SCFFT_OK) {
     scfft_destroy(c);
@@ -1659,6 +1670,7 @@ void scfft_destroy(scfft_ctx* c) {
   if (c->hsdev) cudaFreeHost(c->hsdev);
   free_work(c->wf);
   free_work(c->wd);
+  free_work(c->wq);
   if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
   if (c->loop_graph) cudaGraphDestroy(c->loop_graph);
   cudaFree(c->ctrl); cudaFree(c->ppd); cudaFree(c->partials); cudaFree(c->mask); cudaFree(c->ib); cudaFree(c->errbits);
@@ -1698,30 +1710,25 @@ scfft_status scfft_set_jc_map(scfft_ctx* c, const double* jc) {
   const long long N = c->g.N;
   c->fsal_valid = false;
   c->epoch++;
-  if (c->opt.precision == SCFFT_PREC_F32) {
-    cudaFree(c->wf.jc);
-    c->wf.jc = nullptr;
+  return by_prec(c, [&](auto z) -> scfft_status {
+    typedef decltype(z) T;
+    Work<T>& w = work<T>(c);
+    cudaFree(w.jc);
+    w.jc = nullptr;
     if (jc) {
-      CK(cudaMalloc(&c->wf.jc, sizeof(float) * N));
-      CK(launch_convert<float>(jc, c->wf.jc, N, c->st));
+      CK(cudaMalloc(&w.jc, sizeof(T) * N));
+      CK(launch_convert<T>(jc, w.jc, N, c->st));
     }
-  } else {
-    cudaFree(c->wd.jc);
-    c->wd.jc = nullptr;
-    if (jc) {
-      CK(cudaMalloc(&c->wd.jc, sizeof(double) * N));
-      CK(launch_convert<double>(jc, c->wd.jc, N, c->st));
-    }
-  }
-  return SCFFT_OK;
+    return SCFFT_OK;
+  });
 }
 
 scfft_status scfft_set_curl(scfft_ctx* c, int kind) {
   if (!c || (kind != SCFFT_CURL_SPECTRAL && kind != SCFFT_CURL_FD)) return SCFFT_EINVAL;
   if (kind == c->curl_kind) return SCFFT_OK;
   if (kind == SCFFT_CURL_FD) {
-    const size_t bytes = (c->opt.precision == SCFFT_PREC_F32 ? sizeof(float) : sizeof(double)) * 3 * (size_t)c->g.N;
-    void** jd = c->opt.precision == SCFFT_PREC_F32 ? (void**)&c->wf.Jd : (void**)&c->wd.Jd;
+    const size_t bytes = by_prec(c, [](auto z) { return sizeof(z); }) * 3 * (size_t)c->g.N;
+    void** jd = by_prec(c, [&](auto z) { return (void**)&work<decltype(z)>(c).Jd; });
     if (!*jd && cudaMalloc(jd, bytes) != cudaSuccess) {
       cudaGetLastError();
       *jd = nullptr;
@@ -1781,9 +1788,10 @@ scfft_status scfft_precompute_kernel(scfft_ctx* c) {
   if (cudaMalloc(&scratch, sizeof(double) * 6 * oct) != cudaSuccess) return SCFFT_ENOMEM;
   const double dx = 2 * c->L[0] / g.nx, dy = 2 * c->L[1] / g.ny, dz = 2 * c->L[2] / g.nz;
   const double sig = c->opt.sigma_scale * 0.5 * sqrt(dx * dx + dy * dy + dz * dz);
-  cudaError_t e = (c->opt.precision == SCFFT_PREC_F32)
-                      ? launch_kernel_spectrum<float>(launch_of<float>(c), c->L[0], c->L[1], c->L[2], sig, scratch)
-                      : launch_kernel_spectrum<double>(launch_of<double>(c), c->L[0], c->L[1], c->L[2], sig, scratch);
+  cudaError_t e = by_prec(c, [&](auto z) {
+    typedef decltype(z) T;
+    return launch_kernel_spectrum<T>(launch_of<T>(c), c->L[0], c->L[1], c->L[2], sig, scratch);
+  });
   cudaError_t e2 = cudaStreamSynchronize(c->st);
   cudaFree(scratch);
   if (e != cudaSuccess || e2 != cudaSuccess) return SCFFT_ECUDA;
@@ -1802,13 +1810,13 @@ scfft_status scfft_rhs(scfft_ctx* c, double t, int left, const double* h, double
 
 scfft_status scfft_curl(scfft_ctx* c, const double* f, double* out) {
   if (!c || !f || !out || f == out) return SCFFT_EINVAL;
-  return c->opt.precision == SCFFT_PREC_F32 ? curl_impl<float>(c, f, out) : curl_impl<double>(c, f, out);
+  return by_prec(c, [&](auto z) { return curl_impl<decltype(z)>(c, f, out); });
 }
 
 scfft_status scfft_phi(scfft_ctx* c, const double* j, double* out) {
   if (!c || !j || !out || j == out) return SCFFT_EINVAL;
   if (!c->have_kernel) return SCFFT_ESTATE;
-  return c->opt.precision == SCFFT_PREC_F32 ? phi_impl<float>(c, j, out) : phi_impl<double>(c, j, out);
+  return by_prec(c, [&](auto z) { return phi_impl<decltype(z)>(c, j, out); });
 }
 
 scfft_status scfft_step(scfft_ctx* c, double* t, double* dt, double tstop, double* h, double* warm, int* rejected) {
@@ -2009,8 +2017,7 @@ scfft_status scfft_rhs_vjp(scfft_ctx* c, const double* h, const double* lam, dou
   if (!c || !h || !lam || !mu_h || mu_h == h || mu_h == lam) return SCFFT_EINVAL;
   if (!c->have_geom || !c->have_kernel || c->law || c->curl_kind != SCFFT_CURL_SPECTRAL) return SCFFT_ESTATE;
   c->fsal_valid = false;
-  return c->opt.precision == SCFFT_PREC_F32 ? vjp_impl<float>(c, h, lam, mu_h, mu_g, mu_jc, mu_a)
-                                            : vjp_impl<double>(c, h, lam, mu_h, mu_g, mu_jc, mu_a);
+  return by_prec(c, [&](auto z) { return vjp_impl<decltype(z)>(c, h, lam, mu_h, mu_g, mu_jc, mu_a); });
 }
 
 }  // extern "C"
@@ -2150,8 +2157,7 @@ scfft_status adj_call(scfft_ctx* c, AdjRec& r, double t, int left, const double*
                       double* grad_jc, double* grad_path, double* mu_a_acc) {
   AdjBufs& b = r.b;
   double ma[3];
-  CS_(c->opt.precision == SCFFT_PREC_F32 ? vjp_impl<float>(c, Y, lam, b.mh, b.mg, grad_jc ? b.jct : nullptr, ma)
-                                         : vjp_impl<double>(c, Y, lam, b.mh, b.mg, grad_jc ? b.jct : nullptr, ma));
+  CS_(by_prec(c, [&](auto z) { return vjp_impl<decltype(z)>(c, Y, lam, b.mh, b.mg, grad_jc ? b.jct : nullptr, ma); }));
   if (grad_jc) CK(axpy(c, grad_jc, grad_jc, 1.0, b.jct, c->g.N));
   path_grad(c, t, left, ma, grad_path);
   if (mu_a_acc)

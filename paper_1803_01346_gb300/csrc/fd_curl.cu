@@ -58,28 +58,30 @@ __global__ void fd_efield_kernel(Src h, const uint8_t* __restrict__ mask, const 
     const int x = (int)(i % g.nx);
     const long long r = i / g.nx;
     const int y = (int)(r % g.ny), z = (int)(r / g.ny);
-    T j[3];
-    curl_at<T>([&](long long k) { return h.at(k); }, x, y, z, g, inv2d0, inv2d1, inv2d2, j);
-    T f[3];
+    typedef typename acc_of<T>::type A;  // the law's arithmetic (FP64 for double-float)
+    T jt[3];
+    curl_at<T>([&](long long k) { return h.at(k); }, x, y, z, g, inv2d0, inv2d1, inv2d2, jt);
+    const A j[3] = {to_acc(jt[0]), to_acc(jt[1]), to_acc(jt[2])};
+    A f[3];
     if (mask[i]) {
-      T jcv = jcmap ? jcmap[i] : (T)pp.jc;
-      T a[3] = {(T)1, (T)1, (T)1};
+      A jcv = jcmap ? to_acc(jcmap[i]) : (A)pp.jc;
+      A a[3] = {(A)1, (A)1, (A)1};
       if (pp.law) {
         if (pp.kim_h0 > 0) {
-          const T h0 = (T)h.at(i), h1 = (T)h.at(N + i), h2 = (T)h.at(2 * N + i);
-          jcv = jcv / ((T)1 + sqrt(h0 * h0 + h1 * h1 + h2 * h2) / (T)pp.kim_h0);
+          const A h0 = (A)h.at(i), h1 = (A)h.at(N + i), h2 = (A)h.at(2 * N + i);
+          jcv = jcv / ((A)1 + sqrt(h0 * h0 + h1 * h1 + h2 * h2) / (A)pp.kim_h0);
         }
-        for (int q = 0; q < 3; ++q) a[q] = (T)pp.aniso[q];
+        for (int q = 0; q < 3; ++q) a[q] = (A)pp.aniso[q];
       }
-      const T u0 = a[0] * j[0], u1 = a[1] * j[1], u2 = a[2] * j[2];
-      const T rho = rho_fd<T>(sqrt(u0 * u0 + u1 * u1 + u2 * u2), jcv, (T)pp.n, (T)pp.e0);
+      const A u0 = a[0] * j[0], u1 = a[1] * j[1], u2 = a[2] * j[2];
+      const A rho = rho_fd<A>(sqrt(u0 * u0 + u1 * u1 + u2 * u2), jcv, (A)pp.n, (A)pp.e0);
       for (int q = 0; q < 3; ++q) f[q] = rho * a[q] * a[q];
     } else {
-      f[0] = f[1] = f[2] = (T)pp.rho_out;
+      f[0] = f[1] = f[2] = (A)pp.rho_out;
     }
-    out[i] = f[0] * j[0];
-    out[N + i] = f[1] * j[1];
-    out[2 * N + i] = f[2] * j[2];
+    out[i] = from_acc<T>(f[0] * j[0]);
+    out[N + i] = from_acc<T>(f[1] * j[1]);
+    out[2 * N + i] = from_acc<T>(f[2] * j[2]);
   }
 }
 
@@ -187,6 +189,7 @@ cudaError_t launch_fd_curl_mask(const Launch<T>& L, T* out, const double* d, boo
   template cudaError_t launch_fd_curl_mask<T>(const Launch<T>&, T*, const double*, bool);
 INST_FD(float)
 INST_FD(double)
+INST_FD(dfloat)
 #undef INST_FD
 
 }  // namespace scfft

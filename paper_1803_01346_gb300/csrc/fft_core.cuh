@@ -13,12 +13,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df64.cuh"
+
 namespace scfft {
 
 // ---------------------------------------------------------------- complex
 template <typename T> struct cplx_of;
 template <> struct cplx_of<float> { typedef float2 type; };
 template <> struct cplx_of<double> { typedef double2 type; };
+template <> struct cplx_of<dfloat> { typedef dfloat2 type; };
 
 __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
@@ -81,6 +84,25 @@ template <typename V, int R, bool INV> struct TwiddleConst {
       return INV ? mk(h * (sc * a.x - ss * a.y), h * (ss * a.x + sc * a.y))
                  : mk(h * (sc * a.x + ss * a.y), h * (sc * a.y - ss * a.x));
     }
+    return INV ? mk(a.x * c - a.y * s, a.x * s + a.y * c) : mk(a.x * c + a.y * s, a.y * c - a.x * s);
+  }
+};
+// double-float: the constants are the nearest double-floats of the FP64 values (folded at
+// compile time); the sign flips of the odd multiples of pi/4 are negations, not products
+template <int R, bool INV> struct TwiddleConst<dfloat2, R, INV> {
+  static __device__ __forceinline__ dfloat2 apply(dfloat2 a, int m) {
+    const int q = ((2 * m * 24 / R) % 48 + 48) % 48;
+    if (q == 0) return a;
+    if (q == 24) return mk(-a.x, -a.y);
+    if (q == 12) return INV ? mk(-a.y, a.x) : mk(a.y, -a.x);
+    if (q == 36) return INV ? mk(a.y, -a.x) : mk(-a.y, a.x);
+    if (q % 12 == 6) {
+      const dfloat h(0.7071067811865475244008444);
+      const dfloat ax = cos24(q) > 0 ? a.x : -a.x, ay = cos24(q) > 0 ? a.y : -a.y;  // sign(c) a
+      const dfloat bx = sin24(q) > 0 ? a.x : -a.x, by = sin24(q) > 0 ? a.y : -a.y;  // sign(s) a
+      return INV ? mk(h * (ax - by), h * (bx + ay)) : mk(h * (ax + by), h * (ay - bx));
+    }
+    const dfloat c(cos24(q)), s(sin24(q));
     return INV ? mk(a.x * c - a.y * s, a.x * s + a.y * c) : mk(a.x * c + a.y * s, a.y * c - a.x * s);
   }
 };

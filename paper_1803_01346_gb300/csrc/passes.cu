@@ -61,6 +61,23 @@ FftPlan make_plan(int L) {
 template <typename V> __device__ __forceinline__ V vzero();
 template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
 template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ dfloat2 vzero<dfloat2>() { return mk(dfloat(0.f, 0.f), dfloat(0.f, 0.f)); }
+
+// Euclidean norm of the change of one node's iterate (the Eq. 5 residual's summand): in FP64
+// for the FP32 and FP64 passes, from the high parts of the double-float difference for the
+// double-float passes (a stop test needs no more)
+__device__ __forceinline__ double dnorm3(float v0, float o0, float v1, float o1, float v2, float o2) {
+  const double d0 = (double)v0 - (double)o0, d1 = (double)v1 - (double)o1, d2 = (double)v2 - (double)o2;
+  return sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+}
+__device__ __forceinline__ double dnorm3(double v0, double o0, double v1, double o1, double v2, double o2) {
+  const double d0 = v0 - o0, d1 = v1 - o1, d2 = v2 - o2;
+  return sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+}
+__device__ __forceinline__ double dnorm3(dfloat v0, dfloat o0, dfloat v1, dfloat o1, dfloat v2, dfloat o2) {
+  const float d0 = (v0 - o0).hi, d1 = (v1 - o1).hi, d2 = (v2 - o2).hi;
+  return (double)sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+}
 
 // Power law of Eq. 1: returns rho(|j|) for |j| = jn.  FP32 evaluates
 // |j/jc|^(n-1) as 2^((n-1) log2(|j|/jc)) so that large n cannot overflow an
@@ -90,6 +107,7 @@ struct XArgs {
   const V* tw_in;
   const V* tw_out;
   const double* src_f64;
+  const T* src_t;     // real input rows in the pass's own type (instead of src_f64), or nullptr
   double* dst_f64;
   const double* warm;
   const uint8_t* mask;
@@ -169,7 +187,7 @@ __global__ void __launch_bounds__(kThreads) xpass_kernel(const XArgs<T> a) {
       T v = 0;
       if (q < nrows) {
         const size_t node = (size_t)q * nx + n;
-        v = (T)a.src_f64[(size_t)c * N + node];
+        v = a.src_t ? a.src_t[(size_t)c * N + node] : (T)a.src_f64[(size_t)c * N + node];
         if (MODE == X_ADJ_PAD && a.mask[node]) v = 0;   // (1 - chi)
         if (MODE == X_ADJ_IN && !a.mask[node]) v = 0;   // chi
       }
@@ -182,7 +200,9 @@ __global__ void __launch_bounds__(kThreads) xpass_kernel(const XArgs<T> a) {
   // ---- node-wise step on the real rows held in `data`
   double part = 0.0;
   if (kC2R) {
+    typedef typename acc_of<T>::type A;
     const PointParams& pp = a.pp;
+    const T he0 = (T)pp.hedot[0], he1 = (T)pp.hedot[1], he2 = (T)pp.hedot[2];
     for (int idx = tid; idx < R * nx; idx += nth) {
       const int n = idx % nx, r = idx / nx;
       const int q = q0 + r;
@@ -193,28 +213,30 @@ __global__ void __launch_bounds__(kThreads) xpass_kernel(const XArgs<T> a) {
       T* p2 = half_of<T>(&data[2 * CS + (r >> 1) + n * ES], r & 1);
       T v0 = *p0, v1 = *p1, v2 = *p2;
       if (MODE == X_POWERLAW) {
-        T rho;
+        A w0 = to_acc(v0), w1 = to_acc(v1), w2 = to_acc(v2);
+        A rho;
         if (a.mask[node]) {
-          T jcv = a.jc ? a.jc[node] : (T)pp.jc;
+          A jcv = a.jc ? to_acc(a.jc[node]) : (A)pp.jc;
           if (pp.law) {
             // e(j, h): jc(h) = jc / (1 + |h| / h0) (Kim), e = rho(|A j|) A^2 j
             if (pp.kim_h0 > 0) {
-              const T h0 = (T)a.src_f64[node], h1 = (T)a.src_f64[N + node], h2 = (T)a.src_f64[2 * N + node];
-              jcv = jcv / ((T)1 + sqrt(h0 * h0 + h1 * h1 + h2 * h2) / (T)pp.kim_h0);
+              const A h0 = (A)a.src_f64[node], h1 = (A)a.src_f64[N + node], h2 = (A)a.src_f64[2 * N + node];
+              jcv = jcv / ((A)1 + sqrt(h0 * h0 + h1 * h1 + h2 * h2) / (A)pp.kim_h0);
             }
-            const T ax = (T)pp.aniso[0], ay = (T)pp.aniso[1], az = (T)pp.aniso[2];
-            const T u0 = ax * v0, u1 = ay * v1, u2 = az * v2;
-            rho = rho_power(sqrt(u0 * u0 + u1 * u1 + u2 * u2), jcv, (T)pp.n, (T)pp.e0);
-            v0 *= rho * ax * ax; v1 *= rho * ay * ay; v2 *= rho * az * az;
+            const A ax = (A)pp.aniso[0], ay = (A)pp.aniso[1], az = (A)pp.aniso[2];
+            const A u0 = ax * w0, u1 = ay * w1, u2 = az * w2;
+            rho = rho_power(sqrt(u0 * u0 + u1 * u1 + u2 * u2), jcv, (A)pp.n, (A)pp.e0);
+            w0 *= rho * ax * ax; w1 *= rho * ay * ay; w2 *= rho * az * az;
           } else {
-            const T jn = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
-            rho = rho_power(jn, jcv, (T)pp.n, (T)pp.e0);
-            v0 *= rho; v1 *= rho; v2 *= rho;
+            const A jn = sqrt(w0 * w0 + w1 * w1 + w2 * w2);
+            rho = rho_power(jn, jcv, (A)pp.n, (A)pp.e0);
+            w0 *= rho; w1 *= rho; w2 *= rho;
           }
         } else {
-          rho = (T)pp.rho_out;
-          v0 *= rho; v1 *= rho; v2 *= rho;
+          rho = (A)pp.rho_out;
+          w0 *= rho; w1 *= rho; w2 *= rho;
         }
+        v0 = from_acc<T>(w0); v1 = from_acc<T>(w1); v2 = from_acc<T>(w2);
       } else if (MODE == X_ASSEMBLE) {
         if (a.mask[node]) {
           const T s = -(T)pp.inv_mu0;
@@ -230,9 +252,8 @@ __global__ void __launch_bounds__(kThreads) xpass_kernel(const XArgs<T> a) {
         if (a.mask[node]) {
           v0 = o0; v1 = o1; v2 = o2;
         } else {
-          v0 = (T)pp.hedot[0] + v0; v1 = (T)pp.hedot[1] + v1; v2 = (T)pp.hedot[2] + v2;
-          const double d0 = (double)v0 - (double)o0, d1 = (double)v1 - (double)o1, d2 = (double)v2 - (double)o2;
-          part += sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+          v0 = he0 + v0; v1 = he1 + v1; v2 = he2 + v2;
+          part += dnorm3(v0, o0, v1, o1, v2, o2);
         }
         a.hnew[node] = v0; a.hnew[N + node] = v1; a.hnew[2 * N + node] = v2;
       } else if (MODE == X_TO_F64 || MODE == X_CROP_F64) {
@@ -246,22 +267,24 @@ __global__ void __launch_bounds__(kThreads) xpass_kernel(const XArgs<T> a) {
         a.dst_f64[2 * N + node] = (double)v2 + (in ? a.src_f64[2 * N + node] : 0.0);
       } else if (MODE == X_ADJ_POWERLAW) {
         // lam_e = -(curl lam_u)/mu0; lam_j = J_e^T lam_e; J_e = rho (I + (n-1) jhat jhat^T) in Omega
-        const T s = -(T)pp.inv_mu0;
-        const T l0 = s * v0, l1 = s * v1, l2 = s * v2;
+        const A s = -(A)pp.inv_mu0;
+        const A l0 = s * to_acc(v0), l1 = s * to_acc(v1), l2 = s * to_acc(v2);
+        A w0, w1, w2;
         if (a.mask[node]) {
-          const T j0 = (T)a.src_f64[node], j1 = (T)a.src_f64[N + node], j2 = (T)a.src_f64[2 * N + node];
-          const T jcv = a.jc ? a.jc[node] : (T)pp.jc;
-          const T jn = sqrt(j0 * j0 + j1 * j1 + j2 * j2);
-          const T rho = rho_power(jn, jcv, (T)pp.n, (T)pp.e0);
-          const T jl = j0 * l0 + j1 * l1 + j2 * l2;
-          const T f = jn > 0 ? ((T)pp.n - 1) * jl / (jn * jn) : (T)0;
-          v0 = rho * (l0 + f * j0); v1 = rho * (l1 + f * j1); v2 = rho * (l2 + f * j2);
-          if (a.dst_f64) a.dst_f64[node] = (double)(-(T)pp.n * rho / jcv * jl);
+          const A j0 = (A)a.src_f64[node], j1 = (A)a.src_f64[N + node], j2 = (A)a.src_f64[2 * N + node];
+          const A jcv = a.jc ? to_acc(a.jc[node]) : (A)pp.jc;
+          const A jn = sqrt(j0 * j0 + j1 * j1 + j2 * j2);
+          const A rho = rho_power(jn, jcv, (A)pp.n, (A)pp.e0);
+          const A jl = j0 * l0 + j1 * l1 + j2 * l2;
+          const A f = jn > 0 ? ((A)pp.n - 1) * jl / (jn * jn) : (A)0;
+          w0 = rho * (l0 + f * j0); w1 = rho * (l1 + f * j1); w2 = rho * (l2 + f * j2);
+          if (a.dst_f64) a.dst_f64[node] = (double)(-(A)pp.n * rho / jcv * jl);
         } else {
-          const T r = (T)pp.rho_out;
-          v0 = r * l0; v1 = r * l1; v2 = r * l2;
+          const A r = (A)pp.rho_out;
+          w0 = r * l0; w1 = r * l1; w2 = r * l2;
           if (a.dst_f64) a.dst_f64[node] = 0.0;
         }
+        v0 = from_acc<T>(w0); v1 = from_acc<T>(w1); v2 = from_acc<T>(w2);
       }
       if (kR2C) { *p0 = v0; *p1 = v1; *p2 = v2; }
     }
@@ -548,6 +571,10 @@ __global__ void scale_convert_kernel(const double* __restrict__ src, double s, d
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     dst[i] = src[i] * s;
 }
+__global__ void scale_convert_kernel(const double* __restrict__ src, double s, dfloat* dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = dfloat(src[i] * s);
+}
 
 // ---------------------------------------------------------------- launchers
 static int grid_for(long long n) {
@@ -567,14 +594,10 @@ template <typename T> static int x_pairs(int Lmax) {
 }
 
 template <typename T>
-cudaError_t launch_x(const Launch<T>& L, XMode mode, const PointParams& pp, const double* src_f64, double* dst_f64,
-                     const double* warm, int in_buf, int out_buf, bool check_done) {
+static cudaError_t launch_x_impl(const Launch<T>& L, XMode mode, const PointParams& pp, const double* src_f64,
+                                 const T* src_t, double* dst_f64, const double* warm, int in_buf, int out_buf,
+                                 bool check_done) {
   typedef typename cplx_of<T>::type V;
-  // the FP32 forward passes use the register-resident kernels; the transposed
-  // (reverse-mode) passes use this shared-memory kernel in both precisions
-  if constexpr (sizeof(T) == 4)
-    if (mode < X_ADJ_PAD || mode == X_POWERLAW_H || mode == X_UPDATE_FD)
-      return launch_x_reg(L, mode, pp, src_f64, dst_f64, warm, in_buf, out_buf, check_done);
   if (mode == X_POWERLAW_H) mode = X_POWERLAW;
   if (mode == X_UPDATE_FD) mode = X_UPDATE;  // its R2C output is not read by the stencil curl
   XArgs<T> a{};
@@ -600,6 +623,7 @@ cudaError_t launch_x(const Launch<T>& L, XMode mode, const PointParams& pp, cons
   a.tw_in = a.Lin ? (pin ? L.w->twp[0] : L.w->twu[0]) : nullptr;
   a.tw_out = a.Lout ? (pout ? L.w->twp[0] : L.w->twu[0]) : nullptr;
   a.src_f64 = src_f64;
+  a.src_t = src_t;
   a.dst_f64 = dst_f64;
   a.warm = warm;
   a.mask = L.mask;
@@ -627,6 +651,22 @@ cudaError_t launch_x(const Launch<T>& L, XMode mode, const PointParams& pp, cons
 #undef XCASE
   }
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_x(const Launch<T>& L, XMode mode, const PointParams& pp, const double* src_f64, double* dst_f64,
+                     const double* warm, int in_buf, int out_buf, bool check_done) {
+  // the FP32 forward passes use the register-resident kernels; the transposed
+  // (reverse-mode) passes use the shared-memory kernel in every precision
+  if constexpr (sizeof(T) == 4)
+    if (mode < X_ADJ_PAD || mode == X_POWERLAW_H || mode == X_UPDATE_FD)
+      return launch_x_reg(L, mode, pp, src_f64, dst_f64, warm, in_buf, out_buf, check_done);
+  return launch_x_impl<T>(L, mode, pp, src_f64, nullptr, dst_f64, warm, in_buf, out_buf, check_done);
+}
+
+template <typename T>
+cudaError_t launch_x_pad_rows(const Launch<T>& L, const PointParams& pp, const T* rows, bool check_done) {
+  return launch_x_impl<T>(L, X_PAD_F64, pp, nullptr, rows, nullptr, nullptr, 0, 0, check_done);
 }
 
 template <typename T> static int col_tile() { return sizeof(T) == 4 ? 16 : 8; }
@@ -749,6 +789,7 @@ cudaError_t launch_kernel_spectrum(const Launch<T>& L, double Lx, double Ly, dou
 #define INST(T)                                                                                                  \
   template cudaError_t launch_x<T>(const Launch<T>&, XMode, const PointParams&, const double*, double*,        \
                                    const double*, int, int, bool);                                             \
+  template cudaError_t launch_x_pad_rows<T>(const Launch<T>&, const PointParams&, const T*, bool);             \
   template cudaError_t launch_y<T>(const Launch<T>&, bool, bool, bool);                                        \
   template cudaError_t launch_z_curl<T>(const Launch<T>&, bool, double);                                       \
   template cudaError_t launch_z_kernel<T>(const Launch<T>&, bool);                                             \
@@ -757,6 +798,7 @@ cudaError_t launch_kernel_spectrum(const Launch<T>& L, double Lx, double Ly, dou
   template cudaError_t launch_kernel_spectrum<T>(const Launch<T>&, double, double, double, double, double*);
 INST(float)
 INST(double)
+INST(dfloat)
 #undef INST
 
 }  // namespace scfft

@@ -130,10 +130,13 @@ struct Launch {
   cudaStream_t st;
 };
 
-// Pass launchers (defined in passes.cu, instantiated for float and double).
+// Pass launchers (defined in passes.cu, instantiated for float, double and dfloat).
 template <typename T> cudaError_t launch_x(const Launch<T>& L, XMode mode, const PointParams& pp,
                                            const double* src_f64, double* dst_f64, const double* warm,
                                            int in_buf, int out_buf, bool check_done);
+// X_PAD_F64 with its real input rows in the pass's own type (FP64 and double-float passes)
+template <typename T> cudaError_t launch_x_pad_rows(const Launch<T>& L, const PointParams& pp, const T* rows,
+                                                    bool check_done);
 template <typename T> cudaError_t launch_y(const Launch<T>& L, bool padded, bool inverse, bool check_done);
 template <typename T> cudaError_t launch_z_curl(const Launch<T>& L, bool check_done, double scale);
 template <typename T> cudaError_t launch_z_kernel(const Launch<T>& L, bool check_done);

@@ -104,3 +104,21 @@ def test_rhs_fp32_lens128_graph_loop_stops_with_the_oracle(lens):
     st = ctx.stats()
     assert abs(st["last_residual"] - r[-1]) < 5e-2 * r[-1], (st["last_residual"], r[-1])
     _check3("lens128 graph loop", out.cpu().numpy().reshape(h.shape), ref.hdot)
+
+
+@pytest.mark.parametrize("prec", [S.PREC_F64, S.PREC_DF64])
+def test_rhs_fp64_and_df64_lens128_fixed_iterations_match_oracle(lens, prec):
+    """The FP64 and double-float paths at the benchmark's grid (the shared-memory passes
+    at 256^3 padding): the same five iterations against the oracle at the FP64 tier."""
+    cfg, prob, h, g0, ref = lens
+    ctx = S.Context(cfg.n, cfg.L, n_power=cfg.n_power, rho_out=cfg.rho_out, precision=prec, delta_it=0.0,
+                    max_iter=ITERS)
+    ctx.set_geometry(cfg.mask)
+    ctx.set_field_path(cfg.knots_t, cfg.knots_he)
+    ctx.precompute_kernel()
+    out = torch.empty(h.size, dtype=torch.float64, device="cuda")
+    assert ctx.rhs(T, _dev(h), _dev(g0), out) == ITERS
+    torch.cuda.synchronize()
+    e = _rel(out.cpu().numpy().reshape(h.shape), ref.hdot)
+    print(f"[fp64/df64 error] lens128 precision {prec}: {e:.2e}")
+    assert e < 1e-10
