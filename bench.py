@@ -188,6 +188,7 @@ def make_ctx(S, cfg, precision, delta_it=2e-5, max_iter=100):
     ctx.set_geometry(cfg.mask)
     ctx.set_field_path(cfg.knots_t, cfg.knots_he)
     ctx.precompute_kernel()
+    ctx.autotune()  # launch schedule of the FP32 passes (cached per grid; a no-op otherwise)
     return ctx
 
 
@@ -268,12 +269,16 @@ def bench_batch(S, torch, steps: int, warmup: int):
     cfgs = I.batch_configs(64, seed=1803)
     streams = [torch.cuda.Stream() for _ in cfgs]
     inst = []
+    schedules = {}
     for c, st in zip(cfgs, streams):
         ctx = S.Context(c.n, c.L, n_power=c.n_power, rho_out=c.rho_out, precision=S.PREC_F32, rtol=c.rtol,
                         atol=c.atol, stream=st.cuda_stream)
         ctx.set_geometry(c.mask)
         ctx.set_field_path(c.knots_t, c.knots_he)
         ctx.precompute_kernel()
+        sched = ctx.autotune()  # timed once per grid size, then cached
+        if c.n[0] not in schedules:
+            schedules[c.n[0]] = sched
         N = int(np.prod(c.n))
         h = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
         w = torch.zeros(3 * N, dtype=torch.float64, device="cuda")
@@ -292,12 +297,15 @@ def bench_batch(S, torch, steps: int, warmup: int):
         t, dt, _ = S.batch_step(ctxs, t, dt, stop, hs, wsv)
     torch.cuda.synchronize()
     c0 = [x[0].stats()["rhs_calls"] for x in inst]
+    i0 = [x[0].stats()["iterations"] for x in inst]
     t0 = time.perf_counter()
     for _ in range(steps):
         t, dt, _ = S.batch_step(ctxs, t, dt, stop, hs, wsv)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     evals = sum(x[3] * (x[0].stats()["rhs_calls"] - c) for x, c in zip(inst, c0))
+    rcs = sum(x[0].stats()["rhs_calls"] - c for x, c in zip(inst, c0))
+    its = sum(x[0].stats()["iterations"] - c for x, c in zip(inst, i0))
     # the same instances, one after another
     t1 = time.perf_counter()
     for i, (ctx, h, w, N) in enumerate(inst):
@@ -309,6 +317,9 @@ def bench_batch(S, torch, steps: int, warmup: int):
     return {"instances": len(inst), "grids": sorted({c.n[0] for c in cfgs}), "steps": steps,
             "instance_steps_per_s": len(inst) * steps / el, "voxel_rhs_evals_per_s": evals / el,
             "sequential_instance_steps_per_s": len(inst) * steps / seq, "speedup_vs_sequential": seq / el,
+            "iters_per_rhs": its / max(1, rcs),
+            "schedules": {str(k): {kk: v[kk] for kk in ("z_kernel_tile", "z_curl_tile", "y_unpadded_tile",
+                                                         "y_padded_tma")} for k, v in sorted(schedules.items())},
             "timing": "wall clock around synchronous batch calls, device synchronised on both sides"}
 
 
@@ -383,6 +394,7 @@ def bench_ours(args, ws, rank, local):
     N = cfg.n[0] * cfg.n[1] * cfg.n[2]
     n3 = 3 * N
     ctx = make_ctx(S, cfg, S.PREC_F32)
+    sched_used = ctx.get_schedule()  # chosen by the autotuner in make_ctx
     h = torch.zeros(n3, dtype=torch.float64, device="cuda")
     warm = torch.zeros(n3, dtype=torch.float64, device="cuda")
     warm.view(3, N)[2] = cfg.knots_he[1][2] / cfg.knots_t[1]  # dh_e/dt at t = 0
@@ -651,6 +663,7 @@ def bench_ours(args, ws, rank, local):
                    "seconds_to_t_start": round(pre_s, 2), "rhs_per_step": rhs_calls / args.steps,
                    "iters_per_rhs": iters / max(rhs_calls, 1), "steps_taken": taken,
                    "stepping": "device-resident: the K steps are one CUDA graph launch (scfft_advance)",
+                   "schedule": sched_used,
                    "l2": "inputs larger than L2 (FP64 state and "
                    "stage buffers 7 x 50 MB, padded spectrum 101 MB per pass)",
                    "parallelism": f"replicas x{ws}"},

@@ -128,6 +128,39 @@ scfft_status scfft_set_jc_map(scfft_ctx* ctx, const double* jc_dev);
 #define SCFFT_CURL_FD 1
 scfft_status scfft_set_curl(scfft_ctx* ctx, int kind);
 
+/* Launch schedule of the FP32 passes that carry the transforms of Eqs. 3-7: how the spectral
+ * columns are tiled over CTAs and whether the padded y passes load through TMA.  A schedule
+ * never changes the arithmetic of a column: every schedule gives the same results bit for
+ * bit, only their speed differs by grid size.
+ *   z_kernel_tile    padded z pass with the Biot-Savart kernel product (Eq. 7): 4 or 8 columns
+ *   z_curl_tile      z pass of the smoothed curl (Eq. 4): 8 or 16 columns
+ *   y_unpadded_tile  y passes on the unpadded grid: 8 or 16 columns
+ *   y_padded_tma     padded y passes: 1 = TMA-fed persistent kernel, 0 = plain loads
+ *   us               scfft_autotune only: mean time (microseconds) of the candidates in the order
+ *                    z_kernel 8, 4; z_curl 8, 16; y_unpadded 8, 16 (forward + inverse);
+ *                    y_padded TMA, plain (forward + inverse); 0 where not timed. */
+typedef struct {
+  int z_kernel_tile;
+  int z_curl_tile;
+  int y_unpadded_tile;
+  int y_padded_tma;
+  double us[8];
+} scfft_schedule;
+
+/* Autotuner of the schedule: times each candidate of each knob on the context's own workspace
+ * (a few launches each, CUDA events on its stream; the scratch spectra are overwritten, no
+ * state is touched), keeps the fastest, and caches the choice per device and grid for the
+ * process, so that later contexts of that grid (a batch) reuse it without timing; retune != 0
+ * times again.  Rebuilds the context's captured graphs on their next launch.  FP64 and
+ * double-float contexts have no schedule: SCFFT_OK, nothing timed.  out (may be NULL)
+ * receives the schedule in use.  Errors: SCFFT_EINVAL (NULL ctx), SCFFT_ECUDA. */
+scfft_status scfft_autotune(scfft_ctx* ctx, int retune, scfft_schedule* out);
+/* The schedule in use (out->us zero). */
+scfft_status scfft_get_schedule(scfft_ctx* ctx, scfft_schedule* out);
+/* Impose a schedule (FP32 contexts; SCFFT_EINVAL for a value outside the lists above, for
+ * y_padded_tma = 1 without TMA descriptors, or for another precision). */
+scfft_status scfft_set_schedule(scfft_ctx* ctx, const scfft_schedule* sched);
+
 /* The e(j, h) law in Omega.  §2 (after Eq. 1) notes that another current-voltage relation,
  * e(j) or e(j, h) with h the local magnetic field, can replace the power law; two are
  * provided, alone or together:

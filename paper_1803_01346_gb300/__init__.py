@@ -38,6 +38,7 @@ EXPORTS = ("scfft_create", "scfft_set_geometry", "scfft_set_jc_map", "scfft_set_
            "scfft_rhs_vjp", "scfft_adjoint_integrate", "scfft_batch_step", "scfft_sync", "scfft_get_stats", "scfft_status_string", "scfft_destroy",
            "scfft_curl_noalloc", "scfft_last_cuda_error", "scfft_inject_fault", "scfft_checkpoint_save",
            "scfft_checkpoint_load", "scfft_step_host", "scfft_adjoint_record", "scfft_adjoint_step", "scfft_set_ej_law", "scfft_set_curl",
+           "scfft_autotune", "scfft_get_schedule", "scfft_set_schedule",
            "scfft_advance")
 
 NKINDS = 14
@@ -79,6 +80,11 @@ class _FieldPath(ctypes.Structure):
 
 class _EjLaw(ctypes.Structure):
     _fields_ = [("kim_h0", ctypes.c_double), ("aniso", ctypes.c_double * 3)]
+
+
+class _Schedule(ctypes.Structure):
+    _fields_ = [("z_kernel_tile", ctypes.c_int), ("z_curl_tile", ctypes.c_int), ("y_unpadded_tile", ctypes.c_int),
+                ("y_padded_tma", ctypes.c_int), ("us", ctypes.c_double * 8)]
 
 
 class _Stats(ctypes.Structure):
@@ -134,6 +140,9 @@ def load_library(path: Optional[str] = None):
         "scfft_adjoint_step": (I, [P, I, P, P, P]),
         "scfft_set_ej_law": (I, [P, ctypes.POINTER(_EjLaw)]),
         "scfft_set_curl": (I, [P, I]),
+        "scfft_autotune": (I, [P, I, P]),
+        "scfft_get_schedule": (I, [P, P]),
+        "scfft_set_schedule": (I, [P, P]),
         "scfft_advance": (I, [P, ctypes.POINTER(D), ctypes.POINTER(D), D, I, P, P, ctypes.POINTER(I)]),
         "scfft_batch_step": (I, [P, I, P, P, P, P, P, P]),
     }
@@ -234,6 +243,28 @@ class Context:
     def set_curl(self, kind: int):
         """CURL_SPECTRAL (§2) or CURL_FD (central differences) for the curls of the rhs."""
         self._check(self._lib.scfft_set_curl(self._h, int(kind)), "scfft_set_curl")
+
+    _SCHED_KEYS = ("z_kernel_tile", "z_curl_tile", "y_unpadded_tile", "y_padded_tma")
+
+    def autotune(self, retune: bool = False):
+        """Time the launch schedules of the FP32 passes on this context's grid and keep the
+        fastest (cached per device and grid); returns the schedule and the candidates' times."""
+        o = _Schedule()
+        self._check(self._lib.scfft_autotune(self._h, 1 if retune else 0, ctypes.byref(o)), "scfft_autotune")
+        d = {k: getattr(o, k) for k in self._SCHED_KEYS}
+        d["us"] = list(o.us)
+        return d
+
+    def get_schedule(self):
+        o = _Schedule()
+        self._check(self._lib.scfft_get_schedule(self._h, ctypes.byref(o)), "scfft_get_schedule")
+        return {k: getattr(o, k) for k in self._SCHED_KEYS}
+
+    def set_schedule(self, **kw):
+        cur = self.get_schedule()
+        cur.update(kw)
+        o = _Schedule(*(int(cur[k]) for k in self._SCHED_KEYS))
+        self._check(self._lib.scfft_set_schedule(self._h, ctypes.byref(o)), "scfft_set_schedule")
 
     def set_ej_law(self, kim_h0: float = 0.0, aniso=(1.0, 1.0, 1.0)):
         """The e(j, h) law in Omega (see scfft_set_ej_law): Kim's jc(|h|) = jc/(1 + |h|/kim_h0)

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -1721,6 +1722,150 @@ scfft_status scfft_set_jc_map(scfft_ctx* c, const double* jc) {
     }
     return SCFFT_OK;
   });
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- schedule autotuner
+namespace {
+
+// Schedules chosen per device and grid, shared by every context of that grid (a batch of
+// instances tunes once per grid size).
+std::mutex g_tune_mutex;
+std::map<std::vector<int>, Sched> g_tune_cache;
+
+// Drop the captured graphs of a context: they hold the launches of the old schedule.
+void drop_loop_graph(scfft_ctx* c) {
+  if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+  if (c->loop_graph) cudaGraphDestroy(c->loop_graph);
+  c->loop_exec = nullptr;
+  c->loop_graph = nullptr;
+  c->loop_failed = false;
+  c->epoch++;  // the step graph and the batch graph are rebuilt on their next launch
+}
+
+void to_public(const Sched& s, scfft_schedule* o) {
+  o->z_kernel_tile = s.zk_tc;
+  o->z_curl_tile = s.zc_tc;
+  o->y_unpadded_tile = s.yu_tc;
+  o->y_padded_tma = s.yp_tma;
+}
+
+bool sched_ok(const scfft_schedule* s) {
+  return (s->z_kernel_tile == 4 || s->z_kernel_tile == 8) && (s->z_curl_tile == 8 || s->z_curl_tile == 16) &&
+         (s->y_unpadded_tile == 8 || s->y_unpadded_tile == 16) && (s->y_padded_tma == 0 || s->y_padded_tma == 1);
+}
+
+// Mean device time (us) of one call of f (a few pass launches) on the context's stream: two
+// untimed calls, then five between CUDA events.
+template <typename F> scfft_status time_us(scfft_ctx* c, F&& f, double* us) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return SCFFT_ECUDA;
+  }
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = f();
+  if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
+  for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = f();
+  if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) {
+    note_cuda_error(e, __FILE__, __LINE__);
+    return SCFFT_ECUDA;
+  }
+  *us = 1e3 * ms / 5.0;
+  return SCFFT_OK;
+}
+
+// Time each candidate of each knob of the FP32 passes on the context's own workspace (the
+// passes transform its scratch spectra in place; their contents are not used afterwards) and
+// keep the fastest; knobs act on different passes, so they are tuned one at a time.
+scfft_status autotune_f32(scfft_ctx* c, double us[8]) {
+  Launch<float> L = launch_of<float>(c);
+  L.fault = nullptr;
+  Sched& s = c->wf.sched;
+  const double inv_n = 1.0 / (double)c->g.N;
+  auto pick = [&](int* knob, const int cand[2], double* t, auto launch) -> scfft_status {
+    for (int k = 0; k < 2; ++k) {
+      *knob = cand[k];
+      CS_(time_us(c, launch, &t[k]));
+    }
+    *knob = t[1] < t[0] ? cand[1] : cand[0];
+    return SCFFT_OK;
+  };
+  const int zk[2] = {8, 4}, zc[2] = {8, 16}, yu[2] = {8, 16}, yp[2] = {1, 0};
+  CS_(pick(&s.zk_tc, zk, us + 0, [&] { return launch_z_kernel<float>(L, false); }));
+  CS_(pick(&s.zc_tc, zc, us + 2, [&] { return launch_z_curl<float>(L, false, inv_n); }));
+  CS_(pick(&s.yu_tc, yu, us + 4, [&] {
+    const cudaError_t e = launch_y<float>(L, false, false, false);
+    return e != cudaSuccess ? e : launch_y<float>(L, false, true, false);
+  }));
+  if (c->wf.ym) {
+    CS_(pick(&s.yp_tma, yp, us + 6, [&] {
+      const cudaError_t e = launch_y<float>(L, true, false, false);
+      return e != cudaSuccess ? e : launch_y<float>(L, true, true, false);
+    }));
+  } else {
+    s.yp_tma = 0;
+  }
+  return SCFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+scfft_status scfft_autotune(scfft_ctx* c, int retune, scfft_schedule* out) {
+  if (!c) return SCFFT_EINVAL;
+  if (out) memset(out, 0, sizeof(*out));
+  if (c->opt.precision != SCFFT_PREC_F32) {  // the shared-memory passes have no schedule to choose
+    if (out) to_public(Sched(), out);
+    return SCFFT_OK;
+  }
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const std::vector<int> key = {dev, c->g.nx, c->g.ny, c->g.nz};
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  CK(cudaStreamSynchronize(c->st));
+  auto it = g_tune_cache.find(key);
+  if (it != g_tune_cache.end() && !retune) {
+    c->wf.sched = it->second;
+  } else {
+    double us[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    CS_(autotune_f32(c, us));
+    g_tune_cache[key] = c->wf.sched;
+    if (out)
+      for (int i = 0; i < 8; ++i) out->us[i] = us[i];
+  }
+  drop_loop_graph(c);
+  if (out) to_public(c->wf.sched, out);
+  return SCFFT_OK;
+}
+
+scfft_status scfft_get_schedule(scfft_ctx* c, scfft_schedule* out) {
+  if (!c || !out) return SCFFT_EINVAL;
+  memset(out, 0, sizeof(*out));
+  to_public(c->opt.precision == SCFFT_PREC_F32 ? c->wf.sched : Sched(), out);
+  return SCFFT_OK;
+}
+
+scfft_status scfft_set_schedule(scfft_ctx* c, const scfft_schedule* s) {
+  if (!c || !s || !sched_ok(s)) return SCFFT_EINVAL;
+  if (c->opt.precision != SCFFT_PREC_F32) return SCFFT_EINVAL;
+  if (s->y_padded_tma && !c->wf.ym) return SCFFT_EINVAL;
+  CK(cudaStreamSynchronize(c->st));
+  c->wf.sched.zk_tc = s->z_kernel_tile;
+  c->wf.sched.zc_tc = s->z_curl_tile;
+  c->wf.sched.yu_tc = s->y_unpadded_tile;
+  c->wf.sched.yp_tma = s->y_padded_tma;
+  drop_loop_graph(c);
+  return SCFFT_OK;
 }
 
 scfft_status scfft_set_curl(scfft_ctx* c, int kind) {

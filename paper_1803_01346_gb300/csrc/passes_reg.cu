@@ -172,15 +172,21 @@ template <template <int, int> class F, typename... A> cudaError_t by_length(int 
   return cudaErrorInvalidValue;
 }
 
+// (the column tiles TC of the unpadded y passes and of both z passes follow the context's
+// schedule, Sched; the tile changes which CTA holds a column, not the column's arithmetic)
 template <int R1, int R2> struct YFwdU {
   static cudaError_t run(const Launch<float>& L, bool chk) {
     const Geo& g = L.g;
+    if (L.w->sched.yu_tc == 16)
+      return go_y<R1, R2, 16, false, false, false, false>(L, L.w->U, g.ny, g.sxu, g.nx / 2 + 1, L.w->twu[1], chk);
     return go_y<R1, R2, 8, false, false, false, false>(L, L.w->U, g.ny, g.sxu, g.nx / 2 + 1, L.w->twu[1], chk);
   }
 };
 template <int R1, int R2> struct YInvU {
   static cudaError_t run(const Launch<float>& L, bool chk) {
     const Geo& g = L.g;
+    if (L.w->sched.yu_tc == 16)
+      return go_y<R1, R2, 16, true, false, false, false>(L, L.w->U, g.ny, g.sxu, g.nx / 2 + 1, L.w->twu[1], chk);
     return go_y<R1, R2, 8, true, false, false, false>(L, L.w->U, g.ny, g.sxu, g.nx / 2 + 1, L.w->twu[1], chk);
   }
 };
@@ -199,12 +205,16 @@ template <int R1, int R2> struct YInvP {
 template <int R1, int R2> struct ZCurl {
   static cudaError_t run(const Launch<float>& L, bool chk, double scale) {
     const Geo& g = L.g;
+    if (L.w->sched.zc_tc == 16)
+      return go_z<R1, R2, 16, 0>(L, L.w->U, g.ny, g.sxu, g.nx / 2 + 1, L.w->twu[2], scale, chk);
     return go_z<R1, R2, 8, 0>(L, L.w->U, g.ny, g.sxu, g.nx / 2 + 1, L.w->twu[2], scale, chk);
   }
 };
 template <int R1, int R2> struct ZKern {
   static cudaError_t run(const Launch<float>& L, bool chk) {
     const Geo& g = L.g;
+    if (L.w->sched.zk_tc == 4)
+      return go_z<R1, R2, 4, 1>(L, L.w->Pd, 2 * g.ny, g.sxp, g.nx + 1, L.w->twp[2], 1.0, chk);
     return go_z<R1, R2, 8, 1>(L, L.w->Pd, 2 * g.ny, g.sxp, g.nx + 1, L.w->twp[2], 1.0, chk);
   }
 };
@@ -212,7 +222,7 @@ template <int R1, int R2> struct ZKern {
 }  // namespace
 
 cudaError_t launch_y_reg(const Launch<float>& L, bool padded, bool inverse, bool check_done) {
-  if (L.w->ym) {
+  if (L.w->ym && L.w->sched.yp_tma) {
     const cudaError_t e = launch_y_tma(L, padded, inverse, check_done);
     if (e != cudaErrorNotSupported) return e;
   }

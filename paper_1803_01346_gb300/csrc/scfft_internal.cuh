@@ -59,6 +59,16 @@ struct YMaps {
   CUtensorMap m[2];
 };
 
+// Launch schedule of the FP32 register passes (chosen by scfft_autotune): how the spectral
+// columns are tiled over CTAs and how the padded y passes load, never the arithmetic of a
+// column, so every schedule gives the same bits.
+struct Sched {
+  int zk_tc = 8;   // padded z pass (Biot-Savart kernel product): columns per CTA, 4 or 8
+  int zc_tc = 8;   // smoothed-curl z pass: columns per CTA, 8 or 16
+  int yu_tc = 8;   // unpadded y passes: columns per CTA, 8 or 16
+  int yp_tma = 1;  // padded y passes: TMA-fed persistent kernel (1) or plain loads, 16 columns (0)
+};
+
 // Device workspaces of one FFT precision T.
 template <typename T>
 struct Work {
@@ -75,6 +85,7 @@ struct Work {
   V* twp[3] = {nullptr, nullptr, nullptr}; // twiddles, L = 2nx, 2ny, 2nz
   YMaps* ym = nullptr;   // FP32 only: TMA descriptors of the y passes (nullptr: plain-load y passes)
   T* Jd = nullptr;       // [3][N] masked stencil curl of the iterate (local-stencil curl option only)
+  Sched sched;           // FP32 only: launch schedule of the register passes
 };
 
 enum XMode : int {
