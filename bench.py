@@ -49,7 +49,7 @@ REF_ITERS_PER_RHS = 5.0
 T_START = 0.3  # start of the timed steps on the lens ramp (h_e reaches 0.8 at t = 0.8)
 # DRAM bytes (read + write) per launch from the committed ncu capture
 # profiles/ncu_zpass_xupdate_lens128_fp32.md; an entry is removed when its kernel changes.
-NCU_TRAFFIC = {"z_kernel": 161975040 + 59192320}
+NCU_TRAFFIC = {}
 
 
 def _peaks():
@@ -155,10 +155,26 @@ class ClockSampler:
                 "window_ms": round((self.t_end - self.t_begin) * 1e3, 1) if self.t_begin is not None else None}
 
 
-def algorithmic_bytes(kind: str, n, fp_bytes: int) -> float:
-    """Bytes a pass must move per launch (each array read or written once)."""
+def source_box(mask) -> tuple:
+    """Fractions of the planes (z) and of the rows (y, z) that hold Omega's bounding box, with
+    the y bounds rounded out to even rows as the library does: the Eq. 5 convolution's source
+    chi curl dh^i vanishes outside, and the forward padded passes skip the rest."""
+    m = np.asarray(mask, dtype=bool)  # [z][y][x]
+    zs = np.nonzero(m.any(axis=(1, 2)))[0]
+    ys = np.nonzero(m.any(axis=(0, 2)))[0]
+    nz, ny = m.shape[0], m.shape[1]
+    y0, y1 = int(ys[0]) & ~1, min(ny, (int(ys[-1]) + 2) & ~1)
+    nzb, nyb = int(zs[-1]) - int(zs[0]) + 1, y1 - y0
+    return nzb / nz, nzb * nyb / (nz * ny)
+
+
+def algorithmic_bytes(kind: str, n, fp_bytes: int, box=(1.0, 1.0)) -> float:
+    """Bytes a pass must move per launch (each array read or written once); box = the plane
+    and row fractions of the Eq. 5 source's support (source_box), which bound what the
+    forward padded passes of an iteration must read and write."""
     nx, ny, nz = n
     N = nx * ny * nz
+    fz, fyz = box
     c = 2 * fp_bytes                     # one complex value
     U = 3 * (nx // 2 + 1) * ny * nz * c  # unpadded half spectrum, 3 components
     Pin = 3 * (nx + 1) * ny * nz * c     # padded spectrum, rows y < ny
@@ -169,14 +185,14 @@ def algorithmic_bytes(kind: str, n, fp_bytes: int) -> float:
         "x_fwd_state": 3 * N * 8 + U,
         "x_powerlaw": 2 * U + N,
         "x_assemble": 2 * U + N + real + 3 * N * 8,
-        "x_maskpad": U + N + Pin,
+        "x_maskpad": (U + N + Pin) * fyz,
         "x_update": Pin + 2 * real + N + U,
         "y_fwd_unpadded": 2 * U,
         "y_inv_unpadded": 2 * U,
         "z_curl": 2 * U,
-        "y_fwd_padded": Pin + Pall,
+        "y_fwd_padded": Pin * fyz + Pall * fz,
         "y_inv_padded": Pall + Pin,
-        "z_kernel": 2 * Pall + kap,
+        "z_kernel": Pall * fz + Pall + kap,
         "finalize": real + 2 * 3 * N * 8,
     }
     return float(table.get(kind, 0.0))
@@ -473,11 +489,15 @@ def bench_ours(args, ws, rank, local):
     kinds = {k: v for k, v in prof.items() if v[0] > 0}
     # the dominant pass among those with algorithmic HBM bytes (the one-thread stage kernels
     # of the device-resident step carry none)
+    box = source_box(cfg.mask)
     dom = max((k for k in kinds if algorithmic_bytes(k, cfg.n, 4) > 0), key=lambda k: kinds[k][1])
     cnt, tot = kinds[dom]
     avg_ms = tot / cnt
     peak, peak_src = _peaks()
+    # algorithmic bytes: the pass's per-unit figure for the whole grid (each array read or
+    # written once); the same with the source box, the least the pass must move here
     achieved = algorithmic_bytes(dom, cfg.n, 4) / (avg_ms * 1e-3) / 1e9
+    achieved_box = algorithmic_bytes(dom, cfg.n, 4, box) / (avg_ms * 1e-3) / 1e9
     total_prof_ms = sum(v[1] for v in kinds.values())
     shares = {k: round(v[1] / total_prof_ms, 4) for k, v in sorted(kinds.items(), key=lambda kv: -kv[1][1])}
 
@@ -680,6 +700,9 @@ def bench_ours(args, ws, rank, local):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src, "traffic": NCU_TRAFFIC.get(dom),
                      "bytes_per_launch": algorithmic_bytes(dom, cfg.n, 4), "avg_launch_ms": avg_ms,
+                     "source_box": {"plane_fraction": box[0], "row_fraction": box[1],
+                                    "bytes_per_launch": algorithmic_bytes(dom, cfg.n, 4, box),
+                                    "achieved": achieved_box, "frac": achieved_box / peak},
                      "launches": cnt},
         "pass_shares": shares,
         "clocks": clk,

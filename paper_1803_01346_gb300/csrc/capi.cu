@@ -37,6 +37,7 @@ struct scfft_ctx {
   Work<float> wf;
   Work<double> wd;
   Work<dfloat> wq;  // double-float FFT passes (SCFFT_PREC_DF64)
+  int box[4] = {0, 0, 0, 0};  // bounding box of Omega's nodes: y in [box0, box1) (even), z in [box2, box3)
   Ctrl* ctrl = nullptr;        // device
   PointParams* ppd = nullptr;  // device copy of the current rhs's PointParams
   double* partials = nullptr;  // device
@@ -170,7 +171,18 @@ template <typename T> Launch<T> launch_of(scfft_ctx* c) {
   L.ppd = c->ppd;
   L.fault = &c->fault;
   L.st = c->st;
+  L.by0 = c->box[0];
+  L.by1 = c->box[1];
+  L.bz0 = c->box[2];
+  L.bz1 = c->box[3];
   return L;
+}
+
+// The same launch description with the source box on (the forward passes of an Eq. 5 iteration).
+template <typename T> Launch<T> boxed(const Launch<T>& L) {
+  Launch<T> B = L;
+  B.use_box = B.by1 > B.by0 && B.bz1 > B.bz0;
+  return B;
 }
 
 // ---------------------------------------------------------------- profiling
@@ -342,16 +354,17 @@ template <typename T> cudaError_t fd_maskpad(scfft_ctx* c, const Launch<T>& L, c
 template <typename T> cudaError_t iteration(scfft_ctx* c, const Launch<T>& L, PointParams pp, int i, bool chk) {
   cudaError_t e;
   const bool fd = c->curl_kind == SCFFT_CURL_FD;
+  const Launch<T> LB = boxed(L);  // the source chi curl dh^i vanishes outside Omega's box
   if (fd) {
     if ((e = fd_maskpad<T>(c, L, pp, chk)) != cudaSuccess) return e;
   } else {
     if ((e = curl_in_U<T>(c, L, chk)) != cudaSuccess) return e;
     if ((e = run(c, SCFFT_K_X_MASKPAD,
-                 [&] { return launch_x<T>(L, X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, chk); })) != cudaSuccess)
+                 [&] { return launch_x<T>(LB, X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, chk); })) != cudaSuccess)
       return e;
   }
-  if ((e = run(c, SCFFT_K_Y_FWD_P, [&] { return launch_y<T>(L, true, false, chk); })) != cudaSuccess) return e;
-  if ((e = run(c, SCFFT_K_Z_KERNEL, [&] { return launch_z_kernel<T>(L, chk); })) != cudaSuccess) return e;
+  if ((e = run(c, SCFFT_K_Y_FWD_P, [&] { return launch_y<T>(LB, true, false, chk); })) != cudaSuccess) return e;
+  if ((e = run(c, SCFFT_K_Z_KERNEL, [&] { return launch_z_kernel<T>(LB, chk); })) != cudaSuccess) return e;
   if ((e = run(c, SCFFT_K_Y_INV_P, [&] { return launch_y<T>(L, true, true, chk); })) != cudaSuccess) return e;
   pp.iter = i;
   return run(c, SCFFT_K_X_UPDATE, [&] {
@@ -389,10 +402,11 @@ cudaError_t loop_body(const Launch<float>& L, const PointParams& pp, cudaGraphCo
     if ((e = launch_y<float>(L, false, false, false)) != cudaSuccess) return e;
     if ((e = launch_z_curl<float>(L, false, 1.0 / (double)L.g.N)) != cudaSuccess) return e;
     if ((e = launch_y<float>(L, false, true, false)) != cudaSuccess) return e;
-    if ((e = launch_x<float>(L, X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, false)) != cudaSuccess) return e;
+    if ((e = launch_x<float>(boxed(L), X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, false)) != cudaSuccess)
+      return e;
   }
-  if ((e = launch_y<float>(L, true, false, false)) != cudaSuccess) return e;
-  if ((e = launch_z_kernel<float>(L, false)) != cudaSuccess) return e;
+  if ((e = launch_y<float>(boxed(L), true, false, false)) != cudaSuccess) return e;
+  if ((e = launch_z_kernel<float>(boxed(L), false)) != cudaSuccess) return e;
   if ((e = launch_y<float>(L, true, true, false)) != cudaSuccess) return e;
   if ((e = launch_x<float>(L, fd ? X_UPDATE_FD : X_UPDATE, pp, nullptr, nullptr, nullptr, 0, 1, false)) != cudaSuccess)
     return e;
@@ -1688,14 +1702,31 @@ scfft_status scfft_set_geometry(scfft_ctx* c, const uint8_t* mask) {
   if (!c || !mask) return SCFFT_EINVAL;
   const Geo& g = c->g;
   long long nin = 0;
+  int y0 = g.ny, y1 = 0, z0 = g.nz, z1 = 0;
   for (int z = 0; z < g.nz; ++z)
     for (int y = 0; y < g.ny; ++y)
       for (int x = 0; x < g.nx; ++x) {
         if (!mask[((long long)z * g.ny + y) * g.nx + x]) continue;
         ++nin;
         if (x < 2 || y < 2 || z < 2 || x >= g.nx - 2 || y >= g.ny - 2 || z >= g.nz - 2) return SCFFT_EINVAL;
+        y0 = std::min(y0, y);
+        y1 = std::max(y1, y + 1);
+        z0 = std::min(z0, z);
+        z1 = std::max(z1, z + 1);
       }
   if (nin == 0) return SCFFT_EINVAL;
+  // the row pairs of the x passes start at even y: round the box out to even bounds
+  c->box[0] = y0 & ~1;
+  c->box[1] = std::min(g.ny, (y1 + 1) & ~1);
+  c->box[2] = z0;
+  c->box[3] = z1;
+  // the captured Eq. 5 loop holds the launches of the old box
+  CK(cudaStreamSynchronize(c->st));
+  if (c->loop_exec) cudaGraphExecDestroy(c->loop_exec);
+  if (c->loop_graph) cudaGraphDestroy(c->loop_graph);
+  c->loop_exec = nullptr;
+  c->loop_graph = nullptr;
+  c->loop_failed = false;
   std::vector<uint8_t> m(mask, mask + g.N);
   for (auto& v : m) v = v ? 1 : 0;
   CK(cudaMemcpy(c->mask, m.data(), g.N, cudaMemcpyHostToDevice));

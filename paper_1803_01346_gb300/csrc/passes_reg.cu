@@ -42,12 +42,14 @@ template <> __device__ __forceinline__ double2 zero_v<double2>() { return make_d
 }  // namespace
 
 // ---------------------------------------------------------------- y pass
-// grid (ceil(HX/TC), nzs, 3), block TC*R1 threads.
+// grid (ceil(HX/TC), planes, 3), block TC*R1 threads; the planes are z = zoff + blockIdx.y, and
+// input rows outside [ylo, yhi) read as zero (a source that vanishes outside Omega's box).
 template <typename T, int R1, int R2, int TC, bool INV, bool PIN, bool POUT>
 __global__ void __launch_bounds__(TC * R1) ypass_reg_kernel(typename cplx_of<T>::type* __restrict__ base, int rows,
                                                             int sx, int HX, int nzs,
                                                             const typename cplx_of<T>::type* __restrict__ twg,
-                                                            const Ctrl* ctrl, int check_done, int ahead) {
+                                                            const Ctrl* ctrl, int check_done, int ahead, int zoff,
+                                                            int ylo, int yhi) {
   typedef typename cplx_of<T>::type V;
   constexpr int L = R1 * R2;
   constexpr int S2 = R1 * TC + kPad8;  // transpose row stride
@@ -58,14 +60,14 @@ __global__ void __launch_bounds__(TC * R1) ypass_reg_kernel(typename cplx_of<T>:
   const int t = threadIdx.x;
   for (int i = t; i < L; i += TC * R1) tw[i] = twg[i];
   const int c = t % TC, n1 = t / TC;
-  const int cz = blockIdx.z, z = blockIdx.y, kx = blockIdx.x * TC + c;
+  const int cz = blockIdx.z, z = zoff + blockIdx.y, kx = blockIdx.x * TC + c;
   const bool colok = kx < HX;
   V* col = base + ((size_t)(cz * nzs + z) * rows) * sx + kx;
   if (ahead > 0) {  // prefetch into L2 the input columns of the CTA one wave of resident CTAs later
     const int gx = gridDim.x, gy = gridDim.y;
     const int nb = blockIdx.x + gx * (blockIdx.y + gy * blockIdx.z) + ahead;
     if (nb < gx * gy * (int)gridDim.z) {
-      const int bx = nb % gx, zz = (nb / gx) % gy, cc = nb / (gx * gy);
+      const int bx = nb % gx, zz = zoff + (nb / gx) % gy, cc = nb / (gx * gy);
       const V* ncol = base + ((size_t)(cc * nzs + zz) * rows) * sx + bx * TC;
       constexpr int NR = PIN ? L / 2 : L;
       const int last = (bx * TC + TC <= HX ? TC : HX - bx * TC) - 1;
@@ -78,7 +80,8 @@ __global__ void __launch_bounds__(TC * R1) ypass_reg_kernel(typename cplx_of<T>:
     if (PIN && n2 >= R2 / 2) {
       v[n2] = zero_v<V>();
     } else {
-      v[n2] = colok ? col[(size_t)(n1 + R1 * n2) * sx] : zero_v<V>();
+      const int row = n1 + R1 * n2;
+      v[n2] = (colok && row >= ylo && row < yhi) ? col[(size_t)row * sx] : zero_v<V>();
     }
   }
   __syncthreads();  // twiddles staged
@@ -110,7 +113,7 @@ __global__ void zpass_reg2_kernel(float2* __restrict__ base, int rows, int sx, i
                                   const float* __restrict__ kt1, const float* __restrict__ kt2,
                                   const float* __restrict__ st0, const float* __restrict__ st1,
                                   const float* __restrict__ st2, float scale, const float4* __restrict__ kap4, int nx,
-                                  int ny, int nz, const Ctrl* ctrl, int check_done);
+                                  int ny, int nz, const Ctrl* ctrl, int check_done, int zlo, int zhi);
 
 // ---------------------------------------------------------------- launchers
 namespace {
@@ -123,7 +126,9 @@ cudaError_t go_y(const Launch<float>& L, float2* base, int rows, int sx, int HX,
   const size_t smem = sizeof(float2) * (Lt + R2 * (R1 * TC + kPad8));
   auto k = ypass_reg_kernel<float, R1, R2, TC, INV, PIN, POUT>;
   allow_smem<ypass_reg_kernel<float, R1, R2, TC, INV, PIN, POUT>>();
-  dim3 grid((HX + TC - 1) / TC, L.g.nz, 3);
+  // the padded forward pass of an Eq. 5 iteration: only the planes and rows of Omega's box
+  const bool box = L.use_box && PIN;
+  dim3 grid((HX + TC - 1) / TC, box ? L.bz1 - L.bz0 : L.g.nz, 3);
   static const int resident = [&] {  // CTAs resident at once: the prefetch distance
     if (!PF) return 0;
     int per_sm = 0, dev = 0, sms = 0;
@@ -132,7 +137,8 @@ cudaError_t go_y(const Launch<float>& L, float2* base, int rows, int sx, int HX,
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return per_sm > 0 && sms > 0 ? per_sm * sms : 0;
   }();
-  k<<<grid, TC * R1, smem, L.st>>>(base, rows, sx, HX, L.g.nz, tw, L.ctrl, chk ? 1 : 0, resident);
+  k<<<grid, TC * R1, smem, L.st>>>(base, rows, sx, HX, L.g.nz, tw, L.ctrl, chk ? 1 : 0, resident, box ? L.bz0 : 0,
+                                   box ? L.by0 : 0, box ? L.by1 : rows);
   return cudaGetLastError();
 }
 
@@ -152,8 +158,10 @@ cudaError_t go_z(const Launch<float>& L, float2* base, int rows, int sx, int HX,
   const int nfull = HX / TC, rem = HX - nfull * TC;
   const dim3 grid = PACK ? dim3(nfull * rows + (rows * rem + TC - 1) / TC, 1, 1) : dim3((HX + TC - 1) / TC, rows, 1);
   const Work<float>& w = *L.w;
+  const bool box = KIND == 1 && L.use_box;
   k<<<grid, TC * R1, smem, L.st>>>(base, rows, sx, HX, L.g.nz, tw, w.kt[0], w.kt[1], w.kt[2], w.st[0], w.st[1],
-                                   w.st[2], (float)scale, w.kap4, L.g.nx, L.g.ny, L.g.nz, L.ctrl, chk ? 1 : 0);
+                                   w.st[2], (float)scale, w.kap4, L.g.nx, L.g.ny, L.g.nz, L.ctrl, chk ? 1 : 0,
+                                   box ? L.bz0 : 0, box ? L.bz1 : Lt);
   return cudaGetLastError();
 }
 
@@ -275,9 +283,28 @@ struct XRArgs {
   double* partials;
   int check_done;
   int out_buf;
+  // mask/pad pass of an Eq. 5 iteration: only the row pairs of Omega's box (y in [by0, by1),
+  // z in [bz0, bz1)); the rows outside hold zeros of the source and are not read downstream
+  int use_box, by0, by1, bz0, bz1;
 };
 
 namespace {
+
+// (z, y) of the first row of row pair gp, over every pair of the grid or over the box's
+__device__ __forceinline__ void pair_rows(const XRArgs& a, int gp, int& z, int& y) {
+  if (a.use_box) {
+    const int hp = (a.by1 - a.by0) >> 1, zb = gp / hp;
+    z = a.bz0 + zb;
+    y = a.by0 + 2 * (gp - zb * hp);
+  } else {
+    const int q = 2 * gp;
+    z = q / a.g.ny;
+    y = q - z * a.g.ny;
+  }
+}
+__host__ __device__ __forceinline__ int pair_count(const XRArgs& a) {
+  return a.use_box ? (a.bz1 - a.bz0) * ((a.by1 - a.by0) >> 1) : a.g.ny * a.g.nz / 2;
+}
 
 
 template <int MODE, int R1i, int R2i, int R2o> struct XS {
@@ -336,7 +363,7 @@ cudaError_t go_x(const XRArgs& a, cudaStream_t st) {
       sizeof(float2) * ((S::Li > 0 ? S::Li : 1) + (S::Lo > 0 ? S::Lo : 1) + 3 * kPairs * XL + kPairs * TT);
   auto k = xpass_reg2_kernel<MODE, R1i, R2i, R2o, kPairs>;
   allow_smem<xpass_reg2_kernel<MODE, R1i, R2i, R2o, kPairs>>();
-  const int npairs = a.g.ny * a.g.nz / 2;
+  const int npairs = pair_count(a);
   const int ntiles = (npairs + kPairs - 1) / kPairs;
   // one wave of resident CTAs (the kernel loops over tiles)
   static const int resident = [&] {
@@ -417,6 +444,11 @@ cudaError_t launch_x_reg_io(const Launch<float>& L, XMode mode, const PointParam
   a.partials = L.partials;
   a.check_done = check_done ? 1 : 0;
   a.out_buf = out_buf;
+  a.use_box = (L.use_box && mode == X_MASKPAD) ? 1 : 0;
+  a.by0 = L.by0;
+  a.by1 = L.by1;
+  a.bz0 = L.bz0;
+  a.bz1 = L.bz1;
   switch (mode) {
     case X_FWD_F64: return go_x_n<X_FWD_F64>(g.nx, a, L.st);
     case X_POWERLAW: return go_x_n<X_POWERLAW>(g.nx, a, L.st);
@@ -453,7 +485,7 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 4 : 1) zpas
                                                              const float* __restrict__ st1,
                                                              const float* __restrict__ st2, float scale,
                                                              const float4* __restrict__ kap4, int nx, int ny, int nz,
-                                                             const Ctrl* ctrl, int check_done) {
+                                                             const Ctrl* ctrl, int check_done, int zlo, int zhi) {
   constexpr int L = R1 * R2;
   constexpr bool PR = (KIND == 1);
   constexpr int S2 = R1 * TC + kPad8;  // forward transpose [k2][n1][c]
@@ -516,7 +548,10 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 4 : 1) zpas
   for (int q = 0; q < 3; ++q)
 #pragma unroll
     for (int n2 = 0; n2 < NL; ++n2)
-      pre[q][n2] = colok ? col[q * cstride + (size_t)(n1 + R1 * n2) * zstride] : make_float2(0.f, 0.f);
+      // (input planes outside [zlo, zhi) are zero: the source vanishes outside Omega's box)
+      pre[q][n2] = (colok && n1 + R1 * n2 >= zlo && n1 + R1 * n2 < zhi)
+                       ? col[q * cstride + (size_t)(n1 + R1 * n2) * zstride]
+                       : make_float2(0.f, 0.f);
   if constexpr (OWN) {
     // Forward, one component at a time.  In stage B the thread (c, k2 = n1 < R2) reads the
     // slots Fq[k2 S2 + m TC + c] that no other thread reads, so it writes its spectrum
@@ -764,7 +799,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
     for (int i = tid; i < Lo; i += NT) two[i] = a.tw_out[(i % R1o) * (i / R1o)];
   const int ny = a.g.ny, nz = a.g.nz;
   const long long N = a.g.N;
-  const int npairs = ny * nz / 2;
+  const int npairs = pair_count(a);
   const int ntiles = (npairs + P - 1) / P;
   float partf = 0.f;
   static_assert(XL % TP == 0 && 32 % TP == 0, "a row pair's nodes split evenly over its lanes, inside one warp");
@@ -783,7 +818,9 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
           const int ln = i % lines, rr = i / lines;
           const int qrow = nrow0 + rr;
           if (qrow < 2 * npairs) {
-            const int zz = qrow / ny, yy = qrow - zz * ny;
+            int zz, yy;
+            pair_rows(a, qrow >> 1, zz, yy);
+            yy += qrow & 1;
             prefetch_l2(a.spec_in + ((size_t)zz * a.in_rows + yy) * a.in_sx + ln * 16);
           }
         }
@@ -802,8 +839,9 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
     }
     const int gp = tile * P + p;
     const bool pok = gp < npairs;
-    const int qa = 2 * (pok ? gp : 0);
-    const int z = qa / ny, ya = qa - z * ny;
+    int z, ya;
+    pair_rows(a, pok ? gp : 0, z, ya);
+    const int qa = z * ny + ya;  // flat index of the pair's first row
     float2* Tp = T + p * TT;
 
     // L2 prefetch of everything this CTA reads after its first phase (components 1
@@ -818,7 +856,9 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
           const int ln = i % lines, rr = (i / lines) % nrow, q = 1 + i / (lines * nrow);
           const int qrow = row0 + rr;
           if (qrow < 2 * npairs) {
-            const int zz = qrow / ny, yy = qrow - zz * ny;
+            int zz, yy;
+            pair_rows(a, qrow >> 1, zz, yy);
+            yy += qrow & 1;
             prefetch_l2(a.spec_in + ((size_t)(q * nz + zz) * a.in_rows + yy) * a.in_sx + ln * 16);
           }
         }
@@ -837,7 +877,13 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
         }
       if (UPD || MODE == X_ASSEMBLE || MODE == X_MASKPAD || MODE == X_POWERLAW || MODE == X_POWERLAW_H)
         for (int i = tid * 128; i < nrow * XL; i += NT * 128)
-          if (row0 + i / XL < 2 * npairs) prefetch_l2(a.mask + nb0 + i);
+          if (row0 + i / XL < 2 * npairs) {
+            int zz, yy;
+            const int qrow = row0 + i / XL;
+            pair_rows(a, qrow >> 1, zz, yy);
+            yy += qrow & 1;
+            prefetch_l2(a.mask + ((size_t)zz * ny + yy) * XL + i % XL);
+          }
     }
 
     if constexpr (S::C2R) {

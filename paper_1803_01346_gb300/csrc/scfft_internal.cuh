@@ -139,6 +139,12 @@ struct Launch {
                                      // argument when set: rhs parameters computed on the device)
   int* fault = nullptr;        // host: armed one-shot fault injection (scfft_inject_fault), or nullptr
   cudaStream_t st;
+  // Support of the source chi_Omega curl dh^i of the Eq. 5 convolution: Omega's bounding box of
+  // node rows y in [by0, by1) (even bounds) and planes z in [bz0, bz1).  With use_box set, the
+  // FP32 passes that transform that source forward (mask and pad in x, the padded y pass, the
+  // padded z pass's input) skip everything outside the box, where it is zero.
+  int by0 = 0, by1 = 0, bz0 = 0, bz1 = 0;
+  bool use_box = false;
 };
 
 // Pass launchers (defined in passes.cu, instantiated for float, double and dfloat).

@@ -69,12 +69,15 @@ template <int R1, int R2, int TC, bool PIN> struct YT {
   static constexpr size_t smem = 128 + sizeof(float2) * (2 * SBX + L);
 };
 
-// grid: persistent (at most one wave); block TC*R1 threads; tiles t = chunk + nch * plane.
+// grid: persistent (at most one wave); block TC*R1 threads; tiles t = chunk + nch * p over the
+// 3 nzp planes p = (component, z = zoff + p mod nzp); input rows outside [ylo, yhi) read as zero
+// (the forward pass of an Eq. 5 iteration runs on Omega's box only: its source vanishes outside).
 template <int R1, int R2, int TC, bool INV, bool PIN, bool POUT>
 __global__ void __launch_bounds__(TC * R1) ypass_tma_kernel(const __grid_constant__ CUtensorMap tmap,
                                                             float2* __restrict__ base, int rows, int sx, int HX,
                                                             int nzs, const float2* __restrict__ twg, Ctrl* ctrl,
-                                                            int check_done, int inject) {
+                                                            int check_done, int inject, int zoff, int nzp, int ylo,
+                                                            int yhi) {
   typedef YT<R1, R2, TC, PIN> S;
   constexpr int L = S::L, SB = S::SB, SBX = S::SBX, S2 = S::S2, NT = TC * R1;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -83,7 +86,9 @@ __global__ void __launch_bounds__(TC * R1) ypass_tma_kernel(const __grid_constan
   float2* stage = reinterpret_cast<float2*>(smem_raw + 128);      // [2][SBX], 128-byte aligned
   float2* tw = stage + 2 * SBX;                                   // [L]
   const int t = threadIdx.x, c = t % TC, n1 = t / TC;
-  const int nch = (HX + TC - 1) / TC, ntiles = nch * 3 * nzs;
+  const int nch = (HX + TC - 1) / TC, ntiles = nch * 3 * nzp;
+  // plane of the tile's columns in the [component][z] planes of the spectrum
+  auto plane_of = [&](int tile) { const int p = tile / nch, q = p / nzp; return q * nzs + zoff + (p - q * nzp); };
   const unsigned bytes = (unsigned)(SB * sizeof(float2));
   if (t == 0) {
     mbar_init(&mbar[0], 1);
@@ -99,7 +104,7 @@ __global__ void __launch_bounds__(TC * R1) ypass_tma_kernel(const __grid_constan
       if (tile < ntiles) {
         // (inject: a test of the timeout path; stage 0 then waits for 16 bytes that never come)
         mbar_expect_tx(&mbar[s], bytes + (s == 0 && inject ? 16u : 0u));
-        tma_load_3d(stage + s * SBX, &tmap, (tile % nch) * TC, 0, tile / nch, &mbar[s]);
+        tma_load_3d(stage + s * SBX, &tmap, (tile % nch) * TC, 0, plane_of(tile), &mbar[s]);
       }
     }
   }
@@ -111,7 +116,8 @@ __global__ void __launch_bounds__(TC * R1) ypass_tma_kernel(const __grid_constan
     float2 v[R2];
 #pragma unroll
     for (int n2 = 0; n2 < R2; ++n2)
-      v[n2] = (PIN && n2 >= R2 / 2) ? make_float2(0.f, 0.f) : st[(n1 + R1 * n2) * TC + c];
+      v[n2] = ((PIN && n2 >= R2 / 2) || n1 + R1 * n2 < ylo || n1 + R1 * n2 >= yhi) ? make_float2(0.f, 0.f)
+                                                                                  : st[(n1 + R1 * n2) * TC + c];
     if (__syncthreads_or(timed_out)) {  // every thread has read stage s (or the wait gave up)
       if (t == 0) {
         ctrl->status = SCFFT_ETIMEOUT;
@@ -120,7 +126,7 @@ __global__ void __launch_bounds__(TC * R1) ypass_tma_kernel(const __grid_constan
       }
       return;
     }
-    const int chunk = tile % nch, plane = tile / nch;
+    const int chunk = tile % nch, plane = plane_of(tile);
     const int kx = chunk * TC + c;
     const bool colok = kx < HX;
     float2* col = base + (size_t)plane * rows * sx + kx;
@@ -150,7 +156,7 @@ __global__ void __launch_bounds__(TC * R1) ypass_tma_kernel(const __grid_constan
       if (nt < ntiles) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&mbar[s], bytes);
-        tma_load_3d(stage + s * SBX, &tmap, (nt % nch) * TC, 0, nt / nch, &mbar[s]);
+        tma_load_3d(stage + s * SBX, &tmap, (nt % nch) * TC, 0, plane_of(nt), &mbar[s]);
       }
     }
   }
@@ -163,7 +169,9 @@ cudaError_t go_y_tma(const Launch<float>& L, const CUtensorMap& map, float2* bas
   typedef YT<R1, R2, TC, PIN> S;
   auto k = ypass_tma_kernel<R1, R2, TC, INV, PIN, POUT>;
   allow_smem<ypass_tma_kernel<R1, R2, TC, INV, PIN, POUT>>();
-  const int ntiles = ((HX + TC - 1) / TC) * 3 * L.g.nz;
+  const bool box = L.use_box && PIN;  // the forward pass of an Eq. 5 iteration: Omega's box only
+  const int nzp = box ? L.bz1 - L.bz0 : L.g.nz;
+  const int ntiles = ((HX + TC - 1) / TC) * 3 * nzp;
   static const int resident = [&] {  // one wave of resident CTAs (the kernel loops over tiles)
     int per_sm = 0, dev = 0, sms = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, TC * R1, S::smem);
@@ -174,7 +182,8 @@ cudaError_t go_y_tma(const Launch<float>& L, const CUtensorMap& map, float2* bas
   const int grid = ntiles < resident ? ntiles : resident;
   const int inject = (L.fault && *L.fault == SCFFT_FAULT_TMA_WAIT) ? 1 : 0;
   if (inject) *L.fault = 0;  // one shot
-  k<<<grid, TC * R1, S::smem, L.st>>>(map, base, rows, sx, HX, L.g.nz, tw, L.ctrl, chk ? 1 : 0, inject);
+  k<<<grid, TC * R1, S::smem, L.st>>>(map, base, rows, sx, HX, L.g.nz, tw, L.ctrl, chk ? 1 : 0, inject,
+                                      box ? L.bz0 : 0, nzp, box ? L.by0 : 0, box ? L.by1 : rows);
   return cudaGetLastError();
 }
 
