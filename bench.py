@@ -49,7 +49,7 @@ REF_ITERS_PER_RHS = 5.0
 T_START = 0.3  # start of the timed steps on the lens ramp (h_e reaches 0.8 at t = 0.8)
 # DRAM bytes (read + write) per launch from the committed ncu capture
 # profiles/ncu_zpass_xupdate_lens128_fp32.md; an entry is removed when its kernel changes.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"z_kernel": 86282240 + 57672704}
 
 
 def _peaks():

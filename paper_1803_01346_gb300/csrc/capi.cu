@@ -358,7 +358,13 @@ template <typename T> cudaError_t iteration(scfft_ctx* c, const Launch<T>& L, Po
   if (fd) {
     if ((e = fd_maskpad<T>(c, L, pp, chk)) != cudaSuccess) return e;
   } else {
-    if ((e = curl_in_U<T>(c, L, chk)) != cudaSuccess) return e;
+    // the curl of dh^i: forward over the whole grid; its z output and the inverse y pass only
+    // where the mask keeps it (Omega's box)
+    if ((e = run(c, SCFFT_K_Y_FWD_U, [&] { return launch_y<T>(L, false, false, chk); })) != cudaSuccess) return e;
+    if ((e = run(c, SCFFT_K_Z_CURL, [&] { return launch_z_curl<T>(LB, chk, 1.0 / (double)L.g.N); })) !=
+        cudaSuccess)
+      return e;
+    if ((e = run(c, SCFFT_K_Y_INV_U, [&] { return launch_y<T>(LB, false, true, chk); })) != cudaSuccess) return e;
     if ((e = run(c, SCFFT_K_X_MASKPAD,
                  [&] { return launch_x<T>(LB, X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, chk); })) != cudaSuccess)
       return e;
@@ -400,8 +406,8 @@ cudaError_t loop_body(const Launch<float>& L, const PointParams& pp, cudaGraphCo
       return e;
   } else {
     if ((e = launch_y<float>(L, false, false, false)) != cudaSuccess) return e;
-    if ((e = launch_z_curl<float>(L, false, 1.0 / (double)L.g.N)) != cudaSuccess) return e;
-    if ((e = launch_y<float>(L, false, true, false)) != cudaSuccess) return e;
+    if ((e = launch_z_curl<float>(boxed(L), false, 1.0 / (double)L.g.N)) != cudaSuccess) return e;
+    if ((e = launch_y<float>(boxed(L), false, true, false)) != cudaSuccess) return e;
     if ((e = launch_x<float>(boxed(L), X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, false)) != cudaSuccess)
       return e;
   }

@@ -42,8 +42,9 @@ template <> __device__ __forceinline__ double2 zero_v<double2>() { return make_d
 }  // namespace
 
 // ---------------------------------------------------------------- y pass
-// grid (ceil(HX/TC), planes, 3), block TC*R1 threads; the planes are z = zoff + blockIdx.y, and
-// input rows outside [ylo, yhi) read as zero (a source that vanishes outside Omega's box).
+// grid (ceil(HX/TC), planes, 3), block TC*R1 threads; the planes are z = zoff + blockIdx.y.  Rows
+// outside [ylo, yhi): the forward pass reads them as zero (a source that vanishes outside
+// Omega's box), the inverse pass does not write them (nothing downstream reads them).
 template <typename T, int R1, int R2, int TC, bool INV, bool PIN, bool POUT>
 __global__ void __launch_bounds__(TC * R1) ypass_reg_kernel(typename cplx_of<T>::type* __restrict__ base, int rows,
                                                             int sx, int HX, int nzs,
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(TC * R1) ypass_reg_kernel(typename cplx_of<T>:
       v[n2] = zero_v<V>();
     } else {
       const int row = n1 + R1 * n2;
-      v[n2] = (colok && row >= ylo && row < yhi) ? col[(size_t)row * sx] : zero_v<V>();
+      v[n2] = (colok && (INV || (row >= ylo && row < yhi))) ? col[(size_t)row * sx] : zero_v<V>();
     }
   }
   __syncthreads();  // twiddles staged
@@ -101,6 +102,7 @@ __global__ void __launch_bounds__(TC * R1) ypass_reg_kernel(typename cplx_of<T>:
 #pragma unroll
       for (int k1 = 0; k1 < R1; ++k1) {
         if (POUT && k1 >= R1 / 2) continue;
+        if (INV && (k2 + R2 * k1 < ylo || k2 + R2 * k1 >= yhi)) continue;
         col[(size_t)(k2 + R2 * k1) * sx] = w[k1];
       }
     }
@@ -126,8 +128,9 @@ cudaError_t go_y(const Launch<float>& L, float2* base, int rows, int sx, int HX,
   const size_t smem = sizeof(float2) * (Lt + R2 * (R1 * TC + kPad8));
   auto k = ypass_reg_kernel<float, R1, R2, TC, INV, PIN, POUT>;
   allow_smem<ypass_reg_kernel<float, R1, R2, TC, INV, PIN, POUT>>();
-  // the padded forward pass of an Eq. 5 iteration: only the planes and rows of Omega's box
-  const bool box = L.use_box && PIN;
+  // the padded forward pass and the curl's unpadded inverse pass of an Eq. 5 iteration: only
+  // the planes and rows of Omega's box
+  const bool box = L.use_box && (PIN || (INV && !POUT));
   dim3 grid((HX + TC - 1) / TC, box ? L.bz1 - L.bz0 : L.g.nz, 3);
   static const int resident = [&] {  // CTAs resident at once: the prefetch distance
     if (!PF) return 0;
@@ -158,7 +161,8 @@ cudaError_t go_z(const Launch<float>& L, float2* base, int rows, int sx, int HX,
   const int nfull = HX / TC, rem = HX - nfull * TC;
   const dim3 grid = PACK ? dim3(nfull * rows + (rows * rem + TC - 1) / TC, 1, 1) : dim3((HX + TC - 1) / TC, rows, 1);
   const Work<float>& w = *L.w;
-  const bool box = KIND == 1 && L.use_box;
+  // box: the padded pass's input planes, or the curl pass's output planes (both Omega's box)
+  const bool box = L.use_box;
   k<<<grid, TC * R1, smem, L.st>>>(base, rows, sx, HX, L.g.nz, tw, w.kt[0], w.kt[1], w.kt[2], w.st[0], w.st[1],
                                    w.st[2], (float)scale, w.kap4, L.g.nx, L.g.ny, L.g.nz, L.ctrl, chk ? 1 : 0,
                                    box ? L.bz0 : 0, box ? L.bz1 : Lt);
@@ -549,7 +553,7 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 4 : 1) zpas
 #pragma unroll
     for (int n2 = 0; n2 < NL; ++n2)
       // (input planes outside [zlo, zhi) are zero: the source vanishes outside Omega's box)
-      pre[q][n2] = (colok && n1 + R1 * n2 >= zlo && n1 + R1 * n2 < zhi)
+      pre[q][n2] = (colok && (!PR || (n1 + R1 * n2 >= zlo && n1 + R1 * n2 < zhi)))
                        ? col[q * cstride + (size_t)(n1 + R1 * n2) * zstride]
                        : make_float2(0.f, 0.f);
   if constexpr (OWN) {
@@ -661,6 +665,9 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 4 : 1) zpas
 #pragma unroll
         for (int m2 = 0; m2 < R2; ++m2) {
           if (PR && m2 >= R2 / 2) continue;
+          // (the curl's pass of an Eq. 5 iteration writes only the planes of Omega's box: the
+          // masked curl downstream reads nothing else)
+          if (!PR && (n1 + R1 * m2 < zlo || n1 + R1 * m2 >= zhi)) continue;
           col[q * cstride + (size_t)(n1 + R1 * m2) * zstride] = v[m2];
         }
       }
@@ -749,6 +756,9 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 4 : 1) zpas
 #pragma unroll
         for (int m2 = 0; m2 < R2; ++m2) {
           if (PR && m2 >= R2 / 2) continue;
+          // (the curl's pass of an Eq. 5 iteration writes only the planes of Omega's box: the
+          // masked curl downstream reads nothing else)
+          if (!PR && (n1 + R1 * m2 < zlo || n1 + R1 * m2 >= zhi)) continue;
           col[q * cstride + (size_t)(n1 + R1 * m2) * zstride] = v[m2];
         }
       }
