@@ -148,8 +148,9 @@ typedef struct {
 } scfft_schedule;
 
 /* Autotuner of the schedule: times each candidate of each knob on the context's own workspace
- * (a few launches each, CUDA events on its stream; the scratch spectra are overwritten, no
- * state is touched), keeps the fastest, and caches the choice per device and grid for the
+ * (ten launches each after three, CUDA events on its stream; the scratch spectra are
+ * overwritten, no state is touched), keeps the fastest (an alternative to the first candidate
+ * only when it is more than 3% faster), and caches the choice per device and grid for the
  * process, so that later contexts of that grid (a batch) reuse it without timing; retune != 0
  * times again.  Rebuilds the context's captured graphs on their next launch.  FP64 and
  * double-float contexts have no schedule: SCFFT_OK, nothing timed.  out (may be NULL)

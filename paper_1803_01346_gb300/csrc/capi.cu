@@ -1793,8 +1793,8 @@ bool sched_ok(const scfft_schedule* s) {
          (s->y_unpadded_tile == 8 || s->y_unpadded_tile == 16) && (s->y_padded_tma == 0 || s->y_padded_tma == 1);
 }
 
-// Mean device time (us) of one call of f (a few pass launches) on the context's stream: two
-// untimed calls, then five between CUDA events.
+// Mean device time (us) of one call of f (a few pass launches) on the context's stream: three
+// untimed calls, then ten between CUDA events.
 template <typename F> scfft_status time_us(scfft_ctx* c, F&& f, double* us) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0));
@@ -1803,9 +1803,9 @@ template <typename F> scfft_status time_us(scfft_ctx* c, F&& f, double* us) {
     return SCFFT_ECUDA;
   }
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = f();
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = f();
   if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
-  for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = f();
+  for (int i = 0; i < 10 && e == cudaSuccess; ++i) e = f();
   if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
   if (e == cudaSuccess) e = cudaEventSynchronize(e1);
   float ms = 0.f;
@@ -1816,13 +1816,14 @@ template <typename F> scfft_status time_us(scfft_ctx* c, F&& f, double* us) {
     note_cuda_error(e, __FILE__, __LINE__);
     return SCFFT_ECUDA;
   }
-  *us = 1e3 * ms / 5.0;
+  *us = 1e3 * ms / 10.0;
   return SCFFT_OK;
 }
 
 // Time each candidate of each knob of the FP32 passes on the context's own workspace (the
 // passes transform its scratch spectra in place; their contents are not used afterwards) and
-// keep the fastest; knobs act on different passes, so they are tuned one at a time.
+// keep the fastest (the second candidate only when it is faster by more than 3%, so that timing
+// noise does not flip a choice); knobs act on different passes, so they are tuned one at a time.
 scfft_status autotune_f32(scfft_ctx* c, double us[8]) {
   Launch<float> L = launch_of<float>(c);
   L.fault = nullptr;
@@ -1833,7 +1834,7 @@ scfft_status autotune_f32(scfft_ctx* c, double us[8]) {
       *knob = cand[k];
       CS_(time_us(c, launch, &t[k]));
     }
-    *knob = t[1] < t[0] ? cand[1] : cand[0];
+    *knob = t[1] < 0.97 * t[0] ? cand[1] : cand[0];
     return SCFFT_OK;
   };
   const int zk[2] = {8, 4}, zc[2] = {8, 16}, yu[2] = {8, 16}, yp[2] = {1, 0};

@@ -83,7 +83,17 @@ struct XArgs {
   double* partials;
   int check_done;
   int out_buf;
+  // mask/pad pass of an Eq. 5 iteration: only the rows of Omega's box (y in [by0, by1), z in
+  // [bz0, bz1)); the source vanishes outside, and nothing downstream reads the rows left out
+  int use_box, by0, by1, bz0, bz1;
 };
+
+// flat (z, y) row index of the pass's q-th row: every row of the grid, or the box's rows
+template <typename T> __device__ __forceinline__ int flat_row(const XArgs<T>& a, int q) {
+  if (!a.use_box) return q;
+  const int nyb = a.by1 - a.by0, zb = q / nyb;
+  return (a.bz0 + zb) * a.g.ny + a.by0 + (q - zb * nyb);
+}
 
 template <typename T>
 __device__ __forceinline__ T* half_of(typename cplx_of<T>::type* p, int h) {
@@ -100,7 +110,7 @@ __global__ void __launch_bounds__(kThreads) xpass_kernel(const XArgs<T> a) {
   const int QP = a.QP, ES = QP + 1, CS = a.Lmax * ES;
   const int R = 2 * QP;
   const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-  const int nrows = ny * nz;
+  const int nrows = a.use_box ? (a.bz1 - a.bz0) * (a.by1 - a.by0) : ny * nz;
   const long long N = a.g.N;
   const int q0 = blockIdx.x * R;
   V* bufA = reinterpret_cast<V*>(smem_raw);
@@ -125,7 +135,7 @@ __global__ void __launch_bounds__(kThreads) xpass_kernel(const XArgs<T> a) {
       const int q = q0 + r;
       V v = vzero<V>();
       if (q < nrows) {
-        const int z = q / ny, y = q - z * ny;
+        const int fq = flat_row(a, q), z = fq / ny, y = fq - z * ny;
         v = a.spec_in[((size_t)(c * nz + z) * a.in_rows + y) * a.in_sx + k];
       }
       if (k == 0 || k == L / 2) v.y = 0;  // C2R reads only the real part of DC and Nyquist
@@ -150,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) xpass_kernel(const XArgs<T> a) {
       const int q = q0 + r;
       T v = 0;
       if (q < nrows) {
-        const size_t node = (size_t)q * nx + n;
+        const size_t node = (size_t)flat_row(a, q) * nx + n;
         v = a.src_t ? a.src_t[(size_t)c * N + node] : (T)a.src_f64[(size_t)c * N + node];
         if (MODE == X_ADJ_PAD && a.mask[node]) v = 0;   // (1 - chi)
         if (MODE == X_ADJ_IN && !a.mask[node]) v = 0;   // chi
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) xpass_kernel(const XArgs<T> a) {
       const int n = idx % nx, r = idx / nx;
       const int q = q0 + r;
       if (q >= nrows) continue;
-      const size_t node = (size_t)q * nx + n;
+      const size_t node = (size_t)flat_row(a, q) * nx + n;
       T* p0 = half_of<T>(&data[0 * CS + (r >> 1) + n * ES], r & 1);
       T* p1 = half_of<T>(&data[1 * CS + (r >> 1) + n * ES], r & 1);
       T* p2 = half_of<T>(&data[2 * CS + (r >> 1) + n * ES], r & 1);
@@ -280,7 +290,7 @@ __global__ void __launch_bounds__(kThreads) xpass_kernel(const XArgs<T> a) {
       V o;
       if ((r & 1) == 0) o = mk((Zk.x + Zm.x) * half, (Zk.y - Zm.y) * half);
       else o = mk((Zk.y + Zm.y) * half, (Zm.x - Zk.x) * half);
-      const int z = q / ny, y = q - z * ny;
+      const int fq = flat_row(a, q), z = fq / ny, y = fq - z * ny;
       a.spec_out[((size_t)(c * nz + z) * a.out_rows + y) * a.out_sx + k] = o;
     }
   }
@@ -344,6 +354,7 @@ struct YArgs {
   const V* tw;
   const Ctrl* ctrl;
   int check_done;
+  int zoff, ylo, yhi;  // planes z = zoff + blockIdx.y; input rows outside [ylo, yhi) read as zero
 };
 
 template <typename T, bool INV>
@@ -356,13 +367,13 @@ __global__ void __launch_bounds__(kThreads) ypass_kernel(const YArgs<T> a) {
   V* bufA = reinterpret_cast<V*>(smem_raw);
   V* bufB = bufA + L * ES;
   V* tw = bufB + L * ES;
-  const int c = blockIdx.z, z = blockIdx.y, kx0 = blockIdx.x * TC;
+  const int c = blockIdx.z, z = a.zoff + blockIdx.y, kx0 = blockIdx.x * TC;
   for (int i = tid; i < L; i += nth) tw[i] = a.tw[i];
   V* col = a.base + ((size_t)(c * a.nzs + z) * a.rows) * a.sx + kx0;
   for (int idx = tid; idx < L * TC; idx += nth) {
     const int ci = idx % TC, l = idx / TC;
     V v = vzero<V>();
-    if (l < a.Lin && kx0 + ci < a.HX) v = col[(size_t)l * a.sx + ci];
+    if (l < a.Lin && l >= a.ylo && l < a.yhi && kx0 + ci < a.HX) v = col[(size_t)l * a.sx + ci];
     bufA[l * ES + ci] = v;
   }
   __syncthreads();
@@ -392,6 +403,7 @@ struct ZArgs {
   int nx, ny, nz;
   const Ctrl* ctrl;
   int check_done;
+  int zlo, zhi;  // the padded pass's input planes outside [zlo, zhi) read as zero
 };
 
 template <typename T, int KIND>
@@ -412,7 +424,7 @@ __global__ void __launch_bounds__(kThreads) zpass_kernel(const ZArgs<T> a) {
   for (int idx = tid; idx < 3 * L * TC; idx += nth) {
     const int ci = idx % TC, l = (idx / TC) % L, c = idx / (TC * L);
     V v = vzero<V>();
-    if (l < a.nzs && kx0 + ci < a.HX) v = col[c * cstride + l * zstride + ci];
+    if (l < a.nzs && l >= a.zlo && l < a.zhi && kx0 + ci < a.HX) v = col[c * cstride + l * zstride + ci];
     bufA[c * CS + l * ES + ci] = v;
   }
   __syncthreads();
@@ -509,7 +521,12 @@ static cudaError_t launch_x_impl(const Launch<T>& L, XMode mode, const PointPara
   a.partials = L.partials;
   a.check_done = check_done ? 1 : 0;
   a.out_buf = out_buf;
-  const int rows = g.ny * g.nz;
+  a.use_box = (L.use_box && mode == X_MASKPAD) ? 1 : 0;
+  a.by0 = L.by0;
+  a.by1 = L.by1;
+  a.bz0 = L.bz0;
+  a.bz1 = L.bz1;
+  const int rows = a.use_box ? (L.bz1 - L.bz0) * (L.by1 - L.by0) : g.ny * g.nz;
   const int R = 2 * a.QP;
   const int grid = (rows + R - 1) / R;
   const size_t smem = (size_t)(2 * 3 * a.Lmax * (a.QP + 1) + 512) * sizeof(V);
@@ -564,7 +581,12 @@ cudaError_t launch_y(const Launch<T>& L, bool padded, bool inverse, bool check_d
   a.tw = padded ? L.w->twp[1] : L.w->twu[1];
   a.ctrl = L.ctrl;
   a.check_done = check_done ? 1 : 0;
-  dim3 grid((a.HX + a.TC - 1) / a.TC, g.nz, 3);
+  // the padded forward pass of an Eq. 5 iteration: only the planes and rows of Omega's box
+  const bool box = L.use_box && padded && !inverse;
+  a.zoff = box ? L.bz0 : 0;
+  a.ylo = box ? L.by0 : 0;
+  a.yhi = box ? L.by1 : Ly;
+  dim3 grid((a.HX + a.TC - 1) / a.TC, box ? L.bz1 - L.bz0 : g.nz, 3);
   const size_t smem = (size_t)(2 * Ly * (a.TC + 1) + 256) * sizeof(V);
   if (inverse) {
     allow_smem<ypass_kernel<T, true>>();
@@ -602,6 +624,8 @@ static cudaError_t launch_z(const Launch<T>& L, bool padded, bool check_done, do
   a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
   a.ctrl = L.ctrl;
   a.check_done = check_done ? 1 : 0;
+  a.zlo = (padded && L.use_box) ? L.bz0 : 0;  // the source box of an Eq. 5 iteration
+  a.zhi = (padded && L.use_box) ? L.bz1 : Lz;
   dim3 grid((a.HX + a.TC - 1) / a.TC, a.rows, 1);
   const size_t smem = (size_t)(2 * 3 * Lz * (a.TC + 1) + 256) * sizeof(V);
   if (padded) {
