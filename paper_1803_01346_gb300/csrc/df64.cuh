@@ -66,11 +66,67 @@ __device__ __forceinline__ dfloat operator*(dfloat x, dfloat y) {
 __device__ __forceinline__ dfloat& operator+=(dfloat& x, dfloat y) { return x = x + y; }
 __device__ __forceinline__ dfloat& operator*=(dfloat& x, dfloat y) { return x = x * y; }
 
-// complex double-float
+// ---------------------------------------------------------------- two lanes at once
+// The same steps on two double-floats held lane-wise in float2 pairs (hi lanes, lo lanes), as
+// the two-lane FP32 instructions of sm_100 and later: each lane rounds exactly as the scalar
+// step does (b * -1 + a rounds as a - b), so a lane gives the scalar result bit for bit and
+// the pair costs one instruction per step instead of two.
+struct dfpair {
+  float2 hi, lo;
+};
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ dfpair fast_two_sum2(float2 a, float2 b) {
+  const float2 s = __fadd2_rn(a, b);
+  dfpair r;
+  r.hi = s;
+  r.lo = sub2(b, sub2(s, a));
+  return r;
+}
+// lane-wise x + y (the scalar operator+ above in each lane)
+__device__ __forceinline__ dfpair add2(dfpair x, dfpair y) {
+  const float2 s = __fadd2_rn(x.hi, y.hi);
+  const float2 bv = sub2(s, x.hi);
+  const float2 av = sub2(s, bv);
+  const float2 e = __fadd2_rn(sub2(x.hi, av), sub2(y.hi, bv));
+  return fast_two_sum2(s, __fadd2_rn(e, __fadd2_rn(x.lo, y.lo)));
+}
+// lane-wise x * y (the scalar operator* above in each lane)
+__device__ __forceinline__ dfpair mul2(dfpair x, dfpair y) {
+  const float2 p = __fmul2_rn(x.hi, y.hi);
+  float2 e = __ffma2_rn(x.hi, y.hi, neg2(p));
+  e = __ffma2_rn(x.hi, y.lo, e);
+  e = __ffma2_rn(x.lo, y.hi, e);
+  return fast_two_sum2(p, e);
+}
+__device__ __forceinline__ dfpair pr(dfloat a, dfloat b) {  // lanes (a, b)
+  dfpair r;
+  r.hi = make_float2(a.hi, b.hi);
+  r.lo = make_float2(a.lo, b.lo);
+  return r;
+}
+__device__ __forceinline__ dfloat lane0(dfpair p) { return dfloat(p.hi.x, p.lo.x); }
+__device__ __forceinline__ dfloat lane1(dfpair p) { return dfloat(p.hi.y, p.lo.y); }
+
+// complex double-float: the real and imaginary parts travel as the two lanes
 __device__ __forceinline__ dfloat2 mk(dfloat a, dfloat b) { dfloat2 r; r.x = a; r.y = b; return r; }
-__device__ __forceinline__ dfloat2 operator+(dfloat2 a, dfloat2 b) { return mk(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ dfloat2 operator-(dfloat2 a, dfloat2 b) { return mk(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ dfloat2 scl(dfloat2 a, dfloat s) { return mk(a.x * s, a.y * s); }
+__device__ __forceinline__ dfloat2 mk(dfpair p) { return mk(lane0(p), lane1(p)); }
+__device__ __forceinline__ dfloat2 operator+(dfloat2 a, dfloat2 b) { return mk(add2(pr(a.x, a.y), pr(b.x, b.y))); }
+__device__ __forceinline__ dfloat2 operator-(dfloat2 a, dfloat2 b) {
+  return mk(add2(pr(a.x, a.y), pr(-b.x, -b.y)));
+}
+__device__ __forceinline__ dfloat2 scl(dfloat2 a, dfloat s) { return mk(mul2(pr(a.x, a.y), pr(s, s))); }
+// a * b and a * conj(b), with the products and sums of the generic complex forms in each lane
+__device__ __forceinline__ dfloat2 cmul(dfloat2 a, dfloat2 b) {
+  const dfpair p = mul2(pr(a.x, a.x), pr(b.x, b.y));  // (ax bx, ax by)
+  const dfpair q = mul2(pr(a.y, a.y), pr(b.y, b.x));  // (ay by, ay bx)
+  return mk(add2(p, pr(-lane0(q), lane1(q))));
+}
+__device__ __forceinline__ dfloat2 cmulc(dfloat2 a, dfloat2 b) {
+  const dfpair p = mul2(pr(a.x, a.y), pr(b.x, b.x));  // (ax bx, ay bx)
+  const dfpair q = mul2(pr(a.y, a.x), pr(b.y, b.y));  // (ay by, ax by)
+  return mk(add2(p, pr(lane0(q), -lane1(q))));
+}
 
 // Precision of the node-wise arithmetic in the passes (power law, material laws, reverse-mode
 // Jacobians): the FFT's own precision, except that the double-float passes evaluate those

@@ -465,6 +465,31 @@ def test_integrate_stencil_curl_fixed_steps_matches_oracle():
         assert rel(host(h).reshape(ref.y.shape), ref.y) < tol, prec
 
 
+def _off_centre_mask(g, L):
+    X, Y, Z = g.coords()
+    return ((np.abs(X - 0.2 * L[0]) < 0.35 * L[0]) & (np.abs(Y + 0.29 * L[1]) < 0.27 * L[1]) &
+            (np.abs(Z - 0.41 * L[2]) < 0.23 * L[2]))
+
+
+@pytest.mark.parametrize("prec", [S.PREC_F64, S.PREC_DF64])
+@pytest.mark.parametrize("curl", ["spectral", "fd"])
+def test_rhs_fp64_and_df64_off_centre_source_box_matches_oracle(prec, curl):
+    """The source box in the shared-memory passes (FP64, double-float), with either curl."""
+    n, L = (32, 48, 64), (1.0, 1.2, 1.4)
+    g = O.Grid(n, L)
+    mask = _off_centre_mask(g, L)
+    ctx, prob = make(n, L, mask, n_power=25.0, prec=prec, max_iter=4)
+    if curl == "fd":
+        ctx.set_curl(S.CURL_FD)
+        prob.curl = "fd"
+    h = _state(prob, 97)
+    g0 = I.random_field(h.shape, 98, 0.1)
+    ref = O.rhs(prob, 0.4, h, g0, delta_it=0.0, max_iter=4)
+    hd = torch.empty(h.size, dtype=torch.float64, device="cuda")
+    assert ctx.rhs(0.4, dev(h).reshape(-1), dev(g0).reshape(-1), hd) == 4
+    assert rel(host(hd).reshape(h.shape), ref.hdot) < 1e-10
+
+
 @pytest.mark.parametrize("n,L", [((32, 48, 64), (1.0, 1.2, 1.4)), ((64, 32, 16), (1.4, 0.9, 0.6))])
 def test_rhs_fp32_off_centre_source_box_matches_oracle(n, L):
     """The forward padded passes of an Eq. 5 iteration skip everything outside Omega's
@@ -472,9 +497,7 @@ def test_rhs_fp32_off_centre_source_box_matches_oracle(n, L):
     starts at odd rows and planes, on non-cubic grids, must still give the oracle's dh/dt
     at a fixed iteration count and through the graph-captured loop with its stop."""
     g = O.Grid(n, L)
-    X, Y, Z = g.coords()
-    mask = ((np.abs(X - 0.2 * L[0]) < 0.35 * L[0]) & (np.abs(Y + 0.29 * L[1]) < 0.27 * L[1]) &
-            (np.abs(Z - 0.41 * L[2]) < 0.23 * L[2]))
+    mask = _off_centre_mask(g, L)
     zs = np.nonzero(mask.any(axis=(1, 2)))[0]
     ys = np.nonzero(mask.any(axis=(0, 2)))[0]
     assert zs[0] > 2 and ys[0] > 2 and zs[-1] < n[2] - 3 and ys[-1] < n[1] - 3
