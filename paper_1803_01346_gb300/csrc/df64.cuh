@@ -108,25 +108,16 @@ __device__ __forceinline__ dfpair pr(dfloat a, dfloat b) {  // lanes (a, b)
 __device__ __forceinline__ dfloat lane0(dfpair p) { return dfloat(p.hi.x, p.lo.x); }
 __device__ __forceinline__ dfloat lane1(dfpair p) { return dfloat(p.hi.y, p.lo.y); }
 
-// complex double-float: the real and imaginary parts travel as the two lanes
+// complex double-float: sums and differences run the real and imaginary parts as the two lanes
+// (products stay scalar: their two-lane forms need the operands' lanes rearranged, which cost
+// more than the lanes saved)
 __device__ __forceinline__ dfloat2 mk(dfloat a, dfloat b) { dfloat2 r; r.x = a; r.y = b; return r; }
 __device__ __forceinline__ dfloat2 mk(dfpair p) { return mk(lane0(p), lane1(p)); }
 __device__ __forceinline__ dfloat2 operator+(dfloat2 a, dfloat2 b) { return mk(add2(pr(a.x, a.y), pr(b.x, b.y))); }
 __device__ __forceinline__ dfloat2 operator-(dfloat2 a, dfloat2 b) {
   return mk(add2(pr(a.x, a.y), pr(-b.x, -b.y)));
 }
-__device__ __forceinline__ dfloat2 scl(dfloat2 a, dfloat s) { return mk(mul2(pr(a.x, a.y), pr(s, s))); }
-// a * b and a * conj(b), with the products and sums of the generic complex forms in each lane
-__device__ __forceinline__ dfloat2 cmul(dfloat2 a, dfloat2 b) {
-  const dfpair p = mul2(pr(a.x, a.x), pr(b.x, b.y));  // (ax bx, ax by)
-  const dfpair q = mul2(pr(a.y, a.y), pr(b.y, b.x));  // (ay by, ay bx)
-  return mk(add2(p, pr(-lane0(q), lane1(q))));
-}
-__device__ __forceinline__ dfloat2 cmulc(dfloat2 a, dfloat2 b) {
-  const dfpair p = mul2(pr(a.x, a.y), pr(b.x, b.x));  // (ax bx, ay bx)
-  const dfpair q = mul2(pr(a.y, a.x), pr(b.y, b.y));  // (ay by, ax by)
-  return mk(add2(p, pr(lane0(q), -lane1(q))));
-}
+__device__ __forceinline__ dfloat2 scl(dfloat2 a, dfloat s) { return mk(a.x * s, a.y * s); }
 
 // Precision of the node-wise arithmetic in the passes (power law, material laws, reverse-mode
 // Jacobians): the FFT's own precision, except that the double-float passes evaluate those

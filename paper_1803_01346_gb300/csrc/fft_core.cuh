@@ -96,22 +96,14 @@ template <int R, bool INV> struct TwiddleConst<dfloat2, R, INV> {
     if (q == 24) return mk(-a.x, -a.y);
     if (q == 12) return INV ? mk(-a.y, a.x) : mk(a.y, -a.x);
     if (q == 36) return INV ? mk(a.y, -a.x) : mk(-a.y, a.x);
-    // (two-lane forms: the lanes are the real and imaginary parts, each rounded as in the
-    // scalar forms mk(h (ax - by), h (bx + ay)) and mk(ax c - ay s, ax s + ay c), inverse)
     if (q % 12 == 6) {
       const dfloat h(0.7071067811865475244008444);
       const dfloat ax = cos24(q) > 0 ? a.x : -a.x, ay = cos24(q) > 0 ? a.y : -a.y;  // sign(c) a
       const dfloat bx = sin24(q) > 0 ? a.x : -a.x, by = sin24(q) > 0 ? a.y : -a.y;  // sign(s) a
-      const dfpair sum = INV ? add2(pr(ax, bx), pr(-by, ay)) : add2(pr(ax, ay), pr(by, -bx));
-      return mk(mul2(pr(h, h), sum));
+      return INV ? mk(h * (ax - by), h * (bx + ay)) : mk(h * (ax + by), h * (ay - bx));
     }
     const dfloat c(cos24(q)), s(sin24(q));
-    if (INV) {
-      const dfpair p = mul2(pr(a.x, a.x), pr(c, s)), r = mul2(pr(a.y, a.y), pr(s, c));
-      return mk(add2(p, pr(-lane0(r), lane1(r))));
-    }
-    const dfpair p = mul2(pr(a.x, a.y), pr(c, c)), r = mul2(pr(a.y, a.x), pr(s, s));
-    return mk(add2(p, pr(lane0(r), -lane1(r))));
+    return INV ? mk(a.x * c - a.y * s, a.x * s + a.y * c) : mk(a.x * c + a.y * s, a.y * c - a.x * s);
   }
 };
 template <typename V, int R, bool INV> __device__ __forceinline__ V twiddle_const(V a, int m) {
