@@ -67,15 +67,14 @@ __device__ __forceinline__ dfloat& operator+=(dfloat& x, dfloat y) { return x = 
 __device__ __forceinline__ dfloat& operator*=(dfloat& x, dfloat y) { return x = x * y; }
 
 // ---------------------------------------------------------------- two lanes at once
-// The same steps on two double-floats held lane-wise in float2 pairs (hi lanes, lo lanes), as
-// the two-lane FP32 instructions of sm_100 and later: each lane rounds exactly as the scalar
-// step does (b * -1 + a rounds as a - b), so a lane gives the scalar result bit for bit and
-// the pair costs one instruction per step instead of two.
+// The sum on two double-floats held lane-wise in float2 pairs (hi lanes, lo lanes), as the
+// two-lane FP32 instructions of sm_100 and later: each lane rounds exactly as the scalar step
+// does (b * -1 + a rounds as a - b), so a lane gives the scalar result bit for bit and the pair
+// costs one instruction per step instead of two.
 struct dfpair {
   float2 hi, lo;
 };
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ dfpair fast_two_sum2(float2 a, float2 b) {
   const float2 s = __fadd2_rn(a, b);
   dfpair r;
@@ -90,14 +89,6 @@ __device__ __forceinline__ dfpair add2(dfpair x, dfpair y) {
   const float2 av = sub2(s, bv);
   const float2 e = __fadd2_rn(sub2(x.hi, av), sub2(y.hi, bv));
   return fast_two_sum2(s, __fadd2_rn(e, __fadd2_rn(x.lo, y.lo)));
-}
-// lane-wise x * y (the scalar operator* above in each lane)
-__device__ __forceinline__ dfpair mul2(dfpair x, dfpair y) {
-  const float2 p = __fmul2_rn(x.hi, y.hi);
-  float2 e = __ffma2_rn(x.hi, y.hi, neg2(p));
-  e = __ffma2_rn(x.hi, y.lo, e);
-  e = __ffma2_rn(x.lo, y.hi, e);
-  return fast_two_sum2(p, e);
 }
 __device__ __forceinline__ dfpair pr(dfloat a, dfloat b) {  // lanes (a, b)
   dfpair r;
