@@ -78,3 +78,19 @@ def test_cufft_baseline_kernel_spectrum_matches_the_oracle():
     ref = O.hockney_kernel_spectrum(g)[:, :, :, : n[0] + 1]
     K = C.kernel_spectrum(torch, n, L, g.sigma, device="cpu").numpy()
     assert np.abs(K - ref).max() < 1e-6 * np.abs(ref).max()
+
+
+def test_source_box_fractions():
+    """The bench's source box (for the box-aware bytes of the forward padded passes) takes
+    Omega's bounding planes and rows, the rows rounded out to even bounds as the library
+    rounds them for its row pairs."""
+    import numpy as np
+    bench = _bench()
+    m = np.zeros((16, 20, 8), dtype=bool)  # [z][y][x]
+    m[3:7, 5:9, 2:4] = True                # planes 3..6, rows 5..8 -> rows 4..9 after rounding
+    fz, fyz = bench.source_box(m)
+    assert fz == 4 / 16
+    assert fyz == (4 * 6) / (16 * 20)
+    m[:] = False
+    m[2, 18, 1] = True                     # one node in the last even row pair: rows 18..19
+    assert bench.source_box(m) == (1 / 16, 2 / (16 * 20))
