@@ -262,8 +262,10 @@ scfft_status scfft_advance(scfft_ctx* ctx, double* t, double* dt, double tstop, 
  * only when the step reads it, i.e. always on the FP64 path and on the FP32 path unless the
  * step continues the context's own trajectory on these device buffers (FSAL, as in
  * scfft_step), whose warm start the context then holds itself.  The bytes copied are added to
- * scfft_stats.h2d_bytes / d2h_bytes.  Statuses as scfft_step; on an error nothing is copied
- * back.  Synchronous. */
+ * scfft_stats.h2d_bytes / d2h_bytes.  warm_host may be NULL: the warm start then lives only
+ * in the device buffer warm (a caller that continues its trajectory on this context, or that
+ * has put a warm start into warm itself) and is copied in neither direction.  Statuses as
+ * scfft_step; on an error nothing is copied back.  Synchronous. */
 scfft_status scfft_step_host(scfft_ctx* ctx, double* t, double* dt, double tstop, double* h_host,
                              double* warm_host, double* h, double* warm, int* rejected);
 

@@ -318,15 +318,19 @@ class Context:
 
     def step_host(self, t: float, dt: float, tstop: float, h_host, warm_host, h, warm):
         """One accepted BS23 step with the state in host memory (h_host, warm_host: CPU
-        tensors, pinned for speed), run on the device buffers h, warm; returns
+        tensors, pinned for speed; warm_host may be None: the warm start then stays in the
+        device buffer warm), run on the device buffers h, warm; returns
         (t_new, dt_next, rejected_trials)."""
         import torch
         for a in (h_host, warm_host):
+            if a is None and a is warm_host:
+                continue
             if a.device.type != "cpu" or a.dtype != torch.float64 or not a.is_contiguous():
                 raise ValueError("h_host, warm_host: contiguous float64 CPU tensors")
         tt, dd, rj = ctypes.c_double(t), ctypes.c_double(dt), ctypes.c_int(0)
         self._check(self._lib.scfft_step_host(self._h, ctypes.byref(tt), ctypes.byref(dd), float(tstop),
-                                              ctypes.c_void_p(h_host.data_ptr()), ctypes.c_void_p(warm_host.data_ptr()),
+                                              ctypes.c_void_p(h_host.data_ptr()),
+                                              ctypes.c_void_p(None if warm_host is None else warm_host.data_ptr()),
                                               _ptr(h), _ptr(warm), ctypes.byref(rj)), "scfft_step_host")
         return tt.value, dd.value, rj.value
 

@@ -2033,21 +2033,22 @@ scfft_status scfft_advance(scfft_ctx* c, double* t, double* dt, double tstop, in
 
 scfft_status scfft_step_host(scfft_ctx* c, double* t, double* dt, double tstop, double* h_host, double* warm_host,
                              double* h, double* warm, int* rejected) {
-  if (!c || !t || !dt || !h_host || !warm_host || !h || !warm || !(*dt > 0) || !(tstop > *t)) return SCFFT_EINVAL;
+  if (!c || !t || !dt || !h_host || !h || !warm || !(*dt > 0) || !(tstop > *t)) return SCFFT_EINVAL;
   if (!c->have_geom || !c->have_kernel || !c->have_path) return SCFFT_ESTATE;
   const size_t bytes = sizeof(double) * 3 * (size_t)c->g.N;
-  // the FP32 step reads the caller's warm start only when it starts a trajectory (FSAL below)
+  // the FP32 step reads the caller's warm start only when it starts a trajectory (FSAL below);
+  // without warm_host the warm start stays in the device buffer warm
   const bool continues = c->fsal_valid && c->fsal_t == *t && c->fsal_h == h && c->fsal_g == warm;
-  const bool reads_warm = c->opt.precision != SCFFT_PREC_F32 || !continues;
+  const bool reads_warm = warm_host && (c->opt.precision != SCFFT_PREC_F32 || !continues);
   CK(cudaMemcpyAsync(h, h_host, bytes, cudaMemcpyHostToDevice, c->st));
   if (reads_warm) CK(cudaMemcpyAsync(warm, warm_host, bytes, cudaMemcpyHostToDevice, c->st));
   c->stats.h2d_bytes += (long long)(reads_warm ? 2 : 1) * (long long)bytes;
   const scfft_status s = step_any(c, t, dt, tstop, h, warm, 0.0, rejected);
   if (s != SCFFT_OK) return s;
   CK(cudaMemcpyAsync(h_host, h, bytes, cudaMemcpyDeviceToHost, c->st));
-  CK(cudaMemcpyAsync(warm_host, warm, bytes, cudaMemcpyDeviceToHost, c->st));
+  if (warm_host) CK(cudaMemcpyAsync(warm_host, warm, bytes, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
-  c->stats.d2h_bytes += 2 * (long long)bytes;
+  c->stats.d2h_bytes += (warm_host ? 2 : 1) * (long long)bytes;
   return SCFFT_OK;
 }
 

@@ -99,3 +99,18 @@ def test_step_host_matches_step_bit_for_bit(prec):
     assert st["h2d_bytes"] == (2 * k * nb if prec == S.PREC_F64 else (k + 1) * nb)
     with pytest.raises(ValueError):
         b.step_host(t, dt, 2.0, hd, w_host, hd, wd)  # device tensor where a host one belongs
+    # without warm_host the warm start stays in the device buffer: the same trajectory bit for
+    # bit, with only h copied in and out on every step
+    c = _ctx(prec)
+    h_host2 = torch.zeros(n3, dtype=torch.float64).pin_memory()
+    hd2 = torch.full_like(h, float("nan"))
+    wd2 = torch.zeros_like(h)
+    wd2.view(3, -1)[2] = 0.5
+    t, dt = 0.0, 1e-3
+    for _ in range(k):
+        t, dt, _ = c.step_host(t, dt, 2.0, h_host2, None, hd2, wd2)
+    assert (t, dt) == (t_ref, dt_ref)
+    assert np.array_equal(h_host2.numpy(), h.cpu().numpy())
+    assert np.array_equal(wd2.cpu().numpy(), warm.cpu().numpy())
+    st = c.stats()
+    assert st["h2d_bytes"] == k * nb and st["d2h_bytes"] == k * nb
