@@ -136,15 +136,21 @@ scfft_status scfft_set_curl(scfft_ctx* ctx, int kind);
  *   z_curl_tile      z pass of the smoothed curl (Eq. 4): 8 or 16 columns
  *   y_unpadded_tile  y passes on the unpadded grid: 8 or 16 columns
  *   y_padded_tma     padded y passes: 1 = TMA-fed persistent kernel, 0 = plain loads
+ *   z_kernel_tmem    padded z pass of a 256-point z transform (nz = 128): 1 = each thread keeps the
+ *                    spectra of two components between the forward transforms, the product and
+ *                    the inverse transforms in tensor memory, 0 = in shared memory; 0 on other
+ *                    grids
  *   us               scfft_autotune only: mean time (microseconds) of the candidates in the order
  *                    z_kernel 8, 4; z_curl 8, 16; y_unpadded 8, 16 (forward + inverse);
- *                    y_padded TMA, plain (forward + inverse); 0 where not timed. */
+ *                    y_padded TMA, plain (forward + inverse); z_kernel_tmem 0, 1; 0 where not
+ *                    timed. */
 typedef struct {
   int z_kernel_tile;
   int z_curl_tile;
   int y_unpadded_tile;
   int y_padded_tma;
-  double us[8];
+  int z_kernel_tmem;
+  double us[10];
 } scfft_schedule;
 
 /* Autotuner of the schedule: times each candidate of each knob on the context's own workspace
@@ -159,7 +165,8 @@ scfft_status scfft_autotune(scfft_ctx* ctx, int retune, scfft_schedule* out);
 /* The schedule in use (out->us zero). */
 scfft_status scfft_get_schedule(scfft_ctx* ctx, scfft_schedule* out);
 /* Impose a schedule (FP32 contexts; SCFFT_EINVAL for a value outside the lists above, for
- * y_padded_tma = 1 without TMA descriptors, or for another precision). */
+ * y_padded_tma = 1 without TMA descriptors, for z_kernel_tmem = 1 when nz != 128, or for
+ * another precision). */
 scfft_status scfft_set_schedule(scfft_ctx* ctx, const scfft_schedule* sched);
 
 /* The e(j, h) law in Omega.  §2 (after Eq. 1) notes that another current-voltage relation,

@@ -1786,12 +1786,17 @@ void to_public(const Sched& s, scfft_schedule* o) {
   o->z_curl_tile = s.zc_tc;
   o->y_unpadded_tile = s.yu_tc;
   o->y_padded_tma = s.yp_tma;
+  o->z_kernel_tmem = s.zk_tm;
 }
 
 bool sched_ok(const scfft_schedule* s) {
   return (s->z_kernel_tile == 4 || s->z_kernel_tile == 8) && (s->z_curl_tile == 8 || s->z_curl_tile == 16) &&
-         (s->y_unpadded_tile == 8 || s->y_unpadded_tile == 16) && (s->y_padded_tma == 0 || s->y_padded_tma == 1);
+         (s->y_unpadded_tile == 8 || s->y_unpadded_tile == 16) && (s->y_padded_tma == 0 || s->y_padded_tma == 1) &&
+         (s->z_kernel_tmem == 0 || s->z_kernel_tmem == 1);
 }
+
+// the tensor-memory form of the padded z pass exists for its 16 x 16 split (a 256-point z transform)
+bool tmem_z_ok(const scfft_ctx* c) { return 2 * c->g.nz == 256; }
 
 // Mean device time (us) of one call of f (a few pass launches) on the context's stream: three
 // untimed calls, then ten between CUDA events.
@@ -1824,7 +1829,7 @@ template <typename F> scfft_status time_us(scfft_ctx* c, F&& f, double* us) {
 // passes transform its scratch spectra in place; their contents are not used afterwards) and
 // keep the fastest (the second candidate only when it is faster by more than 3%, so that timing
 // noise does not flip a choice); knobs act on different passes, so they are tuned one at a time.
-scfft_status autotune_f32(scfft_ctx* c, double us[8]) {
+scfft_status autotune_f32(scfft_ctx* c, double us[10]) {
   Launch<float> L = launch_of<float>(c);
   L.fault = nullptr;
   Sched& s = c->wf.sched;
@@ -1837,8 +1842,10 @@ scfft_status autotune_f32(scfft_ctx* c, double us[8]) {
     *knob = t[1] < 0.97 * t[0] ? cand[1] : cand[0];
     return SCFFT_OK;
   };
-  const int zk[2] = {8, 4}, zc[2] = {8, 16}, yu[2] = {8, 16}, yp[2] = {1, 0};
+  const int zk[2] = {8, 4}, zc[2] = {8, 16}, yu[2] = {8, 16}, yp[2] = {1, 0}, zm[2] = {0, 1};
+  s.zk_tm = 0;
   CS_(pick(&s.zk_tc, zk, us + 0, [&] { return launch_z_kernel<float>(L, false); }));
+  if (tmem_z_ok(c)) CS_(pick(&s.zk_tm, zm, us + 8, [&] { return launch_z_kernel<float>(L, false); }));
   CS_(pick(&s.zc_tc, zc, us + 2, [&] { return launch_z_curl<float>(L, false, inv_n); }));
   CS_(pick(&s.yu_tc, yu, us + 4, [&] {
     const cudaError_t e = launch_y<float>(L, false, false, false);
@@ -1875,11 +1882,11 @@ scfft_status scfft_autotune(scfft_ctx* c, int retune, scfft_schedule* out) {
   if (it != g_tune_cache.end() && !retune) {
     c->wf.sched = it->second;
   } else {
-    double us[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double us[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     CS_(autotune_f32(c, us));
     g_tune_cache[key] = c->wf.sched;
     if (out)
-      for (int i = 0; i < 8; ++i) out->us[i] = us[i];
+      for (int i = 0; i < 10; ++i) out->us[i] = us[i];
   }
   drop_loop_graph(c);
   if (out) to_public(c->wf.sched, out);
@@ -1897,7 +1904,9 @@ scfft_status scfft_set_schedule(scfft_ctx* c, const scfft_schedule* s) {
   if (!c || !s || !sched_ok(s)) return SCFFT_EINVAL;
   if (c->opt.precision != SCFFT_PREC_F32) return SCFFT_EINVAL;
   if (s->y_padded_tma && !c->wf.ym) return SCFFT_EINVAL;
+  if (s->z_kernel_tmem && !tmem_z_ok(c)) return SCFFT_EINVAL;
   CK(cudaStreamSynchronize(c->st));
+  c->wf.sched.zk_tm = s->z_kernel_tmem;
   c->wf.sched.zk_tc = s->z_kernel_tile;
   c->wf.sched.zc_tc = s->z_curl_tile;
   c->wf.sched.yu_tc = s->y_unpadded_tile;

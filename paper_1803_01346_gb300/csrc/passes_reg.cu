@@ -33,6 +33,81 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Tensor memory (TMEM) as per-thread storage.  A warp reaches only the 32 lanes of its quarter
+// (warp % 4) of the 128 lanes, one lane per thread, with the 32x32b access shape, so a value
+// a thread stores is read back only by that thread.  Allocation is by columns, one warp per
+// CTA; every CTA that allocates frees its columns before it exits.
+__device__ __forceinline__ void tm_alloc(unsigned* slot, unsigned ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+               ::"r"((unsigned)__cvta_generic_to_shared(slot)), "r"(ncols) : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tm_dealloc(unsigned taddr, unsigned ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+#define SCFFT_U(v) "r"(__float_as_uint(v))
+// store 4 complex (8 columns) of two slots; returns once the stores are complete
+__device__ __forceinline__ void tm_st4x2(unsigned ta, const float2* a, unsigned tb, const float2* b) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9};\n\t"
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%1], {%10, %11, %12, %13, %14, %15, %16, %17};\n\t"
+      "tcgen05.wait::st.sync.aligned;" ::"r"(ta), "r"(tb),
+      SCFFT_U(a[0].x), SCFFT_U(a[0].y), SCFFT_U(a[1].x), SCFFT_U(a[1].y), SCFFT_U(a[2].x), SCFFT_U(a[2].y),
+      SCFFT_U(a[3].x), SCFFT_U(a[3].y), SCFFT_U(b[0].x), SCFFT_U(b[0].y), SCFFT_U(b[1].x), SCFFT_U(b[1].y),
+      SCFFT_U(b[2].x), SCFFT_U(b[2].y), SCFFT_U(b[3].x), SCFFT_U(b[3].y)
+      : "memory");
+}
+// store 16 complex (32 columns); returns once the stores are complete
+__device__ __forceinline__ void tm_st16(unsigned ta, const float2* a) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n\t"
+      "tcgen05.wait::st.sync.aligned;" ::"r"(ta),
+      SCFFT_U(a[0].x), SCFFT_U(a[0].y), SCFFT_U(a[1].x), SCFFT_U(a[1].y), SCFFT_U(a[2].x), SCFFT_U(a[2].y),
+      SCFFT_U(a[3].x), SCFFT_U(a[3].y), SCFFT_U(a[4].x), SCFFT_U(a[4].y), SCFFT_U(a[5].x), SCFFT_U(a[5].y),
+      SCFFT_U(a[6].x), SCFFT_U(a[6].y), SCFFT_U(a[7].x), SCFFT_U(a[7].y), SCFFT_U(a[8].x), SCFFT_U(a[8].y),
+      SCFFT_U(a[9].x), SCFFT_U(a[9].y), SCFFT_U(a[10].x), SCFFT_U(a[10].y), SCFFT_U(a[11].x), SCFFT_U(a[11].y),
+      SCFFT_U(a[12].x), SCFFT_U(a[12].y), SCFFT_U(a[13].x), SCFFT_U(a[13].y), SCFFT_U(a[14].x), SCFFT_U(a[14].y),
+      SCFFT_U(a[15].x), SCFFT_U(a[15].y)
+      : "memory");
+}
+#undef SCFFT_U
+// load 4 complex of two slots; the values are complete when the call returns
+__device__ __forceinline__ void tm_ld4x2(unsigned ta, float2* a, unsigned tb, float2* b) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(ta), "r"(tb)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    a[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+    b[i] = make_float2(__uint_as_float(r[8 + 2 * i]), __uint_as_float(r[8 + 2 * i + 1]));
+  }
+}
+// load 16 complex (32 columns); the values are complete when the call returns
+__device__ __forceinline__ void tm_ld16(unsigned ta, float2* a) {
+  unsigned r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+}
+
 template <typename V> __device__ __forceinline__ V tw_mul(V a, V w, bool inv) { return inv ? cmulc(a, w) : cmul(a, w); }
 
 template <typename V> __device__ __forceinline__ V zero_v();
@@ -149,15 +224,15 @@ template <int R1, int R2, int TC, int KIND>
 cudaError_t go_z(const Launch<float>& L, float2* base, int rows, int sx, int HX, const float2* tw, double scale,
                  bool chk) {
   constexpr int Lt = R1 * R2;
-  constexpr int CS = (R1 == R2 && KIND == 1) ? cmax(R2 * (R1 * TC + kPad8), R1 * (R2 * TC + kPad8))
+  constexpr int CS = (R1 == R2 && KIND >= 1) ? cmax(R2 * (R1 * TC + kPad8), R1 * (R2 * TC + kPad8))
                                : cmax(cmax(R2 * (R1 * TC + kPad8), R1 * (R2 * TC + kPad8)), Lt * TC);
   // (the own-slot form stages K^ in component 2's buffer once the forward transforms are done)
   const size_t smem = sizeof(float2) * (Lt + 3 * CS);
   static_assert((Lt + 2 * CS) % 2 == 0, "16-byte alignment of the staged kernel spectrum");
   auto k = zpass_reg2_kernel<R1, R2, TC, KIND>;
   allow_smem<zpass_reg2_kernel<R1, R2, TC, KIND>>();
-  constexpr bool PACK = (R1 == R2 && KIND == 1);  // as in the kernel's column map
-  if (KIND == 1 && Lt != 2 * L.g.nz) return cudaErrorInvalidValue;  // the padded pass folds kz about Lt/2
+  constexpr bool PACK = (R1 == R2 && KIND >= 1);  // as in the kernel's column map
+  if (KIND >= 1 && Lt != 2 * L.g.nz) return cudaErrorInvalidValue;  // the padded pass folds kz about Lt/2
   const int nfull = HX / TC, rem = HX - nfull * TC;
   const dim3 grid = PACK ? dim3(nfull * rows + (rows * rem + TC - 1) / TC, 1, 1) : dim3((HX + TC - 1) / TC, rows, 1);
   const Work<float>& w = *L.w;
@@ -225,6 +300,14 @@ template <int R1, int R2> struct ZCurl {
 template <int R1, int R2> struct ZKern {
   static cudaError_t run(const Launch<float>& L, bool chk) {
     const Geo& g = L.g;
+    // the tensor-memory form of the own-slot product exists for the 16 x 16 split (L = 256)
+    if constexpr (R1 == 16 && R2 == 16) {
+      if (L.w->sched.zk_tm) {
+        if (L.w->sched.zk_tc == 4)
+          return go_z<R1, R2, 4, 2>(L, L.w->Pd, 2 * g.ny, g.sxp, g.nx + 1, L.w->twp[2], 1.0, chk);
+        return go_z<R1, R2, 8, 2>(L, L.w->Pd, 2 * g.ny, g.sxp, g.nx + 1, L.w->twp[2], 1.0, chk);
+      }
+    }
     if (L.w->sched.zk_tc == 4)
       return go_z<R1, R2, 4, 1>(L, L.w->Pd, 2 * g.ny, g.sxp, g.nx + 1, L.w->twp[2], 1.0, chk);
     return go_z<R1, R2, 8, 1>(L, L.w->Pd, 2 * g.ny, g.sxp, g.nx + 1, L.w->twp[2], 1.0, chk);
@@ -480,7 +563,7 @@ cudaError_t launch_x_reg_io(const Launch<float>& L, XMode mode, const PointParam
 namespace scfft {
 
 template <int R1, int R2, int TC, int KIND>
-__global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 4 : 1) zpass_reg2_kernel(float2* __restrict__ base, int rows, int sx, int HX,
+__global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND >= 1) ? 4 : 1) zpass_reg2_kernel(float2* __restrict__ base, int rows, int sx, int HX,
                                                              int nzs, const float2* __restrict__ twg,
                                                              const float* __restrict__ kt0,
                                                              const float* __restrict__ kt1,
@@ -491,10 +574,14 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 4 : 1) zpas
                                                              const float4* __restrict__ kap4, int nx, int ny, int nz,
                                                              const Ctrl* ctrl, int check_done, int zlo, int zhi) {
   constexpr int L = R1 * R2;
-  constexpr bool PR = (KIND == 1);
+  constexpr bool PR = (KIND >= 1);
+  // KIND 2: the own-slot spectra of components 0 and 1 live in tensor memory instead of
+  // shared memory (the same arithmetic in the same order, so the same bits as KIND 1)
+  constexpr bool TM = (KIND == 2);
   constexpr int S2 = R1 * TC + kPad8;  // forward transpose [k2][n1][c]
   constexpr int S1 = R2 * TC + kPad8;  // inverse transpose [m1][k2][c]
-  constexpr bool OWN = (R1 == R2 && KIND == 1);  // own-slot product (square split, Biot-Savart kernel)
+  constexpr bool OWN = (R1 == R2 && KIND >= 1);  // own-slot product (square split, Biot-Savart kernel)
+  static_assert(!TM || (OWN && R1 == 16), "tensor-memory spectra: the own-slot form of the 16 x 16 split");
   constexpr int CS = OWN ? cmax(R2 * S2, R1 * S1) : cmax(cmax(R2 * S2, R1 * S1), L * TC);
   constexpr int NT = TC * R1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -536,7 +623,20 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 4 : 1) zpas
   float2* col = base + (size_t)y * sx + kx;
   // (an L2 prefetch of the input columns of the CTA one wave later paid at three CTAs per SM;
   // at four it measured 2% slower and is gone)
-  __syncthreads();  // twiddles staged
+  // KIND 2: 64 tensor-memory columns per CTA, 16 complex of component 0 at columns 0-31 and of
+  // component 1 at 32-63 in each thread's lane (at most eight CTAs of this kernel fit an SM by
+  // registers, so the 512 columns of an SM always suffice)
+  __shared__ unsigned tm_slot;
+  if constexpr (TM) {
+    if (t < 32) tm_alloc(&tm_slot, 64u);
+    tm_fence_before();
+  }
+  __syncthreads();  // twiddles staged (and the tensor-memory address published)
+  unsigned tmq = 0;  // this thread's lane of the allocation
+  if constexpr (TM) {
+    tm_fence_after();
+    tmq = tm_slot + ((unsigned)(32 * ((t >> 5) & 3)) << 16);
+  }
   // This thread's twiddles W_L^{n1 j}: stage A uses j = k2 with its own n1, and
   // stage A' (run by the thread whose k2 equals this n1) uses j = m1, so one set
   // of registers serves both directions for all three components.
@@ -577,12 +677,16 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 4 : 1) zpas
 #pragma unroll
         for (int m = 0; m < R1; ++m) w[m] = Fq[n1 * S2 + m * TC + c];
         DFT<R1, false, float2>::run(w);
+        if (TM && q < 2) {
+          tm_st16(tmq + 32u * q, w);
+        } else {
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) {
-          if (q < 2)
-            Fq[n1 * S2 + k1 * TC + c] = w[k1];
-          else
-            w2[k1] = w[k1];
+          for (int k1 = 0; k1 < R1; ++k1) {
+            if (q < 2)
+              Fq[n1 * S2 + k1 * TC + c] = w[k1];
+            else
+              w2[k1] = w[k1];
+          }
         }
       }
     }
@@ -610,19 +714,44 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 4 : 1) zpas
       const float syg = (y <= ny) ? 1.f : -1.f;
       float2* F0 = F + k2 * S2 + c;
       float2* F1 = F0 + CS;
+      if constexpr (TM) {
+        // four points of components 0 and 1 per tensor-memory load and store
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) {
-        const int kz = k2 + R2 * k1;
-        const int fz = (kz <= L / 2) ? kz : L - kz;  // L = 2 nz: a constant, so most folds resolve at compile time
-        const float4 K = Ks[fz * TC + c];
-        const float ax = K.x, ay = syg * K.y, az = (kz <= L / 2) ? K.z : -K.z;
-        const float2 G0 = F0[k1 * TC], G1 = F1[k1 * TC], G2 = w2[k1];
-        const float2 cx = make_float2(ay * G2.x - az * G1.x, ay * G2.y - az * G1.y);
-        const float2 cy = make_float2(az * G0.x - ax * G2.x, az * G0.y - ax * G2.y);
-        const float2 cz = make_float2(ax * G1.x - ay * G0.x, ax * G1.y - ay * G0.y);
-        F0[k1 * TC] = make_float2(-cx.y, cx.x);
-        F1[k1 * TC] = make_float2(-cy.y, cy.x);
-        w2[k1] = make_float2(-cz.y, cz.x);
+        for (int b = 0; b < R1 / 4; ++b) {
+          float2 g0[4], g1[4];
+          tm_ld4x2(tmq + 8u * b, g0, tmq + 32u + 8u * b, g1);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int k1 = 4 * b + i;
+            const int kz = k2 + R2 * k1;
+            const int fz = (kz <= L / 2) ? kz : L - kz;
+            const float4 K = Ks[fz * TC + c];
+            const float ax = K.x, ay = syg * K.y, az = (kz <= L / 2) ? K.z : -K.z;
+            const float2 G0 = g0[i], G1 = g1[i], G2 = w2[k1];
+            const float2 cx = make_float2(ay * G2.x - az * G1.x, ay * G2.y - az * G1.y);
+            const float2 cy = make_float2(az * G0.x - ax * G2.x, az * G0.y - ax * G2.y);
+            const float2 cz = make_float2(ax * G1.x - ay * G0.x, ax * G1.y - ay * G0.y);
+            g0[i] = make_float2(-cx.y, cx.x);
+            g1[i] = make_float2(-cy.y, cy.x);
+            w2[k1] = make_float2(-cz.y, cz.x);
+          }
+          tm_st4x2(tmq + 8u * b, g0, tmq + 32u + 8u * b, g1);
+        }
+      } else {
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) {
+          const int kz = k2 + R2 * k1;
+          const int fz = (kz <= L / 2) ? kz : L - kz;  // L = 2 nz: a constant, so most folds resolve at compile time
+          const float4 K = Ks[fz * TC + c];
+          const float ax = K.x, ay = syg * K.y, az = (kz <= L / 2) ? K.z : -K.z;
+          const float2 G0 = F0[k1 * TC], G1 = F1[k1 * TC], G2 = w2[k1];
+          const float2 cx = make_float2(ay * G2.x - az * G1.x, ay * G2.y - az * G1.y);
+          const float2 cy = make_float2(az * G0.x - ax * G2.x, az * G0.y - ax * G2.y);
+          const float2 cz = make_float2(ax * G1.x - ay * G0.x, ax * G1.y - ay * G0.y);
+          F0[k1 * TC] = make_float2(-cx.y, cx.x);
+          F1[k1 * TC] = make_float2(-cy.y, cy.x);
+          w2[k1] = make_float2(-cz.y, cz.x);
+        }
       }
     }
     // ---- inverse: y[m1 + R1 m2] = sum_k2 W_R2^{-m2 k2} W_L^{-m1 k2} (sum_k1 X[k2 + R2 k1] W_R1^{-m1 k1}).
@@ -645,12 +774,23 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND == 1) ? 4 : 1) zpas
 #pragma unroll
         for (int m1 = 0; m1 < R1; ++m1) Fb[m1 * S1 + k2 * TC + c] = m1 == 0 ? wr[0] : cmulc(wr[m1], twr[m1]);
         if (q < 4) {  // the next component's own slots, read before the barrier that frees its buffer
-          const float2* Fn = F + (q - 2) * CS + k2 * S2 + c;
+          if constexpr (TM) {
+            tm_ld16(tmq + 32u * (q - 2), wr);
+          } else {
+            const float2* Fn = F + (q - 2) * CS + k2 * S2 + c;
 #pragma unroll
-          for (int k1 = 0; k1 < R1; ++k1) wr[k1] = Fn[k1 * TC];
+            for (int k1 = 0; k1 < R1; ++k1) wr[k1] = Fn[k1 * TC];
+          }
         }
       }
+      if (TM && q == 3) tm_fence_before();  // the last tensor-memory access of every thread
       __syncthreads();
+    }
+    if constexpr (TM) {
+      if (t < 32) {
+        tm_fence_after();
+        tm_dealloc(tm_slot, 64u);
+      }
     }
     // the last stage is left rolled over the components: a third of the unrolled code, and
     // fewer registers (154, from 168), measured 2% faster

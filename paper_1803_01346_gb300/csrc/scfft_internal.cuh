@@ -67,6 +67,7 @@ struct Sched {
   int zc_tc = 8;   // smoothed-curl z pass: columns per CTA, 8 or 16
   int yu_tc = 8;   // unpadded y passes: columns per CTA, 8 or 16
   int yp_tma = 1;  // padded y passes: TMA-fed persistent kernel (1) or plain loads, 16 columns (0)
+  int zk_tm = 0;   // padded z pass, 16 x 16 split: own-slot spectra in tensor memory (1) or shared memory (0)
 };
 
 // Device workspaces of one FFT precision T.

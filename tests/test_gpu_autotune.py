@@ -54,7 +54,8 @@ def test_every_schedule_gives_the_same_bits(n, L):
     ref_it, ref = _rhs(ctx, h, g0)
     for zk, zc, yu, yp in itertools.product((8, 4), (8, 16), (8, 16), (1, 0)):
         ctx.set_schedule(z_kernel_tile=zk, z_curl_tile=zc, y_unpadded_tile=yu, y_padded_tma=yp)
-        assert ctx.get_schedule() == dict(z_kernel_tile=zk, z_curl_tile=zc, y_unpadded_tile=yu, y_padded_tma=yp)
+        assert ctx.get_schedule() == dict(z_kernel_tile=zk, z_curl_tile=zc, y_unpadded_tile=yu, y_padded_tma=yp,
+                                          z_kernel_tmem=0)
         it, out = _rhs(ctx, h, g0)
         assert it == ref_it and np.array_equal(out, ref), (zk, zc, yu, yp)
     o = O.rhs(prob, 0.2, hs, g0s, delta_it=2e-5, max_iter=50)
@@ -75,7 +76,8 @@ def test_autotune_times_once_per_grid_and_keeps_the_results():
     sa = a.autotune(retune=True)
     assert sa["z_kernel_tile"] in (4, 8) and sa["z_curl_tile"] in (8, 16)
     assert sa["y_unpadded_tile"] in (8, 16) and sa["y_padded_tma"] in (0, 1)
-    assert all(u > 0 for u in sa["us"]), sa  # every candidate was timed
+    assert all(u > 0 for u in sa["us"][:8]), sa  # every candidate was timed
+    assert sa["z_kernel_tmem"] == 0 and sa["us"][8:] == [0.0, 0.0]  # no tensor-memory form at nz = 64
     print(f"[autotune 64^3] {sa}")
     sb = b.autotune()  # the same grid: the cached choice, nothing timed
     assert {k: sb[k] for k in S.Context._SCHED_KEYS} == {k: sa[k] for k in S.Context._SCHED_KEYS}
@@ -97,3 +99,34 @@ def test_autotune_is_a_no_op_without_a_schedule():
     ctx = _ctx(n, L, mask)
     with pytest.raises(S.ScfftError):
         ctx.set_schedule(z_kernel_tile=5)
+    with pytest.raises(S.ScfftError):  # the tensor-memory z pass needs a 256-point z transform
+        ctx.set_schedule(z_kernel_tmem=1)
+
+
+def test_tensor_memory_z_pass_gives_the_same_bits():
+    """nz = 128 (a 256-point padded z transform, 16 x 16 split): both column tiles with the
+    spectra in shared memory and in tensor memory give the same Eq. 5 iteration count and
+    dh/dt bit for bit, and the oracle's answer; the autotuner times both forms."""
+    n, L = (32, 16, 128), (1.0, 0.5, 4.0)
+    mask = I.lens(n, L, 0.4, 1.5, 0.08, 0.06)
+    ctx = _ctx(n, L, mask)
+    g = O.Grid(n, L)
+    prob = O.Problem(g, mask, O.Material(n=30.0, rho_out=100.0), O.FieldPath([0.0, 1.0], [[0, 0, 0], [0.3, -0.2, 0.9]]))
+    jr = O.curl_s(I.random_field((3,) + g.shape, 93, 0.3), g) * mask[None]
+    hs = O.phi_hockney(jr, g) + np.array([0.05, -0.02, 0.1])[:, None, None, None]
+    g0s = np.broadcast_to(prob.path.hedot(0.2)[:, None, None, None], hs.shape).copy()
+    h = torch.from_numpy(hs.reshape(-1).copy()).cuda()
+    g0 = torch.from_numpy(g0s.reshape(-1).copy()).cuda()
+    ref_it, ref = _rhs(ctx, h, g0)
+    for zk, zm in itertools.product((8, 4), (0, 1)):
+        ctx.set_schedule(z_kernel_tile=zk, z_kernel_tmem=zm)
+        assert ctx.get_schedule()["z_kernel_tmem"] == zm
+        it, out = _rhs(ctx, h, g0)
+        assert it == ref_it and np.array_equal(out, ref), (zk, zm)
+    o = O.rhs(prob, 0.2, hs, g0s, delta_it=2e-5, max_iter=50)
+    assert abs(o.iters - ref_it) <= 1
+    e = [float(np.abs(ref.reshape(hs.shape)[q] - o.hdot[q]).max() / np.abs(o.hdot[q]).max()) for q in range(3)]
+    assert max(e) < 6e-6, e
+    s = ctx.autotune(retune=True)
+    assert s["z_kernel_tmem"] in (0, 1) and s["us"][8] > 0 and s["us"][9] > 0, s
+    print(f"[autotune 32x16x128] {s}")
