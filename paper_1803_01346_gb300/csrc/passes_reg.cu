@@ -373,6 +373,9 @@ struct XRArgs {
   // mask/pad pass of an Eq. 5 iteration: only the row pairs of Omega's box (y in [by0, by1),
   // z in [bz0, bz1)); the rows outside hold zeros of the source and are not read downstream
   int use_box, by0, by1, bz0, bz1;
+  // mask/pad pass: each work item is one component of a tile (the components are independent
+  // in this mode), three times the parallelism of a tile of all three
+  int comp_split;
 };
 
 namespace {
@@ -451,7 +454,7 @@ cudaError_t go_x(const XRArgs& a, cudaStream_t st) {
   auto k = xpass_reg2_kernel<MODE, R1i, R2i, R2o, kPairs>;
   allow_smem<xpass_reg2_kernel<MODE, R1i, R2i, R2o, kPairs>>();
   const int npairs = pair_count(a);
-  const int ntiles = (npairs + kPairs - 1) / kPairs;
+  const int ntiles = (npairs + kPairs - 1) / kPairs * ((MODE == X_MASKPAD && a.comp_split) ? 3 : 1);
   // one wave of resident CTAs (the kernel loops over tiles)
   static const int resident = [&] {
     int per_sm = 0, dev = 0, sms = 0;
@@ -532,6 +535,7 @@ cudaError_t launch_x_reg_io(const Launch<float>& L, XMode mode, const PointParam
   a.check_done = check_done ? 1 : 0;
   a.out_buf = out_buf;
   a.use_box = (L.use_box && mode == X_MASKPAD) ? 1 : 0;
+  a.comp_split = a.use_box;  // the mask/pad pass of an Eq. 5 iteration: one wave of small work
   a.by0 = L.by0;
   a.by1 = L.by1;
   a.bz0 = L.bz0;
@@ -950,7 +954,10 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
   const int ny = a.g.ny, nz = a.g.nz;
   const long long N = a.g.N;
   const int npairs = pair_count(a);
+  constexpr bool CSPL = (MODE == X_MASKPAD);  // the components are independent in this mode
+  const bool split = CSPL && a.comp_split;
   const int ntiles = (npairs + P - 1) / P;
+  const int nwork = split ? 3 * ntiles : ntiles;
   float partf = 0.f;
   static_assert(XL % TP == 0 && 32 % TP == 0, "a row pair's nodes split evenly over its lanes, inside one warp");
   __syncthreads();  // twiddle tables
@@ -958,9 +965,12 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
   // every shared-memory exchange stays within one row pair, whose TP lanes lie in one warp, so
   // the tile needs warp barriers only and the warps of a CTA run independently of each other.
   // Lane r of pair p owns the nodes x = r + TP j of both rows in the node-wise step.
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int wk = blockIdx.x; wk < nwork; wk += gridDim.x) {
+    // a work item: tile wk of all three components, or (split) component wk % 3 of tile wk / 3
+    const int tile = split ? wk / 3 : wk;
+    const int q0 = split ? wk - 3 * tile : 0, q1 = split ? q0 + 1 : 3;
     // prefetch the next tile's first-phase rows into L2 while this tile runs
-    if (tile + (int)gridDim.x < ntiles) {
+    if (!split && tile + (int)gridDim.x < ntiles) {
       const int nrow0 = 2 * (tile + (int)gridDim.x) * P;
       if constexpr (S::C2R) {
         const int lines = ((Li / 2 + 1) * 8 + 127) / 128;
@@ -997,7 +1007,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
     // L2 prefetch of everything this CTA reads after its first phase (components 1
     // and 2 of the input rows, and the node-wise step's rows), so that those later
     // phases see L2 rather than DRAM latency; it costs no registers.
-    {
+    if (!split) {
       const int row0 = 2 * tile * P;  // first (z, y) row of this CTA
       const int nrow = 2 * P;
       if constexpr (S::C2R) {
@@ -1037,7 +1047,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
     }
 
     if constexpr (S::C2R) {
-      for (int q = 0; q < 3; ++q) {
+      for (int q = q0; q < q1; ++q) {
         const int n1 = r;
         if (n1 < R1i) {
           const float2* ra = a.spec_in + ((size_t)(q * nz + z) * a.in_rows + ya) * a.in_sx;
@@ -1181,6 +1191,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
             u[q] = make_float2(va, vb);
           }
         } else if (MODE == X_MASKPAD) {
+          // (a split work item holds one component; the other slots are not read downstream)
   #pragma unroll
           for (int q = 0; q < 3; ++q) u[q] = make_float2(ia ? u[q].x : 0.f, ib ? u[q].y : 0.f);
         } else if (UPD) {
@@ -1218,7 +1229,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
     }
 
     if constexpr (S::R2C) {
-      for (int q = 0; q < 3; ++q) {
+      for (int q = q0; q < q1; ++q) {
         const int n1 = r;
         if (n1 < R1o) {
           float2 u[R2o];
