@@ -195,6 +195,10 @@ def algorithmic_bytes(kind: str, n, fp_bytes: int, box=(1.0, 1.0)) -> float:
         "y_fwd_padded": Pin * fyz + Pall * fz,
         "y_inv_padded": Pall + Pin,
         "z_kernel": Pall * fz + Pall + kap,
+        # the curl's inverse y pass, mask/pad and the padded forward y pass as one launch: the
+        # curl's half spectrum on the box's planes in, the mask on its rows, the padded spectrum
+        # of its planes out
+        "box_fused": U * fz + N * fyz + Pall * fz,
         "finalize": real + 2 * 3 * N * 8,
     }
     return float(table.get(kind, 0.0))
@@ -338,7 +342,7 @@ def bench_batch(S, torch, steps: int, warmup: int):
             "sequential_instance_steps_per_s": len(inst) * steps / seq, "speedup_vs_sequential": seq / el,
             "iters_per_rhs": its / max(1, rcs),
             "schedules": {str(k): {kk: v[kk] for kk in ("z_kernel_tile", "z_curl_tile", "y_unpadded_tile",
-                                                         "y_padded_tma", "z_kernel_tmem")}
+                                                         "y_padded_tma", "z_kernel_tmem", "box_fused")}
                           for k, v in sorted(schedules.items())},
             "timing": "wall clock around synchronous batch calls, device synchronised on both sides"}
 

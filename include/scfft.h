@@ -140,17 +140,24 @@ scfft_status scfft_set_curl(scfft_ctx* ctx, int kind);
  *                    spectra of two components between the forward transforms, the product and
  *                    the inverse transforms in tensor memory, 0 = in shared memory; 0 on other
  *                    grids
+ *   box_fused        Eq. 5 iteration with the spectral curl: 1 = the curl's inverse y pass, the
+ *                    mask/pad x pass and the padded forward y pass, which see only Omega's
+ *                    bounding box, run as one launch with one CTA per (component, plane of the
+ *                    box) and their intermediates in shared memory; 0 = three launches.  Applies
+ *                    where nx = ny and the box's rows fit shared memory (the three passes run
+ *                    otherwise)
  *   us               scfft_autotune only: mean time (microseconds) of the candidates in the order
  *                    z_kernel 8, 4; z_curl 8, 16; y_unpadded 8, 16 (forward + inverse);
- *                    y_padded TMA, plain (forward + inverse); z_kernel_tmem 0, 1; 0 where not
- *                    timed. */
+ *                    y_padded TMA, plain (forward + inverse); z_kernel_tmem 0, 1; box_fused 0, 1
+ *                    (the three passes, the fused pass); 0 where not timed. */
 typedef struct {
   int z_kernel_tile;
   int z_curl_tile;
   int y_unpadded_tile;
   int y_padded_tma;
   int z_kernel_tmem;
-  double us[10];
+  int box_fused;
+  double us[12];
 } scfft_schedule;
 
 /* Autotuner of the schedule: times each candidate of each knob on the context's own workspace
@@ -319,7 +326,8 @@ enum {
   SCFFT_K_FINALIZE = 11,   /* dh/dt and warm start written out                    */
   SCFFT_K_RK = 12,         /* integrator stage sums and error norm                */
   SCFFT_K_OTHER = 13,      /* passes of scfft_curl / scfft_phi                    */
-  SCFFT_NKINDS = 14
+  SCFFT_K_BOX = 14,        /* fused on Omega's box: y inverse, mask/pad x, padded y forward */
+  SCFFT_NKINDS = 15
 };
 scfft_status scfft_profile(scfft_ctx* ctx, int enable);
 scfft_status scfft_profile_read(scfft_ctx* ctx, long long* counts, double* ms);

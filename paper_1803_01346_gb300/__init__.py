@@ -41,7 +41,7 @@ EXPORTS = ("scfft_create", "scfft_set_geometry", "scfft_set_jc_map", "scfft_set_
            "scfft_autotune", "scfft_get_schedule", "scfft_set_schedule",
            "scfft_advance")
 
-NKINDS = 14
+NKINDS = 15
 
 
 def library_path() -> str:
@@ -84,7 +84,8 @@ class _EjLaw(ctypes.Structure):
 
 class _Schedule(ctypes.Structure):
     _fields_ = [("z_kernel_tile", ctypes.c_int), ("z_curl_tile", ctypes.c_int), ("y_unpadded_tile", ctypes.c_int),
-                ("y_padded_tma", ctypes.c_int), ("z_kernel_tmem", ctypes.c_int), ("us", ctypes.c_double * 10)]
+                ("y_padded_tma", ctypes.c_int), ("z_kernel_tmem", ctypes.c_int), ("box_fused", ctypes.c_int),
+                ("us", ctypes.c_double * 12)]
 
 
 class _Stats(ctypes.Structure):
@@ -244,7 +245,7 @@ class Context:
         """CURL_SPECTRAL (§2) or CURL_FD (central differences) for the curls of the rhs."""
         self._check(self._lib.scfft_set_curl(self._h, int(kind)), "scfft_set_curl")
 
-    _SCHED_KEYS = ("z_kernel_tile", "z_curl_tile", "y_unpadded_tile", "y_padded_tma", "z_kernel_tmem")
+    _SCHED_KEYS = ("z_kernel_tile", "z_curl_tile", "y_unpadded_tile", "y_padded_tma", "z_kernel_tmem", "box_fused")
 
     def autotune(self, retune: bool = False):
         """Time the launch schedules of the FP32 passes on this context's grid and keep the

@@ -185,6 +185,9 @@ template <typename T> Launch<T> boxed(const Launch<T>& L) {
   return B;
 }
 
+// The schedule asks for the fused box passes and they apply to this launch (FP32, nx == ny).
+bool box_fused_on(const Launch<float>& L) { return L.w->sched.box_fused && box_fused_ok(L); }
+
 // ---------------------------------------------------------------- profiling
 cudaError_t prof_flush(scfft_ctx* c) {
   if (c->pused == 0) return cudaSuccess;
@@ -355,6 +358,7 @@ template <typename T> cudaError_t iteration(scfft_ctx* c, const Launch<T>& L, Po
   cudaError_t e;
   const bool fd = c->curl_kind == SCFFT_CURL_FD;
   const Launch<T> LB = boxed(L);  // the source chi curl dh^i vanishes outside Omega's box
+  bool fused = false;              // FP32: the three passes on Omega's box as one launch
   if (fd) {
     if ((e = fd_maskpad<T>(c, L, pp, chk)) != cudaSuccess) return e;
   } else {
@@ -364,12 +368,21 @@ template <typename T> cudaError_t iteration(scfft_ctx* c, const Launch<T>& L, Po
     if ((e = run(c, SCFFT_K_Z_CURL, [&] { return launch_z_curl<T>(LB, chk, 1.0 / (double)L.g.N); })) !=
         cudaSuccess)
       return e;
-    if ((e = run(c, SCFFT_K_Y_INV_U, [&] { return launch_y<T>(LB, false, true, chk); })) != cudaSuccess) return e;
-    if ((e = run(c, SCFFT_K_X_MASKPAD,
-                 [&] { return launch_x<T>(LB, X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, chk); })) != cudaSuccess)
-      return e;
+    if constexpr (std::is_same<T, float>::value) {
+      fused = box_fused_on(LB);
+      // the curl's inverse y pass, the mask/pad x pass and the padded forward y pass, fused
+      if (fused && (e = run(c, SCFFT_K_BOX, [&] { return launch_box_fused(LB, chk); })) != cudaSuccess) return e;
+    }
+    if (!fused) {
+      if ((e = run(c, SCFFT_K_Y_INV_U, [&] { return launch_y<T>(LB, false, true, chk); })) != cudaSuccess) return e;
+      if ((e = run(c, SCFFT_K_X_MASKPAD,
+                   [&] { return launch_x<T>(LB, X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, chk); })) !=
+          cudaSuccess)
+        return e;
+    }
   }
-  if ((e = run(c, SCFFT_K_Y_FWD_P, [&] { return launch_y<T>(LB, true, false, chk); })) != cudaSuccess) return e;
+  if (!fused && (e = run(c, SCFFT_K_Y_FWD_P, [&] { return launch_y<T>(LB, true, false, chk); })) != cudaSuccess)
+    return e;
   if ((e = run(c, SCFFT_K_Z_KERNEL, [&] { return launch_z_kernel<T>(LB, chk); })) != cudaSuccess) return e;
   if ((e = run(c, SCFFT_K_Y_INV_P, [&] { return launch_y<T>(L, true, true, chk); })) != cudaSuccess) return e;
   pp.iter = i;
@@ -394,11 +407,13 @@ __global__ void loop_cond_kernel(cudaGraphConditionalHandle h, Ctrl* ctrl, int m
 }
 
 constexpr int kLoopLaunches = 9;    // kernels per iteration of the graph body
+constexpr int kLoopLaunchesBox = 7; // the same with the fused box passes
 constexpr int kLoopLaunchesFd = 7;  // the same with the local-stencil curl
 
 cudaError_t loop_body(const Launch<float>& L, const PointParams& pp, cudaGraphConditionalHandle h, int max_iter,
                       bool fd, const double* dcell) {
   cudaError_t e;
+  bool fused = false;
   if (fd) {
     if ((e = launch_fd_curl_mask<float>(L, L.w->Jd, dcell, false)) != cudaSuccess) return e;
     if ((e = launch_x_reg_io(L, X_PAD_F64, pp, nullptr, L.w->Jd, nullptr, nullptr, nullptr, 0, 0, false)) !=
@@ -407,11 +422,16 @@ cudaError_t loop_body(const Launch<float>& L, const PointParams& pp, cudaGraphCo
   } else {
     if ((e = launch_y<float>(L, false, false, false)) != cudaSuccess) return e;
     if ((e = launch_z_curl<float>(boxed(L), false, 1.0 / (double)L.g.N)) != cudaSuccess) return e;
-    if ((e = launch_y<float>(boxed(L), false, true, false)) != cudaSuccess) return e;
-    if ((e = launch_x<float>(boxed(L), X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, false)) != cudaSuccess)
-      return e;
+    fused = box_fused_on(boxed(L));
+    if (fused) {
+      if ((e = launch_box_fused(boxed(L), false)) != cudaSuccess) return e;
+    } else {
+      if ((e = launch_y<float>(boxed(L), false, true, false)) != cudaSuccess) return e;
+      if ((e = launch_x<float>(boxed(L), X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, false)) != cudaSuccess)
+        return e;
+    }
   }
-  if ((e = launch_y<float>(boxed(L), true, false, false)) != cudaSuccess) return e;
+  if (!fused && (e = launch_y<float>(boxed(L), true, false, false)) != cudaSuccess) return e;
   if ((e = launch_z_kernel<float>(boxed(L), false)) != cudaSuccess) return e;
   if ((e = launch_y<float>(L, true, true, false)) != cudaSuccess) return e;
   if ((e = launch_x<float>(L, fd ? X_UPDATE_FD : X_UPDATE, pp, nullptr, nullptr, nullptr, 0, 1, false)) != cudaSuccess)
@@ -508,7 +528,10 @@ void absorb_ctrl(scfft_ctx* c, const Ctrl& hc, bool graph_iters) {
   c->iters_seen = hc.iter_total;
   c->stats.iterations += (long long)d;
   if (graph_iters)
-    c->stats.launches += (long long)(c->curl_kind == SCFFT_CURL_FD ? kLoopLaunchesFd : kLoopLaunches) * (long long)d;
+    c->stats.launches += (long long)(c->curl_kind == SCFFT_CURL_FD     ? kLoopLaunchesFd
+                                     : box_fused_on(boxed(launch_of<float>(c))) ? kLoopLaunchesBox
+                                                                                : kLoopLaunches) *
+                         (long long)d;
   c->stats.last_iters = hc.iters;
   c->stats.last_residual = hc.residual;
   c->graph_pending = false;
@@ -1624,7 +1647,8 @@ const char* scfft_status_string(scfft_status s) {
 const char* scfft_kind_name(int kind) {
   static const char* names[SCFFT_NKINDS] = {
       "x_fwd_state", "x_powerlaw", "x_assemble", "x_maskpad", "x_update", "y_fwd_unpadded", "y_inv_unpadded",
-      "z_curl",      "y_fwd_padded", "y_inv_padded", "z_kernel", "finalize", "rk_stage", "io_pass"};
+      "z_curl",      "y_fwd_padded", "y_inv_padded", "z_kernel", "finalize", "rk_stage", "io_pass",
+      "box_fused"};
   return (kind >= 0 && kind < SCFFT_NKINDS) ? names[kind] : "unknown";
 }
 
@@ -1787,12 +1811,13 @@ void to_public(const Sched& s, scfft_schedule* o) {
   o->y_unpadded_tile = s.yu_tc;
   o->y_padded_tma = s.yp_tma;
   o->z_kernel_tmem = s.zk_tm;
+  o->box_fused = s.box_fused;
 }
 
 bool sched_ok(const scfft_schedule* s) {
   return (s->z_kernel_tile == 4 || s->z_kernel_tile == 8) && (s->z_curl_tile == 8 || s->z_curl_tile == 16) &&
          (s->y_unpadded_tile == 8 || s->y_unpadded_tile == 16) && (s->y_padded_tma == 0 || s->y_padded_tma == 1) &&
-         (s->z_kernel_tmem == 0 || s->z_kernel_tmem == 1);
+         (s->z_kernel_tmem == 0 || s->z_kernel_tmem == 1) && (s->box_fused == 0 || s->box_fused == 1);
 }
 
 // the tensor-memory form of the padded z pass exists for its 16 x 16 split (a 256-point z transform)
@@ -1829,7 +1854,7 @@ template <typename F> scfft_status time_us(scfft_ctx* c, F&& f, double* us) {
 // passes transform its scratch spectra in place; their contents are not used afterwards) and
 // keep the fastest (the second candidate only when it is faster by more than 3%, so that timing
 // noise does not flip a choice); knobs act on different passes, so they are tuned one at a time.
-scfft_status autotune_f32(scfft_ctx* c, double us[10]) {
+scfft_status autotune_f32(scfft_ctx* c, double us[12]) {
   Launch<float> L = launch_of<float>(c);
   L.fault = nullptr;
   Sched& s = c->wf.sched;
@@ -1859,6 +1884,19 @@ scfft_status autotune_f32(scfft_ctx* c, double us[10]) {
   } else {
     s.yp_tma = 0;
   }
+  // the three passes on Omega's box against the fused pass (after the y passes' own choice)
+  const Launch<float> LB = boxed(L);
+  s.box_fused = 0;
+  if (box_fused_ok(LB) && c->curl_kind == SCFFT_CURL_SPECTRAL) {
+    const int bf[2] = {0, 1};
+    PointParams pp = base_params(c);
+    CS_(pick(&s.box_fused, bf, us + 10, [&] {
+      if (s.box_fused) return launch_box_fused(LB, false);
+      cudaError_t e = launch_y<float>(LB, false, true, false);
+      if (e == cudaSuccess) e = launch_x<float>(LB, X_MASKPAD, pp, nullptr, nullptr, nullptr, 0, 0, false);
+      return e != cudaSuccess ? e : launch_y<float>(LB, true, false, false);
+    }));
+  }
   return SCFFT_OK;
 }
 
@@ -1882,11 +1920,11 @@ scfft_status scfft_autotune(scfft_ctx* c, int retune, scfft_schedule* out) {
   if (it != g_tune_cache.end() && !retune) {
     c->wf.sched = it->second;
   } else {
-    double us[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double us[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     CS_(autotune_f32(c, us));
     g_tune_cache[key] = c->wf.sched;
     if (out)
-      for (int i = 0; i < 10; ++i) out->us[i] = us[i];
+      for (int i = 0; i < 12; ++i) out->us[i] = us[i];
   }
   drop_loop_graph(c);
   if (out) to_public(c->wf.sched, out);
@@ -1911,6 +1949,7 @@ scfft_status scfft_set_schedule(scfft_ctx* c, const scfft_schedule* s) {
   c->wf.sched.zc_tc = s->z_curl_tile;
   c->wf.sched.yu_tc = s->y_unpadded_tile;
   c->wf.sched.yp_tma = s->y_padded_tma;
+  c->wf.sched.box_fused = s->box_fused;
   drop_loop_graph(c);
   return SCFFT_OK;
 }

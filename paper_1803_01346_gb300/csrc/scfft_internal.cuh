@@ -68,6 +68,7 @@ struct Sched {
   int yu_tc = 8;   // unpadded y passes: columns per CTA, 8 or 16
   int yp_tma = 1;  // padded y passes: TMA-fed persistent kernel (1) or plain loads, 16 columns (0)
   int zk_tm = 0;   // padded z pass, 16 x 16 split: own-slot spectra in tensor memory (1) or shared memory (0)
+  int box_fused = 0;  // Eq. 5 iteration: the three passes on Omega's box fused into one launch (1) or not (0)
 };
 
 // Device workspaces of one FFT precision T.
@@ -170,6 +171,12 @@ cudaError_t launch_y_reg(const Launch<float>& L, bool padded, bool inverse, bool
 bool make_ymaps(Work<float>& w, const Geo& g);
 cudaError_t launch_y_tma(const Launch<float>& L, bool padded, bool inverse, bool check_done);
 cudaError_t launch_z_reg(const Launch<float>& L, bool padded, bool check_done, double scale);
+// The curl's inverse y pass, the mask/pad x pass and the padded forward y pass of an Eq. 5
+// iteration (all on Omega's box) as one launch (boxpass.cu); box_fused_ok: the launch applies
+// (the box set, nx == ny, a supported length); cudaErrorNotSupported where it does not apply or
+// the box's rows do not fit shared memory (the three passes run instead).
+bool box_fused_ok(const Launch<float>& L);
+cudaError_t launch_box_fused(const Launch<float>& L, bool check_done);
 
 cudaError_t launch_x_reg(const Launch<float>& L, XMode mode, const PointParams& pp, const double* src_f64,
                          double* dst_f64, const double* warm, int in_buf, int out_buf, bool check_done);

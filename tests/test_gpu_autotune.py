@@ -40,8 +40,10 @@ def _rhs(ctx, h, g0):
 
 @pytest.mark.parametrize("n,L", [((32, 32, 32), (1.0, 1.0, 1.0)), ((48, 32, 16), (1.2, 0.9, 0.8))])
 def test_every_schedule_gives_the_same_bits(n, L):
-    """All 16 schedules: the same Eq. 5 iteration count and the same dh/dt bit for bit (the
-    loop graph is rebuilt after each change), and the oracle's answer."""
+    """All 32 schedules: the same Eq. 5 iteration count and the same dh/dt bit for bit (the
+    loop graph is rebuilt after each change), and the oracle's answer.  On the first grid
+    (nx = ny) the fused box passes run; on the second they do not apply and the three
+    passes run whatever the knob says."""
     mask = I.lens(n, L, 0.6 * min(L), 0.5 * min(L), 0.1, 0.1)
     ctx = _ctx(n, L, mask)
     g = O.Grid(n, L)
@@ -52,12 +54,12 @@ def test_every_schedule_gives_the_same_bits(n, L):
     h = torch.from_numpy(hs.reshape(-1).copy()).cuda()
     g0 = torch.from_numpy(g0s.reshape(-1).copy()).cuda()
     ref_it, ref = _rhs(ctx, h, g0)
-    for zk, zc, yu, yp in itertools.product((8, 4), (8, 16), (8, 16), (1, 0)):
-        ctx.set_schedule(z_kernel_tile=zk, z_curl_tile=zc, y_unpadded_tile=yu, y_padded_tma=yp)
+    for zk, zc, yu, yp, bf in itertools.product((8, 4), (8, 16), (8, 16), (1, 0), (0, 1)):
+        ctx.set_schedule(z_kernel_tile=zk, z_curl_tile=zc, y_unpadded_tile=yu, y_padded_tma=yp, box_fused=bf)
         assert ctx.get_schedule() == dict(z_kernel_tile=zk, z_curl_tile=zc, y_unpadded_tile=yu, y_padded_tma=yp,
-                                          z_kernel_tmem=0)
+                                          z_kernel_tmem=0, box_fused=bf)
         it, out = _rhs(ctx, h, g0)
-        assert it == ref_it and np.array_equal(out, ref), (zk, zc, yu, yp)
+        assert it == ref_it and np.array_equal(out, ref), (zk, zc, yu, yp, bf)
     o = O.rhs(prob, 0.2, hs, g0s, delta_it=2e-5, max_iter=50)
     assert abs(o.iters - ref_it) <= 1
     e = [float(np.abs(ref.reshape(hs.shape)[q] - o.hdot[q]).max() / np.abs(o.hdot[q]).max()) for q in range(3)]
@@ -77,7 +79,8 @@ def test_autotune_times_once_per_grid_and_keeps_the_results():
     assert sa["z_kernel_tile"] in (4, 8) and sa["z_curl_tile"] in (8, 16)
     assert sa["y_unpadded_tile"] in (8, 16) and sa["y_padded_tma"] in (0, 1)
     assert all(u > 0 for u in sa["us"][:8]), sa  # every candidate was timed
-    assert sa["z_kernel_tmem"] == 0 and sa["us"][8:] == [0.0, 0.0]  # no tensor-memory form at nz = 64
+    assert sa["z_kernel_tmem"] == 0 and sa["us"][8:10] == [0.0, 0.0]  # no tensor-memory form at nz = 64
+    assert sa["box_fused"] in (0, 1) and sa["us"][10] > 0 and sa["us"][11] > 0, sa  # three passes, fused
     print(f"[autotune 64^3] {sa}")
     sb = b.autotune()  # the same grid: the cached choice, nothing timed
     assert {k: sb[k] for k in S.Context._SCHED_KEYS} == {k: sa[k] for k in S.Context._SCHED_KEYS}

@@ -517,3 +517,36 @@ def test_rhs_fp32_off_centre_source_box_matches_oracle(n, L):
         out[mode] = host(o)
         ctx.profile(False)
     assert np.array_equal(out["host"], out["graph"])
+
+
+@pytest.mark.parametrize("n,L", [((16, 16, 32), (0.8, 0.8, 1.2)), ((32, 32, 16), (1.0, 1.0, 0.6)),
+                                 ((48, 48, 32), (1.1, 1.1, 0.8)), ((64, 64, 16), (1.2, 1.2, 0.5)),
+                                 ((96, 96, 16), (1.4, 1.4, 0.4)), ((128, 128, 16), (1.6, 1.6, 0.3))])
+def test_rhs_fp32_fused_box_passes_match_three_passes_and_oracle(n, L):
+    """The curl's inverse y pass, the mask/pad x pass and the padded forward y pass of an Eq.
+    5 iteration fused into one launch over Omega's box (nx = ny, every x length): with an
+    off-centre solid whose box starts at odd rows and planes, the same dh/dt bit for bit as
+    the three launches (host-driven and graph loops) and the oracle's at a fixed iteration
+    count."""
+    g = O.Grid(n, L)
+    mask = _off_centre_mask(g, L)
+    ctx, prob = make(n, L, mask, n_power=25.0, prec=S.PREC_F32, max_iter=4)
+    h = _state(prob, 99)
+    g0 = I.random_field(h.shape, 100, 0.1)
+    ref = O.rhs(prob, 0.4, h, g0, delta_it=0.0, max_iter=4)
+    out = {}
+    for bf in (0, 1):
+        ctx.set_schedule(box_fused=bf)
+        for mode in ("host", "graph"):
+            ctx.profile(mode == "host")
+            o = torch.empty(h.size, dtype=torch.float64, device="cuda")
+            assert ctx.rhs(0.4, dev(h).reshape(-1), dev(g0).reshape(-1), o) == 4
+            out[bf, mode] = host(o)
+            if mode == "host":
+                prof = ctx.profile_read()
+                # the fused launch runs in place of the three (4 iterations per rhs)
+                assert prof["box_fused"][0] == (4 if bf else 0), prof
+                assert prof["x_maskpad"][0] == (0 if bf else 4), prof
+            ctx.profile(False)
+    assert all(np.array_equal(out[0, "host"], v) for v in out.values())
+    check3(f"rhs fused box passes {n}", out[1, "graph"].reshape(h.shape), ref.hdot, RHS32)
