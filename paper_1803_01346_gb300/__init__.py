@@ -85,7 +85,7 @@ class _EjLaw(ctypes.Structure):
 class _Schedule(ctypes.Structure):
     _fields_ = [("z_kernel_tile", ctypes.c_int), ("z_curl_tile", ctypes.c_int), ("y_unpadded_tile", ctypes.c_int),
                 ("y_padded_tma", ctypes.c_int), ("z_kernel_tmem", ctypes.c_int), ("box_fused", ctypes.c_int),
-                ("us", ctypes.c_double * 12)]
+                ("us", ctypes.c_double * 13)]
 
 
 class _Stats(ctypes.Structure):

@@ -192,6 +192,11 @@ __global__ void zpass_reg2_kernel(float2* __restrict__ base, int rows, int sx, i
                                   const float* __restrict__ st2, float scale, const float4* __restrict__ kap4, int nx,
                                   int ny, int nz, const Ctrl* ctrl, int check_done, int zlo, int zhi);
 
+template <int TC>
+__global__ void zpass_tm2_kernel(float2* __restrict__ base, int rows, int sx, int HX, int nzs,
+                                 const float2* __restrict__ twg, const float4* __restrict__ kap4, int nx, int ny,
+                                 int nz, const Ctrl* ctrl, int check_done, int zlo, int zhi);
+
 // ---------------------------------------------------------------- launchers
 namespace {
 
@@ -242,6 +247,23 @@ cudaError_t go_z(const Launch<float>& L, float2* base, int rows, int sx, int HX,
                                    w.st[2], (float)scale, w.kap4, L.g.nx, L.g.ny, L.g.nz, L.ctrl, chk ? 1 : 0,
                                    box ? L.bz0 : 0, box ? L.bz1 : Lt);
   return cudaGetLastError();
+}
+
+// The two-buffer tensor-memory form of the padded z pass (256-point z transforms only).
+template <int TC> cudaError_t go_z_tm2(const Launch<float>& L, bool chk) {
+  constexpr int Lt = 256, CS = 16 * (16 * TC + kPad8);
+  const size_t smem = sizeof(float2) * (Lt + 2 * CS);
+  auto k = zpass_tm2_kernel<TC>;
+  allow_smem<zpass_tm2_kernel<TC>>();
+  const Geo& g = L.g;
+  if (2 * g.nz != Lt) return cudaErrorInvalidValue;
+  const int rows = 2 * g.ny, HX = g.nx + 1;
+  const int nfull = HX / TC, rem = HX - nfull * TC;
+  const dim3 grid(nfull * rows + (rows * rem + TC - 1) / TC, 1, 1);
+  const bool box = L.use_box;
+  k<<<grid, TC * 16, smem, L.st>>>(L.w->Pd, rows, g.sxp, HX, g.nz, L.w->twp[2], L.w->kap4, g.nx, g.ny, g.nz, L.ctrl,
+                                   chk ? 1 : 0, box ? L.bz0 : 0, box ? L.bz1 : Lt);
+  return checked_launch("zpass_tm2_kernel", grid, TC * 16, smem);
 }
 
 // Dispatch a length to its (R1, R2) split with R1 >= R2.
@@ -302,6 +324,7 @@ template <int R1, int R2> struct ZKern {
     const Geo& g = L.g;
     // the tensor-memory form of the own-slot product exists for the 16 x 16 split (L = 256)
     if constexpr (R1 == 16 && R2 == 16) {
+      if (L.w->sched.zk_tm == 2) return L.w->sched.zk_tc == 4 ? go_z_tm2<4>(L, chk) : go_z_tm2<8>(L, chk);
       if (L.w->sched.zk_tm) {
         if (L.w->sched.zk_tc == 4)
           return go_z<R1, R2, 4, 2>(L, L.w->Pd, 2 * g.ny, g.sxp, g.nx + 1, L.w->twp[2], 1.0, chk);
@@ -666,6 +689,19 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND >= 1) ? 4 : 1) zpas
     // X_q[k2 + R2 k1] back into those same slots without a barrier ("own slots"); the
     // last component's spectrum stays in registers.
     float2 w2[R1];
+    // This column's kernel spectrum K^(kx, fy, fz), fz = 0..nz (the fold of kz, which halves the
+    // reads), is copied with 16-byte cp.async into Ks[fz][c]: in component 2's buffer once every
+    // thread has read it (shared-memory spectra), or (tensor-memory spectra) in component 0's
+    // buffer, free once component 0's spectrum has gone to tensor memory, so that the copy runs
+    // during component 1's and 2's transforms.
+    float4* Ks = reinterpret_cast<float4*>(F + (TM ? 0 : 2) * CS);
+    static_assert(CS * sizeof(float2) >= (L / 2 + 1) * TC * sizeof(float4), "K^ fits a component's buffer");
+    auto copy_kernel_spectrum = [&] {
+      const int fy = (y <= ny) ? y : 2 * ny - y;
+      const size_t plane = (size_t)(ny + 1) * (nx + 1);
+      const float4* src = kap4 + (size_t)fy * (nx + 1) + (colok ? kx : 0);
+      for (int fz = n1; fz <= L / 2; fz += R1) cp_async16(Ks + fz * TC + c, src + fz * plane);
+    };
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       float2* Fq = F + q * CS;
@@ -676,6 +712,8 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND >= 1) ? 4 : 1) zpas
 #pragma unroll
       for (int k2 = 0; k2 < R2; ++k2) Fq[k2 * S2 + n1 * TC + c] = k2 == 0 ? v[0] : cmul(v[k2], twr[k2]);
       __syncthreads();
+      // (past this barrier every thread has moved component 0's spectrum to tensor memory)
+      if (TM && q == 1) copy_kernel_spectrum();
       if (n1 < R2) {
         float2 w[R1];
 #pragma unroll
@@ -694,19 +732,11 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND >= 1) ? 4 : 1) zpas
         }
       }
     }
-    // This column's kernel spectrum K^(kx, fy, fz), fz = 0..nz (the fold of kz, which halves
-    // the reads), is copied with 16-byte cp.async into Ks[fz][c], in component 2's buffer, free
-    // once every thread has read it.  Keeping K^ out of a buffer of its own (as when it was
-    // copied during the forward transforms) leaves 53 KB per CTA, so four CTAs fit per SM
-    // (128 registers): measured 5% faster.
-    float4* Ks = reinterpret_cast<float4*>(F + 2 * CS);
-    static_assert(CS * sizeof(float2) >= (L / 2 + 1) * TC * sizeof(float4), "K^ fits component 2's buffer");
-    __syncthreads();  // component 2's buffer read by all
-    {
-      const int fy = (y <= ny) ? y : 2 * ny - y;
-      const size_t plane = (size_t)(ny + 1) * (nx + 1);
-      const float4* src = kap4 + (size_t)fy * (nx + 1) + (colok ? kx : 0);
-      for (int fz = n1; fz <= L / 2; fz += R1) cp_async16(Ks + fz * TC + c, src + fz * plane);
+    // Keeping K^ out of a buffer of its own (as when it was copied during the forward transforms)
+    // leaves 53 KB per CTA, so four CTAs fit per SM (128 registers): measured 5% faster.
+    if constexpr (!TM) {
+      __syncthreads();  // component 2's buffer read by all
+      copy_kernel_spectrum();
     }
     cp_async_wait_all();
     __syncthreads();  // Ks complete and visible
@@ -905,6 +935,182 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND >= 1) ? 4 : 1) zpas
           if (!PR && (n1 + R1 * m2 < zlo || n1 + R1 * m2 >= zhi)) continue;
           col[q * cstride + (size_t)(n1 + R1 * m2) * zstride] = v[m2];
         }
+      }
+    }
+  }
+}
+
+// Padded z pass with the Biot-Savart kernel product, 256-point z transforms (16 x 16 split), in
+// a leaner form: the spectra of components 0 and 1 wait for the product in tensor memory (as in
+// KIND 2), so the transposes need only two shared-memory buffers (A, B) instead of three, and a
+// component's input is loaded while the previous component is transformed instead of all three
+// up front.  37 KB of shared memory and at most 96 registers per thread: five CTAs per SM (20
+// warps) instead of four.  The arithmetic of every point is that of zpass_reg2_kernel in the same
+// order, so the results are the same bits.
+//   forward:  component 0 through A, 1 through B, 2 through B (after one more barrier); K^ is
+//             copied into A while components 1 and 2 are transformed
+//   inverse:  component 2 through B, 0 through A, 1 through B
+template <int TC>
+__global__ void __launch_bounds__(TC * 16, 5)
+    zpass_tm2_kernel(float2* __restrict__ base, int rows, int sx, int HX, int nzs, const float2* __restrict__ twg,
+                     const float4* __restrict__ kap4, int nx, int ny, int nz, const Ctrl* ctrl, int check_done,
+                     int zlo, int zhi) {
+  constexpr int R = 16, L = R * R, NL = R / 2;
+  constexpr int S2 = R * TC + kPad8;  // transpose row stride (both directions: R1 = R2)
+  constexpr int CS = R * S2;          // one buffer
+  constexpr int NT = TC * R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (check_done && ctrl->done) return;
+  float2* tw = reinterpret_cast<float2*>(smem_raw);
+  float2* FA = tw + L;
+  float2* FB = FA + CS;
+  float4* Ks = reinterpret_cast<float4*>(FA);
+  static_assert(CS * sizeof(float2) >= (L / 2 + 1) * TC * sizeof(float4), "K^ fits buffer A");
+  static_assert(L % 2 == 0, "16-byte alignment of buffer A");
+  const int t = threadIdx.x;
+  for (int i = t; i < L; i += NT) tw[i] = twg[(i % R) * (i / R)];  // [j][n1]: W_L^{n1 j}
+  const int c = t % TC, n1 = t / TC;
+  // column map: TC consecutive kx of one row per CTA; the Nyquist columns kx = HX - 1 packed TC
+  // (row, kx) pairs to a CTA, and those CTAs first (as in zpass_reg2_kernel)
+  int y, kx;
+  bool colok;
+  {
+    const int nfull = HX / TC, rem = HX - nfull * TC;
+    const int ntail = (rows * rem + TC - 1) / TC;
+    const int b = blockIdx.x;
+    if (b >= ntail) {
+      y = (b - ntail) / nfull;
+      kx = (b - ntail - y * nfull) * TC + c;
+      colok = true;
+    } else {
+      const int e = b * TC + c;
+      colok = e < rows * rem;
+      y = colok ? e / rem : 0;
+      kx = colok ? nfull * TC + (e - y * rem) : 0;
+    }
+  }
+  const size_t zstride = (size_t)rows * sx;
+  const size_t cstride = (size_t)nzs * zstride;
+  float2* col = base + (size_t)y * sx + kx;
+  // 64 tensor-memory columns: component 0's 16 complex at columns 0-31, component 1's at 32-63
+  __shared__ unsigned tm_slot;
+  if (t < 32) tm_alloc(&tm_slot, 64u);
+  tm_fence_before();
+  __syncthreads();  // twiddles staged, tensor-memory address published
+  tm_fence_after();
+  const unsigned tmq = tm_slot + ((unsigned)(32 * ((t >> 5) & 3)) << 16);
+  const float2* twn = tw + n1;  // W_L^{n1 j} at twn[j * R] (table laid out [j][n1])
+
+  // input of one component: planes n1 + R n2 < L / 2, zero outside [zlo, zhi)
+  bool zin[NL];
+#pragma unroll
+  for (int n2 = 0; n2 < NL; ++n2) zin[n2] = colok && n1 + R * n2 >= zlo && n1 + R * n2 < zhi;
+  float2 nxt[NL];
+#pragma unroll
+  for (int n2 = 0; n2 < NL; ++n2)
+    nxt[n2] = zin[n2] ? col[(size_t)(n1 + R * n2) * zstride] : make_float2(0.f, 0.f);
+  float2 w2[R];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    float2 v[R];
+#pragma unroll
+    for (int n2 = 0; n2 < R; ++n2) v[n2] = n2 < NL ? nxt[n2] : make_float2(0.f, 0.f);
+    if (q < 2) {  // the next component's input, in flight during this component's transform
+#pragma unroll
+      for (int n2 = 0; n2 < NL; ++n2)
+        nxt[n2] = zin[n2] ? col[(q + 1) * cstride + (size_t)(n1 + R * n2) * zstride] : make_float2(0.f, 0.f);
+    }
+    dft_maybe_half<R, false, true>(v);
+    float2* Fq = q == 0 ? FA : FB;
+    if (q == 2) __syncthreads();  // every thread has read component 1's transpose out of B
+#pragma unroll
+    for (int k2 = 0; k2 < R; ++k2) Fq[k2 * S2 + n1 * TC + c] = k2 == 0 ? v[0] : cmul(v[k2], twn[k2 * R]);
+    __syncthreads();
+    if (q == 1) {
+      // component 0's transpose has been read out of A by every thread: copy this column's
+      // kernel spectrum K^(kx, fy, fz), fz = 0..L/2 (kz folded), into A with 16-byte cp.async
+      const int fy = (y <= ny) ? y : 2 * ny - y;
+      const size_t plane = (size_t)(ny + 1) * (nx + 1);
+      const float4* src = kap4 + (size_t)fy * (nx + 1) + (colok ? kx : 0);
+      for (int fz = n1; fz <= L / 2; fz += R) cp_async16(Ks + fz * TC + c, src + fz * plane);
+    }
+    float2 w[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) w[m] = Fq[n1 * S2 + m * TC + c];
+    DFT<R, false, float2>::run(w);
+    if (q < 2) {
+      tm_st16(tmq + 32u * q, w);
+    } else {
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) w2[k1] = w[k1];
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();  // K^ complete and visible
+  // ---- product at kz = k2 + R k1 (k2 = n1) on the thread's own points: components 0 and 1 from
+  // tensor memory, component 2 in registers; K^ is odd in ky (component y) and in kz (component z)
+  // about the fold
+  {
+    const int k2 = n1;
+    const float syg = (y <= ny) ? 1.f : -1.f;
+#pragma unroll
+    for (int b = 0; b < R / 4; ++b) {
+      float2 g0[4], g1[4];
+      tm_ld4x2(tmq + 8u * b, g0, tmq + 32u + 8u * b, g1);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k1 = 4 * b + i;
+        const int kz = k2 + R * k1;
+        const int fz = (kz <= L / 2) ? kz : L - kz;
+        const float4 K = Ks[fz * TC + c];
+        const float ax = K.x, ay = syg * K.y, az = (kz <= L / 2) ? K.z : -K.z;
+        const float2 G0 = g0[i], G1 = g1[i], G2 = w2[k1];
+        const float2 cx = make_float2(ay * G2.x - az * G1.x, ay * G2.y - az * G1.y);
+        const float2 cy = make_float2(az * G0.x - ax * G2.x, az * G0.y - ax * G2.y);
+        const float2 cz = make_float2(ax * G1.x - ay * G0.x, ax * G1.y - ay * G0.y);
+        g0[i] = make_float2(-cx.y, cx.x);
+        g1[i] = make_float2(-cy.y, cy.x);
+        w2[k1] = make_float2(-cz.y, cz.x);
+      }
+      tm_st4x2(tmq + 8u * b, g0, tmq + 32u + 8u * b, g1);
+    }
+  }
+  // ---- inverse: y[m1 + R m2] = sum_k2 W_R^{-m2 k2} W_L^{-m1 k2} (sum_k1 X[k2 + R k1] W_R^{-m1 k1}),
+  // the outputs m2 < R/2 (planes below L/2) only
+  // components in the order 2 (through B), 0 (through A), 1 (through B); stage A' of one
+  // component and stage B' of the previous one share a barrier interval
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (s > 0) {  // stage B' of the component of step s - 1
+      const int q = s == 1 ? 2 : (s == 2 ? 0 : 1);
+      const float2* Fb = s == 2 ? FA : FB;
+      float2 v[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) v[j] = Fb[n1 * S2 + j * TC + c];
+      DFT<R, true, float2>::run(v);
+      if (colok) {
+#pragma unroll
+        for (int m2 = 0; m2 < R / 2; ++m2) col[q * cstride + (size_t)(n1 + R * m2) * zstride] = v[m2];
+      }
+    }
+    if (s < 3) {  // stage A' of component 2, 0, 1
+      float2* Fb = s == 1 ? FA : FB;
+      float2 wr[R];
+      if (s == 0) {
+#pragma unroll
+        for (int k1 = 0; k1 < R; ++k1) wr[k1] = w2[k1];
+      } else {
+        tm_ld16(tmq + 32u * (s - 1), wr);
+      }
+      DFT<R, true, float2>::run(wr);
+#pragma unroll
+      for (int m1 = 0; m1 < R; ++m1) Fb[m1 * S2 + n1 * TC + c] = m1 == 0 ? wr[0] : cmulc(wr[m1], twn[m1 * R]);
+      if (s == 2) tm_fence_before();  // the last tensor-memory access of every thread
+      // s = 0: every thread is past the product (A is free); s = 1: B has been read by all
+      __syncthreads();
+      if (s == 2 && t < 32) {
+        tm_fence_after();
+        tm_dealloc(tm_slot, 64u);
       }
     }
   }

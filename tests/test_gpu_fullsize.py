@@ -74,13 +74,14 @@ def _check3(name, a, b):
 def test_rhs_fp32_lens128_fixed_iterations_matches_oracle(lens):
     """Five Eq. 5 iterations, no early stop: every pass of the right-hand side at
     the benchmark's grid against the oracle's same five iterations, with the padded z
-    pass keeping its spectra in shared memory and in tensor memory, and with the three
+    pass keeping its spectra in shared memory and in tensor memory (three or two transpose
+    buffers), and with the three
     passes on Omega's box as three launches and as one fused launch (the same bits)."""
     cfg, prob, h, g0, ref = lens
     assert ref.iters == ITERS
     ctx = _ctx(cfg, 0.0, ITERS)
     got = []
-    for tm, bf in ((0, 0), (1, 0), (0, 1), (1, 1)):
+    for tm, bf in ((0, 0), (1, 0), (2, 0), (0, 1), (2, 1)):
         ctx.set_schedule(z_kernel_tmem=tm, box_fused=bf)
         out = torch.empty(h.size, dtype=torch.float64, device="cuda")
         it = ctx.rhs(T, _dev(h), _dev(g0), out)
@@ -91,7 +92,7 @@ def test_rhs_fp32_lens128_fixed_iterations_matches_oracle(lens):
     assert all(np.array_equal(got[0], g) for g in got[1:])
 
 
-@pytest.mark.parametrize("tm,bf", [(0, 0), (1, 0), (0, 1)])
+@pytest.mark.parametrize("tm,bf", [(0, 0), (1, 0), (2, 0), (0, 1)])
 def test_rhs_fp32_lens128_graph_loop_stops_with_the_oracle(lens, tm, bf):
     """The Eq. 5 loop as the benchmark runs it (one CUDA graph, the stop decided on
     the device), with the stop threshold set between the oracle's residuals after
