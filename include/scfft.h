@@ -140,8 +140,8 @@ scfft_status scfft_set_curl(scfft_ctx* ctx, int kind);
  *                    spectra of two components between the forward transforms, the product and
  *                    the inverse transforms in tensor memory, 0 = in shared memory; 2 = tensor
  *                    memory as in 1 with two shared-memory transpose buffers instead of three and
- *                    at most 96 registers per thread (five CTAs per SM instead of four); 0 on
- *                    other grids
+ *                    at most 96 registers per thread (five CTAs per SM instead of four), the
+ *                    default where it exists; 0 on other grids
  *   box_fused        Eq. 5 iteration with the spectral curl: 1 = the curl's inverse y pass, the
  *                    mask/pad x pass and the padded forward y pass, which see only Omega's
  *                    bounding box, run as one launch with one CTA per (component, plane of the
@@ -150,7 +150,7 @@ scfft_status scfft_set_curl(scfft_ctx* ctx, int kind);
  *                    otherwise)
  *   us               scfft_autotune only: mean time (microseconds) of the candidates in the order
  *                    z_kernel 8, 4; z_curl 8, 16; y_unpadded 8, 16 (forward + inverse);
- *                    y_padded TMA, plain (forward + inverse); z_kernel_tmem 0, 1, 2; box_fused 0,
+ *                    y_padded TMA, plain (forward + inverse); z_kernel_tmem 2, 1, 0; box_fused 0,
  *                    1 (the three passes, the fused pass); 0 where not timed. */
 typedef struct {
   int z_kernel_tile;

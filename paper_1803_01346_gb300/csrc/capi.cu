@@ -1676,6 +1676,9 @@ scfft_status scfft_create(const scfft_grid* grid, const scfft_material* mat, con
   c->mat = *mat;
   c->opt = *opt;
   c->st = (cudaStream_t)stream;
+  // default schedule: the two-buffer tensor-memory z pass where it exists (a 256-point padded z
+  // transform), measured the fastest of the three forms
+  if (2 * c->g.nz == 256) c->wf.sched.zk_tm = 2;
   scfft_status s = SCFFT_OK;
   if (cudaMalloc(&c->ctrl, sizeof(Ctrl)) != cudaSuccess || cudaMalloc(&c->ppd, sizeof(PointParams)) != cudaSuccess ||
       cudaMalloc(&c->partials, sizeof(double) * (c->g.ny * c->g.nz / 2 + 8)) != cudaSuccess ||
@@ -1874,10 +1877,10 @@ scfft_status autotune_f32(scfft_ctx* c, double us[13]) {
   auto pick = [&](int* knob, const int cand[2], double* t, auto launch) -> scfft_status {
     return pick_n(knob, cand, 2, t, launch);
   };
-  const int zk[2] = {8, 4}, zc[2] = {8, 16}, yu[2] = {8, 16}, yp[2] = {1, 0}, zm[3] = {0, 1, 2};
+  const int zk[2] = {8, 4}, zc[2] = {8, 16}, yu[2] = {8, 16}, yp[2] = {1, 0}, zm[3] = {2, 1, 0};
   // the padded z pass as the Eq. 5 iteration runs it: input planes of Omega's box only
   const Launch<float> LZ = boxed(L);
-  s.zk_tm = 0;
+  s.zk_tm = tmem_z_ok(c) ? 2 : 0;
   CS_(pick(&s.zk_tc, zk, us + 0, [&] { return launch_z_kernel<float>(LZ, false); }));
   if (tmem_z_ok(c)) CS_(pick_n(&s.zk_tm, zm, 3, us + 8, [&] { return launch_z_kernel<float>(LZ, false); }));
   CS_(pick(&s.zc_tc, zc, us + 2, [&] { return launch_z_curl<float>(L, false, inv_n); }));

@@ -1039,7 +1039,7 @@ __global__ void __launch_bounds__(TC * 16, 5)
     for (int m = 0; m < R; ++m) w[m] = Fq[n1 * S2 + m * TC + c];
     DFT<R, false, float2>::run(w);
     if (q < 2) {
-      tm_st16(tmq + 32u * q, w);
+      tm_st16(tmq + 32u * (unsigned)q, w);
     } else {
 #pragma unroll
       for (int k1 = 0; k1 < R; ++k1) w2[k1] = w[k1];
@@ -1078,10 +1078,18 @@ __global__ void __launch_bounds__(TC * 16, 5)
   // ---- inverse: y[m1 + R m2] = sum_k2 W_R^{-m2 k2} W_L^{-m1 k2} (sum_k1 X[k2 + R k1] W_R^{-m1 k1}),
   // the outputs m2 < R/2 (planes below L/2) only
   // components in the order 2 (through B), 0 (through A), 1 (through B); stage A' of one
-  // component and stage B' of the previous one share a barrier interval
+  // component and stage B' of the previous one share a barrier interval.  Stage A' of component
+  // 2 (from registers) comes first; the rest is a loop left rolled (less code: instruction-cache
+  // misses stalled the unrolled form), the same arithmetic.
+  {
+    DFT<R, true, float2>::run(w2);
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    if (s > 0) {  // stage B' of the component of step s - 1
+    for (int m1 = 0; m1 < R; ++m1) FB[m1 * S2 + n1 * TC + c] = m1 == 0 ? w2[0] : cmulc(w2[m1], twn[m1 * R]);
+  }
+  __syncthreads();  // (also: every thread is past the product, so A is free)
+#pragma unroll 1
+  for (int s = 1; s < 4; ++s) {
+    {  // stage B' of the component of step s - 1
       const int q = s == 1 ? 2 : (s == 2 ? 0 : 1);
       const float2* Fb = s == 2 ? FA : FB;
       float2 v[R];
@@ -1093,21 +1101,15 @@ __global__ void __launch_bounds__(TC * 16, 5)
         for (int m2 = 0; m2 < R / 2; ++m2) col[q * cstride + (size_t)(n1 + R * m2) * zstride] = v[m2];
       }
     }
-    if (s < 3) {  // stage A' of component 2, 0, 1
+    if (s < 3) {  // stage A' of component 0 (through A), then 1 (through B)
       float2* Fb = s == 1 ? FA : FB;
       float2 wr[R];
-      if (s == 0) {
-#pragma unroll
-        for (int k1 = 0; k1 < R; ++k1) wr[k1] = w2[k1];
-      } else {
-        tm_ld16(tmq + 32u * (s - 1), wr);
-      }
+      tm_ld16(tmq + 32u * (unsigned)(s - 1), wr);
       DFT<R, true, float2>::run(wr);
 #pragma unroll
       for (int m1 = 0; m1 < R; ++m1) Fb[m1 * S2 + n1 * TC + c] = m1 == 0 ? wr[0] : cmulc(wr[m1], twn[m1 * R]);
       if (s == 2) tm_fence_before();  // the last tensor-memory access of every thread
-      // s = 0: every thread is past the product (A is free); s = 1: B has been read by all
-      __syncthreads();
+      __syncthreads();  // s = 1: B has been read by all
       if (s == 2 && t < 32) {
         tm_fence_after();
         tm_dealloc(tm_slot, 64u);
