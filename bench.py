@@ -50,8 +50,8 @@ T_START = 0.3  # start of the timed steps on the lens ramp (h_e reaches 0.8 at t
 AUTOTUNE = True  # --no-autotune: keep the default launch schedule (profiling runs: under ncu the
                  # tuner's own timings are distorted and may pick another schedule)
 # DRAM bytes (read + write) per launch from the committed ncu capture
-# profiles/ncu_zpass_xupdate_lens128_fp32.md; an entry is removed when its kernel changes.
-NCU_TRAFFIC = {"z_kernel": 86282240 + 57672704}
+# profiles/ncu_zpass_tm2_lens128_fp32.md; an entry is removed when its kernel changes.
+NCU_TRAFFIC = {"z_kernel": 87209216 + 58943744}
 
 
 def _peaks():
