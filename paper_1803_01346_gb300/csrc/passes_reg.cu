@@ -951,7 +951,7 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND >= 1) ? 4 : 1) zpas
 //             copied into A while components 1 and 2 are transformed
 //   inverse:  component 2 through B, 0 through A, 1 through B
 template <int TC>
-__global__ void __launch_bounds__(TC * 16, 5)
+__global__ void __launch_bounds__(TC * 16, 6)
     zpass_tm2_kernel(float2* __restrict__ base, int rows, int sx, int HX, int nzs, const float2* __restrict__ twg,
                      const float4* __restrict__ kap4, int nx, int ny, int nz, const Ctrl* ctrl, int check_done,
                      int zlo, int zhi) {
