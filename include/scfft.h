@@ -140,7 +140,7 @@ scfft_status scfft_set_curl(scfft_ctx* ctx, int kind);
  *                    spectra of two components between the forward transforms, the product and
  *                    the inverse transforms in tensor memory, 0 = in shared memory; 2 = tensor
  *                    memory as in 1 with two shared-memory transpose buffers instead of three and
- *                    at most 96 registers per thread (five CTAs per SM instead of four), the
+ *                    at most 80 registers per thread (six CTAs per SM instead of four), the
  *                    default where it exists; 0 on other grids
  *   box_fused        Eq. 5 iteration with the spectral curl: 1 = the curl's inverse y pass, the
  *                    mask/pad x pass and the padded forward y pass, which see only Omega's

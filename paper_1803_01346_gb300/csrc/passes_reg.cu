@@ -944,7 +944,7 @@ __global__ void __launch_bounds__(TC * R1, (R1 == R2 && KIND >= 1) ? 4 : 1) zpas
 // a leaner form: the spectra of components 0 and 1 wait for the product in tensor memory (as in
 // KIND 2), so the transposes need only two shared-memory buffers (A, B) instead of three, and a
 // component's input is loaded while the previous component is transformed instead of all three
-// up front.  37 KB of shared memory and at most 96 registers per thread: five CTAs per SM (20
+// up front.  37 KB of shared memory and at most 80 registers per thread: six CTAs per SM (24
 // warps) instead of four.  The arithmetic of every point is that of zpass_reg2_kernel in the same
 // order, so the results are the same bits.
 //   forward:  component 0 through A, 1 through B, 2 through B (after one more barrier); K^ is
