@@ -342,7 +342,8 @@ def bench_batch(S, torch, steps: int, warmup: int):
             "sequential_instance_steps_per_s": len(inst) * steps / seq, "speedup_vs_sequential": seq / el,
             "iters_per_rhs": its / max(1, rcs),
             "schedules": {str(k): {kk: v[kk] for kk in ("z_kernel_tile", "z_curl_tile", "y_unpadded_tile",
-                                                         "y_padded_tma", "z_kernel_tmem", "box_fused")}
+                                                         "y_padded_tma", "z_kernel_tmem", "box_fused",
+                                                         "x_update_split")}
                           for k, v in sorted(schedules.items())},
             "timing": "wall clock around synchronous batch calls, device synchronised on both sides"}
 

@@ -131,7 +131,7 @@ scfft_status scfft_set_curl(scfft_ctx* ctx, int kind);
 /* Launch schedule of the FP32 passes that carry the transforms of Eqs. 3-7: how the spectral
  * columns are tiled over CTAs and whether the padded y passes load through TMA.  A schedule
  * never changes the arithmetic of a column: every schedule gives the same results bit for
- * bit, only their speed differs by grid size.
+ * bit (x_update_split: see there), only their speed differs by grid size.
  *   z_kernel_tile    padded z pass with the Biot-Savart kernel product (Eq. 7): 4 or 8 columns
  *   z_curl_tile      z pass of the smoothed curl (Eq. 4): 8 or 16 columns
  *   y_unpadded_tile  y passes on the unpadded grid: 8 or 16 columns
@@ -148,10 +148,16 @@ scfft_status scfft_set_curl(scfft_ctx* ctx, int kind);
  *                    box) and their intermediates in shared memory; 0 = three launches.  Applies
  *                    where nx = ny and the box's rows fit shared memory (the three passes run
  *                    otherwise)
+ *   x_update_split   Eq. 5 update pass: 1 = the three components' transforms side by side in
+ *                    three warp groups of a CTA (their input rows in flight at once), 0 = one
+ *                    component after another.  The iterate and dh/dt are the same bits; the
+ *                    residual's per-thread partial sums cover other nodes, so its last bits (and,
+ *                    on an exact tie with the stop threshold, the iteration count) may differ
  *   us               scfft_autotune only: mean time (microseconds) of the candidates in the order
  *                    z_kernel 8, 4; z_curl 8, 16; y_unpadded 8, 16 (forward + inverse);
  *                    y_padded TMA, plain (forward + inverse); z_kernel_tmem 2, 1, 0; box_fused 0,
- *                    1 (the three passes, the fused pass); 0 where not timed. */
+ *                    1 (the three passes, the fused pass); x_update_split 0, 1; 0 where not
+ *                    timed. */
 typedef struct {
   int z_kernel_tile;
   int z_curl_tile;
@@ -159,7 +165,8 @@ typedef struct {
   int y_padded_tma;
   int z_kernel_tmem;
   int box_fused;
-  double us[13];
+  int x_update_split;
+  double us[15];
 } scfft_schedule;
 
 /* Autotuner of the schedule: times each candidate of each knob on the context's own workspace

@@ -85,7 +85,7 @@ class _EjLaw(ctypes.Structure):
 class _Schedule(ctypes.Structure):
     _fields_ = [("z_kernel_tile", ctypes.c_int), ("z_curl_tile", ctypes.c_int), ("y_unpadded_tile", ctypes.c_int),
                 ("y_padded_tma", ctypes.c_int), ("z_kernel_tmem", ctypes.c_int), ("box_fused", ctypes.c_int),
-                ("us", ctypes.c_double * 13)]
+                ("x_update_split", ctypes.c_int), ("us", ctypes.c_double * 15)]
 
 
 class _Stats(ctypes.Structure):
@@ -245,7 +245,8 @@ class Context:
         """CURL_SPECTRAL (§2) or CURL_FD (central differences) for the curls of the rhs."""
         self._check(self._lib.scfft_set_curl(self._h, int(kind)), "scfft_set_curl")
 
-    _SCHED_KEYS = ("z_kernel_tile", "z_curl_tile", "y_unpadded_tile", "y_padded_tma", "z_kernel_tmem", "box_fused")
+    _SCHED_KEYS = ("z_kernel_tile", "z_curl_tile", "y_unpadded_tile", "y_padded_tma", "z_kernel_tmem", "box_fused",
+                  "x_update_split")
 
     def autotune(self, retune: bool = False):
         """Time the launch schedules of the FP32 passes on this context's grid and keep the

@@ -1815,12 +1815,14 @@ void to_public(const Sched& s, scfft_schedule* o) {
   o->y_padded_tma = s.yp_tma;
   o->z_kernel_tmem = s.zk_tm;
   o->box_fused = s.box_fused;
+  o->x_update_split = s.xu3;
 }
 
 bool sched_ok(const scfft_schedule* s) {
   return (s->z_kernel_tile == 4 || s->z_kernel_tile == 8) && (s->z_curl_tile == 8 || s->z_curl_tile == 16) &&
          (s->y_unpadded_tile == 8 || s->y_unpadded_tile == 16) && (s->y_padded_tma == 0 || s->y_padded_tma == 1) &&
-         (s->z_kernel_tmem >= 0 && s->z_kernel_tmem <= 2) && (s->box_fused == 0 || s->box_fused == 1);
+         (s->z_kernel_tmem >= 0 && s->z_kernel_tmem <= 2) && (s->box_fused == 0 || s->box_fused == 1) &&
+         (s->x_update_split == 0 || s->x_update_split == 1);
 }
 
 // the tensor-memory form of the padded z pass exists for its 16 x 16 split (a 256-point z transform)
@@ -1857,7 +1859,7 @@ template <typename F> scfft_status time_us(scfft_ctx* c, F&& f, double* us) {
 // passes transform its scratch spectra in place; their contents are not used afterwards) and
 // keep the fastest (the second candidate only when it is faster by more than 3%, so that timing
 // noise does not flip a choice); knobs act on different passes, so they are tuned one at a time.
-scfft_status autotune_f32(scfft_ctx* c, double us[13]) {
+scfft_status autotune_f32(scfft_ctx* c, double us[15]) {
   Launch<float> L = launch_of<float>(c);
   L.fault = nullptr;
   Sched& s = c->wf.sched;
@@ -1896,6 +1898,22 @@ scfft_status autotune_f32(scfft_ctx* c, double us[13]) {
   } else {
     s.yp_tma = 0;
   }
+  // the Eq. 5 update pass, components one after another or side by side; the pass advances the
+  // device's iteration state, which is put back afterwards (its iterate and spectrum outputs
+  // are scratch)
+  {
+    Ctrl saved;
+    CK(cudaMemcpyAsync(&saved, c->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    const int xs[2] = {0, 1};
+    PointParams pu = base_params(c);
+    const scfft_status ts = pick(&s.xu3, xs, us + 13, [&] {
+      return launch_x<float>(L, X_UPDATE, pu, nullptr, nullptr, nullptr, 0, 1, false);
+    });
+    CK(cudaMemcpyAsync(c->ctrl, &saved, sizeof(Ctrl), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    CS_(ts);
+  }
   // the three passes on Omega's box against the fused pass (after the y passes' own choice)
   const Launch<float> LB = boxed(L);
   s.box_fused = 0;
@@ -1932,11 +1950,11 @@ scfft_status scfft_autotune(scfft_ctx* c, int retune, scfft_schedule* out) {
   if (it != g_tune_cache.end() && !retune) {
     c->wf.sched = it->second;
   } else {
-    double us[13] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double us[15] = {0};
     CS_(autotune_f32(c, us));
     g_tune_cache[key] = c->wf.sched;
     if (out)
-      for (int i = 0; i < 13; ++i) out->us[i] = us[i];
+      for (int i = 0; i < 15; ++i) out->us[i] = us[i];
   }
   drop_loop_graph(c);
   if (out) to_public(c->wf.sched, out);
@@ -1962,6 +1980,7 @@ scfft_status scfft_set_schedule(scfft_ctx* c, const scfft_schedule* s) {
   c->wf.sched.yu_tc = s->y_unpadded_tile;
   c->wf.sched.yp_tma = s->y_padded_tma;
   c->wf.sched.box_fused = s->box_fused;
+  c->wf.sched.xu3 = s->x_update_split;
   drop_loop_graph(c);
   return SCFFT_OK;
 }

@@ -462,6 +462,8 @@ __device__ __forceinline__ void law_factors(float jx, float jy, float jz, bool i
 
 template <int MODE, int R1i, int R2i, int R2o, int P>
 __global__ void xpass_reg2_kernel(const XRArgs a);
+template <int R1i, int R2i, int R2o, int P>
+__global__ void xupdate3_kernel(const XRArgs a);
 
 namespace {
 
@@ -491,11 +493,36 @@ cudaError_t go_x(const XRArgs& a, cudaStream_t st) {
   return checked_launch("xpass_reg2_kernel", dim3(grid), kPairs * S::TP, smem);
 }
 
+constexpr int kPairs3 = 8;  // row pairs per tile of the three-group update pass (x 3 components; 4 measured slower)
+
+template <int R1i, int R2i, int R2o>
+cudaError_t go_xu3(const XRArgs& a, cudaStream_t st) {
+  typedef XS<X_UPDATE, R1i, R2i, R2o> S;
+  constexpr int XL = S::Li / 2;
+  constexpr int TT = cmax(cmax(R2i * (R1i + 1), R2o * (S::R1o + 1)), S::Lo);
+  constexpr int NT = 3 * kPairs3 * S::TP;
+  const size_t smem = sizeof(float2) * (S::Li + S::Lo + 3 * kPairs3 * XL + 3 * kPairs3 * TT);
+  auto k = xupdate3_kernel<R1i, R2i, R2o, kPairs3>;
+  allow_smem<xupdate3_kernel<R1i, R2i, R2o, kPairs3>>();
+  const int ntiles = (pair_count(a) + kPairs3 - 1) / kPairs3;
+  static const int resident = [&] {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, NT, smem);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return per_sm > 0 && sms > 0 ? per_sm * sms : 1024;
+  }();
+  const int grid = ntiles < resident ? ntiles : resident;
+  k<<<grid, NT, smem, st>>>(a);
+  return checked_launch("xupdate3_kernel", dim3(grid), NT, smem);
+}
+
 // Splits per unpadded length n: C2R(n) = (a, b), C2R(2n) = (c, d); the R2C
 // splits follow from R1o = R2i (see the section comment).
-template <int MODE> cudaError_t go_x_n(int n, const XRArgs& a, cudaStream_t st) {
+template <int MODE> cudaError_t go_x_n(int n, const XRArgs& a, cudaStream_t st, bool split3 = false) {
 #define XN(NN, A_, B_, C_, D_)                                                                   \
   case NN:                                                                                       \
+    if constexpr (MODE == X_UPDATE) if (split3) return go_xu3<C_, D_, C_ / 2>(a, st);            \
     if constexpr (MODE == X_FWD_F64) return go_x<MODE, 1, B_, A_>(a, st);                        \
     else if constexpr (MODE == X_PAD_F64) return go_x<MODE, 1, B_, 2 * A_>(a, st);               \
     else if constexpr (MODE == X_POWERLAW || MODE == X_POWERLAW_H || MODE == X_ASSEMBLE) return go_x<MODE, A_, B_, A_>(a, st); \
@@ -569,7 +596,7 @@ cudaError_t launch_x_reg_io(const Launch<float>& L, XMode mode, const PointParam
     case X_POWERLAW_H: return go_x_n<X_POWERLAW_H>(g.nx, a, L.st);
     case X_ASSEMBLE: return go_x_n<X_ASSEMBLE>(g.nx, a, L.st);
     case X_MASKPAD: return go_x_n<X_MASKPAD>(g.nx, a, L.st);
-    case X_UPDATE: return go_x_n<X_UPDATE>(g.nx, a, L.st);
+    case X_UPDATE: return go_x_n<X_UPDATE>(g.nx, a, L.st, L.w->sched.xu3 != 0);
     case X_UPDATE_FD: return go_x_n<X_UPDATE_FD>(g.nx, a, L.st);
     case X_TO_F64: return go_x_n<X_TO_F64>(g.nx, a, L.st);
     case X_PAD_F64: return go_x_n<X_PAD_F64>(g.nx, a, L.st);
@@ -1118,6 +1145,50 @@ __global__ void __launch_bounds__(TC * 16, 6)
   }
 }
 
+// End of an Eq. 5 update pass: the CTA's residual sum (part, per thread) to partials[block];
+// the last CTA adds the partials in block order (deterministic), sets the residual, the
+// iteration count and the stop flag, and resets the arrival counter.
+__device__ __forceinline__ void residual_finish(const XRArgs& a, double part, int it, int NT) {
+  const int tid = threadIdx.x;
+  __shared__ double red[32];
+  __shared__ int am_last;
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((tid & 31) == 0) red[tid >> 5] = part;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (NT + 31) / 32; ++i) s += red[i];
+    a.partials[blockIdx.x] = s;
+    __threadfence();
+    const unsigned prev = atomicAdd(&a.ctrl->counter, 1u);
+    am_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (am_last) {
+    __threadfence();
+    double s = 0.0;
+    for (int i = tid; i < (int)gridDim.x; i += NT) s += __ldcg(&a.partials[i]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if ((tid & 31) == 0) red[tid >> 5] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int i = 0; i < (NT + 31) / 32; ++i) tot += red[i];
+      const double rres = tot * a.ppd->inv_nout;
+      Ctrl* c = a.ctrl;
+      c->residual = rres;
+      c->iters = it + 1;
+      c->iter_total += 1;
+      c->cur = (it + 1) & 1;
+      const bool finite = isfinite(rres);
+      if (!finite) c->status = 6;  // SCFFT_ENONFINITE
+      c->done = (!finite || rres < a.ppd->tol) ? 1 : 0;
+      c->counter = 0;
+    }
+  }
+}
+
 // x pass, one component at a time; the node-wise step reads the three
 // components' real rows from shared memory RS[q][p][x] (complex = rows a, b).
 // At most 128 registers (four CTAs per SM): the batched node-wise loads would otherwise
@@ -1484,46 +1555,7 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
     __syncwarp();  // the pair's shared buffers are reused by the next tile
   }
 
-  if (UPD) {
-    double part = (double)partf;
-    __shared__ double red[32];
-    __shared__ int am_last;
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((tid & 31) == 0) red[tid >> 5] = part;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int i = 0; i < (NT + 31) / 32; ++i) s += red[i];
-      a.partials[blockIdx.x] = s;
-      __threadfence();
-      const unsigned prev = atomicAdd(&a.ctrl->counter, 1u);
-      am_last = (prev == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (am_last) {
-      __threadfence();
-      double s = 0.0;
-      for (int i = tid; i < (int)gridDim.x; i += NT) s += __ldcg(&a.partials[i]);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      __syncthreads();
-      if ((tid & 31) == 0) red[tid >> 5] = s;
-      __syncthreads();
-      if (tid == 0) {
-        double tot = 0.0;
-        for (int i = 0; i < (NT + 31) / 32; ++i) tot += red[i];
-        const double rres = tot * a.ppd->inv_nout;
-        Ctrl* c = a.ctrl;
-        c->residual = rres;
-        c->iters = it + 1;
-        c->iter_total += 1;
-        c->cur = (it + 1) & 1;
-        const bool finite = isfinite(rres);
-        if (!finite) c->status = 6;  // SCFFT_ENONFINITE
-        c->done = (!finite || rres < a.ppd->tol) ? 1 : 0;
-        c->counter = 0;
-      }
-    }
-  }
+  if (UPD) residual_finish(a, (double)partf, it, NT);
   if (MODE == X_ASSEMBLE && blockIdx.x == 0 && tid == 0) {
     *a.ppd = a.pps ? *a.pps : a.pp;
     a.ctrl->trips = 0;
@@ -1533,6 +1565,221 @@ __global__ void __launch_bounds__(P * XS<MODE, R1i, R2i, R2o>::TP, 4)
     a.ctrl->counter = 0;
     a.ctrl->residual = 0.0;
   }
+}
+
+
+// Eq. 5 update pass with the three components side by side: a CTA of three warp groups, group
+// g running component g's C2R (length 2nx, crop) and R2C (length nx) for a tile of P row pairs,
+// so that the three components' input rows are in flight at once (the one-component-at-a-time
+// pass waits for them one after another); the node-wise step between the transforms, which
+// needs all three components of a node, runs on all groups over shared memory (group g takes
+// the nodes x = r + TP j, j = g mod 3, of its lane r).  Every element's arithmetic is that of
+// xpass_reg2_kernel<X_UPDATE> in the same order, so the iterate and the transforms are the same
+// bits; the residual's per-thread FP32 sums cover other nodes, so its last bits may differ.
+template <int R1i, int R2i, int R2o, int P>
+__global__ void __launch_bounds__(3 * P * XS<X_UPDATE, R1i, R2i, R2o>::TP, 16 / P) xupdate3_kernel(const XRArgs a) {
+  typedef XS<X_UPDATE, R1i, R2i, R2o> S;
+  constexpr int TP = S::TP, R1o = S::R1o, Li = S::Li, Lo = S::Lo;
+  constexpr int NG = P * TP;    // threads of a group
+  constexpr int NT = 3 * NG;
+  constexpr int XL = Li / 2;    // nx
+  constexpr int TT = cmax(cmax(R2i * (R1i + 1), R2o * (R1o + 1)), Lo);
+  constexpr int J = XL / TP;    // node pairs of a lane
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (a.check_done && a.ctrl->done) return;
+  const int it = *reinterpret_cast<volatile const int*>(&a.ctrl->iters);
+  const float* h_old = a.hbuf[it & 1];
+  float* h_new = a.hbuf[(it + 1) & 1];
+  float hef[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) hef[q] = (float)a.ppd->hedot[q];
+  float2* twi = reinterpret_cast<float2*>(smem_raw);
+  float2* two = twi + Li;
+  float2* RS = two + Lo;         // [3][P][XL]
+  float2* T = RS + 3 * P * XL;   // [3][P][TT]
+  const int tid = threadIdx.x;
+  const int g = tid / NG, lt = tid - g * NG;
+  const int p = lt / TP, r = lt % TP;
+  for (int i = tid; i < Li; i += NT) twi[i] = a.tw_in[(i % R1i) * (i / R1i)];
+  for (int i = tid; i < Lo; i += NT) two[i] = a.tw_out[(i % R1o) * (i / R1o)];
+  const int ny = a.g.ny, nz = a.g.nz;
+  const long long N = a.g.N;
+  const int npairs = pair_count(a);
+  const int ntiles = (npairs + P - 1) / P;
+  float partf = 0.f;
+  static_assert(XL % TP == 0 && 32 % TP == 0 && NG % 32 == 0, "a pair's lanes in one warp, groups of whole warps");
+  __syncthreads();  // twiddle tables
+  float2* Tp = T + (g * P + p) * TT;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // L2 prefetch of the next tile's input rows (all three components) and of this tile's
+    // node-wise rows (previous iterate, mask), which are read after the transforms
+    {
+      const int lines = ((Li / 2 + 1) * 8 + 127) / 128;
+      if (tile + (int)gridDim.x < ntiles) {
+        const int nrow0 = 2 * (tile + (int)gridDim.x) * P;
+        for (int i = tid; i < 3 * 2 * P * lines; i += NT) {
+          const int ln = i % lines, rr = (i / lines) % (2 * P), q = i / (lines * 2 * P);
+          const int qrow = nrow0 + rr;
+          if (qrow < 2 * npairs) {
+            int zz, yy;
+            pair_rows(a, qrow >> 1, zz, yy);
+            yy += qrow & 1;
+            prefetch_l2(a.spec_in + ((size_t)(q * nz + zz) * a.in_rows + yy) * a.in_sx + ln * 16);
+          }
+        }
+      }
+      const int row0 = 2 * tile * P, nrow = 2 * P;
+      const size_t nb0 = (size_t)row0 * XL;
+      const int rl = (XL * 4 + 127) / 128;
+      for (int i = tid; i < 3 * nrow * rl; i += NT) {
+        const int ln = i % rl, rr = (i / rl) % nrow, q = i / (rl * nrow);
+        if (row0 + rr < 2 * npairs) prefetch_l2(h_old + q * N + nb0 + (size_t)rr * XL + ln * 32);
+      }
+      for (int i = tid * 128; i < nrow * XL; i += NT * 128)
+        if (row0 + i / XL < 2 * npairs) {
+          int zz, yy;
+          const int qrow = row0 + i / XL;
+          pair_rows(a, qrow >> 1, zz, yy);
+          yy += qrow & 1;
+          prefetch_l2(a.mask + ((size_t)zz * ny + yy) * XL + i % XL);
+        }
+    }
+    const int gp = tile * P + p;
+    const bool pok = gp < npairs;
+    int z, ya;
+    pair_rows(a, pok ? gp : 0, z, ya);
+    const int qa = z * ny + ya;
+    // ---- C2R (length 2nx) of component g, the first nx outputs kept
+    {
+      const int q = g;
+      const int n1 = r;
+      if (n1 < R1i) {
+        const float2* ra = a.spec_in + ((size_t)(q * nz + z) * a.in_rows + ya) * a.in_sx;
+        const float2* rb = ra + a.in_sx;
+        float2 v[R2i];
+#pragma unroll
+        for (int n2 = 0; n2 < R2i; ++n2) {
+          const int k = n1 + R1i * n2;
+          const bool lo = k <= Li / 2;
+          const int kk = lo ? k : Li - k;
+          float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+          if (pok) { A = ra[kk]; B = rb[kk]; }
+          if (kk == 0 || kk == Li / 2) { A.y = 0.f; B.y = 0.f; }
+          v[n2] = lo ? make_float2(A.x - B.y, A.y + B.x) : make_float2(A.x + B.y, B.x - A.y);
+        }
+        DFT<R2i, true, float2>::run(v);
+#pragma unroll
+        for (int k2 = 0; k2 < R2i; ++k2) Tp[k2 * (R1i + 1) + n1] = k2 == 0 ? v[0] : cmulc(v[k2], twi[k2 * R1i + n1]);
+      }
+      __syncwarp();
+      const int k2 = r;
+      if (k2 < R2i) {
+        float2 w[R1i];
+#pragma unroll
+        for (int m = 0; m < R1i; ++m) w[m] = Tp[k2 * (R1i + 1) + m];
+        DFT<R1i, true, float2>::run(w);
+#pragma unroll
+        for (int k1 = 0; k1 < S::KX; ++k1) RS[(q * P + p) * XL + k2 + R2i * k1] = w[k1];
+      }
+    }
+    __syncthreads();  // the three components' rows of the tile in RS
+    // ---- node-wise step (Eq. 5 update and residual) on the nodes x = r + TP j, j = g mod 3
+    {
+      constexpr int JG = (J + 2) / 3;  // node pairs of a thread, at most
+      bool mk[JG][2];
+      float ov[JG][3][2];
+#pragma unroll
+      for (int jj = 0; jj < JG; ++jj) {
+        const int j = g + 3 * jj;
+        const int x = r + TP * j;
+        const size_t na = (size_t)qa * XL + x, nb = na + XL;
+        mk[jj][0] = mk[jj][1] = false;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) ov[jj][q][0] = ov[jj][q][1] = 0.f;
+        if (pok && j < J) {
+          mk[jj][0] = a.mask[na];
+          mk[jj][1] = a.mask[nb];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            ov[jj][q][0] = h_old[q * N + na];
+            ov[jj][q][1] = h_old[q * N + nb];
+          }
+        }
+      }
+#pragma unroll
+      for (int jj = 0; jj < JG; ++jj) {
+        const int j = g + 3 * jj;
+        if (!pok || j >= J) continue;
+        const int x = r + TP * j;
+        const size_t na = (size_t)qa * XL + x, nb = na + XL;
+        const bool ia = mk[jj][0], ib = mk[jj][1];
+        float2 u[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) u[q] = RS[(q * P + p) * XL + x];
+        float da = 0.f, db = 0.f;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const float oa = ov[jj][q][0], ob = ov[jj][q][1];
+          const float he = hef[q];
+          const float va = ia ? oa : he + u[q].x;
+          const float vb = ib ? ob : he + u[q].y;
+          h_new[q * N + na] = va;
+          h_new[q * N + nb] = vb;
+          const float dda = va - oa, ddb = vb - ob;
+          da += dda * dda;
+          db += ddb * ddb;
+          u[q] = make_float2(va, vb);
+        }
+        if (!ia) partf += sqrtf(da);
+        if (!ib) partf += sqrtf(db);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) RS[(q * P + p) * XL + x] = u[q];
+      }
+    }
+    __syncthreads();  // the updated rows of every component in RS
+    // ---- R2C (length nx) of component g
+    {
+      const int q = g;
+      const int n1 = r;
+      if (n1 < R1o) {
+        float2 u[R2o];
+#pragma unroll
+        for (int n2 = 0; n2 < R2o; ++n2) {
+          const int x = n1 + R1o * n2;
+          u[n2] = (x < XL) ? RS[(q * P + p) * XL + x] : make_float2(0.f, 0.f);
+        }
+        dft_maybe_half<R2o, false, S::PADOUT>(u);
+#pragma unroll
+        for (int k2 = 0; k2 < R2o; ++k2) Tp[k2 * (R1o + 1) + n1] = k2 == 0 ? u[0] : cmul(u[k2], two[k2 * R1o + n1]);
+      }
+      __syncwarp();
+      const int k2 = r;
+      float2 Zr[R1o];
+      if (k2 < R2o) {
+#pragma unroll
+        for (int m = 0; m < R1o; ++m) Zr[m] = Tp[k2 * (R1o + 1) + m];
+        DFT<R1o, false, float2>::run(Zr);
+      }
+      const int lane = tid & 31;
+      const int src = lane - k2 + (k2 == 0 ? 0 : R2o - k2);
+      float2* ra = a.spec_out + ((size_t)(q * nz + z) * a.out_rows + ya) * a.out_sx;
+      float2* rb = ra + a.out_sx;
+#pragma unroll
+      for (int k1 = 0; k1 <= R1o / 2; ++k1) {
+        const float2 sh = make_float2(__shfl_sync(0xffffffffu, Zr[R1o - 1 - k1].x, src),
+                                      __shfl_sync(0xffffffffu, Zr[R1o - 1 - k1].y, src));
+        const float2 Zk = Zr[k1];
+        const float2 Zm = k2 == 0 ? Zr[(R1o - k1) % R1o] : sh;
+        const int k = k2 + R2o * k1;
+        if (k2 < R2o && pok && k <= Lo / 2) {
+          ra[k] = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
+          rb[k] = make_float2(0.5f * (Zk.y + Zm.y), 0.5f * (Zm.x - Zk.x));
+        }
+      }
+      __syncwarp();  // the group's next C2R overwrites its transpose scratch
+    }
+  }
+  residual_finish(a, (double)partf, it, NT);
 }
 
 }  // namespace scfft

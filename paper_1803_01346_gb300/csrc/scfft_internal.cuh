@@ -69,6 +69,7 @@ struct Sched {
   int yp_tma = 1;  // padded y passes: TMA-fed persistent kernel (1) or plain loads, 16 columns (0)
   int zk_tm = 0;   // padded z pass, 16 x 16 split: own-slot spectra in tensor memory (1) or shared memory (0)
   int box_fused = 0;  // Eq. 5 iteration: the three passes on Omega's box fused into one launch (1) or not (0)
+  int xu3 = 0;        // Eq. 5 update pass: three components side by side in three warp groups (1) or one after another (0)
 };
 
 // Device workspaces of one FFT precision T.

@@ -40,7 +40,7 @@ def _rhs(ctx, h, g0):
 
 @pytest.mark.parametrize("n,L", [((32, 32, 32), (1.0, 1.0, 1.0)), ((48, 32, 16), (1.2, 0.9, 0.8))])
 def test_every_schedule_gives_the_same_bits(n, L):
-    """All 32 schedules: the same Eq. 5 iteration count and the same dh/dt bit for bit (the
+    """All 64 schedules: the same Eq. 5 iteration count and the same dh/dt bit for bit (the
     loop graph is rebuilt after each change), and the oracle's answer.  On the first grid
     (nx = ny) the fused box passes run; on the second they do not apply and the three
     passes run whatever the knob says."""
@@ -54,12 +54,13 @@ def test_every_schedule_gives_the_same_bits(n, L):
     h = torch.from_numpy(hs.reshape(-1).copy()).cuda()
     g0 = torch.from_numpy(g0s.reshape(-1).copy()).cuda()
     ref_it, ref = _rhs(ctx, h, g0)
-    for zk, zc, yu, yp, bf in itertools.product((8, 4), (8, 16), (8, 16), (1, 0), (0, 1)):
-        ctx.set_schedule(z_kernel_tile=zk, z_curl_tile=zc, y_unpadded_tile=yu, y_padded_tma=yp, box_fused=bf)
+    for zk, zc, yu, yp, bf, xs in itertools.product((8, 4), (8, 16), (8, 16), (1, 0), (0, 1), (0, 1)):
+        ctx.set_schedule(z_kernel_tile=zk, z_curl_tile=zc, y_unpadded_tile=yu, y_padded_tma=yp, box_fused=bf,
+                         x_update_split=xs)
         assert ctx.get_schedule() == dict(z_kernel_tile=zk, z_curl_tile=zc, y_unpadded_tile=yu, y_padded_tma=yp,
-                                          z_kernel_tmem=0, box_fused=bf)
+                                          z_kernel_tmem=0, box_fused=bf, x_update_split=xs)
         it, out = _rhs(ctx, h, g0)
-        assert it == ref_it and np.array_equal(out, ref), (zk, zc, yu, yp, bf)
+        assert it == ref_it and np.array_equal(out, ref), (zk, zc, yu, yp, bf, xs)
     o = O.rhs(prob, 0.2, hs, g0s, delta_it=2e-5, max_iter=50)
     assert abs(o.iters - ref_it) <= 1
     e = [float(np.abs(ref.reshape(hs.shape)[q] - o.hdot[q]).max() / np.abs(o.hdot[q]).max()) for q in range(3)]
@@ -81,6 +82,7 @@ def test_autotune_times_once_per_grid_and_keeps_the_results():
     assert all(u > 0 for u in sa["us"][:8]), sa  # every candidate was timed
     assert sa["z_kernel_tmem"] == 0 and sa["us"][8:11] == [0.0] * 3  # no tensor-memory form at nz = 64
     assert sa["box_fused"] in (0, 1) and sa["us"][11] > 0 and sa["us"][12] > 0, sa  # three passes, fused
+    assert sa["x_update_split"] in (0, 1) and sa["us"][13] > 0 and sa["us"][14] > 0, sa
     print(f"[autotune 64^3] {sa}")
     sb = b.autotune()  # the same grid: the cached choice, nothing timed
     assert {k: sb[k] for k in S.Context._SCHED_KEYS} == {k: sa[k] for k in S.Context._SCHED_KEYS}

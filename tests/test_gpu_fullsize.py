@@ -75,25 +75,27 @@ def test_rhs_fp32_lens128_fixed_iterations_matches_oracle(lens):
     """Five Eq. 5 iterations, no early stop: every pass of the right-hand side at
     the benchmark's grid against the oracle's same five iterations, with the padded z
     pass keeping its spectra in shared memory and in tensor memory (three or two transpose
-    buffers), and with the three
+    buffers), with the update pass's components one after another and side by side, and with
+    the three
     passes on Omega's box as three launches and as one fused launch (the same bits)."""
     cfg, prob, h, g0, ref = lens
     assert ref.iters == ITERS
     ctx = _ctx(cfg, 0.0, ITERS)
     got = []
-    for tm, bf in ((0, 0), (1, 0), (2, 0), (0, 1), (2, 1)):
-        ctx.set_schedule(z_kernel_tmem=tm, box_fused=bf)
+    for tm, bf, xs in ((0, 0, 0), (1, 0, 0), (2, 0, 0), (0, 1, 0), (2, 1, 0), (2, 0, 1)):
+        ctx.set_schedule(z_kernel_tmem=tm, box_fused=bf, x_update_split=xs)
         out = torch.empty(h.size, dtype=torch.float64, device="cuda")
         it = ctx.rhs(T, _dev(h), _dev(g0), out)
         torch.cuda.synchronize()
         assert it == ITERS
         got.append(out.cpu().numpy().reshape(h.shape))
-        _check3(f"lens128 fixed, z pass tensor memory {tm}, box passes fused {bf}", got[-1], ref.hdot)
+        _check3(f"lens128 fixed, z pass tensor memory {tm}, box passes fused {bf}, update split {xs}", got[-1],
+                ref.hdot)
     assert all(np.array_equal(got[0], g) for g in got[1:])
 
 
-@pytest.mark.parametrize("tm,bf", [(0, 0), (1, 0), (2, 0), (0, 1)])
-def test_rhs_fp32_lens128_graph_loop_stops_with_the_oracle(lens, tm, bf):
+@pytest.mark.parametrize("tm,bf,xs", [(0, 0, 0), (1, 0, 0), (2, 0, 0), (0, 1, 0), (2, 0, 1)])
+def test_rhs_fp32_lens128_graph_loop_stops_with_the_oracle(lens, tm, bf, xs):
     """The Eq. 5 loop as the benchmark runs it (one CUDA graph, the stop decided on
     the device), with the stop threshold set between the oracle's residuals after
     iterations ITERS - 1 and ITERS (geometric mean): the device loop must stop after
@@ -104,7 +106,7 @@ def test_rhs_fp32_lens128_graph_loop_stops_with_the_oracle(lens, tm, bf):
     hed = float(np.linalg.norm(prob.path.hedot(T)))
     delta_it = float(np.sqrt(r[ITERS - 2] * r[ITERS - 1])) / max(hed, 1.0)
     ctx = _ctx(cfg, delta_it, 4 * ITERS)
-    ctx.set_schedule(z_kernel_tmem=tm, box_fused=bf)
+    ctx.set_schedule(z_kernel_tmem=tm, box_fused=bf, x_update_split=xs)
     out = torch.empty(h.size, dtype=torch.float64, device="cuda")
     it = ctx.rhs(T, _dev(h), _dev(g0), out)
     torch.cuda.synchronize()
