@@ -51,7 +51,7 @@ AUTOTUNE = True  # --no-autotune: keep the default launch schedule (profiling ru
                  # tuner's own timings are distorted and may pick another schedule)
 # DRAM bytes (read + write) per launch from the committed ncu capture
 # profiles/ncu_zpass_tm2_lens128_fp32.md; an entry is removed when its kernel changes.
-NCU_TRAFFIC = {"z_kernel": 87209216 + 58943744}
+NCU_TRAFFIC = {"z_kernel": 86768384 + 58679552}
 
 
 def _peaks():

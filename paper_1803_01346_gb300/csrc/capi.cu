@@ -879,12 +879,28 @@ __global__ void errnorm32_kernel(const double* __restrict__ y, const double* __r
                                  const float* __restrict__ k3, float e4, const float* __restrict__ k4, float rtol,
                                  float atol, long long n, unsigned* out) {
   float m = 0.f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float e = h * (e1 * k1[i] + e2 * k2[i] + e3 * k3[i] + e4 * k4[i]);
-    const float w = fmaxf(rtol * fmaxf(abs_f32_of(y[i]), abs_f32_of(yn[i])), atol);
+  auto one = [&](double yv, double ynv, float a1, float a2, float a3, float a4) {
+    const float e = h * (e1 * a1 + e2 * a2 + e3 * a3 + e4 * a4);
+    const float w = fmaxf(rtol * fmaxf(abs_f32_of(yv), abs_f32_of(ynv)), atol);
     const float r = fabsf(e) / w;
     m = (r > m || r != r) ? r : m;
+  };
+  const long long stride = (long long)gridDim.x * blockDim.x, t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // (two elements per thread and trip with 16- and 8-byte loads where every array allows it)
+  const bool vec = (((uintptr_t)y | (uintptr_t)yn) & 15) == 0 &&
+                   (((uintptr_t)k1 | (uintptr_t)k2 | (uintptr_t)k3 | (uintptr_t)k4) & 7) == 0;
+  long long i0 = 0;
+  if (vec) {
+    for (long long i = t0; i < n / 2; i += stride) {
+      const double2 yv = reinterpret_cast<const double2*>(y)[i], nv = reinterpret_cast<const double2*>(yn)[i];
+      const float2 a = reinterpret_cast<const float2*>(k1)[i], b = reinterpret_cast<const float2*>(k2)[i];
+      const float2 cc = reinterpret_cast<const float2*>(k3)[i], dd = reinterpret_cast<const float2*>(k4)[i];
+      one(yv.x, nv.x, a.x, b.x, cc.x, dd.x);
+      one(yv.y, nv.y, a.y, b.y, cc.y, dd.y);
+    }
+    i0 = n / 2 * 2;
   }
+  for (long long i = i0 + t0; i < n; i += stride) one(y[i], yn[i], k1[i], k2[i], k3[i], k4[i]);
   for (int o = 16; o > 0; o >>= 1) {
     const float q = __shfl_xor_sync(0xffffffffu, m, o);
     m = (q > m || q != q) ? q : m;
@@ -894,16 +910,37 @@ __global__ void errnorm32_kernel(const double* __restrict__ y, const double* __r
 
 // accept: y <- y + d with Kahan compensation c; and the caller's FP64 warm start <- the
 // latest rhs result (FP32)
+__device__ __forceinline__ void accept_one(double& y, double& c, float d, float last, double& warm) {
+  const double u = (double)d - c;
+  const double t = y + u;
+  c = (t - y) - u;
+  y = t;
+  warm = (double)last;
+}
+// (two elements per thread and trip with 16- and 8-byte loads where every array allows it)
 __global__ void accept32_kernel(double* __restrict__ y, double* __restrict__ c, const float* __restrict__ d,
                                 const float* __restrict__ last, double* __restrict__ warm, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double yi = y[i];
-    const double u = (double)d[i] - c[i];
-    const double t = yi + u;
-    c[i] = (t - yi) - u;
-    y[i] = t;
-    warm[i] = (double)last[i];
+  const long long stride = (long long)gridDim.x * blockDim.x, t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const bool vec = (((uintptr_t)y | (uintptr_t)c | (uintptr_t)warm) & 15) == 0 && (((uintptr_t)d | (uintptr_t)last) & 7) == 0;
+  long long i0 = 0;
+  if (vec) {
+    double2* y2 = reinterpret_cast<double2*>(y);
+    double2* c2 = reinterpret_cast<double2*>(c);
+    double2* w2 = reinterpret_cast<double2*>(warm);
+    const float2* d2 = reinterpret_cast<const float2*>(d);
+    const float2* l2 = reinterpret_cast<const float2*>(last);
+    for (long long i = t0; i < n / 2; i += stride) {
+      double2 yv = y2[i], cv = c2[i], wv;
+      const float2 dv = d2[i], lv = l2[i];
+      accept_one(yv.x, cv.x, dv.x, lv.x, wv.x);
+      accept_one(yv.y, cv.y, dv.y, lv.y, wv.y);
+      y2[i] = yv;
+      c2[i] = cv;
+      w2[i] = wv;
+    }
+    i0 = n / 2 * 2;
   }
+  for (long long i = i0 + t0; i < n; i += stride) accept_one(y[i], c[i], d[i], last[i], warm[i]);
 }
 
 __global__ void f64_to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, long long n) {
