@@ -613,8 +613,9 @@ static cudaError_t launch_z(const Launch<T>& L, bool padded, bool check_done, do
   a.nzs = g.nz;
   a.TC = col_tile<T>();
   const int Lz = padded ? 2 * g.nz : g.nz;
-  // keep the 3-component ping-pong pair within ~100 KB
-  while (a.TC > 4 && (size_t)(2 * 3 * Lz * (a.TC + 1)) * sizeof(V) > 100 * 1024) a.TC /= 2;
+  // keep the 3-component ping-pong pair within ~80 KB, so that two CTAs share an SM (the
+  // 256-point padded transform then takes two columns per CTA)
+  while (a.TC > 2 && (size_t)(2 * 3 * Lz * (a.TC + 1)) * sizeof(V) > 80 * 1024) a.TC /= 2;
   a.pl = make_plan(Lz);
   a.tw = padded ? L.w->twp[2] : L.w->twu[2];
   a.kt0 = L.w->kt[0]; a.kt1 = L.w->kt[1]; a.kt2 = L.w->kt[2];
