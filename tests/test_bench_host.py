@@ -94,3 +94,23 @@ def test_source_box_fractions():
     m[:] = False
     m[2, 18, 1] = True                     # one node in the last even row pair: rows 18..19
     assert bench.source_box(m) == (1 / 16, 2 / (16 * 20))
+
+
+def test_algorithmic_bytes_of_the_fused_box_passes():
+    """The fused box passes (the curl's inverse y pass, the mask/pad x pass and the padded
+    forward y pass in one launch) read the curl's half spectrum on the box's planes and the mask
+    on its rows and write the padded spectrum of its planes once: fewer bytes than the three
+    passes on the same box, which each make a round trip."""
+    b = _bench()
+    n = (128, 128, 128)
+    N = 128 ** 3
+    u = 3 * 65 * 128 * 128 * 8
+    p_in = 3 * 129 * 128 * 128 * 8
+    p_all = 3 * 129 * 256 * 128 * 8
+    box = (40 / 128, 40 * 80 / (128 * 128))
+    fused = b.algorithmic_bytes("box_fused", n, 4, box)
+    assert fused == u * box[0] + N * box[1] + p_all * box[0]
+    three = (2 * u + (u + N + p_in) * box[1] + p_in * box[1] + p_all * box[0])
+    assert b.algorithmic_bytes("y_inv_unpadded", n, 4) + b.algorithmic_bytes("x_maskpad", n, 4, box) + \
+        b.algorithmic_bytes("y_fwd_padded", n, 4, box) == three
+    assert fused < three
