@@ -134,3 +134,20 @@ def test_rhs_fp64_and_df64_lens128_fixed_iterations_match_oracle(lens, prec):
     e = _rel(out.cpu().numpy().reshape(h.shape), ref.hdot)
     print(f"[fp64/df64 error] lens128 precision {prec}: {e:.2e}")
     assert e < 1e-10
+
+
+def test_rhs_fp32_lens128_stencil_curl_matches_oracle(lens):
+    """The local-stencil curl option at the benchmark's grid (its three stencil kernels, the
+    padded R2C of the masked stencil curl and the update without R2C), five fixed Eq. 5
+    iterations against the oracle's central-difference curls, through the graph-captured loop."""
+    cfg, prob, h, g0, _ = lens
+    pfd = O.Problem(prob.grid, prob.mask, prob.mat, prob.path)
+    pfd.curl = "fd"
+    pfd.Khat = prob.kernel()  # the same Biot-Savart kernel spectrum
+    ref = O.rhs(pfd, T, h, g0, delta_it=0.0, max_iter=ITERS)
+    ctx = _ctx(cfg, 0.0, ITERS)
+    ctx.set_curl(S.CURL_FD)
+    out = torch.empty(h.size, dtype=torch.float64, device="cuda")
+    assert ctx.rhs(T, _dev(h), _dev(g0), out) == ITERS
+    torch.cuda.synchronize()
+    _check3("lens128 stencil curl", out.cpu().numpy().reshape(h.shape), ref.hdot)
