@@ -151,3 +151,22 @@ def test_rhs_fp32_lens128_stencil_curl_matches_oracle(lens):
     assert ctx.rhs(T, _dev(h), _dev(g0), out) == ITERS
     torch.cuda.synchronize()
     _check3("lens128 stencil curl", out.cpu().numpy().reshape(h.shape), ref.hdot)
+
+
+def test_rhs_fp32_lens128_ej_law_matches_oracle(lens):
+    """The e(j, h) law (Kim's jc(|h|) with an anisotropic norm) in place of Eq. 1 at the
+    benchmark's grid: five fixed Eq. 5 iterations against the oracle's."""
+    import copy
+    cfg, prob, h, g0, _ = lens
+    mat = copy.copy(prob.mat)
+    mat.kim_h0 = 0.3
+    mat.aniso = (1.0, 0.7, 1.5)
+    pl = O.Problem(prob.grid, prob.mask, mat, prob.path)
+    pl.Khat = prob.kernel()
+    ref = O.rhs(pl, T, h, g0, delta_it=0.0, max_iter=ITERS)
+    ctx = _ctx(cfg, 0.0, ITERS)
+    ctx.set_ej_law(kim_h0=0.3, aniso=(1.0, 0.7, 1.5))
+    out = torch.empty(h.size, dtype=torch.float64, device="cuda")
+    assert ctx.rhs(T, _dev(h), _dev(g0), out) == ITERS
+    torch.cuda.synchronize()
+    _check3("lens128 e(j,h) law", out.cpu().numpy().reshape(h.shape), ref.hdot)
