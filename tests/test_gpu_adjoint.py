@@ -251,3 +251,38 @@ def test_integrate_autograd_gradients():
     assert rel(y0t.grad.cpu().numpy().reshape(y0.shape), ref.mu_y0) < 1e-10
     assert rel(jct.grad.cpu().numpy().reshape(ref.mu_jc.shape), ref.mu_jc) < 1e-10
     assert rel(het.grad.numpy().reshape(-1), ref.mu_path[:-1]) < 1e-10
+
+
+@pytest.mark.parametrize("prec,tol", [(S.PREC_F64, 1e-10), (S.PREC_F32, 1e-4)])
+def test_rhs_vjp_lens96_matches_oracle(prec, tol):
+    """The reverse mode's workload grid: the lens at 96^3 with its seeded +-5% jc map (the
+    bench's reverse-mode leg), one rhs with three fixed Eq. 5 iterations, its vector-Jacobian
+    product against the oracle's (FP64 tier and the FP32 path's stated bound)."""
+    K = 3
+    cfg = I.config("lens96")
+    n, L = cfg.n, cfg.L
+    ctx = S.Context(n, L, n_power=cfg.n_power, rho_out=cfg.rho_out, precision=prec, delta_it=0.0, max_iter=K)
+    ctx.set_geometry(cfg.mask)
+    ctx.set_field_path(cfg.knots_t, cfg.knots_he)
+    ctx.set_jc_map(dev(cfg.jc))
+    ctx.precompute_kernel()
+    g = O.Grid(n, L)
+    prob = O.Problem(g, cfg.mask, O.Material(n=cfg.n_power, rho_out=cfg.rho_out, jc=cfg.jc),
+                     O.FieldPath(cfg.knots_t, cfg.knots_he))
+    rng = np.random.default_rng(96)
+    # the field of a random current in the lens, scaled so that the largest |curl h| in the lens
+    # is 1.1 jc (the steep part of Eq. 1 at n = 30), plus a uniform field
+    P = O.phi_hockney(O.curl_s(rng.standard_normal((3,) + g.shape) * 0.3, g) * cfg.mask, g)
+    jP = np.sqrt(np.sum(O.curl_s(P, g) ** 2, axis=0))[cfg.mask].max()
+    h = (1.1 / jP) * P + np.array([0.0, 0.0, 0.4])[:, None, None, None]
+    lam = rng.standard_normal(h.shape)
+    ref = O.rhs_vjp(prob, 0.4, h, lam, K)
+    N = int(np.prod(n))
+    mu_h = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+    mu_jc = torch.empty(N, dtype=torch.float64, device="cuda")
+    ctx.rhs_vjp(dev(h), dev(lam), mu_h, None, mu_jc)
+    torch.cuda.synchronize()
+    e_h = rel(mu_h.cpu().numpy().reshape(h.shape), ref.mu_h)
+    e_jc = rel(mu_jc.cpu().numpy().reshape(ref.mu_jc.shape), ref.mu_jc)
+    print(f"[rhs_vjp lens96 precision {prec}] mu_h {e_h:.2e} mu_jc {e_jc:.2e}")
+    assert e_h < tol and e_jc < tol
