@@ -112,3 +112,44 @@ def test_batch_step_equals_individual_steps(prec):
     for a, b, c2 in zip(A, Bv, C):
         assert torch.equal(a[1], b[1])
         assert float((a[1] - c2[1]).abs().max() / c2[1].abs().max()) < 1e-9
+
+
+def test_bench_batch_sampled_instances_match_oracle():
+    """The batch the bench times (64 shield instances on grids 32^3 ... 96^3, FP32, the autotuned
+    schedules, one graph launch per batch step): two batch steps, then two sampled instances
+    (the first of each of the two smallest grid sizes) against the oracle over the step sizes
+    the GPU chose, Eq. 5 iterated to its fixed point on both sides."""
+    cfgs = I.batch_configs(64, seed=1803)
+    streams = [torch.cuda.Stream() for _ in cfgs]
+    inst = []
+    for c, s in zip(cfgs, streams):
+        ctx, h, w = _make(c, S.PREC_F32, s)
+        ctx.autotune()
+        inst.append((ctx, h, w))
+    nb = len(inst)
+    t, dt = [0.0] * nb, [1e-4] * nb
+    stop = [c.t_end for c in cfgs]
+    hist = [[] for _ in range(nb)]
+    for _ in range(2):
+        t0 = list(t)
+        t, dt, st = S.batch_step([a[0] for a in inst], t, dt, stop, [a[1] for a in inst], [a[2] for a in inst])
+        assert all(v == 0 for v in st)
+        for i in range(nb):
+            hist[i].append(t[i] - t0[i])
+    torch.cuda.synchronize()
+    picked = {}
+    for i, c in enumerate(cfgs):
+        if c.n[0] in (32, 48) and c.n[0] not in picked:
+            picked[c.n[0]] = i
+    assert len(picked) == 2
+    for size, i in sorted(picked.items()):
+        c, (ctx, h, _), dts = cfgs[i], inst[i], hist[i]
+        prob = O.Problem(O.Grid(c.n, c.L), c.mask, O.Material(n=c.n_power, rho_out=c.rho_out),
+                         O.FieldPath(c.knots_t, c.knots_he))
+        ref = O.integrate(prob, 0.0, float(np.sum(dts)), np.zeros((3,) + prob.grid.shape), rtol=c.rtol,
+                          atol=c.atol, dt0=dts[0], delta_it=1e-13, max_iter=80, dt_list=dts)
+        assert ref.accepted == len(dts)
+        got = h.cpu().numpy().reshape(ref.y.shape)
+        err = float(np.abs(got - ref.y).max() / np.abs(ref.y).max())
+        print(f"[batch c4] instance {i} ({size}^3): {err:.2e}")
+        assert err < 1e-4, (c.n, err)
