@@ -286,3 +286,54 @@ def test_rhs_vjp_lens96_matches_oracle(prec, tol):
     e_jc = rel(mu_jc.cpu().numpy().reshape(ref.mu_jc.shape), ref.mu_jc)
     print(f"[rhs_vjp lens96 precision {prec}] mu_h {e_h:.2e} mu_jc {e_jc:.2e}")
     assert e_h < tol and e_jc < tol
+
+
+# the same five steps at the reverse-mode workload's own grid (96^3, a third of the cell size:
+# the explicit steps' stiffness grows ninefold, so the steps are ten times shorter), the second
+# again ending on the kink
+TS96 = [0.11996, 0.11998, 0.12, 0.12002, 0.120045, 0.12007]
+
+
+def test_adjoint_step_lens96_matches_central_differences_of_the_gpu_forward():
+    """The reverse-mode workload's grid (lens 96^3 with its +-5% jc map, FP64): dJ/djc on 8
+    seeded voxels of the lens and dJ/dA for the three ramp-amplitude components across the
+    ramp-to-hold kink, against central differences (step 1e-4) of the GPU's own forward map."""
+    K, n = 3, (96, 96, 96)
+    ctx, prob, cfg, jc, tk, he, y0, rng = _lens_problem(n, S.PREC_F64, K)
+    N = int(np.prod(n))
+    lam = rng.standard_normal(y0.shape)
+    lt = dev(lam)
+    _, _, gjc, gp = _reverse(ctx, TS96, y0, lam, N, 3 * len(tk) + 1)
+    gjc = gjc.cpu().numpy()
+
+    def J():
+        y = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+        ctx.adjoint_record(TS96, dev(y0), y_end=y, checkpoint_every=2)
+        return float((y * lt).sum())
+
+    eps = 1e-4
+    inside = np.flatnonzero(cfg.mask.reshape(-1))
+    vox = np.random.default_rng(96).choice(inside, 8, replace=False)
+    scale = np.abs(gjc).max()
+    for v in vox:
+        vals = []
+        for sgn in (1, -1):
+            j2 = jc.reshape(-1).copy()
+            j2[v] += sgn * eps
+            ctx.set_jc_map(dev(j2))
+            vals.append(J())
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        assert abs(fd - gjc[v]) < 1e-6 * scale + 2e-5 * abs(gjc[v]), (v, fd, gjc[v])
+    ctx.set_jc_map(dev(jc))
+    dA = gp[3:6] + gp[6:9]
+    for a in range(3):
+        vals = []
+        for sgn in (1, -1):
+            h2 = he.copy()
+            h2[1:, a] += sgn * eps
+            ctx.set_field_path(tk, h2)
+            vals.append(J())
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        print(f"[adjoint lens96] dJ/dA_{a}: reverse {dA[a]:.6e}, central difference {fd:.6e}")
+        assert fd == pytest.approx(dA[a], rel=2e-5, abs=1e-9 * np.abs(dA).max()), (a, fd, dA[a])
+    ctx.set_field_path(tk, he)
