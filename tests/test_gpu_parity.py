@@ -550,3 +550,36 @@ def test_rhs_fp32_fused_box_passes_match_three_passes_and_oracle(n, L):
             ctx.profile(False)
     assert all(np.array_equal(out[0, "host"], v) for v in out.values())
     check3(f"rhs fused box passes {n}", out[1, "graph"].reshape(h.shape), ref.hdot, RHS32)
+
+
+# FP32 bound of the single-node case: the state is the field of a point current, whose curl at
+# the node is far rougher than the smooth states above, and Eq. 1 amplifies its FP32 round-off
+# by n - 1 = 24; observed 2.5e-5, 4.8e-6, 2.7e-5 per component at 32^3 (about 3x that here)
+RHS32_POINT = (8e-5, 8e-5, 8e-5)
+
+
+@pytest.mark.parametrize("n,L", [((32, 32, 32), (1.0, 1.0, 1.0)), ((48, 32, 16), (1.2, 0.9, 0.8))])
+@pytest.mark.parametrize("prec", [S.PREC_F64, S.PREC_F32])
+def test_rhs_single_node_omega_matches_oracle(n, L, prec):
+    """The degenerate superconductor: Omega is one node at an odd row and plane, so the source
+    box of the Eq. 5 convolution is one plane and one row pair.  The box passes (FP64; FP32 with
+    three launches and, where nx = ny, the fused one, the same bits) against the oracle at a
+    fixed iteration count."""
+    mask = np.zeros((n[2], n[1], n[0]), dtype=bool)
+    mask[n[2] // 2 + 1, n[1] // 2 + 1, n[0] // 2] = True
+    ctx, prob = make(n, L, mask, n_power=25.0, prec=prec, max_iter=3)
+    h = _state(prob, 101) + np.array([0.02, -0.01, 0.05])[:, None, None, None]
+    g0 = I.random_field(h.shape, 102, 0.1)
+    ref = O.rhs(prob, 0.4, h, g0, delta_it=0.0, max_iter=3)
+    outs = []
+    for bf in ((0, 1) if prec == S.PREC_F32 else (None,)):
+        if bf is not None:
+            ctx.set_schedule(box_fused=bf)
+        o = torch.empty(h.size, dtype=torch.float64, device="cuda")
+        assert ctx.rhs(0.4, dev(h).reshape(-1), dev(g0).reshape(-1), o) == 3
+        outs.append(host(o))
+    assert all(np.array_equal(outs[0], x) for x in outs[1:])
+    if prec == S.PREC_F64:
+        assert rel(outs[0].reshape(h.shape), ref.hdot) < 1e-10
+    else:
+        check3(f"rhs single-node Omega {n}", outs[0].reshape(h.shape), ref.hdot, RHS32_POINT)
