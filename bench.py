@@ -321,11 +321,16 @@ def bench_batch(S, torch, steps: int, warmup: int):
     torch.cuda.synchronize()
     c0 = [x[0].stats()["rhs_calls"] for x in inst]
     i0 = [x[0].stats()["iterations"] for x in inst]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    clocks.begin()
     t0 = time.perf_counter()
     for _ in range(steps):
         t, dt, _ = S.batch_step(ctxs, t, dt, stop, hs, wsv)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
+    clocks.end()
+    clk = clocks.stop()
     evals = sum(x[3] * (x[0].stats()["rhs_calls"] - c) for x, c in zip(inst, c0))
     rcs = sum(x[0].stats()["rhs_calls"] - c for x, c in zip(inst, c0))
     its = sum(x[0].stats()["iterations"] - c for x, c in zip(inst, i0))
@@ -345,7 +350,8 @@ def bench_batch(S, torch, steps: int, warmup: int):
                                                          "y_padded_tma", "z_kernel_tmem", "box_fused",
                                                          "x_update_split")}
                           for k, v in sorted(schedules.items())},
-            "timing": "wall clock around synchronous batch calls, device synchronised on both sides"}
+            "timing": "wall clock around synchronous batch calls, device synchronised on both sides",
+            "clocks": clk}
 
 
 def bench_adjoint(S, torch, nsteps: int, checkpoint: int, K: int):
